@@ -1,0 +1,50 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case below plants one mistake in a copy of napg_oracle.c (a dropped term, a
+wrong sign or index, a wrong degree of freedom, a transposed operand), builds it
+on the CPU, and runs the pin tests against the copy: at least one pin must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "napg_oracle.c")
+PINS = ["tests/test_oracle_special.py", "tests/test_oracle_stats.py"]
+
+MUTANTS = {
+    "pearson_uncentred_y": ("double dv = v[k] - mv, dw = w[k] - mw;", "double dv = v[k] - mv, dw = w[k];"),
+    "tie_rank_off_by_one": ("r2[buf[k].i] = 2 * a + t + 1;", "r2[buf[k].i] = 2 * a + t;"),
+    "chi2_expected_wrong_n": ("double E = (double)row[g] * (double)col[h] / (double)n;",
+                              "double E = (double)row[g] * (double)col[h] / (double)(n + 1);"),
+    "anova_df_within": ("double d1 = (double)(k - 1), d2 = (double)(n - k);",
+                        "double d1 = (double)(k - 1), d2 = (double)(n - k + 1);"),
+    "welch_df_term": ("e1 * e1 / (double)(n1 - 1));", "e1 * e1 / (double)(n1));"),
+    "mwu_continuity_sign": ("(c->mwu_cc ? 0.5 : 0.0)", "(c->mwu_cc ? -0.5 : 0.0)"),
+    "kruskal_no_tie_correction": ("double C = 1.0 - (double)T / (nd * nd * nd - nd);", "double C = 1.0;"),
+    "ibeta_even_term_sign": ("return m * (b - m) * x / ((a + 2.0 * m - 1.0) * (a + 2.0 * m));",
+                             "return m * (b + m) * x / ((a + 2.0 * m - 1.0) * (a + 2.0 * m));"),
+    "gamma_cf_sign": ("-(double)(n - 1) * ((double)(n - 1) - a)", "(double)(n - 1) * ((double)(n - 1) - a)"),
+    "deletion_one_sided": ("if (observed(c, va, s) && observed(c, vb, s)) {", "if (observed(c, va, s)) {"),
+    "transposed_operand": ("y[n] = c->X[vb * c->S + s];", "y[n] = c->X[va * c->S + s];"),
+    "context_ignored": ("if (c->ctx && !c->ctx[s]) return 0;", ""),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site for {name} not found"
+    mutated = src.replace(old, new)
+    csrc = tmp_path / "mutant.c"
+    csrc.write_text(mutated)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                    "-o", str(so), str(csrc), "-lm"], check=True)
+    env = dict(os.environ, NAPG_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
