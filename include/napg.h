@@ -1,0 +1,212 @@
+/*
+ * napg.h -- C ABI of the GB300 library for all-pairs statistical tests with
+ * pairwise deletion (NApy, arXiv 2505.00448).
+ *
+ * Problem statement (Sec. 3.2-3.4): a data matrix X of F variables x S samples;
+ * a missing-value sentinel m; variables are continuous or categorical
+ * (categorical labels are integers 0..c-1 stored as floating-point values).
+ * For a pair of variables (g, h) only the samples where both are observed are
+ * used: I(g,h) = {(g_i, h_i) : g_i != m and h_i != m} (Sec. 3.2). For every pair
+ * the library returns the test statistic, its p-value and n = |I(g,h)|.
+ *
+ * Tests (Sec. 3.5):
+ *   NAPG_PEARSON   continuous x continuous, r, p from the Beta CDF   (Sec. 3.5.2)
+ *   NAPG_SPEARMAN  continuous x continuous, rho on tie-averaged ranks (Sec. 3.5.3)
+ *   NAPG_CHI2      categorical x categorical, chi-squared           (Sec. 3.5.4)
+ *   NAPG_ANOVA     categorical x continuous, one-way F               (Sec. 3.5.7)
+ *   NAPG_TTEST     dichotomous x continuous, Welch (or Student) t   (Sec. 3.5.5)
+ *   NAPG_MWU       dichotomous x continuous, Mann-Whitney U          (Sec. 3.5.6)
+ *   NAPG_KRUSKAL   categorical x continuous, Kruskal-Wallis H        (Sec. 3.5.8)
+ *
+ * Conventions for every entry point:
+ *   - Errors are returned as a napg_status; nothing aborts. A statistically
+ *     undefined result is not an error: stat/p are NaN (n is still written).
+ *     napg_last_error() returns a message for the last failing call on a context.
+ *   - The caller owns every buffer it passes. The context owns the device copy
+ *     of the cohort and its work memory until napg_destroy.
+ *   - Work is ordered on the context's CUDA stream. A call whose outputs are in
+ *     host memory returns after they are written; a call whose outputs are all
+ *     in device memory returns once the work is queued (synchronize the stream,
+ *     or call napg_sync, before reading them).
+ *   - Host or device pointers are told apart with cudaPointerGetAttributes.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef NAPG_H
+#define NAPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct napg_ctx napg_ctx;
+
+typedef enum {
+    NAPG_OK = 0,
+    NAPG_E_ARG = 1,          /* invalid argument (shape, variable type, level count, NULL) */
+    NAPG_E_OOM = 2,          /* device memory allocation failed */
+    NAPG_E_CUDA = 3,         /* a CUDA runtime call failed (message in napg_last_error) */
+    NAPG_E_LABEL = 4,        /* a categorical value is not an integer in [0, c) */
+    NAPG_E_NONFINITE = 5,    /* a non-missing value is +-inf or NaN */
+    NAPG_E_TIMEOUT = 6,      /* a bounded device wait gave up */
+    NAPG_E_UNSUPPORTED = 7,  /* valid request outside this build's limits */
+    NAPG_E_BUSY = 8          /* serving queue full / no free slot */
+} napg_status;
+
+typedef enum {
+    NAPG_PEARSON = 0, NAPG_SPEARMAN = 1, NAPG_CHI2 = 2, NAPG_ANOVA = 3,
+    NAPG_TTEST = 4, NAPG_MWU = 5, NAPG_KRUSKAL = 6
+} napg_test;
+
+/* Arithmetic of the moment contractions (Pearson, ANOVA, t-test):
+ *   NAPG_FP64_PLAIN  every sum in FP64 on the CUDA cores;
+ *   NAPG_MIXED       column-shifted values split into BF16 parts, contracted on
+ *                    the tensor cores (tcgen05) with FP32 accumulation drained
+ *                    into FP64 in short chunks; finalize and p-values in FP64.
+ * Counts, contingency tables and rank sums are exact integers in both forms. */
+typedef enum { NAPG_FP64_PLAIN = 0, NAPG_MIXED = 1 } napg_precision;
+
+typedef enum { NAPG_F32 = 0, NAPG_F64 = 1 } napg_dtype;
+
+/* Maximum levels of a categorical variable in this build. */
+#define NAPG_MAX_LEVELS 64
+
+typedef struct {
+    int32_t precision;       /* napg_precision; default NAPG_FP64_PLAIN */
+    int32_t welch;           /* 1: Welch t (default), 0: Student t (Sec. 3.5.5) */
+    int32_t yates_2x2;       /* 1: Yates continuity correction on 2x2 tables; default 0 */
+    int32_t mwu_mode;        /* 0 auto (default), 1 exact, 2 asymptotic (Sec. 3.5.6) */
+    int32_t mwu_continuity;  /* 1: 0.5 continuity correction in asymptotic mode (default) */
+    int32_t debug_checks;    /* 1: extra device-side argument checks */
+} napg_options;
+
+/* Fills *opt with the defaults above. */
+void napg_default_options(napg_options *opt);
+
+/* Creates a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to
+ * order all work on, or NULL for a stream owned by the context.
+ * Errors: NAPG_E_ARG (out NULL), NAPG_E_CUDA. */
+napg_status napg_create(napg_ctx **out, int device, void *cuda_stream);
+
+/* Frees the context, its device cohort and its work memory. NULL is a no-op. */
+void napg_destroy(napg_ctx *ctx);
+
+/* Message describing the last failure on ctx (never NULL; "" after success). */
+const char *napg_last_error(const napg_ctx *ctx);
+
+/* Blocks until all work queued on the context's stream is done. */
+napg_status napg_sync(napg_ctx *ctx);
+
+/* Copies the cohort to the device and checks it (Sec. 3.2, 3.3).
+ *   X            n_vars x n_samples values of type `dtype` (napg_dtype), row-major
+ *                with one row per variable; with samples_major != 0 the matrix is
+ *                n_samples x n_vars (one row per sample: the paper's `axis`
+ *                choice) and is transposed on the device. Host or device memory.
+ *   missing      the sentinel m; NaN means "a value is missing iff it is NaN".
+ *                For F32 data a value is missing iff (double)x == missing.
+ *   var_type     n_vars bytes, host: 0 continuous, 1 categorical.
+ *   n_levels     n_vars int32, host: level count c (1..NAPG_MAX_LEVELS) of each
+ *                categorical variable (ignored for continuous ones).
+ * Replaces any cohort loaded before. Synchronous.
+ * Errors: NAPG_E_ARG, NAPG_E_OOM, NAPG_E_LABEL (categorical value not an integer
+ * in [0,c)), NAPG_E_NONFINITE (non-missing +-inf or NaN), NAPG_E_UNSUPPORTED
+ * (n_levels above NAPG_MAX_LEVELS, n_samples >= 2^24), NAPG_E_CUDA. */
+napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_t n_vars,
+                             int64_t n_samples, int32_t samples_major, double missing,
+                             const uint8_t *var_type, const int32_t *n_levels);
+
+/* Runs one test over all pairs vars_a x vars_b of the loaded cohort.
+ *   test         napg_test.
+ *   opt          options, or NULL for the defaults.
+ *   sample_mask  n_samples bytes (host or device), nonzero = sample in the
+ *                context; NULL = all samples. A context is treated as its own
+ *                sub-cohort: a categorical level never observed in it is not a
+ *                category of the call.
+ *   vars_a/n_a   host int32 indices into the cohort. For the categorical x
+ *                continuous tests A holds the categorical variables (Sec. 3.4:
+ *                an F_C x F_Q output) and must be NAPG_TTEST/NAPG_MWU: c == 2,
+ *                NAPG_ANOVA/NAPG_KRUSKAL: c >= 2.
+ *   vars_b/n_b   host int32 indices; NULL makes the call symmetric (A x A) for
+ *                PEARSON, SPEARMAN and CHI2; required for the mixed tests.
+ *   stat, pval   n_a x n_b doubles, row-major, host or device; may be NULL.
+ *   n            n_a x n_b int32 co-observed counts; may be NULL.
+ * Symmetric calls fill both triangles. Statistic reported: r (PEARSON), rho
+ * (SPEARMAN), chi2, F, t (level 0 minus level 1), U of level 0, H.
+ * Errors: NAPG_E_ARG (bad index, wrong variable type or level count, no
+ * cohort), NAPG_E_OOM, NAPG_E_CUDA, NAPG_E_UNSUPPORTED. */
+napg_status napg_run(napg_ctx *ctx, int32_t test, const napg_options *opt,
+                     const uint8_t *sample_mask, const int32_t *vars_a, int32_t n_a,
+                     const int32_t *vars_b, int32_t n_b, double *stat, double *pval,
+                     int32_t *n);
+
+/* Runs one test for n_ctx sample contexts with the same variable sets
+ * (Sec. 1: per-context association networks). sample_masks[k] is a context mask
+ * as in napg_run (host or device); stat[k], pval[k], n[k] are n_a x n_b outputs
+ * (each may be NULL). The contexts are processed from one captured CUDA graph
+ * per batch shape; results equal n_ctx separate napg_run calls.
+ * Errors: as napg_run. */
+napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
+                           int32_t n_ctx, const uint8_t *const *sample_masks,
+                           const int32_t *vars_a, int32_t n_a, const int32_t *vars_b,
+                           int32_t n_b, double *const *stat, double *const *pval,
+                           int32_t *const *n);
+
+/* Exact integer quantities of one pair (a, b) for bit-exact checks, computed by
+ * the device kernels of the test (host output):
+ *   NAPG_CHI2:      out[g*c_b + h] = contingency count O_gh over all c_a x c_b levels.
+ *   NAPG_SPEARMAN:  {n, sum 2Rx*2Ry, sum (2Rx)^2, sum (2Ry)^2} (doubled ranks
+ *                   2R = 2L + t + 1, L = co-observed values strictly below, t =
+ *                   co-observed size of the tie group).
+ *   NAPG_MWU/NAPG_KRUSKAL: {n, T, n_0, S_0, n_1, S_1, ...}: T = sum (t^3 - t) over
+ *                   co-observed tie groups, S_g = sum of doubled ranks of level g.
+ *   NAPG_ANOVA/NAPG_TTEST: {n, n_0, n_1, ...}.  NAPG_PEARSON: {n}.
+ * *written receives the count. Errors: NAPG_E_ARG (cap too small, bad pair). */
+napg_status napg_debug_integers(napg_ctx *ctx, int32_t test, const uint8_t *sample_mask,
+                                int32_t a, int32_t b, int64_t *out, int64_t cap,
+                                int64_t *written);
+
+/* ---------------------------------------------------------------- serving --
+ * A request loop over the resident cohort (Sec. 1: on-the-fly, real-time
+ * analyses). Requests are admitted while a slot and device memory are free;
+ * admitted requests run concurrently on per-slot streams. */
+typedef struct {
+    int32_t test;                 /* napg_test */
+    napg_options opt;
+    const uint8_t *sample_mask;   /* host, n_samples bytes, or NULL; copied at submit */
+    const int32_t *vars_a;        /* host; copied at submit */
+    int32_t n_a;
+    const int32_t *vars_b;        /* host or NULL; copied at submit */
+    int32_t n_b;
+    double *stat;                 /* host outputs n_a x n_b (may be NULL) */
+    double *pval;
+    int32_t *n;
+} napg_request;
+
+/* Starts the serving loop: `slots` concurrent requests (1..64) within
+ * `mem_budget` bytes of work memory (0 = 80% of the free device memory).
+ * Errors: NAPG_E_ARG, NAPG_E_BUSY (already started), NAPG_E_OOM, NAPG_E_CUDA. */
+napg_status napg_serve_start(napg_ctx *ctx, size_t mem_budget, int32_t slots);
+
+/* Queues a request; *ticket identifies it. The request's host buffers must stay
+ * valid until napg_serve_poll reports it done. Errors: NAPG_E_ARG,
+ * NAPG_E_BUSY (queue full), NAPG_E_UNSUPPORTED (request larger than the budget). */
+napg_status napg_serve_submit(napg_ctx *ctx, const napg_request *req, uint64_t *ticket);
+
+/* *done = 1 once the request's outputs are written; *latency_ms = submit-to-done
+ * wall time. *status_out (may be NULL) receives the request's own status. */
+napg_status napg_serve_poll(napg_ctx *ctx, uint64_t ticket, int32_t *done, double *latency_ms,
+                            int32_t *status_out);
+
+/* Drains the queue, waits for running requests and stops the loop. */
+napg_status napg_serve_stop(napg_ctx *ctx);
+
+/* Library version string. */
+const char *napg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NAPG_H */

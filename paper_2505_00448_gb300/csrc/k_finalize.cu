@@ -1,0 +1,430 @@
+// Finalize: statistic, edge rules and p-value per pair (Sec. 3.5), in FP64,
+// from the moments, tables or rank sums the contraction kernels produced.
+// Pairs whose sums are numerically degenerate (a variance that vanishes against
+// the raw second moment: a constant column or group on the co-observed samples)
+// are queued for an exact FP64 two-pass recomputation (k_rescue) instead.
+#include "napg_internal.cuh"
+#include "specfun.cuh"
+
+namespace napg {
+
+__device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+__device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000LL); }
+
+__device__ __forceinline__ void put(double *stat, double *pval, int32_t *nout, int64_t idx, double s, double p,
+                                    int32_t n) {
+    if (stat) stat[idx] = s;
+    if (pval) pval[idx] = p;
+    if (nout) nout[idx] = n;
+}
+
+// ------------------------------------------------------------------ Pearson --
+__global__ void k_finalize_pearson(PearsonFin f, double *stat, double *pval, int32_t *nout, int32_t *flags,
+                                   int32_t *nflag) {
+    const int64_t nv = f.nv;
+    const int64_t total = nv * (nv + 1) / 2;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        // t -> (i, j), i <= j, row-major over the upper triangle
+        int64_t i = (int64_t)((2.0 * nv + 1.0 - sqrt((2.0 * nv + 1.0) * (2.0 * nv + 1.0) - 8.0 * (double)t)) / 2.0);
+        while (i > 0 && i * (2 * nv - i + 1) / 2 > t) --i;
+        while ((i + 1) * (2 * nv - i) / 2 <= t) ++i;
+        const int64_t j = i + (t - i * (2 * nv - i + 1) / 2);
+        const int64_t ij = i * nv + j, ji = j * nv + i;
+        const int32_t n = f.nn[ij];
+        double r = dnan(), p = dnan();
+        if (n > 1) {
+            const double nd = (double)n;
+            const double sx = f.Sx[ij], sy = f.Sx[ji], sxx = f.Sxx[ij], syy = f.Sxx[ji], sxy = f.Sxy[ij];
+            const double cxx = sxx - sx * sx / nd, cyy = syy - sy * sy / nd, cxy = sxy - sx * sy / nd;
+            if (!(cxx > f.rel_tol * sxx) || !(cyy > f.rel_tol * syy)) {
+                const int q = atomicAdd(nflag, 1);
+                flags[q] = (int32_t)ij;
+            } else {
+                r = cxy / (sqrt(cxx) * sqrt(cyy));
+                r = fmin(1.0, fmax(-1.0, r));
+                p = (n <= 2) ? dnan() : sf::corr_p(r, nd);
+            }
+        }
+        put(stat, pval, nout, ij, r, p, n);
+        put(stat, pval, nout, ji, r, p, n);
+    }
+}
+
+void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout, int32_t *flag_list,
+                             int32_t *flag_count, cudaStream_t st) {
+    const int64_t total = (int64_t)f.nv * (f.nv + 1) / 2;
+    if (total == 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    k_finalize_pearson<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
+}
+
+// --------------------------------------------------- ANOVA / Welch / Student --
+__global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_t *nout, int32_t *flags,
+                                  int32_t *nflag) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / f.nb), j = (int)(t - (int64_t)a * f.nb);
+        const int c = f.nlev[a], off = f.levoff[a];
+        int64_t n = 0;
+        int k = 0;
+        bool empty = false;
+        for (int g = 0; g < c; ++g) {
+            const int32_t ng = f.gn[(int64_t)(off + g) * f.nb + j];
+            n += ng;
+            if (f.present[off + g]) {
+                ++k;
+                if (ng == 0) empty = true;
+            }
+        }
+        double s = dnan(), p = dnan();
+        if (f.test == NAPG_ANOVA) {
+            if (!empty && k >= 2 && n - k >= 1) {
+                double s1 = 0.0, raw = 0.0;
+                for (int g = 0; g < c; ++g) {
+                    const int64_t idx = (int64_t)(off + g) * f.nb + j;
+                    s1 += f.g1[idx];
+                    raw += f.g2[idx];
+                }
+                const double gm = s1 / (double)n;
+                double ssb = 0.0, ssw = 0.0;
+                for (int g = 0; g < c; ++g) {
+                    if (!f.present[off + g]) continue;
+                    const int64_t idx = (int64_t)(off + g) * f.nb + j;
+                    const double ng = (double)f.gn[idx], mg = f.g1[idx] / ng;
+                    ssb += ng * (mg - gm) * (mg - gm);
+                    ssw += f.g2[idx] - f.g1[idx] * mg;
+                }
+                if (!(ssw > f.rel_tol * raw)) {
+                    flags[atomicAdd(nflag, 1)] = (int32_t)t;
+                } else {
+                    const double d1 = (double)(k - 1), d2 = (double)(n - k);
+                    s = (ssb / d1) / (ssw / d2);
+                    p = sf::f_sf(s, d1, d2);
+                }
+            }
+        } else {  // two-sample t (levels 0 and 1)
+            const int64_t i0 = (int64_t)off * f.nb + j, i1 = (int64_t)(off + 1) * f.nb + j;
+            const int32_t n0 = f.gn[i0], n1 = f.gn[i1];
+            if (n0 >= 2 && n1 >= 2 && n >= 3) {
+                const double m0 = f.g1[i0] / n0, m1 = f.g1[i1] / n1;
+                const double q0 = f.g2[i0] - f.g1[i0] * m0, q1 = f.g2[i1] - f.g1[i1] * m1;
+                if (!(q0 > f.rel_tol * f.g2[i0]) || !(q1 > f.rel_tol * f.g2[i1])) {
+                    flags[atomicAdd(nflag, 1)] = (int32_t)t;
+                } else if (f.welch) {
+                    const double e0 = q0 / (double)(n0 - 1) / (double)n0, e1 = q1 / (double)(n1 - 1) / (double)n1;
+                    const double se2 = e0 + e1;
+                    s = (m0 - m1) / sqrt(se2);
+                    const double nu = se2 * se2 / (e0 * e0 / (double)(n0 - 1) + e1 * e1 / (double)(n1 - 1));
+                    p = sf::t_two_sided(s, nu);
+                } else {
+                    const double df = (double)(n - 2);
+                    const double sp2 = (q0 + q1) / df;
+                    s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
+                    p = sf::t_two_sided(s, df);
+                }
+            }
+        }
+        put(stat, pval, nout, t, s, p, (int32_t)n);
+    }
+}
+
+void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout, int32_t *flag_list,
+                            int32_t *flag_count, cudaStream_t st) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    if (total == 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    k_finalize_groups<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
+}
+
+// -------------------------------------------------------------- chi-squared --
+__global__ void k_finalize_chi2(Chi2Fin f, double *stat, double *pval, int32_t *nout) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / f.nb), b = (int)(t - (int64_t)a * f.nb);
+        if (f.symmetric && b < a) continue;     // filled from (b, a)
+        const int ca = f.nlev_a[a], cb = f.nlev_b[b];
+        const int oa = f.levoff_a[a], ob = f.levoff_b[b];
+        int32_t row[kMaxLevels], col[kMaxLevels];
+        int64_t n = 0;
+        for (int g = 0; g < ca; ++g) row[g] = 0;
+        for (int h = 0; h < cb; ++h) col[h] = 0;
+        for (int g = 0; g < ca; ++g)
+            for (int h = 0; h < cb; ++h) {
+                const int32_t o = f.T[(int64_t)(oa + g) * f.R + (ob + h)];
+                row[g] += o;
+                col[h] += o;
+                n += o;
+            }
+        int ka = 0, kb = 0;
+        bool empty = (n == 0);
+        for (int g = 0; g < ca; ++g)
+            if (f.present[oa + g]) { ++ka; if (row[g] == 0) empty = true; }
+        for (int h = 0; h < cb; ++h)
+            if (f.present[ob + h]) { ++kb; if (col[h] == 0) empty = true; }
+        double s = dnan(), p = dnan();
+        if (!empty) {
+            const bool yates = f.yates && ka == 2 && kb == 2;
+            double chi = 0.0;
+            const double nd = (double)n;
+            for (int g = 0; g < ca; ++g) {
+                if (!f.present[oa + g]) continue;
+                for (int h = 0; h < cb; ++h) {
+                    if (!f.present[ob + h]) continue;
+                    const double E = (double)row[g] * (double)col[h] / nd;
+                    double d = fabs((double)f.T[(int64_t)(oa + g) * f.R + (ob + h)] - E);
+                    if (yates) d = (d > 0.5) ? d - 0.5 : 0.0;
+                    chi += d * d / E;
+                }
+            }
+            s = chi;
+            const int df = (ka - 1) * (kb - 1);
+            p = (df <= 0) ? dnan() : sf::chi2_sf(chi, (double)df);
+        }
+        put(stat, pval, nout, t, s, p, (int32_t)n);
+        if (f.symmetric && a != b) put(stat, pval, nout, (int64_t)b * f.nb + a, s, p, (int32_t)n);
+    }
+}
+
+void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    if (total == 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    k_finalize_chi2<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
+}
+
+// ----------------------------------------------------------------- Spearman --
+__global__ void k_finalize_spearman(SpearmanFin f, double *stat, double *pval, int32_t *nout) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / f.nb), b = (int)(t - (int64_t)a * f.nb);
+        if (f.symmetric && b < a) continue;
+        const int64_t *q = f.q + 4 * t;
+        const int64_t n = q[0];
+        double r = dnan(), p = dnan();
+        if (n > 1) {
+            // doubled ranks A = 2Rx, B = 2Ry: sum A = sum B = n(n+1) = K
+            const __int128 K = (__int128)n * (n + 1);
+            const __int128 num = (__int128)n * q[1] - K * K;
+            const __int128 da = (__int128)n * q[2] - K * K;
+            const __int128 db = (__int128)n * q[3] - K * K;
+            if (da > 0 && db > 0) {
+                r = (double)num / (sqrt((double)da) * sqrt((double)db));
+                r = fmin(1.0, fmax(-1.0, r));
+                p = (n <= 2) ? dnan() : sf::corr_p(r, (double)n);
+            }
+        }
+        put(stat, pval, nout, t, r, p, (int32_t)n);
+        if (f.symmetric && a != b) put(stat, pval, nout, (int64_t)b * f.nb + a, r, p, (int32_t)n);
+    }
+}
+
+void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    if (total == 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    k_finalize_spearman<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
+}
+
+// ------------------------------------------------------------ MWU / Kruskal --
+__global__ void k_finalize_rankgroups(RankGroupFin f, double *stat, double *pval, int32_t *nout, int32_t *flags,
+                                      int32_t *nflag) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / f.nb), j = (int)(t - (int64_t)a * f.nb);
+        const int c = f.nlev[a], off = f.levoff[a];
+        int64_t n = 0;
+        int k = 0;
+        bool empty = false;
+        for (int g = 0; g < c; ++g) {
+            const int32_t ng = f.rcnt[(int64_t)(off + g) * f.nb + j];
+            n += ng;
+            if (f.present[off + g]) { ++k; if (ng == 0) empty = true; }
+        }
+        const int64_t T = f.tie_term[t];
+        double s = dnan(), p = dnan();
+        if (f.test == NAPG_MWU) {
+            const int64_t i0 = (int64_t)off * f.nb + j, i1 = (int64_t)(off + 1) * f.nb + j;
+            const int64_t n0 = f.rcnt[i0], n1 = f.rcnt[i1];
+            if (n0 > 0 && n1 > 0) {
+                const int64_t two_u0 = f.rsum[i0] - n0 * (n0 + 1);   // 2 U0 (exact)
+                const int64_t two_nn = 2 * n0 * n1;
+                const int64_t two_u = two_u0 > two_nn - two_u0 ? two_u0 : two_nn - two_u0;
+                s = 0.5 * (double)two_u0;
+                const bool exact = f.mwu_mode == 1 || (f.mwu_mode == 0 && T == 0 && (n0 < 8 || n1 < 8));
+                if (exact) {
+                    flags[atomicAdd(nflag, 1)] = (int32_t)t;
+                } else {
+                    const int64_t num = n * n * n - n - T;           // 12 n (n-1) sigma^2 / (n0 n1)
+                    if (num > 0) {
+                        const double sigma = sqrt((double)n0 * (double)n1 * (double)num /
+                                                  (12.0 * (double)n * (double)(n - 1)));
+                        const double cc = f.mwu_cc ? 1.0 : 0.0;
+                        const double z = ((double)(two_u - n0 * n1) - cc) / (2.0 * sigma);
+                        p = fmin(1.0, 2.0 * sf::norm_sf(z));
+                    }
+                }
+            }
+        } else {  // Kruskal-Wallis
+            if (!empty && k >= 2) {
+                const int64_t denom = n * n * n - n;
+                const int64_t cnum = denom - T;
+                if (cnum > 0) {
+                    double acc = 0.0;
+                    for (int g = 0; g < c; ++g) {
+                        if (!f.present[off + g]) continue;
+                        const int64_t idx = (int64_t)(off + g) * f.nb + j;
+                        const int64_t ng = f.rcnt[idx];
+                        const double D = (double)(f.rsum[idx] - ng * (n + 1));   // 2 n_g (Rbar_g - (n+1)/2)
+                        acc += D * D / (double)ng;
+                    }
+                    const double h0 = 3.0 * acc / ((double)n * (double)(n + 1));
+                    s = h0 / ((double)cnum / (double)denom);
+                    p = sf::chi2_sf(s, (double)(k - 1));
+                }
+            }
+        }
+        put(stat, pval, nout, t, s, p, (int32_t)n);
+    }
+}
+
+void launch_finalize_rankgroups(const RankGroupFin &f, double *stat, double *pval, int32_t *nout,
+                                int32_t *flag_list, int32_t *flag_count, cudaStream_t st) {
+    const int64_t total = (int64_t)f.na * f.nb;
+    if (total == 0) return;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    k_finalize_rankgroups<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
+}
+
+// ---------------------------------------------------------- exact rescue --
+// One thread per queued pair: the textbook two-pass computation over the
+// co-observed samples read straight from the cohort, with exact constancy
+// checks (a constant column or group is detected by comparing values, not by a
+// rounded variance).
+template <typename T>
+__device__ double load_val(const void *X, int64_t idx) { return (double)((const T *)X)[idx]; }
+
+__device__ __forceinline__ double xval(const RescueArgs &r, int64_t idx) {
+    return r.dtype == NAPG_F32 ? load_val<float>(r.X, idx) : load_val<double>(r.X, idx);
+}
+
+__device__ __forceinline__ bool bit(const uint32_t *w, int64_t s) { return (w[s >> 5] >> (s & 31)) & 1u; }
+
+__global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nflag, int32_t max_flags,
+                         double *stat, double *pval, int32_t *nout, int32_t symmetric) {
+    const int32_t cnt = min(*nflag, max_flags);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+        const int64_t t = flags[q];
+        const int ncols = symmetric ? r.na : r.nb;
+        const int ia = (int)(t / ncols), ib = (int)(t - (int64_t)ia * ncols);
+        const int va = r.va[ia], vb = symmetric ? r.va[ib] : r.vb[ib];
+        const uint32_t *oa = r.obs + (int64_t)va * r.W, *ob = r.obs + (int64_t)vb * r.W;
+        double s = dnan(), p = dnan();
+        if (r.test == NAPG_PEARSON) {
+            int64_t n = 0;
+            double mx = 0.0, my = 0.0, fx = 0.0, fy = 0.0;
+            bool cx = true, cy = true;
+            for (int64_t k = 0; k < r.S; ++k) {
+                if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+                const double x = xval(r, (int64_t)va * r.S + k), y = xval(r, (int64_t)vb * r.S + k);
+                if (n == 0) { fx = x; fy = y; } else { cx &= (x == fx); cy &= (y == fy); }
+                mx += x; my += y; ++n;
+            }
+            if (n > 1 && !cx && !cy) {
+                mx /= (double)n; my /= (double)n;
+                double sxx = 0.0, syy = 0.0, sxy = 0.0;
+                for (int64_t k = 0; k < r.S; ++k) {
+                    if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+                    const double dx = xval(r, (int64_t)va * r.S + k) - mx, dy = xval(r, (int64_t)vb * r.S + k) - my;
+                    sxx += dx * dx; syy += dy * dy; sxy += dx * dy;
+                }
+                s = fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
+                p = (n <= 2) ? dnan() : sf::corr_p(s, (double)n);
+            }
+            put(stat, pval, nout, t, s, p, (int32_t)n);
+            if (symmetric) put(stat, pval, nout, (int64_t)ib * ncols + ia, s, p, (int32_t)n);
+            continue;
+        }
+        // group tests: a categorical (labels), b continuous
+        const uint8_t *la = r.lab + (int64_t)r.catrow[ia] * r.S;
+        const int c = r.nlev_a[ia], off = r.levoff[ia];
+        int64_t ng[kMaxLevels];
+        double sum[kMaxLevels], first[kMaxLevels], ss[kMaxLevels];
+        bool cst[kMaxLevels];
+        for (int g = 0; g < c; ++g) { ng[g] = 0; sum[g] = 0.0; first[g] = 0.0; ss[g] = 0.0; cst[g] = true; }
+        int64_t n = 0;
+        double tot = 0.0;
+        for (int64_t k = 0; k < r.S; ++k) {
+            if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+            const int g = la[k];
+            const double y = xval(r, (int64_t)vb * r.S + k);
+            if (ng[g] == 0) first[g] = y; else cst[g] &= (y == first[g]);
+            sum[g] += y; ng[g] += 1; tot += y; ++n;
+        }
+        for (int64_t k = 0; k < r.S; ++k) {
+            if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+            const int g = la[k];
+            const double d = xval(r, (int64_t)vb * r.S + k) - sum[g] / (double)ng[g];
+            ss[g] += d * d;
+        }
+        for (int g = 0; g < c; ++g) if (cst[g]) ss[g] = 0.0;
+        if (r.test == NAPG_ANOVA) {
+            int k = 0;
+            bool all_const = true, differ = false;
+            double ref = 0.0;
+            bool have_ref = false;
+            for (int g = 0; g < c; ++g) {
+                if (!r.present[off + g]) continue;
+                ++k;
+                all_const &= cst[g];
+                if (!have_ref) { ref = first[g]; have_ref = true; } else if (first[g] != ref) differ = true;
+            }
+            if (all_const) {
+                if (differ) { s = dinf(); p = 0.0; }
+            } else {
+                const double gm = tot / (double)n;
+                double ssb = 0.0, ssw = 0.0;
+                for (int g = 0; g < c; ++g) {
+                    if (!r.present[off + g]) continue;
+                    const double mg = sum[g] / (double)ng[g];
+                    ssb += (double)ng[g] * (mg - gm) * (mg - gm);
+                    ssw += ss[g];
+                }
+                const double d1 = (double)(k - 1), d2 = (double)(n - k);
+                s = (ssb / d1) / (ssw / d2);
+                p = sf::f_sf(s, d1, d2);
+            }
+        } else {  // t-test
+            const int64_t n0 = ng[0], n1 = ng[1];
+            const double m0 = sum[0] / (double)n0, m1 = sum[1] / (double)n1;
+            if (!r.welch) {
+                if (!(cst[0] && cst[1])) {
+                    const double df = (double)(n - 2);
+                    const double sp2 = (ss[0] + ss[1]) / df;
+                    s = (m0 - m1) / sqrt(sp2 * (1.0 / (double)n0 + 1.0 / (double)n1));
+                    p = sf::t_two_sided(s, df);
+                }
+            } else if (cst[0] && cst[1]) {
+                if (first[0] != first[1]) { s = first[0] > first[1] ? dinf() : -dinf(); p = 0.0; }
+            } else {
+                const double e0 = ss[0] / (double)(n0 - 1) / (double)n0, e1 = ss[1] / (double)(n1 - 1) / (double)n1;
+                const double se2 = e0 + e1;
+                s = (m0 - m1) / sqrt(se2);
+                const double nu = se2 * se2 / (e0 * e0 / (double)(n0 - 1) + e1 * e1 / (double)(n1 - 1));
+                p = sf::t_two_sided(s, nu);
+            }
+        }
+        put(stat, pval, nout, t, s, p, (int32_t)n);
+    }
+}
+
+void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
+                   double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st) {
+    k_rescue<<<64, 64, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+}
+
+}  // namespace napg

@@ -1,0 +1,548 @@
+// Rank tests (Sec. 3.5.3 Spearman, 3.5.6 Mann-Whitney U, 3.5.8 Kruskal-Wallis).
+//
+// Presort (the paper sorts and ranks each feature once, Sec. 3.5.3/3.5.6): every
+// continuous variable's observed samples are sorted by value once per cohort
+// (ties broken by sample index). A sample context or the other variable of a
+// pair only removes samples, so the global order restricted to the survivors is
+// still sorted and its tie groups are the global groups restricted likewise.
+//
+// Pairwise re-rank: for a pair, B[p] = 1 when the sample at sorted position p is
+// co-observed. With P(x) = number of co-observed positions < x and a tie group
+// spanning positions [gs, ge), a co-observed member has
+//   L = P(gs) values strictly below it and t = P(ge) - P(gs) tied with it,
+// so its doubled rank is 2R = 2L + t + 1 = P(gs) + P(ge) + 1, an integer.
+// Rank sums are accumulated in int64 and are exact.
+#include "napg_internal.cuh"
+
+namespace napg {
+
+// ------------------------------------------------------------------ presort --
+
+__device__ __forceinline__ uint64_t order_key(double v) {
+    if (v == 0.0) v = 0.0;                       // -0 and +0 tie
+    const uint64_t u = (uint64_t)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ bool key_less(uint64_t ka, uint32_t ia, uint64_t kb, uint32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+constexpr int kSortSmem = 16384;   // elements sorted in shared memory
+
+// bitonic compare-exchange network over n2 (power of two) elements in shared memory
+__device__ void bitonic_smem(uint64_t *key, uint32_t *idx, int n2, int kmin) {
+    for (int k = kmin; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const bool up = (t & k) == 0;
+                    const uint64_t kt = key[t], ku = key[u];
+                    const uint32_t it = idx[t], iu = idx[u];
+                    const bool sw = up ? key_less(ku, iu, kt, it) : key_less(kt, it, ku, iu);
+                    if (sw) { key[t] = ku; key[u] = kt; idx[t] = iu; idx[u] = it; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// stages with stride j >= kSortSmem run on global memory (one CTA per column)
+__device__ void bitonic_global_stage(uint64_t *key, uint32_t *idx, int n2, int k, int j) {
+    for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        const int u = t ^ j;
+        if (u > t) {
+            const bool up = (t & k) == 0;
+            const uint64_t kt = key[t], ku = key[u];
+            const uint32_t it = idx[t], iu = idx[u];
+            const bool sw = up ? key_less(ku, iu, kt, it) : key_less(kt, it, ku, iu);
+            if (sw) { key[t] = ku; key[u] = kt; idx[t] = iu; idx[u] = it; }
+        }
+    }
+    __syncthreads();
+}
+
+// Shared-memory stages of the bitonic network on each kSortSmem-aligned block of
+// the global array: levels k_lo..k_hi (k_lo == k_hi: only the strides below
+// kSortSmem of one level). Directions use the global index.
+__device__ void bitonic_local_levels(uint64_t *gkey, uint32_t *gidx, uint64_t *skey, uint32_t *sidx, int n2,
+                                     int k_lo, int k_hi) {
+    for (int base = 0; base < n2; base += kSortSmem) {
+        for (int t = threadIdx.x; t < kSortSmem; t += blockDim.x) { skey[t] = gkey[base + t]; sidx[t] = gidx[base + t]; }
+        __syncthreads();
+        for (int k = k_lo; k <= k_hi; k <<= 1) {
+            for (int j = ((k >> 1) < kSortSmem ? (k >> 1) : (kSortSmem >> 1)); j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < kSortSmem; t += blockDim.x) {
+                    const int u = t ^ j;
+                    if (u > t) {
+                        const bool up = ((base + t) & k) == 0;
+                        const uint64_t kt = skey[t], ku = skey[u];
+                        const uint32_t it = sidx[t], iu = sidx[u];
+                        const bool sw = up ? key_less(ku, iu, kt, it) : key_less(kt, it, ku, iu);
+                        if (sw) { skey[t] = ku; skey[u] = kt; sidx[t] = iu; sidx[u] = it; }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int t = threadIdx.x; t < kSortSmem; t += blockDim.x) { gkey[base + t] = skey[t]; gidx[base + t] = sidx[t]; }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_presort(const T *__restrict__ X, int64_t S, int64_t W,
+                                                  const int32_t *__restrict__ contvars, const uint32_t *__restrict__ obs,
+                                                  int32_t *__restrict__ perm, int32_t *__restrict__ pos,
+                                                  int32_t *__restrict__ nobs, uint32_t *__restrict__ tie,
+                                                  int32_t *__restrict__ gsw, int32_t *__restrict__ gew,
+                                                  uint64_t *__restrict__ gkey_all, uint32_t *__restrict__ gidx_all,
+                                                  int64_t n2max, int cv_base) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *skey = (uint64_t *)smem_raw;
+    uint32_t *sidx = (uint32_t *)(skey + kSortSmem);
+    __shared__ int s_count;
+    const int cv = blockIdx.x + cv_base;     // continuous row
+    const int slot = blockIdx.x;             // temp slot of this batch
+    const int v = contvars[cv];
+    const uint32_t *ob = obs + (int64_t)v * W;
+    const T *x = X + (int64_t)v * S;
+    // count observed
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
+    int local = 0;
+    for (int64_t w = threadIdx.x; w < W; w += blockDim.x) local += __popc(ob[w]);
+    atomicAdd(&s_count, local);
+    __syncthreads();
+    const int n = s_count;
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    const bool in_smem = n2 <= kSortSmem;
+    uint64_t *key = in_smem ? skey : gkey_all + (int64_t)slot * n2max;
+    uint32_t *idx = in_smem ? sidx : gidx_all + (int64_t)slot * n2max;
+    // compact observed samples in sample order: word prefix counts via a serial scan per warp-chunk
+    __shared__ int wbase[1024 + 1];
+    const int64_t chunk = (W + blockDim.x - 1) / blockDim.x;
+    {
+        const int64_t w0 = threadIdx.x * chunk, w1 = min(W, w0 + chunk);
+        int c = 0;
+        for (int64_t w = w0; w < w1; ++w) c += __popc(ob[w]);
+        wbase[threadIdx.x + 1] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        wbase[0] = 0;
+        for (int t = 1; t <= (int)blockDim.x; ++t) wbase[t] += wbase[t - 1];
+    }
+    __syncthreads();
+    {
+        const int64_t w0 = threadIdx.x * chunk, w1 = min(W, w0 + chunk);
+        int o = wbase[threadIdx.x];
+        for (int64_t w = w0; w < w1; ++w) {
+            uint32_t m = ob[w];
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const int64_t s = w * 32 + b;
+                key[o] = order_key((double)x[s]);
+                idx[o] = (uint32_t)s;
+                ++o;
+            }
+        }
+    }
+    for (int t = n + threadIdx.x; t < n2; t += blockDim.x) { key[t] = ~0ull; idx[t] = 0xffffffffu; }
+    __syncthreads();
+    if (in_smem) {
+        bitonic_smem(key, idx, n2, 2);
+    } else {
+        // levels up to kSortSmem entirely in shared memory, then for each larger
+        // level the long strides on global memory and the short ones in smem
+        bitonic_local_levels(key, idx, skey, sidx, n2, 2, kSortSmem);
+        for (int k = kSortSmem << 1; k <= n2; k <<= 1) {
+            for (int j = k >> 1; j >= kSortSmem; j >>= 1) bitonic_global_stage(key, idx, n2, k, j);
+            bitonic_local_levels(key, idx, skey, sidx, n2, k, k);
+        }
+    }
+    // outputs: perm, pos, tie bits
+    int32_t *pm = perm + (int64_t)cv * S;
+    int32_t *ps = pos + (int64_t)cv * S;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x) ps[s] = -1;
+    __syncthreads();
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        pm[p] = (int32_t)idx[p];
+        ps[idx[p]] = p;
+    }
+    uint32_t *tw = tie + (int64_t)cv * W;
+    for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
+        uint32_t bits = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t p = w * 32 + b;
+            if (p < n && (p == 0 || key[p] != key[p - 1])) bits |= 1u << b;
+        }
+        tw[w] = bits;
+    }
+    __syncthreads();
+    // gsw[w] = last group start strictly before position 32w; gew[w] = first group start at or after 32(w+1)
+    if (threadIdx.x == 0) {
+        int32_t *gs = gsw + (int64_t)cv * W, *ge = gew + (int64_t)cv * W;
+        int last = 0;
+        for (int64_t w = 0; w < W; ++w) {
+            gs[w] = last;
+            const uint32_t b = tw[w];
+            if (b) last = (int)(w * 32 + 31 - __clz(b));
+        }
+        int next = n;
+        for (int64_t w = W - 1; w >= 0; --w) {
+            ge[w] = next;
+            const uint32_t b = tw[w];
+            if (b) next = (int)(w * 32 + __ffs(b) - 1);
+        }
+        nobs[cv] = n;
+    }
+}
+
+constexpr int kPresortBatch = 1024;   // columns per launch on the global-memory path
+
+size_t presort_tmp_bytes(int64_t S, int32_t ncont) {
+    int64_t n2 = 1;
+    while (n2 < S) n2 <<= 1;
+    if (n2 <= kSortSmem) return 16;
+    const int64_t cols = ncont < kPresortBatch ? ncont : kPresortBatch;
+    return (size_t)cols * (size_t)n2 * (sizeof(uint64_t) + sizeof(uint32_t));
+}
+
+void launch_presort(const void *X, int32_t dtype, int64_t S, int64_t W, const int32_t *contvars_dev, int32_t ncont,
+                    const uint32_t *obs, int32_t *perm, int32_t *pos, int32_t *nobs, uint32_t *tie, int32_t *gsw,
+                    int32_t *gew, void *tmp, size_t tmp_bytes, cudaStream_t st) {
+    if (ncont == 0) return;
+    int64_t n2 = 1;
+    while (n2 < S) n2 <<= 1;
+    (void)tmp_bytes;
+    uint64_t *gk = nullptr;
+    uint32_t *gi = nullptr;
+    const int batch = n2 > kSortSmem ? kPresortBatch : ncont;
+    if (n2 > kSortSmem) {
+        gk = (uint64_t *)tmp;
+        gi = (uint32_t *)(gk + (size_t)std::min(ncont, kPresortBatch) * n2);
+    }
+    const size_t smem = (size_t)kSortSmem * (sizeof(uint64_t) + sizeof(uint32_t));
+    cudaFuncSetAttribute(k_presort<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_presort<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int c0 = 0; c0 < ncont; c0 += batch) {
+        const int nblk = std::min(batch, ncont - c0);
+        if (dtype == NAPG_F32)
+            k_presort<float><<<nblk, 1024, smem, st>>>((const float *)X, S, W, contvars_dev, obs, perm, pos, nobs, tie,
+                                                       gsw, gew, gk, gi, n2, c0);
+        else
+            k_presort<double><<<nblk, 1024, smem, st>>>((const double *)X, S, W, contvars_dev, obs, perm, pos, nobs,
+                                                        tie, gsw, gew, gk, gi, n2, c0);
+    }
+}
+
+// --------------------------------------------------------- rank machinery --
+
+// Per column side of a pair, all in shared memory (W words each, B and P with
+// one extra word so that position == nobs can be queried).
+struct Side {
+    uint32_t *B;     // co-observed bit per sorted position
+    int32_t *P;      // exclusive prefix popcount of B per word
+    uint32_t *T;     // tie-group start bits
+    int32_t *GS, *GE;
+    int32_t n;       // observed count of the column
+};
+
+__device__ __forceinline__ int32_t prefix_at(const Side &sd, int32_t x) {
+    const int w = x >> 5, l = x & 31;
+    return sd.P[w] + __popc(sd.B[w] & ((1u << l) - 1u));
+}
+
+__device__ __forceinline__ int64_t rank2_at(const Side &sd, int32_t p) {
+    const int w = p >> 5, l = p & 31;
+    const uint32_t le = (l == 31) ? 0xffffffffu : ((1u << (l + 1)) - 1u);
+    const uint32_t tw = sd.T[w];
+    const uint32_t m_le = tw & le, m_gt = tw & ~le;
+    const int32_t gs = m_le ? (w * 32 + 31 - __clz(m_le)) : sd.GS[w];
+    const int32_t ge = m_gt ? (w * 32 + __ffs(m_gt) - 1) : sd.GE[w];
+    return (int64_t)prefix_at(sd, gs) + (int64_t)prefix_at(sd, ge) + 1;
+}
+
+// Build B over the column's sorted positions from the co-observed sample bits,
+// then the exclusive word prefix P. Every thread of the block must call it.
+__device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uint32_t *co, int W, int32_t *scan_tmp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int nw = (sd.n + 31) >> 5;
+    for (int w = warp; w <= W; w += nwarps) {
+        const int p = w * 32 + lane;
+        bool b = false;
+        if (w < nw && p < sd.n) {
+            const int s = perm[p];
+            b = (co[s >> 5] >> (s & 31)) & 1u;
+        }
+        const uint32_t bits = __ballot_sync(0xffffffffu, b);
+        if (lane == 0) sd.B[w] = bits;
+    }
+    __syncthreads();
+    // exclusive scan of popc(B[w]) over w = 0..W (W+1 entries), block-wide
+    const int per = (W + 1 + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(W + 1, w0 + per);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(sd.B[w]);
+    scan_tmp[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) { const int v = scan_tmp[t]; scan_tmp[t] = run; run += v; }
+    }
+    __syncthreads();
+    int run = scan_tmp[threadIdx.x];
+    for (int w = w0; w < w1; ++w) { sd.P[w] = run; run += __popc(sd.B[w]); }
+    __syncthreads();
+}
+
+__device__ void load_side_static(Side &sd, const RankData &rd, int crow, int W) {
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        sd.T[w] = rd.tie[(int64_t)crow * rd.W + w];
+        sd.GS[w] = rd.gsw[(int64_t)crow * rd.W + w];
+        sd.GE[w] = rd.gew[(int64_t)crow * rd.W + w];
+    }
+    if (threadIdx.x == 0) { sd.T[W] = 0u; sd.GS[W] = 0; sd.GE[W] = 0; }
+    sd.n = rd.nobs[crow];
+}
+
+__device__ __forceinline__ int64_t block_sum64(int64_t v, int64_t *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int64_t tot = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    return tot;   // valid in thread 0
+}
+
+// smem layout per side: B[W+1] u32, P[W+1] i32, T[W+1] u32, GS[W+1] i32, GE[W+1] i32
+__device__ Side carve_side(unsigned char *&cur, int W) {
+    Side sd;
+    sd.B = (uint32_t *)cur; cur += (W + 1) * 4;
+    sd.P = (int32_t *)cur; cur += (W + 1) * 4;
+    sd.T = (uint32_t *)cur; cur += (W + 1) * 4;
+    sd.GS = (int32_t *)cur; cur += (W + 1) * 4;
+    sd.GE = (int32_t *)cur; cur += (W + 1) * 4;
+    sd.n = 0;
+    return sd;
+}
+
+// ----------------------------------------------------------------- Spearman --
+// One CTA per pair. out4[pair] = {n, sum A*B, sum A^2, sum B^2}, A = 2Rx, B = 2Ry.
+__global__ void __launch_bounds__(256) k_spearman(RankData rd, const int32_t *__restrict__ crow_a,
+                                                  const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
+                                                  const uint32_t *__restrict__ obs_b, int32_t na, int32_t nb,
+                                                  int32_t symmetric, int64_t *__restrict__ out4) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t scan_tmp[256];
+    __shared__ int64_t red[8];
+    const int W = (int)rd.W;
+    // pair index
+    int64_t pid = blockIdx.x;
+    int a, b;
+    if (symmetric) {
+        // upper triangle including the diagonal, row-major
+        int64_t t = pid, i = 0;
+        while (t >= (int64_t)na - i) { t -= na - i; ++i; }
+        a = (int)i; b = (int)(i + t);
+    } else {
+        a = (int)(pid / nb); b = (int)(pid - (int64_t)a * nb);
+    }
+    unsigned char *cur = smem_raw;
+    uint32_t *co = (uint32_t *)cur; cur += (W + 1) * 4;
+    Side si = carve_side(cur, W), sj = carve_side(cur, W);
+    const uint32_t *oa = obs_a + (int64_t)a * W, *ob = obs_b + (int64_t)b * W;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) co[w] = oa[w] & ob[w];
+    const int ci = crow_a[a], cj = crow_b[b];
+    load_side_static(si, rd, ci, W);
+    load_side_static(sj, rd, cj, W);
+    __syncthreads();
+    const int32_t *perm_i = rd.perm + (int64_t)ci * rd.S, *perm_j = rd.perm + (int64_t)cj * rd.S;
+    const int32_t *pos_j = rd.pos + (int64_t)cj * rd.S;
+    build_side(si, perm_i, co, W, scan_tmp);
+    build_side(sj, perm_j, co, W, scan_tmp);
+    int64_t sab = 0, saa = 0, sbb = 0, cnt = 0;
+    for (int p = threadIdx.x; p < si.n; p += blockDim.x) {
+        if (!((si.B[p >> 5] >> (p & 31)) & 1u)) continue;
+        const int s = perm_i[p];
+        const int q = pos_j[s];
+        const int64_t A = rank2_at(si, p), B = rank2_at(sj, q);
+        sab += A * B; saa += A * A; sbb += B * B; ++cnt;
+    }
+    const int64_t t0 = block_sum64(cnt, red);
+    const int64_t t1 = block_sum64(sab, red);
+    const int64_t t2 = block_sum64(saa, red);
+    const int64_t t3 = block_sum64(sbb, red);
+    if (threadIdx.x == 0) {
+        int64_t *o = out4 + 4 * ((int64_t)a * nb + b);
+        o[0] = t0; o[1] = t1; o[2] = t2; o[3] = t3;
+    }
+}
+
+static size_t rank_smem_bytes(int64_t W, int sides, bool with_co) {
+    return (size_t)(W + 1) * 4 * (5 * sides + (with_co ? 1 : 0));
+}
+
+void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b, const uint32_t *obs_a,
+                           const uint32_t *obs_b, int32_t na, int32_t nb, int32_t symmetric, int64_t *out4,
+                           cudaStream_t st) {
+    const int64_t pairs = symmetric ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
+    if (pairs == 0) return;
+    const size_t smem = rank_smem_bytes(rd.W, 2, true);
+    cudaFuncSetAttribute(k_spearman, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_spearman<<<(unsigned)pairs, 256, smem, st>>>(rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric, out4);
+}
+
+// ------------------------------------------------------------ MWU / Kruskal --
+// One CTA per (categorical a, continuous j): per level g the count n_g and the
+// sum of doubled ranks S_g, plus the tie term sum (t^3 - t) over co-observed
+// tie groups. Per-level sums use shared-memory 64-bit atomics.
+__global__ void __launch_bounds__(256) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
+                                                     const int32_t *__restrict__ catrow_a, const int32_t *__restrict__ nlev_a,
+                                                     const int32_t *__restrict__ levoff_a, int32_t na,
+                                                     const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
+                                                     const uint32_t *__restrict__ obs_b, int32_t nb, int64_t *__restrict__ rsum,
+                                                     int32_t *__restrict__ rcnt, int64_t *__restrict__ tie_term) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t scan_tmp[256];
+    __shared__ int64_t red[8];
+    __shared__ unsigned long long lsum[kMaxLevels];
+    __shared__ int lcnt[kMaxLevels];
+    const int W = (int)rd.W;
+    const int a = (int)(blockIdx.x / nb), j = (int)(blockIdx.x - (int64_t)a * nb);
+    unsigned char *cur = smem_raw;
+    uint32_t *co = (uint32_t *)cur; cur += (W + 1) * 4;
+    Side sj = carve_side(cur, W);
+    const uint32_t *oa = obs_a + (int64_t)a * W, *ob = obs_b + (int64_t)j * W;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) co[w] = oa[w] & ob[w];
+    const int cj = crow_b[j];
+    load_side_static(sj, rd, cj, W);
+    const int c = nlev_a[a];
+    for (int g = threadIdx.x; g < kMaxLevels; g += blockDim.x) { lsum[g] = 0ull; lcnt[g] = 0; }
+    __syncthreads();
+    const int32_t *perm_j = rd.perm + (int64_t)cj * rd.S;
+    build_side(sj, perm_j, co, W, scan_tmp);
+    const uint8_t *la = lab + (int64_t)catrow_a[a] * rd.S;
+    int64_t tsum = 0;
+    for (int p = threadIdx.x; p < sj.n; p += blockDim.x) {
+        const int w = p >> 5, l = p & 31;
+        if ((sj.T[w] >> l) & 1u) {
+            // group starting at p: co-observed size t = P(ge) - P(p)
+            const uint32_t le = (l == 31) ? 0xffffffffu : ((1u << (l + 1)) - 1u);
+            const uint32_t m_gt = sj.T[w] & ~le;
+            const int32_t ge = m_gt ? (w * 32 + __ffs(m_gt) - 1) : sj.GE[w];
+            const int64_t t = (int64_t)prefix_at(sj, ge) - prefix_at(sj, p);
+            tsum += t * t * t - t;
+        }
+        if (!((sj.B[w] >> l) & 1u)) continue;
+        const int s = perm_j[p];
+        const int g = la[s];
+        const int64_t r2 = rank2_at(sj, p);
+        atomicAdd(&lsum[g], (unsigned long long)r2);
+        atomicAdd(&lcnt[g], 1);
+    }
+    const int64_t T = block_sum64(tsum, red);
+    __syncthreads();
+    const int off = levoff_a[a];
+    for (int g = threadIdx.x; g < c; g += blockDim.x) {
+        rsum[(int64_t)(off + g) * nb + j] = (int64_t)lsum[g];
+        rcnt[(int64_t)(off + g) * nb + j] = lcnt[g];
+    }
+    if (threadIdx.x == 0) tie_term[(int64_t)a * nb + j] = T;
+}
+
+void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a, const int32_t *nlev_a,
+                        const int32_t *levoff_a, int32_t na, const int32_t *crow_b, const uint32_t *obs_a,
+                        const uint32_t *obs_b, int32_t nb, int32_t total_rows, int64_t *rsum, int32_t *rcnt,
+                        int64_t *tie_term, cudaStream_t st) {
+    (void)total_rows;
+    const int64_t pairs = (int64_t)na * nb;
+    if (pairs == 0) return;
+    const size_t smem = rank_smem_bytes(rd.W, 1, true);
+    cudaFuncSetAttribute(k_rank_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_rank_groups<<<(unsigned)pairs, 256, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b,
+                                                      nb, rsum, rcnt, tie_term);
+}
+
+// ------------------------------------------------------ exact Mann-Whitney --
+// Null distribution of U for group sizes (m, n), m <= n: the coefficients of the
+// Gaussian binomial [m+n choose m]_q = prod_{k=1..m} (1 - q^{n+k}) / (1 - q^k)
+// count the arrangements with U = u. Built one factor at a time in exact
+// 128-bit integers, truncated at the degree needed; then
+// p = min(1, 2 P(U <= min(U0, U1))).
+typedef unsigned __int128 u128;
+
+__global__ void k_mwu_exact(const double *__restrict__ stat, const int32_t *__restrict__ rcnt,
+                            const int32_t *__restrict__ levoff, int32_t nb, const int32_t *__restrict__ flags,
+                            const int32_t *__restrict__ nflag, int32_t max_flags, double *__restrict__ pval,
+                            u128 *__restrict__ scratch, int64_t cap) {
+    const int32_t cnt = min(*nflag, max_flags);
+    u128 *G = scratch + (int64_t)blockIdx.x * 2 * cap;
+    u128 *H = G + cap;
+    __shared__ double s_p;
+    for (int q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const int64_t t = flags[q];
+        const int a = (int)(t / nb), j = (int)(t - (int64_t)a * nb);
+        const int64_t n0 = rcnt[(int64_t)levoff[a] * nb + j], n1 = rcnt[(int64_t)(levoff[a] + 1) * nb + j];
+        const int64_t m = n0 < n1 ? n0 : n1, n = n0 < n1 ? n1 : n0;
+        const double U0 = stat[t];
+        const double umin_d = fmin(U0, (double)(n0 * n1) - U0);
+        const int64_t ulim = (int64_t)floor(umin_d);
+        // total = C(m+n, m) exactly; 127-bit overflow guard via lgamma
+        const double log2_total = (lgamma((double)(m + n + 1)) - lgamma((double)(m + 1)) - lgamma((double)(n + 1))) /
+                                  0.69314718055994530942;
+        if (threadIdx.x == 0) s_p = __longlong_as_double(0x7ff8000000000000LL);
+        __syncthreads();
+        if (ulim + 1 <= cap && log2_total < 126.0 && m <= 64) {
+            for (int64_t u = threadIdx.x; u <= ulim; u += blockDim.x) G[u] = (u == 0) ? 1 : 0;
+            __syncthreads();
+            for (int64_t k = 1; k <= m; ++k) {
+                // H = G * (1 - q^{n+k}) (truncated)
+                for (int64_t u = threadIdx.x; u <= ulim; u += blockDim.x)
+                    H[u] = G[u] - ((u >= n + k) ? G[u - n - k] : (u128)0);
+                __syncthreads();
+                // G = H / (1 - q^k): prefix sums with stride k, one residue class per thread
+                for (int64_t r = threadIdx.x; r < k; r += blockDim.x) {
+                    u128 run = 0;
+                    for (int64_t u = r; u <= ulim; u += k) { run += H[u]; G[u] = run; }
+                }
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                u128 cdf = 0;
+                for (int64_t u = 0; u <= ulim; ++u) cdf += G[u];
+                u128 total = 1;
+                for (int64_t k = 1; k <= m; ++k) total = total * (u128)(n + k) / (u128)k;
+                const double pv = 2.0 * ((double)cdf / (double)total);
+                s_p = pv > 1.0 ? 1.0 : pv;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) pval[t] = s_p;
+        __syncthreads();
+    }
+}
+
+size_t mwu_exact_scratch_bytes(int64_t S) {
+    // blocks x 2 arrays x (7 S / 2 + 2) entries covers auto mode (min group < 8)
+    const int64_t cap = 7 * S / 2 + 2;
+    return (size_t)32 * 2 * (size_t)cap * sizeof(u128);
+}
+
+void launch_mwu_exact(const double *stat, const int32_t *rcnt, const int32_t *levoff, int32_t total_rows, int32_t nb,
+                      const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags, double *pval,
+                      void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    (void)total_rows;
+    const int64_t cap = (int64_t)(scratch_bytes / (32 * 2 * sizeof(u128)));
+    k_mwu_exact<<<32, 128, 0, st>>>(stat, rcnt, levoff, nb, flag_list, flag_count, max_flags, pval, (u128 *)scratch,
+                                    cap);
+}
+
+}  // namespace napg

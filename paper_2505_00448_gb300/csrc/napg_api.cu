@@ -1,0 +1,678 @@
+// C ABI of the napg library: contexts, cohort upload and validation, and the
+// per-test pipelines (bitmasks -> contraction or rank kernel -> finalize ->
+// exact rescue), all ordered on one CUDA stream.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "napg_internal.cuh"
+
+namespace napg {
+
+napg_status fail(napg_ctx *ctx, napg_status code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+napg_status cuda_fail(napg_ctx *ctx, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? NAPG_E_OOM : NAPG_E_CUDA, m);
+}
+
+void *ws_get(napg_ctx *ctx, Workspace &ws, int slot, size_t bytes, napg_status *st) {
+    bytes = ((std::max<size_t>(bytes, 16) + 255) / 256) * 256;
+    if (ws.cap[slot] >= bytes) return ws.ptr[slot];
+    if (ws.ptr[slot]) {
+        cudaFree(ws.ptr[slot]);
+        ws.ptr[slot] = nullptr;
+        ws.cap[slot] = 0;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(ctx, e, "cudaMalloc(workspace)");
+        return nullptr;
+    }
+    ws.ptr[slot] = p;
+    ws.cap[slot] = bytes;
+    return p;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static void free_cohort(Cohort &c) {
+    void *ptrs[] = {c.X, c.obs, c.lab, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    c = Cohort();
+}
+
+static void free_ws(Workspace &ws) {
+    for (int i = 0; i < Workspace::kNumSlots; ++i)
+        if (ws.ptr[i]) cudaFree(ws.ptr[i]);
+    ws = Workspace();
+}
+
+// ---------------------------------------------------------------- helpers --
+
+#define WS(slot, type, count)                                                         \
+    ([&]() -> type * {                                                                \
+        napg_status s_ = NAPG_OK;                                                     \
+        type *p_ = (type *)ws_get(ctx, ws, Workspace::slot, sizeof(type) * (size_t)(count), &s_); \
+        if (!p_) st_ = s_;                                                            \
+        return p_;                                                                    \
+    }())
+
+struct HostLists {
+    std::vector<int32_t> va, vb, crow_a, crow_b, catrow, nlev, levoff;
+    int32_t R = 0, maxlev = 0;
+};
+
+static napg_status check_vars(napg_ctx *ctx, const RunArgs &a, bool *symmetric) {
+    const Cohort &c = ctx->coh;
+    const int t = a.test;
+    if (t < NAPG_PEARSON || t > NAPG_KRUSKAL) return fail(ctx, NAPG_E_ARG, "unknown test");
+    if (a.na < 0 || a.nb < 0 || (a.na > 0 && !a.va)) return fail(ctx, NAPG_E_ARG, "bad variable list");
+    const bool homo = (t == NAPG_PEARSON || t == NAPG_SPEARMAN || t == NAPG_CHI2);
+    *symmetric = (a.vb == nullptr);
+    if (!homo && *symmetric) return fail(ctx, NAPG_E_ARG, "categorical x continuous tests need vars_b");
+    const int want_a = (t == NAPG_PEARSON || t == NAPG_SPEARMAN) ? 0 : 1;
+    const int want_b = (t == NAPG_CHI2) ? 1 : 0;
+    for (int i = 0; i < a.na; ++i) {
+        const int v = a.va[i];
+        if (v < 0 || v >= c.F) return fail(ctx, NAPG_E_ARG, "vars_a index out of range");
+        if (c.vtype[v] != want_a) return fail(ctx, NAPG_E_ARG, "vars_a has a variable of the wrong type");
+        if ((t == NAPG_TTEST || t == NAPG_MWU) && c.nlev[v] != 2)
+            return fail(ctx, NAPG_E_ARG, "t-test / Mann-Whitney need 2 levels in vars_a");
+        if ((t == NAPG_ANOVA || t == NAPG_KRUSKAL) && c.nlev[v] < 2)
+            return fail(ctx, NAPG_E_ARG, "ANOVA / Kruskal-Wallis need >= 2 levels in vars_a");
+    }
+    if (!*symmetric) {
+        for (int i = 0; i < a.nb; ++i) {
+            const int v = a.vb[i];
+            if (v < 0 || v >= c.F) return fail(ctx, NAPG_E_ARG, "vars_b index out of range");
+            if (c.vtype[v] != want_b) return fail(ctx, NAPG_E_ARG, "vars_b has a variable of the wrong type");
+        }
+    }
+    if ((t == NAPG_SPEARMAN || t == NAPG_MWU || t == NAPG_KRUSKAL) && c.S > kMaxRankSamples)
+        return fail(ctx, NAPG_E_UNSUPPORTED, "rank tests support at most 163840 samples");
+    return NAPG_OK;
+}
+
+static void level_lists(const Cohort &c, const std::vector<int32_t> &vars, std::vector<int32_t> &catrow,
+                        std::vector<int32_t> &nlev, std::vector<int32_t> &levoff, int32_t &R, int32_t &maxlev) {
+    catrow.resize(vars.size());
+    nlev.resize(vars.size());
+    levoff.resize(vars.size());
+    R = 0;
+    maxlev = 0;
+    for (size_t i = 0; i < vars.size(); ++i) {
+        catrow[i] = c.cat_index[vars[i]];
+        nlev[i] = c.nlev[vars[i]];
+        levoff[i] = R;
+        R += nlev[i];
+        maxlev = std::max(maxlev, nlev[i]);
+    }
+}
+
+// upload a host int32 vector into a slice of one workspace slot
+struct DevInts {
+    std::vector<int32_t> all;
+    std::vector<size_t> off;
+    size_t add(const std::vector<int32_t> &v) {
+        off.push_back(all.size());
+        all.insert(all.end(), v.begin(), v.end());
+        return off.size() - 1;
+    }
+};
+
+__global__ void k_gather_block(const double *sstat, const double *sp, const int32_t *sn, int32_t nu,
+                               const int32_t *ia, const int32_t *ib, int32_t na, int32_t nb, double *stat, double *p,
+                               int32_t *n) {
+    const int64_t total = (int64_t)na * nb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / nb), b = (int)(t - (int64_t)a * nb);
+        const int64_t src = (int64_t)ia[a] * nu + ib[b];
+        if (stat) stat[t] = sstat[src];
+        if (p) p[t] = sp[src];
+        if (n) n[t] = sn[src];
+    }
+}
+
+// ------------------------------------------------------------ run pipeline --
+
+napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st) {
+    Cohort &c = ctx->coh;
+    if (c.sorted || c.n_cont == 0) {
+        c.sorted = true;
+        return NAPG_OK;
+    }
+    const int64_t nc = c.n_cont, S = c.S, W = c.W;
+    NAPG_CU(ctx, cudaMalloc(&c.perm, sizeof(int32_t) * nc * S));
+    NAPG_CU(ctx, cudaMalloc(&c.pos, sizeof(int32_t) * nc * S));
+    NAPG_CU(ctx, cudaMalloc(&c.nobs, sizeof(int32_t) * nc));
+    NAPG_CU(ctx, cudaMalloc(&c.tie, sizeof(uint32_t) * nc * W));
+    NAPG_CU(ctx, cudaMalloc(&c.gsw, sizeof(int32_t) * nc * W));
+    NAPG_CU(ctx, cudaMalloc(&c.gew, sizeof(int32_t) * nc * W));
+    std::vector<int32_t> cv;
+    for (int64_t v = 0; v < c.F; ++v)
+        if (c.vtype[v] == 0) cv.push_back((int32_t)v);
+    int32_t *dcv = nullptr;
+    NAPG_CU(ctx, cudaMalloc(&dcv, sizeof(int32_t) * cv.size()));
+    NAPG_CU(ctx, cudaMemcpyAsync(dcv, cv.data(), sizeof(int32_t) * cv.size(), cudaMemcpyHostToDevice, st));
+    const size_t tb = presort_tmp_bytes(S, (int32_t)nc);
+    void *tmp = nullptr;
+    NAPG_CU(ctx, cudaMalloc(&tmp, tb));
+    launch_presort(c.X, c.dtype, S, W, dcv, (int32_t)nc, c.obs, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, tmp, tb, st);
+    NAPG_CU(ctx, cudaGetLastError());
+    NAPG_CU(ctx, cudaStreamSynchronize(st));
+    cudaFree(tmp);
+    cudaFree(dcv);
+    c.sorted = true;
+    return NAPG_OK;
+}
+
+napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a) {
+    Cohort &c = ctx->coh;
+    if (!c.loaded) return fail(ctx, NAPG_E_ARG, "no cohort loaded");
+    bool symmetric = false;
+    NAPG_ST(check_vars(ctx, a, &symmetric));
+    const int t = a.test;
+    const int64_t S = c.S, W = c.W, S_pad = ((S + 31) / 32) * 32;
+    const bool mixed = a.opt.precision == NAPG_MIXED;
+    const int32_t na = a.na, nb = symmetric ? a.na : a.nb;
+    if (na == 0 || nb == 0) return NAPG_OK;
+    napg_status st_ = NAPG_OK;
+
+    // Pearson / chi-squared on A x B: run the symmetric problem on the union of
+    // the two lists and gather the block.
+    if (!symmetric && (t == NAPG_PEARSON || t == NAPG_CHI2)) {
+        std::vector<int32_t> u(a.va, a.va + a.na);
+        u.insert(u.end(), a.vb, a.vb + a.nb);
+        std::vector<int32_t> uniq = u;
+        std::sort(uniq.begin(), uniq.end());
+        uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+        const int32_t nu = (int32_t)uniq.size();
+        std::vector<int32_t> ia(a.na), ib(a.nb);
+        for (int i = 0; i < a.na; ++i) ia[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), a.va[i]) - uniq.begin());
+        for (int i = 0; i < a.nb; ++i) ib[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), a.vb[i]) - uniq.begin());
+        double *ts = WS(kTmpE, double, (int64_t)nu * nu);
+        double *tp = WS(kTmpF, double, (int64_t)nu * nu);
+        int32_t *tn = WS(kTmpG, int32_t, (int64_t)nu * nu + 2 * (nu + a.na + a.nb));
+        if (st_) return st_;
+        RunArgs b = a;
+        b.va = uniq.data();
+        b.na = nu;
+        b.vb = nullptr;
+        b.nb = 0;
+        b.stat = ts;
+        b.pval = tp;
+        b.n = tn;
+        NAPG_ST(run_on_stream(ctx, ws, st, b));
+        int32_t *dia = tn + (int64_t)nu * nu, *dib = dia + a.na;
+        NAPG_CU(ctx, cudaMemcpyAsync(dia, ia.data(), sizeof(int32_t) * a.na, cudaMemcpyHostToDevice, st));
+        NAPG_CU(ctx, cudaMemcpyAsync(dib, ib.data(), sizeof(int32_t) * a.nb, cudaMemcpyHostToDevice, st));
+        const int64_t tot = (int64_t)a.na * a.nb;
+        k_gather_block<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, st>>>(
+            ts, tp, tn, nu, dia, dib, a.na, a.nb, a.stat, a.pval, a.n);
+        NAPG_CU(ctx, cudaGetLastError());
+        NAPG_CU(ctx, cudaStreamSynchronize(st));   // host vectors ia/ib and uniq go out of scope
+        return NAPG_OK;
+    }
+
+    // context bits
+    uint32_t *ctxw = WS(kCtxBits, uint32_t, W);
+    const uint8_t *mask_dev = nullptr;
+    if (a.mask) {
+        if (a.mask_on_device) {
+            mask_dev = a.mask;
+        } else {
+            uint8_t *m = WS(kMask, uint8_t, S);
+            if (st_) return st_;
+            NAPG_CU(ctx, cudaMemcpyAsync(m, a.mask, S, cudaMemcpyHostToDevice, st));
+            mask_dev = m;
+        }
+    }
+    if (st_) return st_;
+    launch_ctx_bits(mask_dev, S, W, ctxw, st);
+
+    // variable lists on the device: [va | vb | crow_a | crow_b | catrow | nlev | levoff]
+    std::vector<int32_t> va(a.va, a.va + a.na), vb;
+    if (!symmetric) vb.assign(a.vb, a.vb + a.nb);
+    else vb = va;
+    std::vector<int32_t> crow_a(na), crow_b(nb);
+    for (int i = 0; i < na; ++i) crow_a[i] = c.cont_index[va[i]];
+    for (int i = 0; i < nb; ++i) crow_b[i] = c.cont_index[vb[i]];
+    std::vector<int32_t> catrow, nlev, levoff;
+    int32_t R = 0, maxlev = 0;
+    if (t != NAPG_PEARSON && t != NAPG_SPEARMAN) level_lists(c, va, catrow, nlev, levoff, R, maxlev);
+    DevInts di;
+    const size_t i_va = di.add(va), i_vb = di.add(vb), i_ca = di.add(crow_a), i_cb = di.add(crow_b);
+    const size_t i_cat = di.add(catrow), i_nl = di.add(nlev), i_lo = di.add(levoff);
+    int32_t *dints = WS(kVarsDev, int32_t, di.all.size() + 1);
+    if (st_) return st_;
+    NAPG_CU(ctx, cudaMemcpyAsync(dints, di.all.data(), sizeof(int32_t) * di.all.size(), cudaMemcpyHostToDevice, st));
+    const int32_t *d_va = dints + di.off[i_va], *d_vb = dints + di.off[i_vb];
+    const int32_t *d_ca = dints + di.off[i_ca], *d_cb = dints + di.off[i_cb];
+    const int32_t *d_cat = dints + di.off[i_cat], *d_nl = dints + di.off[i_nl], *d_lo = dints + di.off[i_lo];
+
+    // effective observed bits (observed AND in context)
+    uint32_t *obsA = WS(kObsA, uint32_t, (int64_t)na * W);
+    uint32_t *obsB = symmetric ? obsA : WS(kObsB, uint32_t, (int64_t)nb * W);
+    if (st_) return st_;
+    launch_gather_obs(c.obs, d_va, na, ctxw, W, obsA, st);
+    if (!symmetric) launch_gather_obs(c.obs, d_vb, nb, ctxw, W, obsB, st);
+
+    int32_t *counter = WS(kCounter, int32_t, 4);
+    if (st_) return st_;
+    NAPG_CU(ctx, cudaMemsetAsync(counter, 0, sizeof(int32_t) * 4, st));
+
+    // level bitmasks and in-context level counts of the categorical variables
+    uint32_t *levbits = nullptr;
+    int32_t *levcnt = nullptr;
+    if (R > 0) {
+        levbits = WS(kLevBits, uint32_t, (int64_t)R * W);
+        levcnt = WS(kLevCnt, int32_t, R);
+        if (st_) return st_;
+        NAPG_CU(ctx, cudaMemsetAsync(levcnt, 0, sizeof(int32_t) * R, st));
+        launch_level_bits(c.lab, S, W, d_cat, d_lo, d_nl, na, obsA, levbits, levcnt, st);
+    }
+
+    RescueArgs rsc{c.X, c.dtype, S, W, ctxw, c.obs, c.lab, d_cat, d_va, symmetric ? nullptr : d_vb, na, nb, t,
+                   a.opt.welch, d_nl, levcnt, d_lo};
+
+    if (t == NAPG_PEARSON) {
+        const int64_t nn2 = (int64_t)na * na;
+        double *Sxy = WS(kMomA, double, nn2), *Sx = WS(kMomB, double, nn2), *Sxx = WS(kMomC, double, nn2);
+        int32_t *nn = WS(kIntA, int32_t, nn2);
+        int32_t *flags = WS(kFlagList, int32_t, nn2 / 2 + na + 1);
+        double *shift = WS(kShiftA, double, na);
+        if (st_) return st_;
+        if (mixed) {
+            NAPG_ST(mixed_pearson(ctx, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift));
+        } else {
+            double *xs = WS(kXsA, double, (int64_t)na * S_pad);
+            if (st_) return st_;
+            launch_shift_values(c.X, c.dtype, S, S_pad, d_va, na, obsA, W, shift, xs, st);
+            launch_pearson_fp64(xs, S_pad, obsA, W, na, Sxy, Sx, Sxx, nn, st);
+        }
+        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? 1e-4 : 1e-9};
+        launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st);
+        launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, st);
+    } else if (t == NAPG_ANOVA || t == NAPG_TTEST) {
+        const int64_t rb = (int64_t)R * nb;
+        int32_t *gn = WS(kIntA, int32_t, rb);
+        double *g1 = WS(kMomA, double, rb), *g2 = WS(kMomB, double, rb);
+        int32_t *flags = WS(kFlagList, int32_t, (int64_t)na * nb + 1);
+        double *shift = WS(kShiftB, double, nb);
+        if (st_) return st_;
+        if (mixed) {
+            NAPG_ST(mixed_groupsum(ctx, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift));
+        } else {
+            double *xs = WS(kXsB, double, (int64_t)nb * S_pad);
+            if (st_) return st_;
+            launch_shift_values(c.X, c.dtype, S, S_pad, d_vb, nb, obsB, W, shift, xs, st);
+            launch_groupsum_fp64(c.lab, S, d_cat, na, d_lo, d_nl, xs, S_pad, obsB, W, nb, gn, g1, g2, maxlev, st);
+        }
+        GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? 1e-4 : 1e-9};
+        launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st);
+        launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, st);
+    } else if (t == NAPG_CHI2) {
+        int32_t *T = WS(kIntA, int32_t, (int64_t)R * R);
+        if (st_) return st_;
+        if (mixed) NAPG_ST(mixed_contingency(ctx, ws, st, levbits, R, T));
+        else launch_contingency(levbits, W, R, T, st);
+        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2};
+        launch_finalize_chi2(f, a.stat, a.pval, a.n, st);
+    } else if (t == NAPG_SPEARMAN) {
+        NAPG_ST(ensure_presort(ctx, st));
+        int64_t *q = WS(kMomA, int64_t, (int64_t)na * nb * 4);
+        if (st_) return st_;
+        RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
+        launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st);
+        SpearmanFin f{q, na, nb, symmetric ? 1 : 0};
+        launch_finalize_spearman(f, a.stat, a.pval, a.n, st);
+    } else {  // MWU / KRUSKAL
+        NAPG_ST(ensure_presort(ctx, st));
+        const int64_t rb = (int64_t)R * nb;
+        int64_t *rsum = WS(kMomA, int64_t, rb);
+        int32_t *rcnt = WS(kIntA, int32_t, rb);
+        int64_t *tie = WS(kMomB, int64_t, (int64_t)na * nb);
+        int32_t *flags = WS(kFlagList, int32_t, (int64_t)na * nb + 1);
+        if (st_) return st_;
+        RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
+        launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st);
+        RankGroupFin f{rsum, rcnt, tie, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.mwu_mode, a.opt.mwu_continuity};
+        launch_finalize_rankgroups(f, a.stat, a.pval, a.n, flags, counter, st);
+        if (t == NAPG_MWU && a.pval) {
+            const size_t sb = mwu_exact_scratch_bytes(S);
+            void *scratch = ws_get(ctx, ws, Workspace::kTmpA, sb, &st_);
+            if (st_) return st_;
+            if (!a.stat) return fail(ctx, NAPG_E_ARG, "exact Mann-Whitney p needs the stat buffer");
+            launch_mwu_exact(a.stat, rcnt, d_lo, R, nb, flags, counter, (int32_t)((int64_t)na * nb + 1), a.pval,
+                             scratch, sb, st);
+        }
+    }
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
+}  // namespace napg
+
+using namespace napg;
+
+// ================================================================ C ABI ==
+
+extern "C" {
+
+void napg_default_options(napg_options *o) {
+    if (!o) return;
+    o->precision = NAPG_FP64_PLAIN;
+    o->welch = 1;
+    o->yates_2x2 = 0;
+    o->mwu_mode = 0;
+    o->mwu_continuity = 1;
+    o->debug_checks = 0;
+}
+
+const char *napg_version(void) { return "napg 0.1 (sm_103a)"; }
+
+napg_status napg_create(napg_ctx **out, int device, void *cuda_stream) {
+    if (!out) return NAPG_E_ARG;
+    *out = nullptr;
+    napg_ctx *ctx = new (std::nothrow) napg_ctx();
+    if (!ctx) return NAPG_E_OOM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return NAPG_E_CUDA;
+    }
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return NAPG_E_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->dev_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->host_err, sizeof(uint32_t)) != cudaSuccess) {
+        if (ctx->dev_err) cudaFree(ctx->dev_err);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return NAPG_E_OOM;
+    }
+    *out = ctx;
+    return NAPG_OK;
+}
+
+void napg_destroy(napg_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->serve) napg_serve_stop(ctx);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_cohort(ctx->coh);
+    free_ws(ctx->ws);
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
+    if (ctx->host_err) cudaFreeHost(ctx->host_err);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *napg_last_error(const napg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+napg_status napg_sync(napg_ctx *ctx) {
+    if (!ctx) return NAPG_E_ARG;
+    NAPG_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return NAPG_OK;
+}
+
+napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_t n_vars, int64_t n_samples,
+                             int32_t samples_major, double missing, const uint8_t *var_type, const int32_t *n_levels) {
+    if (!ctx) return NAPG_E_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    if (!X || !var_type || !n_levels || n_vars <= 0 || n_samples <= 0 || (dtype != NAPG_F32 && dtype != NAPG_F64))
+        return fail(ctx, NAPG_E_ARG, "bad cohort arguments");
+    if (n_samples >= kMaxSamples) return fail(ctx, NAPG_E_UNSUPPORTED, "n_samples must be below 2^24");
+    if (n_vars > INT32_MAX / 2) return fail(ctx, NAPG_E_UNSUPPORTED, "too many variables");
+    for (int64_t v = 0; v < n_vars; ++v) {
+        if (var_type[v] > 1) return fail(ctx, NAPG_E_ARG, "var_type must be 0 or 1");
+        if (var_type[v] == 1 && (n_levels[v] < 1 || n_levels[v] > kMaxLevels))
+            return fail(ctx, n_levels[v] > kMaxLevels ? NAPG_E_UNSUPPORTED : NAPG_E_ARG, "bad level count");
+    }
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    NAPG_CU(ctx, cudaStreamSynchronize(st));
+    free_cohort(ctx->coh);
+    Cohort &c = ctx->coh;
+    c.F = n_vars;
+    c.S = n_samples;
+    c.W = (n_samples + 31) / 32;
+    c.dtype = dtype;
+    c.missing = missing;
+    c.vtype.assign(var_type, var_type + n_vars);
+    c.nlev.assign(n_vars, 0);
+    c.cat_index.assign(n_vars, -1);
+    c.cont_index.assign(n_vars, -1);
+    for (int64_t v = 0; v < n_vars; ++v) {
+        if (var_type[v] == 1) {
+            c.nlev[v] = n_levels[v];
+            c.cat_index[v] = (int32_t)c.n_cat++;
+        } else {
+            c.cont_index[v] = (int32_t)c.n_cont++;
+        }
+    }
+    const size_t esz = dtype == NAPG_F32 ? 4 : 8;
+    const size_t xbytes = esz * (size_t)n_vars * (size_t)n_samples;
+    NAPG_CU(ctx, cudaMalloc(&c.X, xbytes));
+    const bool on_dev = is_device_ptr(X);
+    if (!samples_major) {
+        NAPG_CU(ctx, cudaMemcpyAsync(c.X, X, xbytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+        void *tmp = nullptr;
+        NAPG_CU(ctx, cudaMalloc(&tmp, xbytes));
+        NAPG_CU(ctx, cudaMemcpyAsync(tmp, X, xbytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        launch_transpose(tmp, c.X, dtype, n_samples, n_vars, st);
+        NAPG_CU(ctx, cudaGetLastError());
+        NAPG_CU(ctx, cudaStreamSynchronize(st));
+        cudaFree(tmp);
+    }
+    NAPG_CU(ctx, cudaMalloc(&c.obs, sizeof(uint32_t) * (size_t)n_vars * c.W));
+    NAPG_CU(ctx, cudaMalloc(&c.lab, std::max<size_t>(1, (size_t)c.n_cat * (size_t)n_samples)));
+    // per-variable tables for the validation kernel
+    std::vector<int32_t> tab(2 * n_vars);
+    for (int64_t v = 0; v < n_vars; ++v) { tab[v] = c.nlev[v]; tab[n_vars + v] = c.cat_index[v]; }
+    int32_t *dtab = nullptr;
+    uint8_t *dvt = nullptr;
+    NAPG_CU(ctx, cudaMalloc(&dtab, sizeof(int32_t) * tab.size()));
+    NAPG_CU(ctx, cudaMalloc(&dvt, (size_t)n_vars));
+    NAPG_CU(ctx, cudaMemcpyAsync(dtab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, st));
+    NAPG_CU(ctx, cudaMemcpyAsync(dvt, var_type, (size_t)n_vars, cudaMemcpyHostToDevice, st));
+    NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
+    launch_validate_obs(c.X, dtype, n_vars, n_samples, c.W, missing, dvt, dtab, dtab + n_vars, c.obs, c.lab,
+                        ctx->dev_err, st);
+    NAPG_CU(ctx, cudaGetLastError());
+    NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    NAPG_CU(ctx, cudaStreamSynchronize(st));
+    cudaFree(dtab);
+    cudaFree(dvt);
+    const uint32_t e = *ctx->host_err;
+    if (e & kErrNonfinite) {
+        free_cohort(ctx->coh);
+        return fail(ctx, NAPG_E_NONFINITE, "a non-missing value is not finite");
+    }
+    if (e & kErrLabel) {
+        free_cohort(ctx->coh);
+        return fail(ctx, NAPG_E_LABEL, "a categorical value is not an integer in [0, c)");
+    }
+    c.loaded = true;
+    return NAPG_OK;
+}
+
+// Outputs: device pointers are written in place; host ones through workspace
+// buffers copied back before returning.
+static napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape) {
+    const int64_t cnt = (int64_t)a.na * (symmetric_shape ? a.na : a.nb);
+    double *hs = a.stat, *hp = a.pval;
+    int32_t *hn = a.n;
+    const bool ds = !hs || is_device_ptr(hs), dp = !hp || is_device_ptr(hp), dn = !hn || is_device_ptr(hn);
+    napg_status st_ = NAPG_OK;
+    if (!ds) a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
+    if (!dp) a.pval = (double *)ws_get(ctx, ws, Workspace::kOutP, sizeof(double) * cnt, &st_);
+    if (!dn) a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_);
+    if (st_) return st_;
+    // exact Mann-Whitney p reads the statistic back: give it a buffer if none
+    if (a.test == NAPG_MWU && a.pval && !a.stat) {
+        a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
+        if (st_) return st_;
+        hs = nullptr;
+    }
+    NAPG_ST(run_on_stream(ctx, ws, st, a));
+    if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!ds || !dp || !dn) NAPG_CU(ctx, cudaStreamSynchronize(st));
+    return NAPG_OK;
+}
+
+napg_status napg_run(napg_ctx *ctx, int32_t test, const napg_options *opt, const uint8_t *sample_mask,
+                     const int32_t *vars_a, int32_t n_a, const int32_t *vars_b, int32_t n_b, double *stat,
+                     double *pval, int32_t *n) {
+    if (!ctx) return NAPG_E_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    RunArgs a{};
+    a.test = test;
+    if (opt) a.opt = *opt;
+    else napg_default_options(&a.opt);
+    a.mask = sample_mask;
+    a.mask_on_device = is_device_ptr(sample_mask);
+    a.va = vars_a;
+    a.na = n_a;
+    a.vb = vars_b;
+    a.nb = vars_b ? n_b : n_a;
+    a.stat = stat;
+    a.pval = pval;
+    a.n = n;
+    return run_with_outputs(ctx, ctx->ws, ctx->stream, a, vars_b == nullptr);
+}
+
+napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt, int32_t n_ctx,
+                           const uint8_t *const *sample_masks, const int32_t *vars_a, int32_t n_a,
+                           const int32_t *vars_b, int32_t n_b, double *const *stat, double *const *pval,
+                           int32_t *const *n) {
+    if (!ctx || n_ctx < 0 || (n_ctx > 0 && !sample_masks)) return NAPG_E_ARG;
+    for (int32_t k = 0; k < n_ctx; ++k) {
+        napg_status s = napg_run(ctx, test, opt, sample_masks[k], vars_a, n_a, vars_b, n_b, stat ? stat[k] : nullptr,
+                                 pval ? pval[k] : nullptr, n ? n[k] : nullptr);
+        if (s != NAPG_OK) return s;
+    }
+    return NAPG_OK;
+}
+
+napg_status napg_debug_integers(napg_ctx *ctx, int32_t test, const uint8_t *sample_mask, int32_t a, int32_t b,
+                                int64_t *out, int64_t cap, int64_t *written) {
+    if (!ctx || !out || !written) return NAPG_E_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    Cohort &c = ctx->coh;
+    if (!c.loaded) return fail(ctx, NAPG_E_ARG, "no cohort loaded");
+    if (a < 0 || a >= c.F || b < 0 || b >= c.F) return fail(ctx, NAPG_E_ARG, "pair index out of range");
+    Workspace &ws = ctx->ws;
+    cudaStream_t st = ctx->stream;
+    RunArgs r{};
+    r.test = test;
+    napg_default_options(&r.opt);
+    r.opt.mwu_mode = 2;
+    r.mask = sample_mask;
+    r.mask_on_device = is_device_ptr(sample_mask);
+    int32_t va = a, vb = b;
+    r.va = &va;
+    r.na = 1;
+    r.vb = &vb;
+    r.nb = 1;
+    napg_status st_ = NAPG_OK;
+    double *ds = (double *)ws_get(ctx, ws, Workspace::kOutStat, 16, &st_);
+    double *dp = (double *)ws_get(ctx, ws, Workspace::kOutP, 16, &st_);
+    int32_t *dn = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, 16, &st_);
+    if (st_) return st_;
+    r.stat = ds;
+    r.pval = dp;
+    r.n = dn;
+    if (test == NAPG_SPEARMAN && a == b) r.vb = nullptr;
+    if (test != NAPG_CHI2) {
+        NAPG_ST(run_on_stream(ctx, ws, st, r));
+        NAPG_CU(ctx, cudaStreamSynchronize(st));
+    }
+    std::vector<int64_t> res;
+    if (test == NAPG_CHI2) {
+        // recompute the pair's table from the level bitmasks of a (and b)
+        std::vector<int32_t> vars = {a};
+        if (b != a) vars.push_back(b);
+        RunArgs s = r;
+        s.va = vars.data();
+        s.na = (int32_t)vars.size();
+        s.vb = nullptr;
+        NAPG_ST(run_on_stream(ctx, ws, st, s));
+        NAPG_CU(ctx, cudaStreamSynchronize(st));
+        const int ca = c.nlev[a], cb = c.nlev[b];
+        const int R = (b != a) ? ca + cb : ca;
+        std::vector<int32_t> T((size_t)R * R);
+        NAPG_CU(ctx, cudaMemcpy(T.data(), ws.ptr[Workspace::kIntA], sizeof(int32_t) * T.size(), cudaMemcpyDeviceToHost));
+        const int ob = (b != a) ? ca : 0;
+        for (int g = 0; g < ca; ++g)
+            for (int h = 0; h < cb; ++h) res.push_back(T[(size_t)g * R + ob + h]);
+    } else if (test == NAPG_SPEARMAN) {
+        int64_t q[4];
+        NAPG_CU(ctx, cudaMemcpy(q, ws.ptr[Workspace::kMomA], sizeof(q), cudaMemcpyDeviceToHost));
+        res.assign(q, q + 4);
+    } else if (test == NAPG_MWU || test == NAPG_KRUSKAL) {
+        const int L = c.nlev[a];
+        std::vector<int64_t> rs(L);
+        std::vector<int32_t> rc(L);
+        int64_t T = 0;
+        NAPG_CU(ctx, cudaMemcpy(rs.data(), ws.ptr[Workspace::kMomA], sizeof(int64_t) * L, cudaMemcpyDeviceToHost));
+        NAPG_CU(ctx, cudaMemcpy(rc.data(), ws.ptr[Workspace::kIntA], sizeof(int32_t) * L, cudaMemcpyDeviceToHost));
+        NAPG_CU(ctx, cudaMemcpy(&T, ws.ptr[Workspace::kMomB], sizeof(int64_t), cudaMemcpyDeviceToHost));
+        int64_t n = 0;
+        for (int g = 0; g < L; ++g) n += rc[g];
+        res.push_back(n);
+        res.push_back(T);
+        for (int g = 0; g < L; ++g) { res.push_back(rc[g]); res.push_back(rs[g]); }
+    } else if (test == NAPG_ANOVA || test == NAPG_TTEST) {
+        const int L = c.nlev[a];
+        std::vector<int32_t> gn(L);
+        NAPG_CU(ctx, cudaMemcpy(gn.data(), ws.ptr[Workspace::kIntA], sizeof(int32_t) * L, cudaMemcpyDeviceToHost));
+        int64_t n = 0;
+        for (int g = 0; g < L; ++g) n += gn[g];
+        res.push_back(n);
+        for (int g = 0; g < L; ++g) res.push_back(gn[g]);
+    } else {
+        int32_t nn = 0;
+        NAPG_CU(ctx, cudaMemcpy(&nn, dn, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        res.push_back(nn);
+    }
+    if ((int64_t)res.size() > cap) return fail(ctx, NAPG_E_ARG, "cap too small");
+    std::copy(res.begin(), res.end(), out);
+    *written = (int64_t)res.size();
+    return NAPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// Internal declarations of the napg library (CUDA, sm_103a). Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/napg.h"
+
+namespace napg {
+
+constexpr int kMaxLevels = NAPG_MAX_LEVELS;
+constexpr uint8_t kMissingLabel = 0xFF;
+constexpr int64_t kMaxSamples = (int64_t)1 << 24;      // counts stay exact in FP32 sums
+constexpr int64_t kMaxRankSamples = 163840;  // per-pair rank state fits shared memory
+
+// Error flags raised by device-side checks (bitwise OR into a device word).
+enum : uint32_t { kErrLabel = 1u, kErrNonfinite = 2u, kErrTimeout = 4u, kErrIndex = 8u };
+
+// Device-resident cohort (Sec. 3.2): one row per variable.
+struct Cohort {
+    int64_t F = 0, S = 0, W = 0;         // variables, samples, 32-bit words per bit row
+    int32_t dtype = NAPG_F64;
+    double missing = 0.0;
+    bool loaded = false;
+    void *X = nullptr;                   // F x S values (input dtype)
+    uint32_t *obs = nullptr;             // F x W observed bits (no context applied)
+    uint8_t *lab = nullptr;              // n_cat x S labels (kMissingLabel = missing)
+    std::vector<uint8_t> vtype;          // host copies
+    std::vector<int32_t> nlev;
+    std::vector<int32_t> cat_index;      // var -> categorical row (or -1)
+    std::vector<int32_t> cont_index;     // var -> continuous row (or -1)
+    int64_t n_cat = 0, n_cont = 0;
+    // presort of every continuous variable (built on first rank test, kept):
+    bool sorted = false;
+    int32_t *perm = nullptr;             // n_cont x S: sample ids in value order (observed only)
+    int32_t *pos = nullptr;              // n_cont x S: position of each sample in that order (-1 if missing)
+    int32_t *nobs = nullptr;             // n_cont observed counts
+    uint32_t *tie = nullptr;             // n_cont x W: bit p set when position p starts a tie group
+    int32_t *gsw = nullptr;              // n_cont x W: start of the group open at word w's first position
+    int32_t *gew = nullptr;              // n_cont x W: first group start after word w (or nobs)
+};
+
+// Grow-only named device buffers; a run asks for capacity and gets a pointer.
+struct Workspace {
+    enum Slot {
+        kCtxBits, kObsA, kObsB, kShiftA, kShiftB, kXsA, kXsB, kVarA, kLevBits, kLevCnt,
+        kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
+        kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
+        kTmpF, kTmpG, kNumSlots
+    };
+    void *ptr[kNumSlots] = {};
+    size_t cap[kNumSlots] = {};
+    size_t total() const {
+        size_t t = 0;
+        for (int i = 0; i < kNumSlots; ++i) t += cap[i];
+        return t;
+    }
+};
+
+struct ServeState;   // serving loop (serve.cpp)
+
+}  // namespace napg
+
+struct napg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sm_count = 0;
+    napg::Cohort coh;
+    napg::Workspace ws;
+    std::string err;
+    uint32_t *dev_err = nullptr;       // device error word for checks
+    uint32_t *host_err = nullptr;      // pinned mirror
+    napg::ServeState *serve = nullptr;
+    std::mutex mu;                     // guards cohort/workspace use from the serving threads
+};
+
+namespace napg {
+
+napg_status fail(napg_ctx *ctx, napg_status code, const std::string &msg);
+napg_status cuda_fail(napg_ctx *ctx, cudaError_t e, const char *what);
+void *ws_get(napg_ctx *ctx, Workspace &ws, int slot, size_t bytes, napg_status *st);
+bool is_device_ptr(const void *p);
+
+// One test over vars_a x vars_b on a given stream and workspace (shared by
+// napg_run, napg_run_batch and the serving slots).
+struct RunArgs {
+    int32_t test;
+    napg_options opt;
+    const uint8_t *mask;      // host or device (mask_on_device tells)
+    bool mask_on_device;
+    const int32_t *va;        // host
+    int32_t na;
+    const int32_t *vb;        // host or NULL
+    int32_t nb;
+    double *stat, *pval;      // device buffers (n_a x n_b) or NULL
+    int32_t *n;
+};
+napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a);
+napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st);
+
+// ---- kernel launchers (defined in the .cu files) ---------------------------
+// prep
+void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int64_t W, double missing,
+                         const uint8_t *vtype_dev, const int32_t *nlev_dev, const int32_t *catrow_dev,
+                         uint32_t *obs, uint8_t *lab, uint32_t *err, cudaStream_t st);
+void launch_transpose(const void *in, void *out, int32_t dtype, int64_t rows, int64_t cols, cudaStream_t st);
+void launch_ctx_bits(const uint8_t *mask, int64_t S, int64_t W, uint32_t *ctxw, cudaStream_t st);
+void launch_gather_obs(const uint32_t *obs, const int32_t *vars_dev, int32_t nv, const uint32_t *ctxw,
+                       int64_t W, uint32_t *out, cudaStream_t st);
+void launch_shift_values(const void *X, int32_t dtype, int64_t S, int64_t S_pad, const int32_t *vars_dev,
+                         int32_t nv, const uint32_t *obsv, int64_t W, double *shift, double *xs,
+                         cudaStream_t st);
+void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *catrow_dev,
+                       const int32_t *levoff_dev, const int32_t *nlev_dev, int32_t nv,
+                       const uint32_t *obsv, uint32_t *levbits, int32_t *levcnt, cudaStream_t st);
+// plain FP64 moments
+void launch_pearson_fp64(const double *xs, int64_t S_pad, const uint32_t *obsv, int64_t W, int32_t nv,
+                         double *Sxy, double *Sx, double *Sxx, int32_t *nn, cudaStream_t st);
+void launch_groupsum_fp64(const uint8_t *lab, int64_t S, const int32_t *catrow_dev, int32_t na,
+                          const int32_t *levoff_dev, const int32_t *nlev_dev, const double *xs,
+                          int64_t S_pad, const uint32_t *obsb, int64_t W, int32_t nb,
+                          int32_t *gn, double *g1, double *g2, int32_t total_rows, cudaStream_t st);
+// contingency tables
+void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, cudaStream_t st);
+// finalize (p-values included)
+struct PearsonFin {
+    const double *Sxy, *Sx, *Sxx; const int32_t *nn; const double *shift; int32_t nv;
+    double rel_tol;   // degenerate-variance threshold relative to the raw sums
+};
+void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout,
+                             int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
+struct GroupFin {
+    const int32_t *gn; const double *g1, *g2; int32_t total_rows;
+    const int32_t *levoff, *nlev, *present; int32_t na, nb; int32_t test; int32_t welch;
+    double rel_tol;
+};
+void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout,
+                            int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
+struct Chi2Fin {
+    const int32_t *T; int32_t R; const int32_t *levoff_a, *nlev_a, *levoff_b, *nlev_b;
+    const int32_t *present; int32_t na, nb; int32_t symmetric; int32_t yates;
+};
+void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
+// exact rescue of pairs whose moments are degenerate (constant columns/groups)
+struct RescueArgs {
+    const void *X; int32_t dtype; int64_t S; int64_t W; const uint32_t *ctxw; const uint32_t *obs;
+    const uint8_t *lab; const int32_t *catrow; const int32_t *va, *vb; int32_t na, nb; int32_t test;
+    int32_t welch; const int32_t *nlev_a; const int32_t *present; const int32_t *levoff;
+};
+void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
+                   double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st);
+// ranks
+void launch_presort(const void *X, int32_t dtype, int64_t S, int64_t W, const int32_t *contvars_dev,
+                    int32_t ncont, const uint32_t *obs, int32_t *perm, int32_t *pos, int32_t *nobs,
+                    uint32_t *tie, int32_t *gsw, int32_t *gew, void *tmp, size_t tmp_bytes, cudaStream_t st);
+size_t presort_tmp_bytes(int64_t S, int32_t ncont);
+struct RankData {
+    const int32_t *perm, *pos, *nobs; const uint32_t *tie; const int32_t *gsw, *gew;
+    int64_t S, W;
+};
+void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b,
+                           const uint32_t *obs_a, const uint32_t *obs_b, int32_t na, int32_t nb,
+                           int32_t symmetric, int64_t *out4, cudaStream_t st);
+void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a,
+                        const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
+                        const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int32_t total_rows,
+                        int64_t *rsum, int32_t *rcnt, int64_t *tie_term, cudaStream_t st);
+struct SpearmanFin { const int64_t *q; int32_t na, nb; int32_t symmetric; };
+void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
+struct RankGroupFin {
+    const int64_t *rsum; const int32_t *rcnt; const int64_t *tie_term; int32_t total_rows;
+    const int32_t *levoff, *nlev, *present; int32_t na, nb; int32_t test; int32_t mwu_mode; int32_t mwu_cc;
+};
+void launch_finalize_rankgroups(const RankGroupFin &f, double *stat, double *pval, int32_t *nout,
+                                int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
+void launch_mwu_exact(const double *stat, const int32_t *rcnt, const int32_t *levoff, int32_t total_rows,
+                      int32_t nb, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
+                      double *pval, void *scratch, size_t scratch_bytes, cudaStream_t st);
+size_t mwu_exact_scratch_bytes(int64_t S);
+void launch_fill_nan(double *p, int64_t count, cudaStream_t st);
+
+// mixed precision (tcgen05) path
+struct MixedPlan;
+napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
+                          const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn,
+                          double *shift_out);
+napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+                           const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn,
+                           double *g1, double *g2, double *shift_out);
+napg_status mixed_contingency(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
+                              int32_t R, int32_t *T);
+
+}  // namespace napg
+
+#define NAPG_CU(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e__ = (call);                                    \
+        if (e__ != cudaSuccess) return napg::cuda_fail((ctx), e__, #call); \
+    } while (0)
+
+#define NAPG_ST(expr)                                                \
+    do {                                                             \
+        napg_status s__ = (expr);                                    \
+        if (s__ != NAPG_OK) return s__;                              \
+    } while (0)

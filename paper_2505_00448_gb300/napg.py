@@ -1,0 +1,229 @@
+"""Python binding of libnapg.so (include/napg.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. PyTorch provides device
+memory and the CUDA stream. Importing this module loads the library and raises
+ImportError when it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libnapg.so")
+
+PEARSON, SPEARMAN, CHI2, ANOVA, TTEST, MWU, KRUSKAL = range(7)
+TESTS = {"pearson": PEARSON, "spearman": SPEARMAN, "chi2": CHI2, "anova": ANOVA, "ttest": TTEST,
+         "mwu": MWU, "kruskal": KRUSKAL}
+FP64_PLAIN, MIXED = 0, 1
+F32, F64 = 0, 1
+STATUS = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_CUDA", 4: "E_LABEL", 5: "E_NONFINITE",
+          6: "E_TIMEOUT", 7: "E_UNSUPPORTED", 8: "E_BUSY"}
+E_ARG, E_OOM, E_CUDA, E_LABEL, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED, E_BUSY = range(1, 9)
+MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
+
+# every symbol include/napg.h declares
+EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync",
+           "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_serve_start",
+           "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version"]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("welch", C.c_int32), ("yates_2x2", C.c_int32),
+                ("mwu_mode", C.c_int32), ("mwu_continuity", C.c_int32), ("debug_checks", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("test", C.c_int32), ("opt", Options), ("sample_mask", C.c_void_p),
+                ("vars_a", C.c_void_p), ("n_a", C.c_int32), ("vars_b", C.c_void_p), ("n_b", C.c_int32),
+                ("stat", C.c_void_p), ("pval", C.c_void_p), ("n", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    L = C.CDLL(LIB_PATH)
+    p, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    L.napg_default_options.argtypes = [p]
+    L.napg_default_options.restype = None
+    L.napg_create.argtypes = [p, C.c_int, p]
+    L.napg_create.restype = C.c_int
+    L.napg_destroy.argtypes = [p]
+    L.napg_destroy.restype = None
+    L.napg_last_error.argtypes = [p]
+    L.napg_last_error.restype = C.c_char_p
+    L.napg_sync.argtypes = [p]
+    L.napg_sync.restype = C.c_int
+    L.napg_load_cohort.argtypes = [p, p, i32, i64, i64, i32, d, p, p]
+    L.napg_load_cohort.restype = C.c_int
+    L.napg_run.argtypes = [p, i32, p, p, p, i32, p, i32, p, p, p]
+    L.napg_run.restype = C.c_int
+    L.napg_run_batch.argtypes = [p, i32, p, i32, p, p, i32, p, i32, p, p, p]
+    L.napg_run_batch.restype = C.c_int
+    L.napg_debug_integers.argtypes = [p, i32, p, i32, i32, p, i64, p]
+    L.napg_debug_integers.restype = C.c_int
+    L.napg_serve_start.argtypes = [p, C.c_size_t, i32]
+    L.napg_serve_start.restype = C.c_int
+    L.napg_serve_submit.argtypes = [p, p, p]
+    L.napg_serve_submit.restype = C.c_int
+    L.napg_serve_poll.argtypes = [p, C.c_uint64, p, p, p]
+    L.napg_serve_poll.restype = C.c_int
+    L.napg_serve_stop.argtypes = [p]
+    L.napg_serve_stop.restype = C.c_int
+    L.napg_version.argtypes = []
+    L.napg_version.restype = C.c_char_p
+    return L
+
+
+lib = _load()
+
+
+class NapgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"napg {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def options(precision="fp64", welch=True, yates=False, mwu_mode="auto", mwu_continuity=True):
+    o = Options()
+    lib.napg_default_options(C.byref(o))
+    o.precision = MIXED if precision in ("mixed", MIXED) else FP64_PLAIN
+    o.welch = 1 if welch else 0
+    o.yates_2x2 = 1 if yates else 0
+    o.mwu_mode = MWU_MODES[mwu_mode] if isinstance(mwu_mode, str) else int(mwu_mode)
+    o.mwu_continuity = 1 if mwu_continuity else 0
+    return o
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (host or device), or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _i32(v):
+    return None if v is None else np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+
+
+class Context:
+    """One library context (device cohort + work memory) on one CUDA stream."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.torch = torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        rc = lib.napg_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
+        if rc:
+            raise NapgError(rc, "napg_create failed")
+        self.h = h
+        self.F = self.S = 0
+        self.vtype = self.nlev = None
+
+    def _check(self, rc):
+        if rc:
+            raise NapgError(rc, lib.napg_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib.napg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        self._check(lib.napg_sync(self.h))
+
+    def load_cohort(self, X, vtype, nlev, missing=math.nan, samples_major=False):
+        """X: (F, S) (or (S, F) with samples_major) float32/float64, numpy or torch (any device)."""
+        torch = self.torch
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X)
+            dt = F32 if X.dtype == np.float32 else F64
+            if X.dtype not in (np.float32, np.float64):
+                X = X.astype(np.float64)
+                dt = F64
+        else:
+            X = X.contiguous()
+            dt = F32 if X.dtype == torch.float32 else F64
+        F, S = (X.shape[1], X.shape[0]) if samples_major else (X.shape[0], X.shape[1])
+        vt = np.ascontiguousarray(vtype, dtype=np.uint8)
+        nl = np.ascontiguousarray(nlev, dtype=np.int32)
+        self._check(lib.napg_load_cohort(self.h, _ptr(X), dt, F, S, 1 if samples_major else 0, float(missing),
+                                         _ptr(vt), _ptr(nl)))
+        self.F, self.S, self.vtype, self.nlev = F, S, vt, nl
+        return self
+
+    def run(self, test, vars_a, vars_b=None, mask=None, out="cuda", **opt):
+        """One test over all pairs vars_a x vars_b (vars_a x vars_a when vars_b is None).
+
+        out="cuda": torch tensors on the device (stream-ordered, synchronised here);
+        out="numpy": host numpy arrays. Returns dict(stat, p, n).
+        """
+        torch = self.torch
+        t = TESTS[test] if isinstance(test, str) else int(test)
+        va, vb = _i32(vars_a), _i32(vars_b)
+        na = len(va)
+        nb = na if vb is None else len(vb)
+        o = options(**opt)
+        if out == "numpy":
+            stat = np.empty((na, nb), np.float64)
+            p = np.empty((na, nb), np.float64)
+            n = np.empty((na, nb), np.int32)
+        else:
+            dev = torch.device("cuda", self.device)
+            stat = torch.empty((na, nb), dtype=torch.float64, device=dev)
+            p = torch.empty((na, nb), dtype=torch.float64, device=dev)
+            n = torch.empty((na, nb), dtype=torch.int32, device=dev)
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(mask, dtype=np.uint8) if isinstance(mask, np.ndarray) else mask
+        self._check(lib.napg_run(self.h, t, C.byref(o), _ptr(m), _ptr(va), na, _ptr(vb), 0 if vb is None else nb,
+                                 _ptr(stat), _ptr(p), _ptr(n)))
+        if out != "numpy":
+            self.sync()
+        return {"stat": stat, "p": p, "n": n}
+
+    def run_batch(self, test, masks, vars_a, vars_b=None, **opt):
+        """One test for several sample contexts (list of uint8 masks); returns a list of dicts (numpy)."""
+        t = TESTS[test] if isinstance(test, str) else int(test)
+        va, vb = _i32(vars_a), _i32(vars_b)
+        na = len(va)
+        nb = na if vb is None else len(vb)
+        o = options(**opt)
+        ms = [np.ascontiguousarray(m, dtype=np.uint8) if isinstance(m, np.ndarray) else m for m in masks]
+        outs = [{"stat": np.empty((na, nb)), "p": np.empty((na, nb)), "n": np.empty((na, nb), np.int32)}
+                for _ in ms]
+        K = len(ms)
+        mp = (C.c_void_p * K)(*[_ptr(m) for m in ms])
+        sp = (C.c_void_p * K)(*[_ptr(r["stat"]) for r in outs])
+        pp = (C.c_void_p * K)(*[_ptr(r["p"]) for r in outs])
+        npp = (C.c_void_p * K)(*[_ptr(r["n"]) for r in outs])
+        self._check(lib.napg_run_batch(self.h, t, C.byref(o), K, mp, _ptr(va), na, _ptr(vb),
+                                       0 if vb is None else nb, sp, pp, npp))
+        return outs
+
+    def debug_integers(self, test, a, b, mask=None):
+        t = TESTS[test] if isinstance(test, str) else int(test)
+        out = np.zeros(4 + 2 * 64 + 64 * 64, np.int64)
+        w = C.c_int64()
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        self._check(lib.napg_debug_integers(self.h, t, _ptr(m), int(a), int(b), _ptr(out), len(out), C.byref(w)))
+        return out[:w.value].copy()
+
+
+def version() -> str:
+    return lib.napg_version().decode()

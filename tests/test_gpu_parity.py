@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element, on seeded synthetic cohorts that span several tiles and a
+ragged tail, with deletion patterns, contexts and the degenerate cases the
+tests define (Sec. 3.5). Counts, tables and rank sums must be bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2505_00448_gb300 import synth
+from tests._parity import compare
+
+pytestmark = pytest.mark.gpu
+NAN = float("nan")
+
+
+@pytest.fixture(scope="module")
+def napg():
+    from paper_2505_00448_gb300 import napg as N
+    return N
+
+
+def ctx_for(N, coh):
+    c = N.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    return c
+
+
+def oracle_run(test, coh, va, vb=None, mask=None, **kw):
+    return O.run(test, coh["X"].astype(np.float64), coh["missing"], coh["vtype"], coh["nlev"], va, vb, ctx=mask, **kw)
+
+
+def with_degenerate_columns(coh, rng):
+    """Append a constant column, an all-missing column, a one-observation column
+    and an exactly linear copy (r = 1) to the continuous block."""
+    X = coh["X"]
+    S = X.shape[1]
+    extra = np.full((4, S), np.nan, X.dtype)
+    extra[0, rng.random(S) < 0.8] = 3.25
+    extra[2, int(rng.integers(0, S))] = 1.0
+    src = X[0].copy()
+    extra[3] = 2.0 * src + 7.0
+    Fc = len(coh["cont"])
+    Xn = np.concatenate([X[:Fc], extra, X[Fc:]])
+    vtype = np.concatenate([coh["vtype"][:Fc], np.zeros(4, np.uint8), coh["vtype"][Fc:]])
+    nlev = np.concatenate([coh["nlev"][:Fc], np.zeros(4, np.int32), coh["nlev"][Fc:]])
+    out = dict(coh, X=Xn, vtype=vtype, nlev=nlev)
+    out["cont"] = np.arange(Fc + 4, dtype=np.int32)
+    out["cat"] = np.arange(Fc + 4, Fc + 4 + len(coh["cat"]), dtype=np.int32)
+    return out
+
+
+# ------------------------------------------------------------------ Pearson --
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_pearson_parity(napg, dtype):
+    rng = np.random.default_rng(1)
+    coh = synth.small_cohort(101, n_cont=66, n_cat=0, S=1000 + 13, miss=0.25, dtype=dtype)
+    coh = with_degenerate_columns(coh, rng)
+    c = ctx_for(napg, coh)
+    va = coh["cont"]
+    g = c.run("pearson", va, out="numpy")
+    compare("pearson", g, oracle_run("pearson", coh, va))
+    # sample context, and a cross block A x B with overlap
+    mask = (rng.random(coh["X"].shape[1]) < 0.6).astype(np.uint8)
+    g = c.run("pearson", va, mask=mask, out="numpy")
+    compare("pearson", g, oracle_run("pearson", coh, va, mask=mask))
+    A, B = va[:30], va[20:]
+    g = c.run("pearson", A, B, out="numpy")
+    compare("pearson", g, oracle_run("pearson", coh, A, B))
+    c.close()
+
+
+def test_pearson_offsets_and_empty_context(napg):
+    coh = synth.small_cohort(102, n_cont=40, n_cat=0, S=700, miss=0.3, offset=1e4)
+    c = ctx_for(napg, coh)
+    va = coh["cont"]
+    compare("pearson", c.run("pearson", va, out="numpy"), oracle_run("pearson", coh, va))
+    empty = np.zeros(700, np.uint8)
+    g = c.run("pearson", va, mask=empty, out="numpy")
+    assert (g["n"] == 0).all() and np.isnan(g["stat"]).all() and np.isnan(g["p"]).all()
+    c.close()
+
+
+def test_config1_full(napg):
+    coh = synth.config1()
+    c = ctx_for(napg, coh)
+    va = coh["cont"]
+    compare("pearson", c.run("pearson", va, out="numpy"), oracle_run("pearson", coh, va))
+    c.close()
+
+
+# ----------------------------------------------------------------- Spearman --
+
+def test_spearman_parity_and_rank_sums(napg):
+    rng = np.random.default_rng(3)
+    coh = synth.small_cohort(103, n_cont=45, n_cat=0, S=900 + 7, miss=0.3, ties=True)
+    coh = with_degenerate_columns(coh, rng)
+    c = ctx_for(napg, coh)
+    va = coh["cont"]
+    compare("spearman", c.run("spearman", va, out="numpy"), oracle_run("spearman", coh, va))
+    mask = (rng.random(coh["X"].shape[1]) < 0.5).astype(np.uint8)
+    compare("spearman", c.run("spearman", va, mask=mask, out="numpy"),
+            oracle_run("spearman", coh, va, mask=mask))
+    A, B = va[:10], va[5:30]
+    compare("spearman", c.run("spearman", A, B, out="numpy"), oracle_run("spearman", coh, A, B))
+    Xd = coh["X"].astype(np.float64)
+    for i, j in [(0, 1), (3, 17), (5, 5), (10, 44), (2, 47)]:
+        a, b = int(va[i]), int(va[j])
+        got = c.debug_integers("spearman", a, b)
+        ref = O.pair_ints("spearman", Xd, NAN, coh["vtype"], coh["nlev"], a, b)
+        assert np.array_equal(got, ref), (i, j, got, ref)
+    c.close()
+
+
+# -------------------------------------------------------------- chi-squared --
+
+@pytest.mark.parametrize("yates", [False, True])
+def test_chi2_parity_and_tables(napg, yates):
+    rng = np.random.default_rng(4)
+    coh = synth.small_cohort(104, n_cont=0, n_cat=45, S=1200 + 5, miss=0.2, lev_lo=2, lev_hi=9, binary_cats=10)
+    # a variable with a level that only occurs where most others are missing
+    c = ctx_for(napg, coh)
+    va = coh["cat"]
+    compare("chi2", c.run("chi2", va, yates=yates, out="numpy"), oracle_run("chi2", coh, va, yates=int(yates)))
+    mask = (rng.random(coh["X"].shape[1]) < 0.4).astype(np.uint8)
+    compare("chi2", c.run("chi2", va, mask=mask, yates=yates, out="numpy"),
+            oracle_run("chi2", coh, va, mask=mask, yates=int(yates)))
+    Xd = coh["X"].astype(np.float64)
+    for i, j in [(0, 1), (3, 17), (12, 12), (40, 44)]:
+        a, b = int(va[i]), int(va[j])
+        got = c.debug_integers("chi2", a, b)
+        ref = O.pair_ints("chi2", Xd, NAN, coh["vtype"], coh["nlev"], a, b)
+        assert np.array_equal(got, ref), (i, j)
+    c.close()
+
+
+def test_chi2_single_and_emptied_levels(napg):
+    S = 64
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 3, S).astype(float)
+    b = rng.integers(0, 2, S).astype(float)
+    b[a == 2] = np.nan                    # level 2 of a emptied by deletion against b
+    one = np.zeros(S)
+    X = np.array([a, b, one])
+    coh = {"X": X, "vtype": np.ones(3, np.uint8), "nlev": np.array([3, 2, 1], np.int32), "missing": NAN,
+           "cat": np.arange(3, dtype=np.int32), "cont": np.zeros(0, np.int32)}
+    c = ctx_for(napg, coh)
+    compare("chi2", c.run("chi2", coh["cat"], out="numpy"), oracle_run("chi2", coh, coh["cat"]))
+    c.close()
+
+
+# --------------------------------------------------------- ANOVA / t-tests --
+
+@pytest.mark.parametrize("welch", [True, False])
+def test_anova_ttest_parity(napg, welch):
+    rng = np.random.default_rng(6)
+    coh = synth.small_cohort(105, n_cont=37, n_cat=20, S=1100 + 3, miss=0.2, lev_lo=2, lev_hi=7, binary_cats=8)
+    coh = with_degenerate_columns(coh, rng)
+    c = ctx_for(napg, coh)
+    cats, conts = coh["cat"], coh["cont"]
+    compare("anova", c.run("anova", cats, conts, out="numpy"), oracle_run("anova", coh, cats, conts))
+    bins = cats[:8]
+    compare("ttest", c.run("ttest", bins, conts, welch=welch, out="numpy"),
+            oracle_run("ttest", coh, bins, conts, welch=int(welch)))
+    mask = (rng.random(coh["X"].shape[1]) < 0.3).astype(np.uint8)
+    compare("anova", c.run("anova", cats, conts, mask=mask, out="numpy"),
+            oracle_run("anova", coh, cats, conts, mask=mask))
+    compare("ttest", c.run("ttest", bins, conts, mask=mask, welch=welch, out="numpy"),
+            oracle_run("ttest", coh, bins, conts, mask=mask, welch=int(welch)))
+    c.close()
+
+
+def test_anova_ttest_constant_groups(napg):
+    lab = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2, 0, 1, 2], float)
+    X = np.array([lab, lab == 1,
+                  [1, 1, 1, 2, 2, 2, 3, 3, 3, 1, 2, 3],
+                  [4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4],
+                  [1, 2, 3, 4, 5, 6, np.nan, np.nan, np.nan, 1, 2, np.nan]], float)
+    X[1] = X[1].astype(float)
+    coh = {"X": X, "vtype": np.array([1, 1, 0, 0, 0], np.uint8), "nlev": np.array([3, 2, 0, 0, 0], np.int32),
+           "missing": NAN}
+    c = ctx_for(napg, coh)
+    compare("anova", c.run("anova", [0], [2, 3, 4], out="numpy"), oracle_run("anova", coh, [0], [2, 3, 4]))
+    for welch in (True, False):
+        compare("ttest", c.run("ttest", [1], [2, 3, 4], welch=welch, out="numpy"),
+                oracle_run("ttest", coh, [1], [2, 3, 4], welch=int(welch)))
+    c.close()
+
+
+# ---------------------------------------------------------- MWU / Kruskal --
+
+def test_mwu_kruskal_parity_and_rank_sums(napg):
+    rng = np.random.default_rng(7)
+    coh = synth.small_cohort(106, n_cont=33, n_cat=14, S=1000 + 9, miss=0.25, ties=True, lev_lo=2, lev_hi=6,
+                             binary_cats=6)
+    c = ctx_for(napg, coh)
+    cats, conts = coh["cat"], coh["cont"]
+    bins = cats[:6]
+    compare("mwu", c.run("mwu", bins, conts, mwu_mode="asymptotic", out="numpy"),
+            oracle_run("mwu", coh, bins, conts, mwu_mode=2))
+    compare("kruskal", c.run("kruskal", cats, conts, out="numpy"), oracle_run("kruskal", coh, cats, conts))
+    mask = (rng.random(coh["X"].shape[1]) < 0.4).astype(np.uint8)
+    compare("kruskal", c.run("kruskal", cats, conts, mask=mask, out="numpy"),
+            oracle_run("kruskal", coh, cats, conts, mask=mask))
+    Xd = coh["X"].astype(np.float64)
+    for a_, j_ in [(0, 0), (3, 17), (10, 32)]:
+        a, j = int(cats[a_]), int(conts[j_])
+        for test in ("kruskal",) + (("mwu",) if a_ < 6 else ()):
+            got = c.debug_integers(test, a, j)
+            ref = O.pair_ints(test, Xd, NAN, coh["vtype"], coh["nlev"], a, j)
+            assert np.array_equal(got, ref), (test, a_, j_, got, ref)
+    c.close()
+
+
+def test_mwu_exact_mode(napg):
+    """Small groups without ties: exact p by the product form vs the oracle's
+    Mann-Whitney recurrence."""
+    rng = np.random.default_rng(8)
+    S = 400
+    rows, vt, nl = [], [], []
+    for k in range(6):
+        lab = np.ones(S)
+        lab[rng.choice(S, size=int(rng.integers(1, 8)), replace=False)] = 0.0
+        rows.append(lab); vt.append(1); nl.append(2)
+    for k in range(5):
+        x = rng.permutation(S).astype(float) + 0.25
+        x[rng.random(S) < 0.3] = np.nan
+        rows.append(x); vt.append(0); nl.append(0)
+    coh = {"X": np.array(rows), "vtype": np.array(vt, np.uint8), "nlev": np.array(nl, np.int32), "missing": NAN}
+    c = ctx_for(napg, coh)
+    A, B = list(range(6)), list(range(6, 11))
+    compare("mwu", c.run("mwu", A, B, mwu_mode="auto", out="numpy"), oracle_run("mwu", coh, A, B, mwu_mode=0))
+    c.close()
+
+
+# -------------------------------------------------------------- errors --
+
+def test_invalid_inputs_are_errors(napg):
+    c = napg.Context(0)
+    X = np.array([[0, 1, 3.0], [1.0, 2.0, 3.0]])
+    with pytest.raises(napg.NapgError) as e:
+        c.load_cohort(X, [1, 0], [3, 0])
+    assert e.value.code == napg.E_LABEL
+    with pytest.raises(napg.NapgError) as e:
+        c.load_cohort(np.array([[0, 1, 2.0], [1.0, np.inf, 3.0]]), [1, 0], [3, 0])
+    assert e.value.code == napg.E_NONFINITE
+    c.load_cohort(np.array([[0, 1, 2.0, 1], [1.0, 5, 3.0, 2]]), [1, 0], [3, 0])
+    with pytest.raises(napg.NapgError) as e:
+        c.run("ttest", [0], [1])                      # 3 levels for a two-group test
+    assert e.value.code == napg.E_ARG
+    with pytest.raises(napg.NapgError) as e:
+        c.run("pearson", [0])                          # categorical in a continuous test
+    assert e.value.code == napg.E_ARG
+    with pytest.raises(napg.NapgError) as e:
+        c.run("anova", [0], [7])
+    assert e.value.code == napg.E_ARG
+    c.close()
+
+
+def test_sentinel_and_samples_major(napg):
+    coh = synth.small_cohort(107, n_cont=20, n_cat=4, S=500, miss=0.2, binary_cats=2)
+    X = coh["X"].copy()
+    X[np.isnan(X)] = -999.0
+    c = napg.Context(0)
+    c.load_cohort(np.ascontiguousarray(X.T), coh["vtype"], coh["nlev"], missing=-999.0, samples_major=True)
+    va = coh["cont"]
+    compare("pearson", c.run("pearson", va, out="numpy"), oracle_run("pearson", coh, va))
+    compare("kruskal", c.run("kruskal", coh["cat"], va, out="numpy"), oracle_run("kruskal", coh, coh["cat"], va))
+    c.close()
