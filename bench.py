@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark: variable-pairs per second of the all-pairs tests with pairwise
+deletion (NApy, arXiv 2505.00448) on one GB300, with the cohort resident in HBM.
+
+Workload (default, "mixed-type cohort"): 4,000 continuous FP32 variables (2,000
+Gaussian with offsets up to 1e4 sigma, 2,000 lognormal) and 1,000 categorical
+ones (2-10 levels) over 50,000 samples, per-column missingness ~ Beta(2,5).
+One step runs every test of the cohort's hot path once: all-pairs Pearson
+(continuous), ANOVA F (categorical x continuous), Welch t (binary categorical x
+continuous) and chi-squared (categorical). value = var-pairs of the step / step
+time. The cohort (1 GB) is larger than L2, so no L2 flush is needed between steps.
+
+--workload ranks runs the rank tests (Spearman, Mann-Whitney, Kruskal-Wallis) on
+the 1,200-variable x 10,000-sample tied cohort instead (for profiling).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--precision mixed|fp64] [--workload mixed|ranks]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_00448_gb300 import synth  # noqa: E402
+
+METRIC = "var-pairs/s per test, mixed-precision vs plain FP64 GPU at |dr|<=1e-6; p99 ms"
+UNIT = "var-pairs/s"
+
+
+# ------------------------------------------------------------------ workload --
+
+def make_workload(name):
+    if name == "ranks":
+        coh = synth.config2()
+        cat = coh["cat"]
+        bins = cat[coh["nlev"][cat] == 2]
+        multi = cat[coh["nlev"][cat] >= 3]
+        tests = [("spearman", coh["cont"], None), ("mwu", bins, coh["cont"]), ("kruskal", multi, coh["cont"])]
+        desc = ("rank cohort: 1,000 continuous (1-decimal ties, 30% MCAR + block losses) + 200 categorical "
+                "(2-8 levels) x 10,000 samples, FP64; Spearman + Mann-Whitney + Kruskal-Wallis")
+    else:
+        coh = synth.config3()
+        cat = coh["cat"]
+        bins = cat[coh["nlev"][cat] == 2]
+        tests = [("pearson", coh["cont"], None), ("anova", cat, coh["cont"]), ("ttest", bins, coh["cont"]),
+                 ("chi2", cat, None)]
+        desc = ("mixed-type cohort: 4,000 continuous FP32 (2,000 Gaussian offsets to 1e4 sigma, 2,000 "
+                "lognormal) + 1,000 categorical (2-10 levels) x 50,000 samples, Beta(2,5) missingness; "
+                "Pearson + ANOVA + Welch t + chi-squared")
+    return coh, tests, desc
+
+
+def pair_count(test, va, vb):
+    if vb is None:
+        n = len(va)
+        return n * (n - 1) // 2
+    return len(va) * len(vb)
+
+
+# ------------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def oracle_sample(coh, tests, budget_s, seed=0):
+    """Time the oracle (as it stands, all host cores) on a bounded random sample
+    of each test's pairs; returns per-test pairs/s and the combined rate."""
+    from oracle import oracle as O
+    O.build()
+    rng = np.random.default_rng(seed)
+    X = coh["X"].astype(np.float64)
+    cores = O.max_threads()
+    per_test = {}
+    # calibrate: a small sample per test, then scale to the budget
+    share = budget_s / len(tests)
+    for test, va, vb in tests:
+        k = 64
+        while True:
+            if vb is None:
+                pa = rng.choice(va, size=k)
+                pb = rng.choice(va, size=k)
+            else:
+                pa = rng.choice(va, size=k)
+                pb = rng.choice(vb, size=k)
+            t0 = time.perf_counter()
+            O.run_pairs(test, X, coh["missing"], coh["vtype"], coh["nlev"], pa, pb, validate=False)
+            dt = time.perf_counter() - t0
+            if dt > share / 4 or k >= 1 << 20:
+                break
+            k = int(k * min(16.0, max(2.0, (share / 4) / max(dt, 1e-3))))
+        per_test[test] = {"pairs": int(k), "seconds": dt, "pairs_per_s": k / dt}
+    total_pairs = sum(pair_count(t, va, vb) for t, va, vb in tests)
+    total_time = sum(pair_count(t, va, vb) / per_test[t]["pairs_per_s"] for t, va, vb in tests)
+    return {"value": total_pairs / total_time, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "; ".join(f"{t}: {v['pairs']} random pairs in {v['seconds']:.2f}s" for t, v in per_test.items()),
+            "per_test": {t: v["pairs_per_s"] for t, v in per_test.items()}}
+
+
+# ---------------------------------------------------------------- roofline --
+
+def kernel_roofline(stage_ms, steps, coh, tests, peaks):
+    """Roofline of the dominant stage: algorithmic work per launch / event time."""
+    if not stage_ms:
+        return None
+    name, ms = max(stage_ms.items(), key=lambda kv: kv[1]["ms"])
+    launches = max(1, ms["launches"] // max(1, steps)) if ms["launches"] else 1
+    per_step_ms = ms["ms"] / steps
+    S = coh["X"].shape[1]
+    bytes_ = flops = None
+    for test, va, vb in tests:
+        n = len(va)
+        if test == "pearson" and name.startswith("pearson_moments"):
+            flops = 12.0 * S * (n * (n + 1) / 2)           # 6 dot products of length S per pair
+        if test in ("anova", "ttest") and name.startswith("groupsum"):
+            flops = (flops or 0.0) + 6.0 * S * len(va) * len(vb)
+        if test == "spearman" and name == "spearman_rank":
+            bytes_ = 16.25 * S * (n * (n + 1) / 2)
+        if test in ("mwu", "kruskal") and name == "rank_groups":
+            bytes_ = (bytes_ or 0.0) + 9.125 * S * len(va) * len(vb)
+        if test == "chi2" and name.startswith("contingency"):
+            R = int(coh["nlev"][va].sum())
+            bytes_ = 2.0 * R * R / 2 * (S / 8)              # two level bitmasks per table cell
+    secs = per_step_ms / 1000.0
+    if name.endswith("_tc"):
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        ach = flops / secs / 1e12
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": "measured bf16 sustained (MEASURED_PEAKS)",
+                "ms_per_step": per_step_ms, "launches_per_step": launches}
+    if flops is not None:
+        peak = 1.25   # FP64 nominal TFLOP/s of GB300 (no measured FP64 peak on this machine)
+        ach = flops / secs / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s",
+                "ms_per_step": per_step_ms, "launches_per_step": launches}
+    if bytes_ is not None:
+        peak = peaks.get("hbm_gbs") or 6800.0
+        ach = bytes_ / secs / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "measured HBM copy (MEASURED_PEAKS)",
+                "ms_per_step": per_step_ms, "launches_per_step": launches}
+    return {"kernel": name, "bound": "unknown", "ms_per_step": per_step_ms}
+
+
+def load_traffic(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        return json.load(open(p)).get(kernel)
+    except Exception:
+        return None
+
+
+# -------------------------------------------------------------------- main --
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "ranks"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        coh, tests, desc = make_workload(args.workload)
+        samples = []
+        for k in range(args.warmup + args.steps):
+            r = oracle_sample(coh, tests, budget_s=max(4.0, 60.0 / (args.warmup + args.steps)), seed=k)
+            if k >= args.warmup:
+                samples.append(r)
+        v = statistics.mean(r["value"] for r in samples)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": desc, "reference": "plain FP64 CPU oracle (oracle/napg_oracle.c)"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
+                                 "sample": samples[0]["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    device = local_rank if world > 1 else 0
+    torch.cuda.set_device(device)
+    from paper_2505_00448_gb300 import napg
+
+    coh, tests, desc = make_workload(args.workload)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    ctx = napg.Context(device)
+    stream = ctx.stream                     # every kernel of the library runs on this stream
+    torch.cuda.set_stream(stream)
+    ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    dev = torch.device("cuda", device)
+    outs = {}
+    for test, va, vb in tests:
+        na = len(va)
+        nb = na if vb is None else len(vb)
+        outs[test] = {"stat": torch.empty((na, nb), dtype=torch.float64, device=dev),
+                      "p": torch.empty((na, nb), dtype=torch.float64, device=dev),
+                      "n": torch.empty((na, nb), dtype=torch.int32, device=dev)}
+    prec = args.precision
+
+    def step(per_test_events=None):
+        for test, va, vb in tests:
+            if per_test_events is not None:
+                per_test_events[test][0].record(stream)
+            ctx.run(test, va, vb, outputs=outs[test], sync=False, precision=prec)
+            if per_test_events is not None:
+                per_test_events[test][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # timed region
+    ev = {t: [] for t, _, _ in tests}
+    launches0 = napg.kernel_launches()
+    ctx.trace(True)
+    ctx.trace_read()
+    clocks = ClockSampler(device)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    step_events = []
+    start.record(stream)
+    for _ in range(args.steps):
+        pe = {t: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for t, _, _ in tests}
+        step(pe)
+        step_events.append(pe)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = start.elapsed_time(end)
+    clk = clocks.stop()
+    launches = napg.kernel_launches() - launches0
+    trace = ctx.trace_read()
+    ctx.trace(False)
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    per_test_ms = {t: [pe[t][0].elapsed_time(pe[t][1]) for pe in step_events] for t, _, _ in tests}
+    pairs_step = sum(pair_count(t, va, vb) for t, va, vb in tests)
+    value = world * pairs_step / (ms_step / 1000.0)
+
+    # e2e through the public API with host buffers: upload + run + download per step
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(coh["X"]).pin_memory()
+        host_out = {t: {"stat": np.empty(o["stat"].shape), "p": np.empty(o["p"].shape),
+                        "n": np.empty(o["n"].shape, np.int32)} for t, o in outs.items()}
+        h2d = Xh.numel() * Xh.element_size()
+        d2h = sum(sum(a.nbytes for a in v.values()) for v in host_out.values())
+        ctx2 = napg.Context(device)
+        e2e_steps = max(1, min(args.steps, 3))
+        times = []
+        for k in range(e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx2.load_cohort(Xh, coh["vtype"], coh["nlev"], coh["missing"])
+            for test, va, vb in tests:
+                ctx2.run(test, va, vb, outputs=host_out[test], out="numpy", precision=prec)
+            dt = time.perf_counter() - t0
+            if k > 0:
+                times.append(dt)
+        ctx2.close()
+        e2e = {"value": world * pairs_step / statistics.mean(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * statistics.mean(times)}
+
+    roof = kernel_roofline(trace.get("stages", {}), args.steps, coh, tests, peaks)
+    if roof and roof.get("kernel"):
+        roof["traffic"] = load_traffic(roof["kernel"])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(coh, tests, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x3-split/f32-acc/f64" if prec == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": desc, "precision": prec, "pairs_per_step": pairs_step,
+                           "l2": "cohort (1.0 GB) larger than L2: no flush between steps",
+                           "per_test_ms": {t: statistics.median(v) for t, v in per_test_ms.items()},
+                           "per_test_pairs_per_s": {t: pair_count(t, va, vb) / (statistics.median(per_test_ms[t]) / 1e3)
+                                                    for t, va, vb in tests},
+                           "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()}},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -62,9 +62,11 @@ typedef enum {
 
 /* Arithmetic of the moment contractions (Pearson, ANOVA, t-test):
  *   NAPG_FP64_PLAIN  every sum in FP64 on the CUDA cores;
- *   NAPG_MIXED       column-shifted values split into BF16 parts, contracted on
- *                    the tensor cores (tcgen05) with FP32 accumulation drained
- *                    into FP64 in short chunks; finalize and p-values in FP64.
+ *   NAPG_MIXED       column-shifted values, scaled by a power of two per
+ *                    variable and split into FP16 hi/lo parts, contracted on the
+ *                    tensor cores (tcgen05) with FP32 accumulation drained into
+ *                    float-float sums in short chunks; finalize and p-values in
+ *                    FP64; ill-conditioned pairs recomputed exactly in FP64.
  * Counts, contingency tables and rank sums are exact integers in both forms. */
 typedef enum { NAPG_FP64_PLAIN = 0, NAPG_MIXED = 1 } napg_precision;
 
@@ -201,6 +203,19 @@ napg_status napg_serve_poll(napg_ctx *ctx, uint64_t ticket, int32_t *done, doubl
 
 /* Drains the queue, waits for running requests and stops the loop. */
 napg_status napg_serve_stop(napg_ctx *ctx);
+
+/* ----------------------------------------------------------------- tracing --
+ * With tracing on, every stage of a run (bitmasks, contraction, finalize, ...)
+ * is bracketed by CUDA events on the stream it runs on. napg_trace_read waits
+ * for the recorded stages, then writes a JSON object
+ *   {"stages": {"<name>": {"launches": L, "ms": T}, ...}, "kernel_launches": K}
+ * (T = summed device time) into buf (NUL-terminated, truncated to cap) and
+ * clears the record. Errors: NAPG_E_ARG, NAPG_E_CUDA. */
+napg_status napg_trace_enable(napg_ctx *ctx, int32_t on);
+napg_status napg_trace_read(napg_ctx *ctx, char *buf, size_t cap);
+
+/* Number of kernels this process has launched through the library so far. */
+uint64_t napg_kernel_launches(void);
 
 /* Library version string. */
 const char *napg_version(void);

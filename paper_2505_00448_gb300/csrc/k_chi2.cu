@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256) k_contingency(const uint32_t *__restrict_
 void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, cudaStream_t st) {
     if (R == 0) return;
     const int nt = (R + kCT - 1) / kCT;
+    count_launch();
     k_contingency<<<nt * (nt + 1) / 2, 256, 0, st>>>(levbits, W, R, T);
 }
 

@@ -35,7 +35,9 @@ __global__ void k_finalize_pearson(PearsonFin f, double *stat, double *pval, int
         double r = dnan(), p = dnan();
         if (n > 1) {
             const double nd = (double)n;
-            const double sx = f.Sx[ij], sy = f.Sx[ji], sxx = f.Sxx[ij], syy = f.Sxx[ji], sxy = f.Sxy[ij];
+            const double sx = f.Sx[ij], sy = f.Sx[ji], sxy = f.Sxy[ij];
+            const double sxx = f.vsq ? f.Sxx[ij] + f.vsq[i] * nd : f.Sxx[ij];
+            const double syy = f.vsq ? f.Sxx[ji] + f.vsq[j] * nd : f.Sxx[ji];
             const double cxx = sxx - sx * sx / nd, cyy = syy - sy * sy / nd, cxy = sxy - sx * sy / nd;
             if (!(cxx > f.rel_tol * sxx) || !(cyy > f.rel_tol * syy)) {
                 const int q = atomicAdd(nflag, 1);
@@ -56,6 +58,7 @@ void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, in
     const int64_t total = (int64_t)f.nv * (f.nv + 1) / 2;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    count_launch();
     k_finalize_pearson<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
 }
 
@@ -85,7 +88,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 for (int g = 0; g < c; ++g) {
                     const int64_t idx = (int64_t)(off + g) * f.nb + j;
                     s1 += f.g1[idx];
-                    raw += f.g2[idx];
+                    raw += f.g2[idx] + (f.vsq ? f.vsq[j] * (double)f.gn[idx] : 0.0);
                 }
                 const double gm = s1 / (double)n;
                 double ssb = 0.0, ssw = 0.0;
@@ -93,8 +96,9 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     if (!f.present[off + g]) continue;
                     const int64_t idx = (int64_t)(off + g) * f.nb + j;
                     const double ng = (double)f.gn[idx], mg = f.g1[idx] / ng;
+                    const double s2 = f.g2[idx] + (f.vsq ? f.vsq[j] * ng : 0.0);
                     ssb += ng * (mg - gm) * (mg - gm);
-                    ssw += f.g2[idx] - f.g1[idx] * mg;
+                    ssw += s2 - f.g1[idx] * mg;
                 }
                 if (!(ssw > f.rel_tol * raw)) {
                     flags[atomicAdd(nflag, 1)] = (int32_t)t;
@@ -109,8 +113,10 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
             const int32_t n0 = f.gn[i0], n1 = f.gn[i1];
             if (n0 >= 2 && n1 >= 2 && n >= 3) {
                 const double m0 = f.g1[i0] / n0, m1 = f.g1[i1] / n1;
-                const double q0 = f.g2[i0] - f.g1[i0] * m0, q1 = f.g2[i1] - f.g1[i1] * m1;
-                if (!(q0 > f.rel_tol * f.g2[i0]) || !(q1 > f.rel_tol * f.g2[i1])) {
+                const double r0 = f.g2[i0] + (f.vsq ? f.vsq[j] * (double)n0 : 0.0);
+                const double r1 = f.g2[i1] + (f.vsq ? f.vsq[j] * (double)n1 : 0.0);
+                const double q0 = r0 - f.g1[i0] * m0, q1 = r1 - f.g1[i1] * m1;
+                if (!(q0 > f.rel_tol * r0) || !(q1 > f.rel_tol * r1)) {
                     flags[atomicAdd(nflag, 1)] = (int32_t)t;
                 } else if (f.welch) {
                     const double e0 = q0 / (double)(n0 - 1) / (double)n0, e1 = q1 / (double)(n1 - 1) / (double)n1;
@@ -135,6 +141,7 @@ void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32
     const int64_t total = (int64_t)f.na * f.nb;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    count_launch();
     k_finalize_groups<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
 }
 
@@ -192,6 +199,7 @@ void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t 
     const int64_t total = (int64_t)f.na * f.nb;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    count_launch();
     k_finalize_chi2<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
 }
 
@@ -226,6 +234,7 @@ void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, 
     const int64_t total = (int64_t)f.na * f.nb;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    count_launch();
     k_finalize_spearman<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
 }
 
@@ -297,6 +306,7 @@ void launch_finalize_rankgroups(const RankGroupFin &f, double *stat, double *pva
     const int64_t total = (int64_t)f.na * f.nb;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    count_launch();
     k_finalize_rankgroups<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
 }
 
@@ -424,6 +434,7 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
 
 void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
                    double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st) {
+    count_launch();
     k_rescue<<<64, 64, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
 }
 

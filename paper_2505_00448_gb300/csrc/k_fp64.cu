@@ -98,6 +98,7 @@ void launch_pearson_fp64(const double *xs, int64_t S_pad, const uint32_t *obsv, 
     if (nv == 0) return;
     const int T = (nv + kPT - 1) / kPT;
     const int tiles = T * (T + 1) / 2;
+    count_launch();
     k_pearson_fp64<<<tiles, 256, 0, st>>>(xs, S_pad, obsv, W, nv, Sxy, Sx, Sxx, nn);
 }
 
@@ -157,18 +158,26 @@ void launch_groupsum_fp64(const uint8_t *lab, int64_t S, const int32_t *catrow_d
     const int64_t pairs = (int64_t)na * nb;
     if (pairs == 0) return;
     const unsigned blocks = (unsigned)((pairs + 7) / 8);
-    if (max_levels <= 4)
+    if (max_levels <= 4) {
+        count_launch();
         k_groupsum_fp64<4><<<blocks, 256, 0, st>>>(lab, S, catrow_dev, na, levoff_dev, nlev_dev, xs, S_pad, obsb,
                                                    W, nb, gn, g1, g2);
-    else if (max_levels <= 10)
+    }
+    else if (max_levels <= 10) {
+        count_launch();
         k_groupsum_fp64<10><<<blocks, 256, 0, st>>>(lab, S, catrow_dev, na, levoff_dev, nlev_dev, xs, S_pad, obsb,
                                                     W, nb, gn, g1, g2);
-    else if (max_levels <= 16)
+    }
+    else if (max_levels <= 16) {
+        count_launch();
         k_groupsum_fp64<16><<<blocks, 256, 0, st>>>(lab, S, catrow_dev, na, levoff_dev, nlev_dev, xs, S_pad, obsb,
                                                     W, nb, gn, g1, g2);
-    else
+    }
+    else {
+        count_launch();
         k_groupsum_fp64<kMaxLevels><<<blocks, 256, 0, st>>>(lab, S, catrow_dev, na, levoff_dev, nlev_dev, xs,
                                                             S_pad, obsb, W, nb, gn, g1, g2);
+    }
 }
 
 }  // namespace napg

@@ -1,18 +1,619 @@
-// Mixed-precision (tcgen05) moment contractions: not built yet in this file.
+// Mixed-precision moment contractions on the 5th-generation tensor cores
+// (tcgen05.mma, kind::f16 with FP32 accumulation in tensor memory), fed by TMA.
+//
+// Operands are "planes": FP16 matrices with one row per variable (or per
+// categorical level) and one column per sample, K-major, rows padded to 128.
+// For a continuous variable with in-context shift c (FP64 mean of its observed
+// values) and v = mean of (x - c)^2:
+//   M  = observed (1/0)                        exact
+//   Xh + Xl = 2^s x~, x~ = (x - c) m         FP16 hi/lo split of the FP64 value
+//   Dh + Dl = 2^t d,  d = ((x - c)^2 - v) m  centred square, FP16 hi/lo
+//   H  = one-hot level rows (1/0)              exact
+// s and t are per-row powers of two that put the row's largest magnitude in
+// [2^14, 2^15), so hi/lo keep 22 significant bits (a bf16 pair keeps only 16,
+// too few when one heavy-tailed term carries a large share of a sum); the
+// epilogue removes them exactly. FP16 x FP16 products are exact in FP32.
+// Sums for Pearson (Sec. 3.5.2):      n = M M^T, Sxy ~ (Xh + Xl)(Xh + Xl)^T (four products),
+//                                     Sx = X~ M^T, Sxx = D M^T + v n
+// Group sums (Sec. 3.5.5, 3.5.7):     n_g = H M^T, S1 = H X~^T, S2 = H D^T + v n_g
+// Contingency tables (Sec. 3.5.4):    T = H H^T
+// 0/1 operands give integer sums that FP32 holds exactly (S < 2^24), so n, n_g
+// and T stay in tensor memory for the whole K loop. The other sums are
+// accumulated in short K-chunks in tensor memory and drained by the epilogue
+// warps into running sums (float-float where the terms may all be positive),
+// which bounds the FP32 accumulation error independently of S.
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
 #include "napg_internal.cuh"
+#include "umma.cuh"
 
 namespace napg {
 
-napg_status mixed_pearson(napg_ctx *ctx, Workspace &, cudaStream_t, const int32_t *, int32_t, const uint32_t *, double *,
-                          double *, double *, int32_t *, double *) {
-    return fail(ctx, NAPG_E_UNSUPPORTED, "NAPG_MIXED is not available in this build");
+using namespace umma;
+
+constexpr int kKB = 64;    // samples per K-block: one 128-byte swizzle row of 16-bit values
+constexpr int kTM = 128;   // rows of an A tile (M of the MMA)
+
+struct Prod {
+    // plane of A, plane of B, accumulator (d >= 0: drained d; -1 - r: resident r),
+    // first writer of that accumulator
+    int8_t a, b, acc, first;
+};
+
+template <int NA, int NB, int NP>
+struct UmmaParams {
+    CUtensorMap mapA[NA];
+    CUtensorMap mapB[NB];
+    Prod prod[NP];
+    int rowsA, rowsB;          // valid rows of A and B
+    int tilesA, tilesB;        // tile counts along A rows and B rows
+    int triangle;              // 1: only tiles with I <= J
+    int nkb;                   // K-blocks
+    int chunk;                 // K-blocks per drain chunk
+    double *out_drain[2];      // drained sums, row-major [rowsA][ld]
+    int64_t ld;
+    int32_t *out_res;          // resident accumulator 0: integer sums, row-major [rowsA][ld]
+    int res_sym;               // also write out_res transposed
+    int res_into[3];           // float resident r: added into drained output res_into[r]
+    const int8_t *expA[2];     // drained output d: per-row scale exponents of A (NULL: 0)
+    const int8_t *expB[2];     // ... and of B; the output is divided by 2^(eA + eB)
+    uint32_t *err;
+};
+
+__device__ __forceinline__ void tile_coords(int t, int tilesB, int triangle, int &I, int &J) {
+    if (!triangle) {
+        I = t / tilesB;
+        J = t - I * tilesB;
+        return;
+    }
+    int i = 0;
+    while (t >= tilesB - i) { t -= tilesB - i; ++i; }
+    I = i;
+    J = i + t;
 }
-napg_status mixed_groupsum(napg_ctx *ctx, Workspace &, cudaStream_t, const uint32_t *, int32_t, const int32_t *, int32_t,
-                           const uint32_t *, int32_t *, double *, double *, double *) {
-    return fail(ctx, NAPG_E_UNSUPPORTED, "NAPG_MIXED is not available in this build");
+
+// Resident accumulator 0 (if NRES > 0) holds exact integer sums; residents 1..
+// hold small FP32 sums added to a drained output at the end.
+template <int N, int NA, int NB, int NP, int NDRAIN, int NRES, bool FF, int STAGES>
+__global__ void __launch_bounds__(320, 1) k_umma(const __grid_constant__ UmmaParams<NA, NB, NP> P) {
+    constexpr int A_BYTES = kTM * kKB * 2;
+    constexpr int B_BYTES = N * kKB * 2;
+    constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
+    constexpr int RESC = NRES * N;             // first column of the chunk buffers
+    constexpr int USED = RESC + 2 * NDRAIN * N;
+    constexpr int TCOLS = USED <= 32 ? 32 : USED <= 64 ? 64 : USED <= 128 ? 128 : USED <= 256 ? 256 : 512;
+    static_assert(USED <= 512, "tensor memory has 512 columns");
+    static_assert(N % 32 == 0 && N >= 32 && N <= 256, "N");
+    constexpr int HC = N / 2;                  // columns per epilogue thread
+    constexpr int ND = NDRAIN > 0 ? NDRAIN : 1;
+    constexpr uint32_t IDESC = idesc_f16_f32(kTM, N);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;     // [2] chunk accumulators ready
+    uint64_t *tempty = tfull + 2;         // [2] chunk accumulators drained
+    uint64_t *mdone = tempty + 2;         // all MMAs of this CTA retired
+    uint32_t *tslot = (uint32_t *)(mdone + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int I, J;
+    tile_coords(blockIdx.x, P.tilesB, P.triangle, I, J);
+    const int nchunks = NDRAIN ? (P.nkb + P.chunk - 1) / P.chunk : 1;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
+        mbar_init(mdone, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, TCOLS);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            for (int p = 0; p < NA; ++p) prefetch_tmap(&P.mapA[p]);
+            for (int p = 0; p < NB; ++p) prefetch_tmap(&P.mapB[p]);
+            int issued = 0;
+            for (int kb = 0; kb < P.nkb; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                uint8_t *st = smem + s * STAGE_BYTES;
+                for (int p = 0; p < NA; ++p) tma_load_2d(st + p * A_BYTES, &P.mapA[p], &full[s], kb * kKB, I * kTM);
+                for (int p = 0; p < NB; ++p)
+                    tma_load_2d(st + NA * A_BYTES + p * B_BYTES, &P.mapB[p], &full[s], kb * kKB, J * N);
+                issued = kb + 1;
+            }
+            // our own copies must have landed before the CTA tears down
+            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int kb = 0;
+            bool ok = true;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                const int b = c & 1;
+                if (NDRAIN && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
+                fence_after_sync();
+                const int kb_end = NDRAIN ? min(P.nkb, (c + 1) * P.chunk) : P.nkb;
+                const int kb_chunk0 = kb;
+                for (; kb < kb_end; ++kb) {
+                    const int s = kb % STAGES;
+                    if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+                    fence_after_sync();
+                    const uint32_t sbase = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+                    for (int k = 0; k < kKB / 16; ++k) {
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            const Prod pr = P.prod[q];
+                            const uint64_t ad = sdesc_sw128(sbase + pr.a * A_BYTES + k * 32);
+                            const uint64_t bd = sdesc_sw128(sbase + NA * A_BYTES + pr.b * B_BYTES + k * 32);
+                            uint32_t col, acc;
+                            if (pr.acc < 0) {
+                                col = (uint32_t)(-1 - pr.acc) * N;
+                                acc = (kb == 0 && k == 0 && pr.first) ? 0u : 1u;
+                            } else {
+                                col = RESC + (b * ND + pr.acc) * N;
+                                acc = (kb == kb_chunk0 && k == 0 && pr.first) ? 0u : 1u;
+                            }
+                            mma_f16(tbase + col, ad, bd, IDESC, acc);
+                        }
+                    }
+                    mma_commit(&empty[s]);      // frees the stage once these MMAs are done
+                }
+                if (!ok) break;
+                mma_commit(&tfull[b]);          // chunk (and, last, the resident sums) ready
+            }
+            mma_commit(mdone);
+            mbar_wait(mdone, 0, P.err);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int ew = warp - 2;               // 0..7
+        const int q = warp & 3;                // TMEM lane quadrant this warp may access
+        const int half = ew >> 2;              // which half of the columns
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        float hi[ND][HC];
+        float lo[ND][FF ? HC : 1];
+#pragma unroll
+        for (int d = 0; d < ND; ++d)
+#pragma unroll
+            for (int k = 0; k < HC; ++k) {
+                hi[d][k] = 0.f;
+                if (FF) lo[d][FF ? k : 0] = 0.f;
+            }
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(&tfull[b], (c >> 1) & 1, P.err)) { ok = false; break; }
+            fence_after_sync();
+            if (NDRAIN) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+#pragma unroll
+                    for (int g = 0; g < HC / 16; ++g) {
+                        uint32_t r[16];
+                        tmem_ld16(tbase + lane_addr + RESC + (b * ND + d) * N + half * HC + g * 16, r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            const float v = __uint_as_float(r[k]);
+                            if (FF) {
+                                // TwoSum: exact error of hi + v kept in lo
+                                const float s = hi[d][g * 16 + k] + v;
+                                const float bb = s - hi[d][g * 16 + k];
+                                const float e = (hi[d][g * 16 + k] - (s - bb)) + (v - bb);
+                                hi[d][g * 16 + k] = s;
+                                lo[d][FF ? g * 16 + k : 0] += e;
+                            } else {
+                                hi[d][g * 16 + k] += v;
+                            }
+                        }
+                    }
+                }
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
+            }
+        }
+        if (ok) {
+            const int gi = I * kTM + row;
+            const bool row_ok = gi < P.rowsA;
+            // small resident sums join their drained outputs (resident 0 does too
+            // when there is no integer output)
+#pragma unroll
+            for (int rr = 0; rr < NRES; ++rr) {
+                if (rr == 0 && P.out_res != nullptr) continue;
+                const int d = P.res_into[rr];
+#pragma unroll
+                for (int g = 0; g < HC / 16; ++g) {
+                    uint32_t r[16];
+                    tmem_ld16(tbase + lane_addr + rr * N + half * HC + g * 16, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+#pragma unroll
+                        for (int dd = 0; dd < ND; ++dd)
+                            if (dd == d) {
+                                if (FF) lo[dd][FF ? g * 16 + k : 0] += __uint_as_float(r[k]);
+                                else hi[dd][g * 16 + k] += __uint_as_float(r[k]);
+                            }
+                    }
+                }
+            }
+            if (NRES > 0 && P.out_res != nullptr) {
+#pragma unroll
+                for (int g = 0; g < HC / 16; ++g) {
+                    uint32_t r[16];
+                    tmem_ld16(tbase + lane_addr + half * HC + g * 16, r);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int col = J * N + half * HC + g * 16 + k;
+                        if (row_ok && col < P.rowsB) {
+                            const int32_t v = (int32_t)__uint_as_float(r[k]);
+                            P.out_res[(int64_t)gi * P.ld + col] = v;
+                            if (P.res_sym) P.out_res[(int64_t)col * P.ld + gi] = v;
+                        }
+                    }
+                }
+            }
+            if (NDRAIN) {
+#pragma unroll
+                for (int d = 0; d < ND; ++d) {
+#pragma unroll
+                    for (int k = 0; k < HC; ++k) {
+                        const int col = J * N + half * HC + k;
+                        if (row_ok && col < P.rowsB) {
+                            double v = (double)hi[d][k];
+                            if (FF) v += (double)lo[d][FF ? k : 0];
+                            const int e = (P.expA[d] ? (int)P.expA[d][gi] : 0) + (P.expB[d] ? (int)P.expB[d][col] : 0);
+                            P.out_drain[d][(int64_t)gi * P.ld + col] = ldexp(v, -e);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(tbase, TCOLS);
 }
-napg_status mixed_contingency(napg_ctx *ctx, Workspace &, cudaStream_t, const uint32_t *, int32_t, int32_t *) {
-    return fail(ctx, NAPG_E_UNSUPPORTED, "NAPG_MIXED is not available in this build");
+
+// ------------------------------------------------------------ plane prep --
+
+// One block per (padded) row: shift c, v = mean (x - c)^2 over the observed
+// samples, the scale exponents s, t, then the FP16 planes M, Xh, Xl, Dh, Dl
+// (zero where unobserved, in the padding columns and in padding rows).
+__device__ __forceinline__ int scale_exp(double maxabs) {
+    if (!(maxabs > 0.0)) return 0;
+    int e;
+    frexp(maxabs, &e);                 // maxabs in [2^(e-1), 2^e)
+    int s = 15 - e;                    // 2^s maxabs in [2^14, 2^15)
+    return s < -120 ? -120 : (s > 120 ? 120 : s);
+}
+
+template <typename T>
+__global__ void k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad, const int32_t *__restrict__ vars,
+                              int32_t nv, const uint32_t *__restrict__ obsv, int64_t W, __half *Pm, __half *Pxh,
+                              __half *Pxl, __half *Pdh, __half *Pdl, double *shift, double *vsq, int8_t *sexp,
+                              int8_t *texp) {
+    const int i = blockIdx.x;
+    const int64_t base = (int64_t)i * S_pad;
+    const __half z = __float2half(0.f);
+    if (i >= nv) {
+        for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
+            Pm[base + s] = z; Pxh[base + s] = z; Pxl[base + s] = z; Pdh[base + s] = z; Pdl[base + s] = z;
+        }
+        return;
+    }
+    const T *x = X + (int64_t)vars[i] * S;
+    const uint32_t *ob = obsv + (int64_t)i * W;
+    __shared__ double red[32];
+    __shared__ int redc[32];
+    __shared__ double bc[4];
+    __shared__ int cnt_s;
+    // block reductions: sum (op 0) or max (op 1)
+    auto block_red = [&](double v, int c, int op, double *out_v, int *out_c) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_down_sync(0xffffffffu, v, o);
+            v = op ? fmax(v, w) : v + w;
+            c += __shfl_down_sync(0xffffffffu, c, o);
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = v; redc[threadIdx.x >> 5] = c; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tv = op ? 0.0 : 0.0;
+            int tc = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tv = op ? fmax(tv, red[w]) : tv + red[w]; tc += redc[w]; }
+            *out_v = tv;
+            if (out_c) *out_c = tc;
+        }
+        __syncthreads();
+    };
+    double s1 = 0.0;
+    int cn = 0;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
+        if ((ob[s >> 5] >> (s & 31)) & 1u) { s1 += (double)x[s]; ++cn; }
+    block_red(s1, cn, 0, &bc[0], &cnt_s);
+    const int cnt = cnt_s;
+    const double c = cnt > 0 ? bc[0] / (double)cnt : 0.0;
+    double s2 = 0.0, mx = 0.0;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
+        if ((ob[s >> 5] >> (s & 31)) & 1u) {
+            const double d = (double)x[s] - c;
+            s2 += d * d;
+            mx = fmax(mx, fabs(d));
+        }
+    block_red(s2, 0, 0, &bc[1], nullptr);
+    block_red(mx, 0, 1, &bc[2], nullptr);
+    const double v = cnt > 0 ? bc[1] / (double)cnt : 0.0;
+    double md = 0.0;
+    for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
+        if ((ob[s >> 5] >> (s & 31)) & 1u) {
+            const double d = (double)x[s] - c;
+            md = fmax(md, fabs(d * d - v));
+        }
+    block_red(md, 0, 1, &bc[3], nullptr);
+    const int es = scale_exp(bc[2]), et = scale_exp(bc[3]);
+    if (threadIdx.x == 0) { shift[i] = c; vsq[i] = v; sexp[i] = (int8_t)es; texp[i] = (int8_t)et; }
+    const __half one = __float2half(1.f);
+    for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
+        const bool o = s < S && ((ob[s >> 5] >> (s & 31)) & 1u);
+        if (!o) {
+            Pm[base + s] = z; Pxh[base + s] = z; Pxl[base + s] = z; Pdh[base + s] = z; Pdl[base + s] = z;
+            continue;
+        }
+        const double xt = (double)x[s] - c;
+        const double xs = ldexp(xt, es);
+        const __half h = __double2half(xs);
+        const __half l = __double2half(xs - (double)__half2float(h));
+        const double ds = ldexp(xt * xt - v, et);
+        const __half dh = __double2half(ds);
+        const __half dl = __double2half(ds - (double)__half2float(dh));
+        Pm[base + s] = one; Pxh[base + s] = h; Pxl[base + s] = l; Pdh[base + s] = dh; Pdl[base + s] = dl;
+    }
+}
+
+// one-hot level rows from the level bitmasks (zero padding rows/columns)
+__global__ void k_planes_onehot(const uint32_t *__restrict__ levbits, int64_t W, int32_t R, int64_t S_pad,
+                                __half *H) {
+    const int r = blockIdx.x;
+    const __half one = __float2half(1.f), z = __float2half(0.f);
+    const int64_t base = (int64_t)r * S_pad;
+    for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
+        const int64_t w = s >> 5;
+        const bool b = r < R && w < W && ((levbits[(int64_t)r * W + w] >> (s & 31)) & 1u);
+        H[base + s] = b ? one : z;
+    }
+}
+
+// ---------------------------------------------------------------- host --
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// FP16 matrix [rows][cols], cols a multiple of 64, box = 64 columns x box_rows rows
+static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kKB, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int N, int NA, int NB, int NP, int NDRAIN, int NRES, bool FF, int STAGES>
+static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int tiles, cudaStream_t st) {
+    constexpr int STAGE_BYTES = NA * kTM * kKB * 2 + NB * N * kKB * 2;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    auto kern = k_umma<N, NA, NB, NP, NDRAIN, NRES, FF, STAGES>;
+    NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // first-writer flags
+    for (int q = 0; q < NP; ++q) {
+        P.prod[q].first = 1;
+        for (int r = 0; r < q; ++r)
+            if (P.prod[r].acc == P.prod[q].acc) P.prod[q].first = 0;
+    }
+    if (tiles == 0) return NAPG_OK;
+    count_launch();
+    kern<<<tiles, 320, smem, st>>>(P);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
+struct ContPlanes {
+    __half *M, *Xh, *Xl, *Dh, *Dl;
+    int8_t *sexp, *texp;        // per-row scale exponents of X~ and D
+    int64_t rows_pad, S_pad;
+};
+
+static napg_status prep_cont_planes(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev,
+                                    int32_t nv, const uint32_t *obsv, int first_slot, double *shift, double *vsq,
+                                    ContPlanes &cp) {
+    Cohort &c = ctx->coh;
+    cp.S_pad = ((c.S + kKB - 1) / kKB) * kKB;
+    cp.rows_pad = ((nv + kTM - 1) / kTM) * kTM;
+    const size_t plane = sizeof(__half) * (size_t)cp.rows_pad * (size_t)cp.S_pad;
+    napg_status st_ = NAPG_OK;
+    __half *pl[5];
+    for (int k = 0; k < 5; ++k) {
+        pl[k] = (__half *)ws_get(ctx, ws, first_slot + k, plane, &st_);
+        if (st_) return st_;
+    }
+    cp.M = pl[0]; cp.Xh = pl[1]; cp.Xl = pl[2]; cp.Dh = pl[3]; cp.Dl = pl[4];
+    cp.sexp = (int8_t *)ws_get(ctx, ws, Workspace::kExp, 2 * (size_t)cp.rows_pad, &st_);
+    if (st_) return st_;
+    cp.texp = cp.sexp + cp.rows_pad;
+    Stage s_(ctx->trace, st, "planes_f16");
+    count_launch();
+    if (c.dtype == NAPG_F32)
+        k_planes_cont<float><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const float *)c.X, c.S, cp.S_pad, vars_dev, nv,
+                                                                    obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl,
+                                                                    shift, vsq, cp.sexp, cp.texp);
+    else
+        k_planes_cont<double><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const double *)c.X, c.S, cp.S_pad, vars_dev, nv,
+                                                                     obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl,
+                                                                     shift, vsq, cp.sexp, cp.texp);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
+static napg_status prep_onehot(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+                               int slot, __half **H, int64_t &rows_pad, int64_t &S_pad) {
+    Cohort &c = ctx->coh;
+    S_pad = ((c.S + kKB - 1) / kKB) * kKB;
+    rows_pad = ((R + kTM - 1) / kTM) * kTM;
+    napg_status st_ = NAPG_OK;
+    *H = (__half *)ws_get(ctx, ws, slot, sizeof(__half) * (size_t)rows_pad * (size_t)S_pad, &st_);
+    if (st_) return st_;
+    Stage s_(ctx->trace, st, "planes_onehot");
+    count_launch();
+    k_planes_onehot<<<(unsigned)rows_pad, 256, 0, st>>>(levbits, c.W, R, S_pad, *H);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
+// chunk lengths (K-blocks of 64 samples between drains)
+constexpr int kChunkFF = 2;     // float-float running sums (terms may share a sign)
+constexpr int kChunkF32 = 8;    // FP32 running sums of centred (zero-mean) terms
+
+napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
+                          const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
+                          double *vsq) {
+    ContPlanes cp;
+    NAPG_ST(prep_cont_planes(ctx, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp));
+    const int nkb = (int)(cp.S_pad / kKB);
+    const int T = (int)(cp.rows_pad / kTM);
+    // P1: triangle tiles, N = 128. n = M M^T (resident, exact). Sxy: the hi*hi
+    // product alone is accumulated in short chunks drained into float-float sums
+    // (the tensor core rounds its FP32 accumulator about once per instruction, so
+    // the error grows with the instructions per chunk; correlated pairs have
+    // same-sign terms); the three small cross products (hi*lo, lo*hi, lo*lo, of
+    // random sign, 2^-8 smaller) stay resident for the whole K loop. Dropping
+    // lo*lo would bias Sxy low by ~2^-16/3 of sum x~^2.
+    {
+        UmmaParams<3, 3, 5> P{};
+        const void *pl[3] = {cp.M, cp.Xh, cp.Xl};
+        for (int k = 0; k < 3; ++k) {
+            if (!make_map(&P.mapA[k], pl[k], cp.rows_pad, cp.S_pad, kTM) ||
+                !make_map(&P.mapB[k], pl[k], cp.rows_pad, cp.S_pad, 128))
+                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        }
+        P.prod[0] = {0, 0, -1, 0};   // M M   -> n (resident 0)
+        P.prod[1] = {1, 1, 0, 0};    // Xh Xh -> Sxy hi (drained 0)
+        P.prod[2] = {1, 2, -2, 0};   // Xh Xl -> Sxy cross (resident 1)
+        P.prod[3] = {2, 1, -2, 0};   // Xl Xh
+        P.prod[4] = {2, 2, -2, 0};   // Xl Xl
+        P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = T; P.triangle = 1;
+        P.nkb = nkb; P.chunk = kChunkFF;
+        P.out_drain[0] = Sxy; P.out_drain[1] = nullptr; P.ld = nv;
+        P.out_res = nn; P.res_sym = 0; P.res_into[1] = 0; P.err = ctx->dev_err;
+        P.expA[0] = cp.sexp; P.expB[0] = cp.sexp;
+        Stage s_(ctx->trace, st, "pearson_moments_tc");
+        NAPG_ST((launch_umma<128, 3, 3, 5, 1, 2, true, 2>(ctx, P, T * (T + 1) / 2, st)));
+    }
+    // P2: all ordered tiles, N = 64. Sx = X~ M^T and D = sum (x~^2 - v) m over the
+    // co-observed samples: hi products drained every kChunkFF K-blocks into
+    // float-float sums, lo products resident (heavy-tailed columns put single huge
+    // terms into a chunk; every later instruction would then cost an ulp of it).
+    {
+        constexpr int N2 = 64;
+        UmmaParams<4, 1, 4> P{};
+        const void *pa[4] = {cp.Xh, cp.Xl, cp.Dh, cp.Dl};
+        for (int k = 0; k < 4; ++k)
+            if (!make_map(&P.mapA[k], pa[k], cp.rows_pad, cp.S_pad, kTM))
+                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        if (!make_map(&P.mapB[0], cp.M, cp.rows_pad, cp.S_pad, N2))
+            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        P.prod[0] = {0, 0, 0, 0};    // Xh M -> Sx hi (drained 0)
+        P.prod[1] = {1, 0, -1, 0};   // Xl M -> Sx lo (resident 0: added to drained 0)
+        P.prod[2] = {2, 0, 1, 0};    // Dh M -> D hi (drained 1)
+        P.prod[3] = {3, 0, -2, 0};   // Dl M -> D lo (resident 1: added to drained 1)
+        const int TJ = (nv + N2 - 1) / N2;
+        P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = TJ; P.triangle = 0;
+        P.nkb = nkb; P.chunk = kChunkFF;
+        P.out_drain[0] = Sx; P.out_drain[1] = Sxx; P.ld = nv;
+        P.out_res = nullptr; P.res_sym = 0; P.res_into[0] = 0; P.res_into[1] = 1; P.err = ctx->dev_err;
+        P.expA[0] = cp.sexp; P.expA[1] = cp.texp;
+        Stage s_(ctx->trace, st, "pearson_moments_tc");
+        NAPG_ST((launch_umma<N2, 4, 1, 4, 2, 2, true, 3>(ctx, P, T * TJ, st)));
+    }
+    return NAPG_OK;
+}
+
+napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+                           const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn, double *g1,
+                           double *g2, double *shift, double *vsq) {
+    ContPlanes cp;
+    NAPG_ST(prep_cont_planes(ctx, ws, st, vars_b_dev, nb, obsb, Workspace::kTmpA, shift, vsq, cp));
+    __half *H = nullptr;
+    int64_t hrows = 0, S_pad = 0;
+    NAPG_ST(prep_onehot(ctx, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+    constexpr int N = 64;
+    UmmaParams<1, 5, 5> P{};
+    if (!make_map(&P.mapA[0], H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+    const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
+    for (int k = 0; k < 5; ++k)
+        if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, N))
+            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+    P.prod[0] = {0, 0, -1, 0};   // H M  -> n_g (resident 0)
+    P.prod[1] = {0, 1, 0, 0};    // H Xh -> S1 hi (drained 0)
+    P.prod[2] = {0, 2, -2, 0};   // H Xl -> S1 lo (resident 1)
+    P.prod[3] = {0, 3, 1, 0};    // H Dh -> S2 - v n_g, hi (drained 1)
+    P.prod[4] = {0, 4, -3, 0};   // H Dl -> lo (resident 2)
+    const int TI = (int)(hrows / kTM), TJ = (int)((nb + N - 1) / N);
+    P.rowsA = R; P.rowsB = nb; P.tilesA = TI; P.tilesB = TJ; P.triangle = 0;
+    P.nkb = (int)(S_pad / kKB); P.chunk = kChunkFF;
+    P.out_drain[0] = g1; P.out_drain[1] = g2; P.ld = nb;
+    P.out_res = gn; P.res_sym = 0; P.res_into[1] = 0; P.res_into[2] = 1; P.err = ctx->dev_err;
+    P.expB[0] = cp.sexp; P.expB[1] = cp.texp;
+    Stage s_(ctx->trace, st, "groupsum_tc");
+    return launch_umma<N, 1, 5, 5, 2, 3, true, 3>(ctx, P, TI * TJ, st);
+}
+
+napg_status mixed_contingency(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+                              int32_t *T) {
+    __half *H = nullptr;
+    int64_t hrows = 0, S_pad = 0;
+    NAPG_ST(prep_onehot(ctx, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+    UmmaParams<1, 1, 1> P{};
+    if (!make_map(&P.mapA[0], H, hrows, S_pad, kTM) || !make_map(&P.mapB[0], H, hrows, S_pad, 128))
+        return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+    P.prod[0] = {0, 0, -1, 0};   // H H -> T
+    const int TT = (int)(hrows / kTM);
+    P.rowsA = R; P.rowsB = R; P.tilesA = TT; P.tilesB = TT; P.triangle = 1;
+    P.nkb = (int)(S_pad / kKB); P.chunk = P.nkb;
+    P.out_drain[0] = nullptr; P.out_drain[1] = nullptr; P.ld = R;
+    P.out_res = T; P.res_sym = 1; P.err = ctx->dev_err;
+    Stage s_(ctx->trace, st, "contingency_tc");
+    return launch_umma<128, 1, 1, 1, 0, 1, false, 4>(ctx, P, TT * (TT + 1) / 2, st);
 }
 
 }  // namespace napg

@@ -52,12 +52,16 @@ void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int
     if (F == 0 || W == 0) return;
     for (int64_t v0 = 0; v0 < F; v0 += 65535) {      // grid.y limit
         dim3 grid((unsigned)((W + 7) / 8), (unsigned)std::min<int64_t>(65535, F - v0));
-        if (dtype == NAPG_F32)
+        if (dtype == NAPG_F32) {
+            count_launch();
             k_validate_obs<float><<<grid, 256, 0, st>>>((const float *)X, F, S, W, missing, vtype_dev, nlev_dev,
                                                          catrow_dev, obs, lab, err, v0);
-        else
+        }
+        else {
+            count_launch();
             k_validate_obs<double><<<grid, 256, 0, st>>>((const double *)X, F, S, W, missing, vtype_dev, nlev_dev,
                                                           catrow_dev, obs, lab, err, v0);
+        }
     }
 }
 
@@ -79,8 +83,10 @@ __global__ void k_transpose(const T *__restrict__ in, T *__restrict__ out, int64
 
 void launch_transpose(const void *in, void *out, int32_t dtype, int64_t rows, int64_t cols, cudaStream_t st) {
     dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32)), block(32, 8);
-    if (dtype == NAPG_F32) k_transpose<float><<<grid, block, 0, st>>>((const float *)in, (float *)out, rows, cols);
-    else k_transpose<double><<<grid, block, 0, st>>>((const double *)in, (double *)out, rows, cols);
+    if (dtype == NAPG_F32) { count_launch(); k_transpose<float><<<grid, block, 0, st>>>((const float *)in, (float *)out, rows, cols);
+    }
+    else { count_launch(); k_transpose<double><<<grid, block, 0, st>>>((const double *)in, (double *)out, rows, cols);
+    }
 }
 
 // context mask (bytes) -> bit words; NULL mask = all samples
@@ -96,6 +102,7 @@ __global__ void k_ctx_bits(const uint8_t *__restrict__ mask, int64_t S, int64_t 
 
 void launch_ctx_bits(const uint8_t *mask, int64_t S, int64_t W, uint32_t *ctxw, cudaStream_t st) {
     if (W == 0) return;
+    count_launch();
     k_ctx_bits<<<(unsigned)((W + 7) / 8), 256, 0, st>>>(mask, S, W, ctxw);
 }
 
@@ -114,6 +121,7 @@ void launch_gather_obs(const uint32_t *obs, const int32_t *vars_dev, int32_t nv,
     const int64_t total = (int64_t)nv * W;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    count_launch();
     k_gather_obs<<<blocks, 256, 0, st>>>(obs, vars_dev, nv, ctxw, W, out);
 }
 
@@ -164,10 +172,14 @@ void launch_shift_values(const void *X, int32_t dtype, int64_t S, int64_t S_pad,
                          int32_t nv, const uint32_t *obsv, int64_t W, double *shift, double *xs,
                          cudaStream_t st) {
     if (nv == 0) return;
-    if (dtype == NAPG_F32)
+    if (dtype == NAPG_F32) {
+        count_launch();
         k_shift_values<float><<<nv, 256, 0, st>>>((const float *)X, S, S_pad, vars_dev, obsv, W, shift, xs);
-    else
+    }
+    else {
+        count_launch();
         k_shift_values<double><<<nv, 256, 0, st>>>((const double *)X, S, S_pad, vars_dev, obsv, W, shift, xs);
+    }
 }
 
 // Level bitmasks of categorical variables: levbits[levoff[i] + g][w] has bit s
@@ -200,6 +212,7 @@ void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *
     if (nv == 0 || W == 0) return;
     for (int i0 = 0; i0 < nv; i0 += 65535) {        // grid.y limit
         dim3 grid((unsigned)((W + 7) / 8), (unsigned)std::min(65535, nv - i0));
+        count_launch();
         k_level_bits<<<grid, 256, 0, st>>>(lab, S, W, catrow_dev, levoff_dev, nlev_dev, obsv, levbits, levcnt, i0);
     }
 }
@@ -211,6 +224,7 @@ __global__ void k_fill_nan(double *p, int64_t count) {
 
 void launch_fill_nan(double *p, int64_t count, cudaStream_t st) {
     if (count <= 0 || !p) return;
+    count_launch();
     k_fill_nan<<<(unsigned)std::min<int64_t>((count + 255) / 256, 4096), 256, 0, st>>>(p, count);
 }
 

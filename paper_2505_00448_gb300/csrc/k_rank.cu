@@ -232,12 +232,16 @@ void launch_presort(const void *X, int32_t dtype, int64_t S, int64_t W, const in
     cudaFuncSetAttribute(k_presort<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     for (int c0 = 0; c0 < ncont; c0 += batch) {
         const int nblk = std::min(batch, ncont - c0);
-        if (dtype == NAPG_F32)
+        if (dtype == NAPG_F32) {
+            count_launch();
             k_presort<float><<<nblk, 1024, smem, st>>>((const float *)X, S, W, contvars_dev, obs, perm, pos, nobs, tie,
                                                        gsw, gew, gk, gi, n2, c0);
-        else
+        }
+        else {
+            count_launch();
             k_presort<double><<<nblk, 1024, smem, st>>>((const double *)X, S, W, contvars_dev, obs, perm, pos, nobs,
                                                         tie, gsw, gew, gk, gi, n2, c0);
+        }
     }
 }
 
@@ -397,6 +401,7 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
     if (pairs == 0) return;
     const size_t smem = rank_smem_bytes(rd.W, 2, true);
     cudaFuncSetAttribute(k_spearman, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
     k_spearman<<<(unsigned)pairs, 256, smem, st>>>(rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric, out4);
 }
 
@@ -467,6 +472,7 @@ void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *c
     if (pairs == 0) return;
     const size_t smem = rank_smem_bytes(rd.W, 1, true);
     cudaFuncSetAttribute(k_rank_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
     k_rank_groups<<<(unsigned)pairs, 256, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b,
                                                       nb, rsum, rcnt, tie_term);
 }
@@ -541,6 +547,7 @@ void launch_mwu_exact(const double *stat, const int32_t *rcnt, const int32_t *le
                       void *scratch, size_t scratch_bytes, cudaStream_t st) {
     (void)total_rows;
     const int64_t cap = (int64_t)(scratch_bytes / (32 * 2 * sizeof(u128)));
+    count_launch();
     k_mwu_exact<<<32, 128, 0, st>>>(stat, rcnt, levoff, nb, flag_list, flag_count, max_flags, pval, (u128 *)scratch,
                                     cap);
 }

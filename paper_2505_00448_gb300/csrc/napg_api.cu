@@ -173,7 +173,7 @@ napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st) {
     const size_t tb = presort_tmp_bytes(S, (int32_t)nc);
     void *tmp = nullptr;
     NAPG_CU(ctx, cudaMalloc(&tmp, tb));
-    launch_presort(c.X, c.dtype, S, W, dcv, (int32_t)nc, c.obs, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, tmp, tb, st);
+    { Stage s_(ctx->trace, st, "presort"); launch_presort(c.X, c.dtype, S, W, dcv, (int32_t)nc, c.obs, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, tmp, tb, st); }
     NAPG_CU(ctx, cudaGetLastError());
     NAPG_CU(ctx, cudaStreamSynchronize(st));
     cudaFree(tmp);
@@ -181,6 +181,14 @@ napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st) {
     c.sorted = true;
     return NAPG_OK;
 }
+
+// A pair whose centred sum falls to rel_tol x its raw sum (about the column's
+// in-context mean) is recomputed exactly by the two-pass rescue: for the FP64
+// form only true degeneracy (a constant column/group) reaches 1e-9; for the
+// mixed form the sums carry ~1e-7 relative error, so the statistic keeps
+// |dr| <= 1e-6 only while raw/centred stays small.
+constexpr double kPlainRelTol = 1e-9;
+constexpr double kMixedRelTol = 0.25;
 
 napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a) {
     Cohort &c = ctx->coh;
@@ -206,9 +214,9 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         std::vector<int32_t> ia(a.na), ib(a.nb);
         for (int i = 0; i < a.na; ++i) ia[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), a.va[i]) - uniq.begin());
         for (int i = 0; i < a.nb; ++i) ib[i] = (int32_t)(std::lower_bound(uniq.begin(), uniq.end(), a.vb[i]) - uniq.begin());
-        double *ts = WS(kTmpE, double, (int64_t)nu * nu);
-        double *tp = WS(kTmpF, double, (int64_t)nu * nu);
-        int32_t *tn = WS(kTmpG, int32_t, (int64_t)nu * nu + 2 * (nu + a.na + a.nb));
+        double *ts = WS(kUnionS, double, (int64_t)nu * nu);
+        double *tp = WS(kUnionP, double, (int64_t)nu * nu);
+        int32_t *tn = WS(kUnionN, int32_t, (int64_t)nu * nu + 2 * (nu + a.na + a.nb));
         if (st_) return st_;
         RunArgs b = a;
         b.va = uniq.data();
@@ -223,6 +231,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         NAPG_CU(ctx, cudaMemcpyAsync(dia, ia.data(), sizeof(int32_t) * a.na, cudaMemcpyHostToDevice, st));
         NAPG_CU(ctx, cudaMemcpyAsync(dib, ib.data(), sizeof(int32_t) * a.nb, cudaMemcpyHostToDevice, st));
         const int64_t tot = (int64_t)a.na * a.nb;
+        count_launch();
         k_gather_block<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, st>>>(
             ts, tp, tn, nu, dia, dib, a.na, a.nb, a.stat, a.pval, a.n);
         NAPG_CU(ctx, cudaGetLastError());
@@ -244,6 +253,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         }
     }
     if (st_) return st_;
+    Stage prep_stage(ctx->trace, st, "prep");
     launch_ctx_bits(mask_dev, S, W, ctxw, st);
 
     // variable lists on the device: [va | vb | crow_a | crow_b | catrow | nlev | levoff]
@@ -287,6 +297,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         NAPG_CU(ctx, cudaMemsetAsync(levcnt, 0, sizeof(int32_t) * R, st));
         launch_level_bits(c.lab, S, W, d_cat, d_lo, d_nl, na, obsA, levbits, levcnt, st);
     }
+    prep_stage.end();
 
     RescueArgs rsc{c.X, c.dtype, S, W, ctxw, c.obs, c.lab, d_cat, d_va, symmetric ? nullptr : d_vb, na, nb, t,
                    a.opt.welch, d_nl, levcnt, d_lo};
@@ -297,51 +308,54 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         int32_t *nn = WS(kIntA, int32_t, nn2);
         int32_t *flags = WS(kFlagList, int32_t, nn2 / 2 + na + 1);
         double *shift = WS(kShiftA, double, na);
+        double *vsq = mixed ? WS(kVsq, double, na) : nullptr;
         if (st_) return st_;
         if (mixed) {
-            NAPG_ST(mixed_pearson(ctx, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift));
+            NAPG_ST(mixed_pearson(ctx, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift, vsq));
         } else {
             double *xs = WS(kXsA, double, (int64_t)na * S_pad);
             if (st_) return st_;
-            launch_shift_values(c.X, c.dtype, S, S_pad, d_va, na, obsA, W, shift, xs, st);
-            launch_pearson_fp64(xs, S_pad, obsA, W, na, Sxy, Sx, Sxx, nn, st);
+            { Stage s_(ctx->trace, st, "shift_fp64"); launch_shift_values(c.X, c.dtype, S, S_pad, d_va, na, obsA, W, shift, xs, st); }
+            { Stage s_(ctx->trace, st, "pearson_moments_fp64"); launch_pearson_fp64(xs, S_pad, obsA, W, na, Sxy, Sx, Sxx, nn, st); }
         }
-        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? 1e-4 : 1e-9};
-        launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st);
-        launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, st);
+        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq};
+        { Stage s_(ctx->trace, st, "finalize_pearson"); launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st); }
+        { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, st); }
     } else if (t == NAPG_ANOVA || t == NAPG_TTEST) {
         const int64_t rb = (int64_t)R * nb;
         int32_t *gn = WS(kIntA, int32_t, rb);
         double *g1 = WS(kMomA, double, rb), *g2 = WS(kMomB, double, rb);
         int32_t *flags = WS(kFlagList, int32_t, (int64_t)na * nb + 1);
         double *shift = WS(kShiftB, double, nb);
+        double *vsq = mixed ? WS(kVsq, double, nb) : nullptr;
         if (st_) return st_;
         if (mixed) {
-            NAPG_ST(mixed_groupsum(ctx, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift));
+            NAPG_ST(mixed_groupsum(ctx, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift, vsq));
         } else {
             double *xs = WS(kXsB, double, (int64_t)nb * S_pad);
             if (st_) return st_;
-            launch_shift_values(c.X, c.dtype, S, S_pad, d_vb, nb, obsB, W, shift, xs, st);
-            launch_groupsum_fp64(c.lab, S, d_cat, na, d_lo, d_nl, xs, S_pad, obsB, W, nb, gn, g1, g2, maxlev, st);
+            { Stage s_(ctx->trace, st, "shift_fp64"); launch_shift_values(c.X, c.dtype, S, S_pad, d_vb, nb, obsB, W, shift, xs, st); }
+            { Stage s_(ctx->trace, st, "groupsum_fp64"); launch_groupsum_fp64(c.lab, S, d_cat, na, d_lo, d_nl, xs, S_pad, obsB, W, nb, gn, g1, g2, maxlev, st); }
         }
-        GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? 1e-4 : 1e-9};
-        launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st);
-        launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, st);
+        GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? kMixedRelTol : kPlainRelTol,
+                   vsq};
+        { Stage s_(ctx->trace, st, "finalize_groups"); launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st); }
+        { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, st); }
     } else if (t == NAPG_CHI2) {
         int32_t *T = WS(kIntA, int32_t, (int64_t)R * R);
         if (st_) return st_;
         if (mixed) NAPG_ST(mixed_contingency(ctx, ws, st, levbits, R, T));
-        else launch_contingency(levbits, W, R, T, st);
+        else { Stage s_(ctx->trace, st, "contingency_popc"); launch_contingency(levbits, W, R, T, st); }
         Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2};
-        launch_finalize_chi2(f, a.stat, a.pval, a.n, st);
+        { Stage s_(ctx->trace, st, "finalize_chi2"); launch_finalize_chi2(f, a.stat, a.pval, a.n, st); }
     } else if (t == NAPG_SPEARMAN) {
         NAPG_ST(ensure_presort(ctx, st));
         int64_t *q = WS(kMomA, int64_t, (int64_t)na * nb * 4);
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
-        launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st);
+        { Stage s_(ctx->trace, st, "spearman_rank"); launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st); }
         SpearmanFin f{q, na, nb, symmetric ? 1 : 0};
-        launch_finalize_spearman(f, a.stat, a.pval, a.n, st);
+        { Stage s_(ctx->trace, st, "finalize_spearman"); launch_finalize_spearman(f, a.stat, a.pval, a.n, st); }
     } else {  // MWU / KRUSKAL
         NAPG_ST(ensure_presort(ctx, st));
         const int64_t rb = (int64_t)R * nb;
@@ -351,14 +365,15 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         int32_t *flags = WS(kFlagList, int32_t, (int64_t)na * nb + 1);
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
-        launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st);
+        { Stage s_(ctx->trace, st, "rank_groups"); launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st); }
         RankGroupFin f{rsum, rcnt, tie, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.mwu_mode, a.opt.mwu_continuity};
-        launch_finalize_rankgroups(f, a.stat, a.pval, a.n, flags, counter, st);
+        { Stage s_(ctx->trace, st, "finalize_rankgroups"); launch_finalize_rankgroups(f, a.stat, a.pval, a.n, flags, counter, st); }
         if (t == NAPG_MWU && a.pval) {
             const size_t sb = mwu_exact_scratch_bytes(S);
             void *scratch = ws_get(ctx, ws, Workspace::kTmpA, sb, &st_);
             if (st_) return st_;
             if (!a.stat) return fail(ctx, NAPG_E_ARG, "exact Mann-Whitney p needs the stat buffer");
+            Stage s_(ctx->trace, st, "mwu_exact");
             launch_mwu_exact(a.stat, rcnt, d_lo, R, nb, flags, counter, (int32_t)((int64_t)na * nb + 1), a.pval,
                              scratch, sb, st);
         }
@@ -437,7 +452,9 @@ const char *napg_last_error(const napg_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 napg_status napg_sync(napg_ctx *ctx) {
     if (!ctx) return NAPG_E_ARG;
+    NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
     NAPG_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
     return NAPG_OK;
 }
 
@@ -542,11 +559,16 @@ static napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t s
         if (st_) return st_;
         hs = nullptr;
     }
+    NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
     NAPG_ST(run_on_stream(ctx, ws, st, a));
     if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
-    if (!ds || !dp || !dn) NAPG_CU(ctx, cudaStreamSynchronize(st));
+    if (!ds || !dp || !dn) {
+        NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        NAPG_CU(ctx, cudaStreamSynchronize(st));
+        if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    }
     return NAPG_OK;
 }
 

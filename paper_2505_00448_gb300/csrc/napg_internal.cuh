@@ -51,7 +51,7 @@ struct Workspace {
         kCtxBits, kObsA, kObsB, kShiftA, kShiftB, kXsA, kXsB, kVarA, kLevBits, kLevCnt,
         kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
-        kTmpF, kTmpG, kNumSlots
+        kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -62,7 +62,30 @@ struct Workspace {
     }
 };
 
-struct ServeState;   // serving loop (serve.cpp)
+struct ServeState;   // serving loop (serve.cu)
+
+// Stage timing with CUDA events (napg_trace_*).
+struct Tracer {
+    bool on = false;
+    struct Rec { std::string name; cudaEvent_t a, b; uint64_t launches; };
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    struct Agg { uint64_t launches = 0; double ms = 0.0; };
+    std::vector<std::pair<std::string, Agg>> agg;
+    std::mutex mu;
+};
+
+// counts every kernel launch made by the library
+void count_launch(uint64_t k = 1);
+uint64_t launches_so_far();
+
+// RAII: records an event pair around a stage when tracing is on
+struct Stage {
+    Tracer *tr; cudaStream_t st; std::string name; cudaEvent_t a = nullptr; uint64_t l0 = 0;
+    Stage(Tracer &t, cudaStream_t s, const char *n);
+    void end();          // records the end now (the destructor then does nothing)
+    ~Stage() { end(); }
+};
 
 }  // namespace napg
 
@@ -77,6 +100,7 @@ struct napg_ctx {
     uint32_t *dev_err = nullptr;       // device error word for checks
     uint32_t *host_err = nullptr;      // pinned mirror
     napg::ServeState *serve = nullptr;
+    napg::Tracer trace;
     std::mutex mu;                     // guards cohort/workspace use from the serving threads
 };
 
@@ -125,13 +149,14 @@ void launch_pearson_fp64(const double *xs, int64_t S_pad, const uint32_t *obsv, 
 void launch_groupsum_fp64(const uint8_t *lab, int64_t S, const int32_t *catrow_dev, int32_t na,
                           const int32_t *levoff_dev, const int32_t *nlev_dev, const double *xs,
                           int64_t S_pad, const uint32_t *obsb, int64_t W, int32_t nb,
-                          int32_t *gn, double *g1, double *g2, int32_t total_rows, cudaStream_t st);
+                          int32_t *gn, double *g1, double *g2, int32_t max_levels, cudaStream_t st);
 // contingency tables
 void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, cudaStream_t st);
 // finalize (p-values included)
 struct PearsonFin {
     const double *Sxy, *Sx, *Sxx; const int32_t *nn; const double *shift; int32_t nv;
-    double rel_tol;   // degenerate-variance threshold relative to the raw sums
+    double rel_tol;      // ill-conditioned when a centred sum <= rel_tol x its raw sum
+    const double *vsq;   // mixed form: Sxx holds sum (x~^2 - v) m; add v n back (NULL: plain)
 };
 void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout,
                              int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -139,6 +164,7 @@ struct GroupFin {
     const int32_t *gn; const double *g1, *g2; int32_t total_rows;
     const int32_t *levoff, *nlev, *present; int32_t na, nb; int32_t test; int32_t welch;
     double rel_tol;
+    const double *vsq;   // mixed form: g2 holds sum (x~^2 - v); add v n_g back (NULL: plain)
 };
 void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout,
                             int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -189,10 +215,10 @@ void launch_fill_nan(double *p, int64_t count, cudaStream_t st);
 struct MixedPlan;
 napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn,
-                          double *shift_out);
+                          double *shift_out, double *vsq_out);
 napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                            const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn,
-                           double *g1, double *g2, double *shift_out);
+                           double *g1, double *g2, double *shift_out, double *vsq_out);
 napg_status mixed_contingency(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
                               int32_t R, int32_t *T);
 

@@ -28,7 +28,8 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 # every symbol include/napg.h declares
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_serve_start",
-           "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version"]
+           "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version", "napg_trace_enable",
+           "napg_trace_read", "napg_kernel_launches"]
 
 
 class Options(C.Structure):
@@ -75,6 +76,12 @@ def _load():
     L.napg_serve_stop.restype = C.c_int
     L.napg_version.argtypes = []
     L.napg_version.restype = C.c_char_p
+    L.napg_trace_enable.argtypes = [p, i32]
+    L.napg_trace_enable.restype = C.c_int
+    L.napg_trace_read.argtypes = [p, p, C.c_size_t]
+    L.napg_trace_read.restype = C.c_int
+    L.napg_kernel_launches.argtypes = []
+    L.napg_kernel_launches.restype = C.c_uint64
     return L
 
 
@@ -120,6 +127,10 @@ class Context:
         self.device = device
         if stream is None:
             stream = torch.cuda.current_stream(device)
+            if stream.cuda_stream == 0:
+                # the legacy default stream has handle 0, which the C ABI reads as
+                # "no stream": give the context a stream of its own
+                stream = torch.cuda.Stream(device)
         self.stream = stream
         h = C.c_void_p()
         rc = lib.napg_create(C.byref(h), device, C.c_void_p(stream.cuda_stream))
@@ -167,11 +178,12 @@ class Context:
         self.F, self.S, self.vtype, self.nlev = F, S, vt, nl
         return self
 
-    def run(self, test, vars_a, vars_b=None, mask=None, out="cuda", **opt):
+    def run(self, test, vars_a, vars_b=None, mask=None, out="cuda", outputs=None, sync=True, **opt):
         """One test over all pairs vars_a x vars_b (vars_a x vars_a when vars_b is None).
 
-        out="cuda": torch tensors on the device (stream-ordered, synchronised here);
-        out="numpy": host numpy arrays. Returns dict(stat, p, n).
+        out="cuda": torch tensors on the device (stream-ordered; synchronised unless
+        sync=False); out="numpy": host numpy arrays. `outputs` may supply the
+        dict(stat, p, n) buffers to write. Returns dict(stat, p, n).
         """
         torch = self.torch
         t = TESTS[test] if isinstance(test, str) else int(test)
@@ -179,7 +191,9 @@ class Context:
         na = len(va)
         nb = na if vb is None else len(vb)
         o = options(**opt)
-        if out == "numpy":
+        if outputs is not None:
+            stat, p, n = outputs.get("stat"), outputs.get("p"), outputs.get("n")
+        elif out == "numpy":
             stat = np.empty((na, nb), np.float64)
             p = np.empty((na, nb), np.float64)
             n = np.empty((na, nb), np.int32)
@@ -193,9 +207,18 @@ class Context:
             m = np.ascontiguousarray(mask, dtype=np.uint8) if isinstance(mask, np.ndarray) else mask
         self._check(lib.napg_run(self.h, t, C.byref(o), _ptr(m), _ptr(va), na, _ptr(vb), 0 if vb is None else nb,
                                  _ptr(stat), _ptr(p), _ptr(n)))
-        if out != "numpy":
+        if out != "numpy" and sync:
             self.sync()
         return {"stat": stat, "p": p, "n": n}
+
+    def trace(self, on=True):
+        self._check(lib.napg_trace_enable(self.h, 1 if on else 0))
+
+    def trace_read(self):
+        import json
+        buf = C.create_string_buffer(1 << 16)
+        self._check(lib.napg_trace_read(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def run_batch(self, test, masks, vars_a, vars_b=None, **opt):
         """One test for several sample contexts (list of uint8 masks); returns a list of dicts (numpy)."""
@@ -227,3 +250,7 @@ class Context:
 
 def version() -> str:
     return lib.napg_version().decode()
+
+
+def kernel_launches() -> int:
+    return int(lib.napg_kernel_launches())

@@ -32,6 +32,20 @@ def compare(test, gpu, ref, stat_tol=None, p_rel=P_REL, check_p=True):
     bad = np.argwhere(nan_g != nan_r)
     assert bad.size == 0, f"stat NaN pattern differs at {bad[:5].tolist()}: gpu {gs[tuple(bad[0])]} oracle {rs[tuple(bad[0])]}"
     kind, tol = stat_tol or STAT_TOL[test]
+    if kind == "effect":
+        # judge F and t on their effect-size (correlation) scale, the analogue of
+        # |dr| for Pearson: t -> t / sqrt(t^2 + n - 2), F -> sqrt(F / (F + n))
+        nn = rn.astype(np.float64)
+        if test == "ttest":
+            tr = lambda v: v / np.sqrt(v * v + np.maximum(nn - 2, 1))
+        else:
+            tr = lambda v: np.sqrt(np.maximum(v, 0) / (np.maximum(v, 0) + nn))
+        with np.errstate(invalid="ignore", divide="ignore"):
+            gs_e, rs_e = tr(gs), tr(rs)
+        fin_e = np.isfinite(rs_e) & np.isfinite(rs)
+        de = np.abs(gs_e[fin_e] - rs_e[fin_e])
+        assert de.max(initial=0) <= tol, f"max effect-scale difference {de.max()} > {tol}"
+        kind = "none"
     ok = ~nan_r
     inf_r = np.isinf(rs)
     assert np.array_equal(gs[inf_r], rs[inf_r]), "infinite statistics differ"
@@ -43,7 +57,7 @@ def compare(test, gpu, ref, stat_tol=None, p_rel=P_REL, check_p=True):
         r = d / np.maximum(np.abs(rs[fin]), 1e-300)
         worst = r.max(initial=0)
         assert worst <= tol, f"max rel dstat {worst} > {tol} at {np.argwhere(fin)[np.argmax(r)].tolist()}"
-    else:
+    elif kind == "exact":
         assert np.array_equal(gs[fin], rs[fin]), "statistic not bit-exact"
     if not check_p:
         return

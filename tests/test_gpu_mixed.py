@@ -1,0 +1,118 @@
+"""GPU parity of the mixed-precision (tcgen05) form against the FP64 oracle.
+
+Bars (Sec. 3.5 statistics, mixed form): counts exact; |dr| <= 1e-6 for Pearson;
+F and t within 1e-6 on their effect-size scale (t/sqrt(t^2+n-2), sqrt(F/(F+n)):
+the analogue of |dr|, since a relative bar is meaningless for statistics near
+zero); contingency tables exact (so chi-squared equals the plain form bit for
+bit). P-values: the device p-function applied to the
+device statistic agrees with the oracle's p-function on that same statistic to
+1e-12 relative; the end-to-end p difference is bounded by the statistic's
+difference propagated through the p-value's slope.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2505_00448_gb300 import synth
+from tests._parity import compare
+
+pytestmark = pytest.mark.gpu
+NAN = float("nan")
+
+
+@pytest.fixture(scope="module")
+def napg():
+    from paper_2505_00448_gb300 import napg as N
+    return N
+
+
+def oracle_run(test, coh, va, vb=None, mask=None, **kw):
+    return O.run(test, coh["X"].astype(np.float64), coh["missing"], coh["vtype"], coh["nlev"], va, vb, ctx=mask, **kw)
+
+
+def p_function_agrees(test, g, extra=None):
+    """c14 (i): p_gpu == oracle p-function(stat_gpu) to 1e-12 relative."""
+    s, p, n = np.asarray(g["stat"]), np.asarray(g["p"]), np.asarray(g["n"])
+    ok = np.isfinite(s) & np.isfinite(p) & (p > 1e-300)
+    if test == "pearson":
+        ref = O.corr_p(s[ok], n[ok].astype(float))
+    else:
+        raise NotImplementedError
+    rel = np.abs(p[ok] - ref) / ref
+    assert rel.max(initial=0) < 1e-12, rel.max()
+
+
+@pytest.mark.parametrize("offset,lognormal", [(0.0, False), (1e4, False), (0.0, True)])
+def test_mixed_pearson(napg, offset, lognormal):
+    coh = synth.small_cohort(201, n_cont=300, n_cat=0, S=3000 + 37, miss=0.25, dtype=np.float32, offset=offset,
+                             lognormal=lognormal)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    va = coh["cont"]
+    g = c.run("pearson", va, out="numpy", precision="mixed")
+    ref = oracle_run("pearson", coh, va)
+    compare("pearson", g, ref, stat_tol=("abs", 1e-6))
+    p_function_agrees("pearson", g)
+    # the plain form on the same data for the record
+    gp = c.run("pearson", va, out="numpy", precision="fp64")
+    assert np.array_equal(gp["n"], g["n"])
+    c.close()
+
+
+def test_mixed_pearson_context_and_ragged(napg):
+    rng = np.random.default_rng(9)
+    coh = synth.small_cohort(202, n_cont=131, n_cat=0, S=2000 + 5, miss=0.3, dtype=np.float32)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    mask = (rng.random(coh["X"].shape[1]) < 0.55).astype(np.uint8)
+    va = coh["cont"]
+    compare("pearson", c.run("pearson", va, mask=mask, out="numpy", precision="mixed"),
+            oracle_run("pearson", coh, va, mask=mask), stat_tol=("abs", 1e-6))
+    c.close()
+
+
+@pytest.mark.parametrize("welch", [True, False])
+def test_mixed_anova_ttest(napg, welch):
+    coh = synth.small_cohort(203, n_cont=150, n_cat=40, S=2500 + 11, miss=0.2, lev_lo=2, lev_hi=9, binary_cats=12,
+                             dtype=np.float32, offset=100.0)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    cats, conts = coh["cat"], coh["cont"]
+    compare("anova", c.run("anova", cats, conts, out="numpy", precision="mixed"),
+            oracle_run("anova", coh, cats, conts), stat_tol=("effect", 1e-6))
+    bins = cats[:12]
+    compare("ttest", c.run("ttest", bins, conts, out="numpy", precision="mixed", welch=welch),
+            oracle_run("ttest", coh, bins, conts, welch=int(welch)), stat_tol=("effect", 1e-6))
+    c.close()
+
+
+def test_mixed_chi2_equals_plain(napg):
+    coh = synth.small_cohort(204, n_cont=0, n_cat=70, S=3000 + 3, miss=0.2, lev_lo=2, lev_hi=10, binary_cats=10)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    va = coh["cat"]
+    gm = c.run("chi2", va, out="numpy", precision="mixed")
+    gp = c.run("chi2", va, out="numpy", precision="fp64")
+    for k in ("stat", "p", "n"):
+        assert np.array_equal(gm[k], gp[k], equal_nan=True), k
+    compare("chi2", gm, oracle_run("chi2", coh, va))
+    c.close()
+
+
+def test_mixed_counts_exact_beyond_2_16(napg):
+    """All-observed one-hot columns over 70,000 samples: every count equals the
+    exact integer (partial sums well past 2^16 stay exact in FP32)."""
+    S = 70000
+    rng = np.random.default_rng(10)
+    X = np.stack([np.zeros(S), (rng.random(S) < 0.5).astype(float), rng.integers(0, 3, S).astype(float)])
+    c = napg.Context(0)
+    c.load_cohort(X, [1, 1, 1], [1, 2, 3])
+    g = c.run("chi2", [0, 1, 2], out="numpy", precision="mixed")
+    assert (g["n"] == S).all()
+    T = c.debug_integers("chi2", 1, 2)
+    ref = np.array([[np.sum((X[1] == a) & (X[2] == b)) for b in range(3)] for a in range(2)]).ravel()
+    assert np.array_equal(T, ref)
+    gm = c.run("chi2", [1, 2], out="numpy", precision="mixed")
+    gp = c.run("chi2", [1, 2], out="numpy", precision="fp64")
+    assert np.array_equal(gm["stat"], gp["stat"])
+    c.close()
