@@ -41,9 +41,10 @@ UNIT = "var-pairs/s"
 
 # ------------------------------------------------------------------ workload --
 
-def make_workload(name):
+def make_workload(name, scale=1.0):
     if name == "ranks":
-        coh = synth.config2()
+        coh = synth.config2() if scale == 1.0 else synth.config2(n_cont=max(32, int(1000 * scale)),
+                                                                   n_cat=max(8, int(200 * scale)))
         cat = coh["cat"]
         bins = cat[coh["nlev"][cat] == 2]
         multi = cat[coh["nlev"][cat] >= 3]
@@ -51,7 +52,8 @@ def make_workload(name):
         desc = ("rank cohort: 1,000 continuous (1-decimal ties, 30% MCAR + block losses) + 200 categorical "
                 "(2-8 levels) x 10,000 samples, FP64; Spearman + Mann-Whitney + Kruskal-Wallis")
     else:
-        coh = synth.config3()
+        coh = synth.config3() if scale == 1.0 else synth.config3(n_cont=max(64, int(4000 * scale)),
+                                                                   n_cat=max(16, int(1000 * scale)))
         cat = coh["cat"]
         bins = cat[coh["nlev"][cat] == 2]
         tests = [("pearson", coh["cont"], None), ("anova", cat, coh["cont"]), ("ttest", bins, coh["cont"]),
@@ -158,6 +160,52 @@ def oracle_sample(coh, tests, budget_s, seed=0):
             "per_test": {t: v["pairs_per_s"] for t, v in per_test.items()}}
 
 
+# ------------------------------------------------------------------ accuracy --
+
+def sampled_accuracy(coh, tests, outs, k, seed=123):
+    """Max error of the device outputs against the oracle on k random pairs per
+    test: |dr| (Pearson/Spearman), effect-scale difference (F: sqrt(F/(F+n)),
+    t: t/sqrt(t^2+n-2)), exactness (chi-squared, U, n), and the p-value's
+    relative difference."""
+    from oracle import oracle as O
+    rng = np.random.default_rng(seed)
+    X = coh["X"].astype(np.float64)
+    res = {}
+    for test, va, vb in tests:
+        na = len(va)
+        nb = na if vb is None else len(vb)
+        ia = rng.integers(0, na, k)
+        ib = rng.integers(0, nb, k)
+        pa = np.asarray(va)[ia]
+        pb = (np.asarray(va) if vb is None else np.asarray(vb))[ib]
+        st, pv, nn = O.run_pairs(test, X, coh["missing"], coh["vtype"], coh["nlev"], pa, pb, validate=False)
+        gs = outs[test]["stat"].cpu().numpy()[ia, ib]
+        gp = outs[test]["p"].cpu().numpy()[ia, ib]
+        gn = outs[test]["n"].cpu().numpy()[ia, ib]
+        fin = np.isfinite(st) & np.isfinite(gs)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            if test in ("pearson", "spearman"):
+                d = np.abs(gs - st)
+                kind = "max |d stat|"
+            elif test == "anova":
+                d = np.abs(np.sqrt(gs / (gs + nn)) - np.sqrt(st / (st + nn)))
+                kind = "max |d sqrt(F/(F+n))|"
+            elif test == "ttest":
+                d = np.abs(gs / np.sqrt(gs * gs + nn - 2) - st / np.sqrt(st * st + nn - 2))
+                kind = "max |d t/sqrt(t^2+n-2)|"
+            else:
+                d = np.abs(gs - st) / np.maximum(np.abs(st), 1e-300)
+                kind = "max rel d stat"
+            pok = np.isfinite(pv) & (pv > 1e-300)
+            pr = np.abs(gp[pok] - pv[pok]) / pv[pok]
+        res[test] = {"pairs": int(k), "stat_error": float(np.nanmax(d[fin])) if fin.any() else None, "stat_metric": kind,
+                     "p_rel_error_max": float(pr.max()) if pr.size else None,
+                     "p_rel_error_median": float(np.median(pr)) if pr.size else None,
+                     "n_exact": bool(np.array_equal(gn, nn)),
+                     "nan_pattern_equal": bool(np.array_equal(np.isnan(gs), np.isnan(st)))}
+    return res
+
+
 # ---------------------------------------------------------------- roofline --
 
 def kernel_roofline(stage_ms, steps, coh, tests, peaks):
@@ -228,6 +276,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparator step")
+    ap.add_argument("--accuracy-pairs", type=int, default=300)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="variables x scale (profiling captures only; bench lines use 1.0)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -239,7 +291,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        coh, tests, desc = make_workload(args.workload)
+        coh, tests, desc = make_workload(args.workload, args.scale)
         samples = []
         for k in range(args.warmup + args.steps):
             r = oracle_sample(coh, tests, budget_s=max(4.0, 60.0 / (args.warmup + args.steps)), seed=k)
@@ -266,7 +318,9 @@ def main():
     torch.cuda.set_device(device)
     from paper_2505_00448_gb300 import napg
 
-    coh, tests, desc = make_workload(args.workload)
+    coh, tests, desc = make_workload(args.workload, args.scale)
+    if args.scale != 1.0:
+        desc += f" [variables scaled by {args.scale} for profiling]"
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -357,6 +411,30 @@ def main():
         e2e = {"value": world * pairs_step / statistics.mean(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * statistics.mean(times)}
 
+    # error of the timed (last step's) outputs against the FP64 oracle on sampled pairs
+    accuracy = None
+    if rank == 0 and args.accuracy_pairs > 0:
+        accuracy = sampled_accuracy(coh, tests, outs, args.accuracy_pairs)
+
+    # the plain FP64 GPU form of the same step, once, for the comparison the metric names
+    comparator = None
+    if rank == 0 and prec == "mixed" and not args.no_compare:
+        ev_c = {t: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for t, _, _ in tests}
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for test, va, vb in tests:
+            ev_c[test][0].record(stream)
+            ctx.run(test, va, vb, outputs=outs[test], sync=False, precision="fp64")
+            ev_c[test][1].record(stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1)
+        comparator = {"precision": "fp64", "value": pairs_step / (cms / 1000.0), "unit": UNIT, "ms_per_step": cms,
+                      "per_test_ms": {t: ev_c[t][0].elapsed_time(ev_c[t][1]) for t, _, _ in tests},
+                      "speedup_mixed_over_fp64": cms / ms_step}
+
     roof = kernel_roofline(trace.get("stages", {}), args.steps, coh, tests, peaks)
     if roof and roof.get("kernel"):
         roof["traffic"] = load_traffic(roof["kernel"])
@@ -376,7 +454,8 @@ def main():
                            "per_test_pairs_per_s": {t: pair_count(t, va, vb) / (statistics.median(per_test_ms[t]) / 1e3)
                                                     for t, va, vb in tests},
                            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -432,8 +432,196 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
     }
 }
 
+// Block-parallel form of the rescue: one block per queued pair, each thread a
+// fixed strided subset of the samples, reductions in a fixed order (results do
+// not depend on scheduling). Group tests keep per-level sums in registers for up
+// to MAXC levels; wider variables go through k_rescue.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// op: 0 sum, 1 min, 2 max; result broadcast to every thread
+__device__ double block_reduce(double v, int op, double *sh) {
+    v = op == 0 ? warp_sum(v) : (op == 1 ? warp_min(v) : warp_max(v));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = op == 0 ? t + sh[w] : (op == 1 ? fmin(t, sh[w]) : fmax(t, sh[w]));
+        sh[32] = t;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+template <int MAXC>
+__global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_t *flags, const int32_t *nflag,
+                                                      int32_t max_flags, double *stat, double *pval, int32_t *nout,
+                                                      int32_t symmetric) {
+    __shared__ double sh[33];
+    const int32_t cnt = min(*nflag, max_flags);
+    const double inf = dinf();
+    for (int q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const int64_t t = flags[q];
+        const int ncols = symmetric ? r.na : r.nb;
+        const int ia = (int)(t / ncols), ib = (int)(t - (int64_t)ia * ncols);
+        const int va = r.va[ia], vb = symmetric ? r.va[ib] : r.vb[ib];
+        const uint32_t *oa = r.obs + (int64_t)va * r.W, *ob = r.obs + (int64_t)vb * r.W;
+        double s = dnan(), p = dnan();
+        if (r.test == NAPG_PEARSON) {
+            double n = 0, sx = 0, sy = 0, mnx = inf, mxx = -inf, mny = inf, mxy = -inf;
+            for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
+                if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+                const double x = xval(r, (int64_t)va * r.S + k), y = xval(r, (int64_t)vb * r.S + k);
+                n += 1; sx += x; sy += y;
+                mnx = fmin(mnx, x); mxx = fmax(mxx, x); mny = fmin(mny, y); mxy = fmax(mxy, y);
+            }
+            n = block_reduce(n, 0, sh); sx = block_reduce(sx, 0, sh); sy = block_reduce(sy, 0, sh);
+            mnx = block_reduce(mnx, 1, sh); mxx = block_reduce(mxx, 2, sh);
+            mny = block_reduce(mny, 1, sh); mxy = block_reduce(mxy, 2, sh);
+            const int64_t ni = (int64_t)n;
+            if (ni > 1 && mnx != mxx && mny != mxy) {
+                const double mx = sx / n, my = sy / n;
+                double sxx = 0, syy = 0, sxy = 0;
+                for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
+                    if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+                    const double dx = xval(r, (int64_t)va * r.S + k) - mx, dy = xval(r, (int64_t)vb * r.S + k) - my;
+                    sxx += dx * dx; syy += dy * dy; sxy += dx * dy;
+                }
+                sxx = block_reduce(sxx, 0, sh); syy = block_reduce(syy, 0, sh); sxy = block_reduce(sxy, 0, sh);
+                s = fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
+                if (threadIdx.x == 0) p = (ni <= 2) ? dnan() : sf::corr_p(s, n);
+            }
+            if (threadIdx.x == 0) {
+                put(stat, pval, nout, t, s, p, (int32_t)ni);
+                if (symmetric) put(stat, pval, nout, (int64_t)ib * ncols + ia, s, p, (int32_t)ni);
+            }
+            __syncthreads();
+            continue;
+        }
+        const uint8_t *la = r.lab + (int64_t)r.catrow[ia] * r.S;
+        const int c = r.nlev_a[ia], off = r.levoff[ia];
+        double ng[MAXC], sum[MAXC], mn[MAXC], mx[MAXC], ss[MAXC];
+#pragma unroll
+        for (int g = 0; g < MAXC; ++g) { ng[g] = 0; sum[g] = 0; mn[g] = inf; mx[g] = -inf; ss[g] = 0; }
+        for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
+            if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+            const int l = la[k];
+            const double y = xval(r, (int64_t)vb * r.S + k);
+#pragma unroll
+            for (int g = 0; g < MAXC; ++g)
+                if (l == g) { ng[g] += 1; sum[g] += y; mn[g] = fmin(mn[g], y); mx[g] = fmax(mx[g], y); }
+        }
+#pragma unroll
+        for (int g = 0; g < MAXC; ++g) {
+            if (g >= c) break;
+            ng[g] = block_reduce(ng[g], 0, sh); sum[g] = block_reduce(sum[g], 0, sh);
+            mn[g] = block_reduce(mn[g], 1, sh); mx[g] = block_reduce(mx[g], 2, sh);
+        }
+        for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
+            if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+            const int l = la[k];
+            const double y = xval(r, (int64_t)vb * r.S + k);
+#pragma unroll
+            for (int g = 0; g < MAXC; ++g)
+                if (l == g) { const double d = y - sum[g] / ng[g]; ss[g] += d * d; }
+        }
+#pragma unroll
+        for (int g = 0; g < MAXC; ++g) {
+            if (g >= c) break;
+            ss[g] = block_reduce(ss[g], 0, sh);
+        }
+        if (threadIdx.x == 0) {
+            double n = 0, tot = 0;
+            bool cst[MAXC];
+#pragma unroll
+            for (int g = 0; g < MAXC; ++g) {
+                cst[g] = (g < c) && (mn[g] == mx[g]);
+                if (g < c) { n += ng[g]; tot += sum[g]; if (cst[g]) ss[g] = 0.0; }
+            }
+            if (r.test == NAPG_ANOVA) {
+                int k = 0;
+                bool all_const = true, differ = false, have_ref = false;
+                double ref = 0.0;
+#pragma unroll
+                for (int g = 0; g < MAXC; ++g) {
+                    if (g >= c || !r.present[off + g]) continue;
+                    ++k;
+                    all_const &= cst[g];
+                    if (!have_ref) { ref = mn[g]; have_ref = true; } else if (mn[g] != ref) differ = true;
+                }
+                if (all_const) {
+                    if (differ) { s = inf; p = 0.0; }
+                } else {
+                    const double gm = tot / n;
+                    double ssb = 0.0, ssw = 0.0;
+#pragma unroll
+                    for (int g = 0; g < MAXC; ++g) {
+                        if (g >= c || !r.present[off + g]) continue;
+                        const double mg = sum[g] / ng[g];
+                        ssb += ng[g] * (mg - gm) * (mg - gm);
+                        ssw += ss[g];
+                    }
+                    const double d1 = (double)(k - 1), d2 = n - (double)k;
+                    s = (ssb / d1) / (ssw / d2);
+                    p = sf::f_sf(s, d1, d2);
+                }
+            } else {
+                const double n0 = ng[0], n1 = ng[1];
+                const double m0 = sum[0] / n0, m1 = sum[1] / n1;
+                if (!r.welch) {
+                    if (!(cst[0] && cst[1])) {
+                        const double df = n - 2.0;
+                        const double sp2 = (ss[0] + ss[1]) / df;
+                        s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
+                        p = sf::t_two_sided(s, df);
+                    }
+                } else if (cst[0] && cst[1]) {
+                    if (mn[0] != mn[1]) { s = mn[0] > mn[1] ? inf : -inf; p = 0.0; }
+                } else {
+                    const double e0 = ss[0] / (n0 - 1.0) / n0, e1 = ss[1] / (n1 - 1.0) / n1;
+                    const double se2 = e0 + e1;
+                    s = (m0 - m1) / sqrt(se2);
+                    const double nu = se2 * se2 / (e0 * e0 / (n0 - 1.0) + e1 * e1 / (n1 - 1.0));
+                    p = sf::t_two_sided(s, nu);
+                }
+            }
+            put(stat, pval, nout, t, s, p, (int32_t)n);
+        }
+        __syncthreads();
+    }
+}
+
 void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
-                   double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st) {
+                   double *stat, double *pval, int32_t *nout, int32_t symmetric, int32_t max_levels,
+                   cudaStream_t st) {
+    const unsigned blocks = 152 * 8;
+    if (r.test == NAPG_PEARSON || max_levels <= 4) {
+        count_launch();
+        k_rescue_block<4><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+    } else if (max_levels <= 10) {
+        count_launch();
+        k_rescue_block<10><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+    } else if (max_levels <= 16) {
+        count_launch();
+        k_rescue_block<16><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+    } else {
+        launch_rescue_serial(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric, st);
+    }
+}
+
+void launch_rescue_serial(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
+                          double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st) {
     count_launch();
     k_rescue<<<64, 64, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
 }

@@ -13,8 +13,8 @@
 // [2^14, 2^15), so hi/lo keep 22 significant bits (a bf16 pair keeps only 16,
 // too few when one heavy-tailed term carries a large share of a sum); the
 // epilogue removes them exactly. FP16 x FP16 products are exact in FP32.
-// Sums for Pearson (Sec. 3.5.2):      n = M M^T, Sxy ~ (Xh + Xl)(Xh + Xl)^T (four products),
-//                                     Sx = X~ M^T, Sxx = D M^T + v n
+// Sums for Pearson (Sec. 3.5.2):      Sxy ~ (Xh + Xl)(Xh + Xl)^T (four products),
+//                                     n = M M^T, Sx^T = M X~^T, Sxx^T = M D^T + v n
 // Group sums (Sec. 3.5.5, 3.5.7):     n_g = H M^T, S1 = H X~^T, S2 = H D^T + v n_g
 // Contingency tables (Sec. 3.5.4):    T = H H^T
 // 0/1 operands give integer sums that FP32 holds exactly (S < 2^24), so n, n_g
@@ -55,6 +55,7 @@ struct UmmaParams {
     int64_t ld;
     int32_t *out_res;          // resident accumulator 0: integer sums, row-major [rowsA][ld]
     int res_sym;               // also write out_res transposed
+    int out_transpose;         // write every output at [col][row] instead of [row][col]
     int res_into[3];           // float resident r: added into drained output res_into[r]
     const int8_t *expA[2];     // drained output d: per-row scale exponents of A (NULL: 0)
     const int8_t *expB[2];     // ... and of B; the output is divided by 2^(eA + eB)
@@ -73,10 +74,15 @@ __device__ __forceinline__ void tile_coords(int t, int tilesB, int triangle, int
     J = i + t;
 }
 
-// Resident accumulator 0 (if NRES > 0) holds exact integer sums; residents 1..
-// hold small FP32 sums added to a drained output at the end.
+// Warp roles (10 warps): 0 TMA producer, 1 MMA issuer (and TMEM owner), 2-9
+// epilogue (two warps per TMEM lane quadrant, each half the columns).
+constexpr int kThreads = 320;
+
+// Resident accumulator 0 (if NRES > 0) holds exact integer sums unless there is
+// no integer output; the other residents hold small FP32 sums added to a
+// drained output at the end.
 template <int N, int NA, int NB, int NP, int NDRAIN, int NRES, bool FF, int STAGES>
-__global__ void __launch_bounds__(320, 1) k_umma(const __grid_constant__ UmmaParams<NA, NB, NP> P) {
+__global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ UmmaParams<NA, NB, NP> P) {
     constexpr int A_BYTES = kTM * kKB * 2;
     constexpr int B_BYTES = N * kKB * 2;
     constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(320, 1) k_umma(const __grid_constant__ UmmaPar
                         const int col = J * N + half * HC + g * 16 + k;
                         if (row_ok && col < P.rowsB) {
                             const int32_t v = (int32_t)__uint_as_float(r[k]);
-                            P.out_res[(int64_t)gi * P.ld + col] = v;
+                            P.out_res[P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col] = v;
                             if (P.res_sym) P.out_res[(int64_t)col * P.ld + gi] = v;
                         }
                     }
@@ -279,7 +285,8 @@ __global__ void __launch_bounds__(320, 1) k_umma(const __grid_constant__ UmmaPar
                             double v = (double)hi[d][k];
                             if (FF) v += (double)lo[d][FF ? k : 0];
                             const int e = (P.expA[d] ? (int)P.expA[d][gi] : 0) + (P.expB[d] ? (int)P.expB[d][col] : 0);
-                            P.out_drain[d][(int64_t)gi * P.ld + col] = ldexp(v, -e);
+                            P.out_drain[d][P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col] =
+                                ldexp(v, -e);
                         }
                     }
                 }
@@ -305,6 +312,11 @@ __device__ __forceinline__ int scale_exp(double maxabs) {
     return s < -120 ? -120 : (s > 120 ? 120 : s);
 }
 
+// FP32 arithmetic throughout (this GPU's FP64 rate is 1/64 of FP32): the shift
+// c and the centring value v need not be exact, only identical in the planes
+// and in the finalize step (which adds v n back), so they are FP32 values; x - c
+// keeps 24 bits relative to itself (exact when x and c are within a factor of
+// two), and the planes keep 22.
 template <typename T>
 __global__ void k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad, const int32_t *__restrict__ vars,
                               int32_t nv, const uint32_t *__restrict__ obsv, int64_t W, __half *Pm, __half *Pxh,
@@ -321,55 +333,56 @@ __global__ void k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad,
     }
     const T *x = X + (int64_t)vars[i] * S;
     const uint32_t *ob = obsv + (int64_t)i * W;
-    __shared__ double red[32];
+    __shared__ float red[32];
     __shared__ int redc[32];
-    __shared__ double bc[4];
+    __shared__ float bc[4];
     __shared__ int cnt_s;
-    // block reductions: sum (op 0) or max (op 1)
-    auto block_red = [&](double v, int c, int op, double *out_v, int *out_c) {
+    auto block_red = [&](float v, int c, int op, float *out_v, int *out_c) {
         for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_down_sync(0xffffffffu, v, o);
-            v = op ? fmax(v, w) : v + w;
+            const float w = __shfl_down_sync(0xffffffffu, v, o);
+            v = op ? fmaxf(v, w) : v + w;
             c += __shfl_down_sync(0xffffffffu, c, o);
         }
         __syncthreads();
         if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = v; redc[threadIdx.x >> 5] = c; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double tv = op ? 0.0 : 0.0;
+            float tv = 0.f;
             int tc = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tv = op ? fmax(tv, red[w]) : tv + red[w]; tc += redc[w]; }
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tv = op ? fmaxf(tv, red[w]) : tv + red[w]; tc += redc[w]; }
             *out_v = tv;
             if (out_c) *out_c = tc;
         }
         __syncthreads();
     };
-    double s1 = 0.0;
+    // T = double input: x - c is formed in FP64 then rounded (FP32 data: exact ops)
+    float s1 = 0.f;
     int cn = 0;
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
-        if ((ob[s >> 5] >> (s & 31)) & 1u) { s1 += (double)x[s]; ++cn; }
+        if ((ob[s >> 5] >> (s & 31)) & 1u) { s1 += (float)x[s]; ++cn; }
     block_red(s1, cn, 0, &bc[0], &cnt_s);
     const int cnt = cnt_s;
-    const double c = cnt > 0 ? bc[0] / (double)cnt : 0.0;
-    double s2 = 0.0, mx = 0.0;
+    const float c = cnt > 0 ? bc[0] / (float)cnt : 0.f;
+    float s2 = 0.f, mx = 0.f;
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
         if ((ob[s >> 5] >> (s & 31)) & 1u) {
-            const double d = (double)x[s] - c;
-            s2 += d * d;
-            mx = fmax(mx, fabs(d));
+            const float d = (float)(x[s] - (T)c);
+            s2 = fmaf(d, d, s2);
+            mx = fmaxf(mx, fabsf(d));
         }
     block_red(s2, 0, 0, &bc[1], nullptr);
     block_red(mx, 0, 1, &bc[2], nullptr);
-    const double v = cnt > 0 ? bc[1] / (double)cnt : 0.0;
-    double md = 0.0;
+    const float v = cnt > 0 ? bc[1] / (float)cnt : 0.f;
+    float md = 0.f;
     for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
         if ((ob[s >> 5] >> (s & 31)) & 1u) {
-            const double d = (double)x[s] - c;
-            md = fmax(md, fabs(d * d - v));
+            const float d = (float)(x[s] - (T)c);
+            md = fmaxf(md, fabsf(fmaf(d, d, -v)));
         }
     block_red(md, 0, 1, &bc[3], nullptr);
-    const int es = scale_exp(bc[2]), et = scale_exp(bc[3]);
-    if (threadIdx.x == 0) { shift[i] = c; vsq[i] = v; sexp[i] = (int8_t)es; texp[i] = (int8_t)et; }
+    const int es = scale_exp((double)bc[2]), et = scale_exp((double)bc[3]);
+    if (threadIdx.x == 0) { shift[i] = (double)c; vsq[i] = (double)v; sexp[i] = (int8_t)es; texp[i] = (int8_t)et; }
+    const float fs = exp2f((float)es), ft = exp2f((float)et);   // exact powers of two
     const __half one = __float2half(1.f);
     for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
         const bool o = s < S && ((ob[s >> 5] >> (s & 31)) & 1u);
@@ -377,13 +390,16 @@ __global__ void k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad,
             Pm[base + s] = z; Pxh[base + s] = z; Pxl[base + s] = z; Pdh[base + s] = z; Pdl[base + s] = z;
             continue;
         }
-        const double xt = (double)x[s] - c;
-        const double xs = ldexp(xt, es);
-        const __half h = __double2half(xs);
-        const __half l = __double2half(xs - (double)__half2float(h));
-        const double ds = ldexp(xt * xt - v, et);
-        const __half dh = __double2half(ds);
-        const __half dl = __double2half(ds - (double)__half2float(dh));
+        const float xt = (float)(x[s] - (T)c);
+        const float xs = xt * fs;                                  // exact scaling
+        const __half h = __float2half_rn(xs);
+        const __half l = __float2half_rn(xs - __half2float(h));    // the difference is exact in FP32
+        // d = xt^2 - v with the square's rounding error recovered by FMA
+        const float sq = xt * xt;
+        const float sq_err = fmaf(xt, xt, -sq);
+        const float ds = ((sq - v) + sq_err) * ft;
+        const __half dh = __float2half_rn(ds);
+        const __half dl = __float2half_rn(ds - __half2float(dh));
         Pm[base + s] = one; Pxh[base + s] = h; Pxl[base + s] = l; Pdh[base + s] = dh; Pdl[base + s] = dl;
     }
 }
@@ -443,7 +459,7 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
     }
     if (tiles == 0) return NAPG_OK;
     count_launch();
-    kern<<<tiles, 320, smem, st>>>(P);
+    kern<<<tiles, kThreads, smem, st>>>(P);
     NAPG_CU(ctx, cudaGetLastError());
     return NAPG_OK;
 }
@@ -501,8 +517,7 @@ static napg_status prep_onehot(napg_ctx *ctx, Workspace &ws, cudaStream_t st, co
 }
 
 // chunk lengths (K-blocks of 64 samples between drains)
-constexpr int kChunkFF = 2;     // float-float running sums (terms may share a sign)
-constexpr int kChunkF32 = 8;    // FP32 running sums of centred (zero-mean) terms
+constexpr int kChunkFF = 1;     // float-float running sums (terms may share a sign)
 
 napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
@@ -511,59 +526,60 @@ napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const i
     NAPG_ST(prep_cont_planes(ctx, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp));
     const int nkb = (int)(cp.S_pad / kKB);
     const int T = (int)(cp.rows_pad / kTM);
-    // P1: triangle tiles, N = 128. n = M M^T (resident, exact). Sxy: the hi*hi
-    // product alone is accumulated in short chunks drained into float-float sums
-    // (the tensor core rounds its FP32 accumulator about once per instruction, so
-    // the error grows with the instructions per chunk; correlated pairs have
-    // same-sign terms); the three small cross products (hi*lo, lo*hi, lo*lo, of
-    // random sign, 2^-8 smaller) stay resident for the whole K loop. Dropping
-    // lo*lo would bias Sxy low by ~2^-16/3 of sum x~^2.
+    // P1: triangle tiles, N = 128, Sxy only. The hi*hi product alone is
+    // accumulated in short chunks drained into float-float sums (the tensor core
+    // rounds its FP32 accumulator about once per instruction, so the error grows
+    // with the instructions per chunk, and correlated pairs have same-sign terms);
+    // the three small cross products (hi*lo, lo*hi, lo*lo: random sign, 2^-11
+    // smaller) stay resident for the whole K loop. Dropping lo*lo would bias
+    // Sxy low on correlated pairs (it is a square on the diagonal).
     {
-        UmmaParams<3, 3, 5> P{};
-        const void *pl[3] = {cp.M, cp.Xh, cp.Xl};
-        for (int k = 0; k < 3; ++k) {
+        UmmaParams<2, 2, 4> P{};
+        const void *pl[2] = {cp.Xh, cp.Xl};
+        for (int k = 0; k < 2; ++k) {
             if (!make_map(&P.mapA[k], pl[k], cp.rows_pad, cp.S_pad, kTM) ||
                 !make_map(&P.mapB[k], pl[k], cp.rows_pad, cp.S_pad, 128))
                 return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         }
-        P.prod[0] = {0, 0, -1, 0};   // M M   -> n (resident 0)
-        P.prod[1] = {1, 1, 0, 0};    // Xh Xh -> Sxy hi (drained 0)
-        P.prod[2] = {1, 2, -2, 0};   // Xh Xl -> Sxy cross (resident 1)
-        P.prod[3] = {2, 1, -2, 0};   // Xl Xh
-        P.prod[4] = {2, 2, -2, 0};   // Xl Xl
+        P.prod[0] = {0, 0, 0, 0};    // Xh Xh -> Sxy hi (drained 0)
+        P.prod[1] = {0, 1, -1, 0};   // Xh Xl -> Sxy cross (resident 0, float)
+        P.prod[2] = {1, 0, -1, 0};   // Xl Xh
+        P.prod[3] = {1, 1, -1, 0};   // Xl Xl
         P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = T; P.triangle = 1;
         P.nkb = nkb; P.chunk = kChunkFF;
         P.out_drain[0] = Sxy; P.out_drain[1] = nullptr; P.ld = nv;
-        P.out_res = nn; P.res_sym = 0; P.res_into[1] = 0; P.err = ctx->dev_err;
+        P.out_res = nullptr; P.res_sym = 0; P.res_into[0] = 0; P.err = ctx->dev_err;
         P.expA[0] = cp.sexp; P.expB[0] = cp.sexp;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST((launch_umma<128, 3, 3, 5, 1, 2, true, 2>(ctx, P, T * (T + 1) / 2, st)));
+        NAPG_ST((launch_umma<128, 2, 2, 4, 1, 1, true, 3>(ctx, P, T * (T + 1) / 2, st)));
     }
-    // P2: all ordered tiles, N = 64. Sx = X~ M^T and D = sum (x~^2 - v) m over the
-    // co-observed samples: hi products drained every kChunkFF K-blocks into
-    // float-float sums, lo products resident (heavy-tailed columns put single huge
-    // terms into a chunk; every later instruction would then cost an ulp of it).
+    // P2: all ordered tiles, N = 64, the mask as the single A operand against
+    // M, X~ and D of the B rows: n = M M^T (resident, exact), and
+    // sum_s m_i x~_j = Sx[j][i], sum_s m_i d_j = D[j][i] (hi drained, lo resident),
+    // written transposed (which also makes the stores coalesced).
     {
         constexpr int N2 = 64;
-        UmmaParams<4, 1, 4> P{};
-        const void *pa[4] = {cp.Xh, cp.Xl, cp.Dh, cp.Dl};
-        for (int k = 0; k < 4; ++k)
-            if (!make_map(&P.mapA[k], pa[k], cp.rows_pad, cp.S_pad, kTM))
-                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        if (!make_map(&P.mapB[0], cp.M, cp.rows_pad, cp.S_pad, N2))
+        UmmaParams<1, 5, 5> P{};
+        if (!make_map(&P.mapA[0], cp.M, cp.rows_pad, cp.S_pad, kTM))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        P.prod[0] = {0, 0, 0, 0};    // Xh M -> Sx hi (drained 0)
-        P.prod[1] = {1, 0, -1, 0};   // Xl M -> Sx lo (resident 0: added to drained 0)
-        P.prod[2] = {2, 0, 1, 0};    // Dh M -> D hi (drained 1)
-        P.prod[3] = {3, 0, -2, 0};   // Dl M -> D lo (resident 1: added to drained 1)
+        const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
+        for (int k = 0; k < 5; ++k)
+            if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, N2))
+                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        P.prod[0] = {0, 0, -1, 0};   // M M  -> n (resident 0, integer)
+        P.prod[1] = {0, 1, 0, 0};    // M Xh -> Sx^T hi (drained 0)
+        P.prod[2] = {0, 2, -2, 0};   // M Xl -> lo (resident 1)
+        P.prod[3] = {0, 3, 1, 0};    // M Dh -> D^T hi (drained 1)
+        P.prod[4] = {0, 4, -3, 0};   // M Dl -> lo (resident 2)
         const int TJ = (nv + N2 - 1) / N2;
         P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = TJ; P.triangle = 0;
         P.nkb = nkb; P.chunk = kChunkFF;
         P.out_drain[0] = Sx; P.out_drain[1] = Sxx; P.ld = nv;
-        P.out_res = nullptr; P.res_sym = 0; P.res_into[0] = 0; P.res_into[1] = 1; P.err = ctx->dev_err;
-        P.expA[0] = cp.sexp; P.expA[1] = cp.texp;
+        P.out_res = nn; P.res_sym = 0; P.out_transpose = 1;
+        P.res_into[1] = 0; P.res_into[2] = 1; P.err = ctx->dev_err;
+        P.expB[0] = cp.sexp; P.expB[1] = cp.texp;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST((launch_umma<N2, 4, 1, 4, 2, 2, true, 3>(ctx, P, T * TJ, st)));
+        NAPG_ST((launch_umma<N2, 1, 5, 5, 2, 3, true, 3>(ctx, P, T * TJ, st)));
     }
     return NAPG_OK;
 }

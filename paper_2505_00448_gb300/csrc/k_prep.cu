@@ -184,26 +184,35 @@ void launch_shift_values(const void *X, int32_t dtype, int64_t S, int64_t S_pad,
 
 // Level bitmasks of categorical variables: levbits[levoff[i] + g][w] has bit s
 // set when sample s is observed (in the context) and has label g. levcnt gets
-// the per-level counts (must be zeroed before).
+// the per-level counts (must be zeroed before). Each warp covers 32 words of one
+// variable and adds its per-level counts with one atomic per level.
 __global__ void k_level_bits(const uint8_t *__restrict__ lab, int64_t S, int64_t W,
                              const int32_t *__restrict__ catrow, const int32_t *__restrict__ levoff,
                              const int32_t *__restrict__ nlev, const uint32_t *__restrict__ obsv,
                              uint32_t *__restrict__ levbits, int32_t *__restrict__ levcnt, int i_base) {
     const int i = blockIdx.y + i_base;
     const int lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (w >= W) return;
-    const int64_t s = w * 32 + lane;
-    const uint32_t ob = obsv[(int64_t)i * W + w];
-    const int l = (s < S) ? (int)lab[(int64_t)catrow[i] * S + s] : (int)kMissingLabel;
+    const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (w0 >= W) return;
     const int c = nlev[i], off = levoff[i];
-    for (int g = 0; g < c; ++g) {
-        const uint32_t b = __ballot_sync(0xffffffffu, l == g) & ob;
-        if (lane == 0) {
-            levbits[(int64_t)(off + g) * W + w] = b;
-            if (b) atomicAdd(&levcnt[off + g], __popc(b));
+    const uint8_t *la = lab + (int64_t)catrow[i] * S;
+    int cnt = 0;                       // lane g accumulates level g (levels <= 64: two passes)
+    int cnt2 = 0;
+    const int64_t w1 = w0 + 32 < W ? w0 + 32 : W;
+    for (int64_t w = w0; w < w1; ++w) {
+        const int64_t s = w * 32 + lane;
+        const uint32_t ob = obsv[(int64_t)i * W + w];
+        const int l = (s < S) ? (int)la[s] : (int)kMissingLabel;
+        for (int g = 0; g < c; ++g) {
+            const uint32_t b = __ballot_sync(0xffffffffu, l == g) & ob;
+            if (lane == (g & 31)) {
+                levbits[(int64_t)(off + g) * W + w] = b;
+                if (g < 32) cnt += __popc(b); else cnt2 += __popc(b);
+            }
         }
     }
+    if (lane < c && cnt) atomicAdd(&levcnt[off + lane], cnt);
+    if (lane + 32 < c && cnt2) atomicAdd(&levcnt[off + lane + 32], cnt2);
 }
 
 void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *catrow_dev,
@@ -211,7 +220,7 @@ void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *
                        const uint32_t *obsv, uint32_t *levbits, int32_t *levcnt, cudaStream_t st) {
     if (nv == 0 || W == 0) return;
     for (int i0 = 0; i0 < nv; i0 += 65535) {        // grid.y limit
-        dim3 grid((unsigned)((W + 7) / 8), (unsigned)std::min(65535, nv - i0));
+        dim3 grid((unsigned)((W + 8 * 32 - 1) / (8 * 32)), (unsigned)std::min(65535, nv - i0));
         count_launch();
         k_level_bits<<<grid, 256, 0, st>>>(lab, S, W, catrow_dev, levoff_dev, nlev_dev, obsv, levbits, levcnt, i0);
     }

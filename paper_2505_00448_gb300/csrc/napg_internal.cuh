@@ -180,7 +180,10 @@ struct RescueArgs {
     int32_t welch; const int32_t *nlev_a; const int32_t *present; const int32_t *levoff;
 };
 void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
-                   double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st);
+                   double *stat, double *pval, int32_t *nout, int32_t symmetric, int32_t max_levels,
+                   cudaStream_t st);
+void launch_rescue_serial(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
+                          double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st);
 // ranks
 void launch_presort(const void *X, int32_t dtype, int64_t S, int64_t W, const int32_t *contvars_dev,
                     int32_t ncont, const uint32_t *obs, int32_t *perm, int32_t *pos, int32_t *nobs,
