@@ -42,6 +42,14 @@ def _compile(src, obj, verbose):
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    # objects from another host architecture (the tree is shared across machines) are stale
+    import platform
+    stamp = os.path.join(BUILD, "HOST_ARCH")
+    arch = platform.machine()
+    if not os.path.exists(stamp) or open(stamp).read().strip() != arch:
+        force = True
+        with open(stamp, "w") as fh:
+            fh.write(arch + "\n")
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = _headers_mtime()
     jobs = []

@@ -45,10 +45,12 @@ __global__ void k_finalize_pearson(PearsonFin f, double *stat, double *pval, int
             } else {
                 r = cxy / (sqrt(cxx) * sqrt(cyy));
                 r = fmin(1.0, fmax(-1.0, r));
-                p = (n <= 2) ? dnan() : sf::corr_p(r, nd);
+                if (n <= 2) p = dnan();
+                else if (fabs(r) >= 1.0) p = 0.0;
+                else if (f.q.jobs) { pjob_push(f.q, PJob{r, nd, 0.0, ij, kPjCorr, (int32_t)nv}); p = dnan(); }
             }
         }
-        put(stat, pval, nout, ij, r, p, n);
+        put(stat, pval, nout, ij, r, p, n);       // p of a queued job is written by the evaluation
         put(stat, pval, nout, ji, r, p, n);
     }
 }
@@ -105,7 +107,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 } else {
                     const double d1 = (double)(k - 1), d2 = (double)(n - k);
                     s = (ssb / d1) / (ssw / d2);
-                    p = sf::f_sf(s, d1, d2);
+                    if (f.q.jobs) pjob_push(f.q, PJob{s, d1, d2, t, kPjF, 0});
                 }
             }
         } else {  // two-sample t (levels 0 and 1)
@@ -123,12 +125,12 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     const double se2 = e0 + e1;
                     s = (m0 - m1) / sqrt(se2);
                     const double nu = se2 * se2 / (e0 * e0 / (double)(n0 - 1) + e1 * e1 / (double)(n1 - 1));
-                    p = sf::t_two_sided(s, nu);
+                    if (f.q.jobs) pjob_push(f.q, PJob{s, nu, 0.0, t, kPjT, 0});
                 } else {
                     const double df = (double)(n - 2);
                     const double sp2 = (q0 + q1) / df;
                     s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
-                    p = sf::t_two_sided(s, df);
+                    if (f.q.jobs) pjob_push(f.q, PJob{s, df, 0.0, t, kPjT, 0});
                 }
             }
         }
@@ -188,7 +190,7 @@ __global__ void k_finalize_chi2(Chi2Fin f, double *stat, double *pval, int32_t *
             }
             s = chi;
             const int df = (ka - 1) * (kb - 1);
-            p = (df <= 0) ? dnan() : sf::chi2_sf(chi, (double)df);
+            if (df > 0 && f.q.jobs) pjob_push(f.q, PJob{chi, (double)df, 0.0, t, kPjChi2, f.symmetric ? f.nb : 0});
         }
         put(stat, pval, nout, t, s, p, (int32_t)n);
         if (f.symmetric && a != b) put(stat, pval, nout, (int64_t)b * f.nb + a, s, p, (int32_t)n);
@@ -222,7 +224,9 @@ __global__ void k_finalize_spearman(SpearmanFin f, double *stat, double *pval, i
             if (da > 0 && db > 0) {
                 r = (double)num / (sqrt((double)da) * sqrt((double)db));
                 r = fmin(1.0, fmax(-1.0, r));
-                p = (n <= 2) ? dnan() : sf::corr_p(r, (double)n);
+                if (n <= 2) p = dnan();
+                else if (fabs(r) >= 1.0) p = 0.0;
+                else if (f.pq.jobs) pjob_push(f.pq, PJob{r, (double)n, 0.0, t, kPjCorr, f.symmetric ? f.nb : 0});
             }
         }
         put(stat, pval, nout, t, r, p, (int32_t)n);
@@ -293,7 +297,7 @@ __global__ void k_finalize_rankgroups(RankGroupFin f, double *stat, double *pval
                     }
                     const double h0 = 3.0 * acc / ((double)n * (double)(n + 1));
                     s = h0 / ((double)cnum / (double)denom);
-                    p = sf::chi2_sf(s, (double)(k - 1));
+                    if (f.q.jobs) pjob_push(f.q, PJob{s, (double)(k - 1), 0.0, t, kPjChi2, 0});
                 }
             }
         }

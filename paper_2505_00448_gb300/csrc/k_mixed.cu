@@ -517,7 +517,13 @@ static napg_status prep_onehot(napg_ctx *ctx, Workspace &ws, cudaStream_t st, co
 }
 
 // chunk lengths (K-blocks of 64 samples between drains)
-constexpr int kChunkFF = 1;     // float-float running sums (terms may share a sign)
+// K-blocks between drains: Sxy of correlated pairs has same-sign terms and the
+// accumulator's per-instruction rounding adds up within a chunk, so its hi*hi
+// sum is drained every K-block; the other sums (n-weighted shifts, centred
+// squares, group sums) are far from the bar and drain every 4 (the epilogue's
+// float-float work then stays below the MMA time).
+constexpr int kChunkSxy = 1;
+constexpr int kChunkOther = 4;
 
 napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
@@ -546,7 +552,7 @@ napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const i
         P.prod[2] = {1, 0, -1, 0};   // Xl Xh
         P.prod[3] = {1, 1, -1, 0};   // Xl Xl
         P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = T; P.triangle = 1;
-        P.nkb = nkb; P.chunk = kChunkFF;
+        P.nkb = nkb; P.chunk = kChunkSxy;
         P.out_drain[0] = Sxy; P.out_drain[1] = nullptr; P.ld = nv;
         P.out_res = nullptr; P.res_sym = 0; P.res_into[0] = 0; P.err = ctx->dev_err;
         P.expA[0] = cp.sexp; P.expB[0] = cp.sexp;
@@ -573,7 +579,7 @@ napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const i
         P.prod[4] = {0, 4, -3, 0};   // M Dl -> lo (resident 2)
         const int TJ = (nv + N2 - 1) / N2;
         P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = TJ; P.triangle = 0;
-        P.nkb = nkb; P.chunk = kChunkFF;
+        P.nkb = nkb; P.chunk = kChunkOther;
         P.out_drain[0] = Sx; P.out_drain[1] = Sxx; P.ld = nv;
         P.out_res = nn; P.res_sym = 0; P.out_transpose = 1;
         P.res_into[1] = 0; P.res_into[2] = 1; P.err = ctx->dev_err;
@@ -606,7 +612,7 @@ napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const 
     P.prod[4] = {0, 4, -3, 0};   // H Dl -> lo (resident 2)
     const int TI = (int)(hrows / kTM), TJ = (int)((nb + N - 1) / N);
     P.rowsA = R; P.rowsB = nb; P.tilesA = TI; P.tilesB = TJ; P.triangle = 0;
-    P.nkb = (int)(S_pad / kKB); P.chunk = kChunkFF;
+    P.nkb = (int)(S_pad / kKB); P.chunk = kChunkOther;
     P.out_drain[0] = g1; P.out_drain[1] = g2; P.ld = nb;
     P.out_res = gn; P.res_sym = 0; P.res_into[1] = 0; P.res_into[2] = 1; P.err = ctx->dev_err;
     P.expB[0] = cp.sexp; P.expB[1] = cp.texp;

@@ -1,0 +1,56 @@
+// P-value evaluation of queued jobs (pjobs.cuh): counting sort by key, then one
+// thread per job in key order, so that neighbouring lanes take the same branch
+// of the special function with continued fractions of similar length.
+#include "napg_internal.cuh"
+#include "pjobs.cuh"
+#include "specfun.cuh"
+
+namespace napg {
+
+// exclusive scan of the per-key histogram; cursors zeroed
+__global__ void k_pj_scan(const int32_t *hist, int32_t *offs, int32_t *cursor) {
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int k = 0; k < kPjBins; ++k) { offs[k] = run; run += hist[k]; cursor[k] = 0; }
+    }
+}
+
+__global__ void k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t capacity, const int32_t *offs,
+                             int32_t *cursor, PJob *sorted) {
+    const int32_t n = min(*count, capacity);
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const PJob j = jobs[t];
+        const int k = pjob_key(j);
+        sorted[offs[k] + atomicAdd(&cursor[k], 1)] = j;
+    }
+}
+
+__global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capacity, double *pval) {
+    const int32_t n = min(*count, capacity);
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const PJob j = sorted[t];
+        double p;
+        switch (j.kind) {
+            case kPjCorr: p = sf::corr_p(j.s, j.a); break;
+            case kPjT: p = sf::t_two_sided(j.s, j.a); break;
+            case kPjF: p = sf::f_sf(j.s, j.a, j.b); break;
+            default: p = sf::chi2_sf(j.s, j.a); break;
+        }
+        pval[j.idx] = p;
+        if (j.mirror > 0) {
+            const int64_t r = j.idx / j.mirror, c = j.idx - r * j.mirror;
+            if (r != c) pval[c * j.mirror + r] = p;
+        }
+    }
+}
+
+void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
+                       cudaStream_t st) {
+    if (!pval) return;
+    count_launch(3);
+    k_pj_scan<<<1, 32, 0, st>>>(q.hist, offs, cursor);
+    k_pj_scatter<<<152 * 8, 256, 0, st>>>(q.jobs, q.count, q.capacity, offs, cursor, sorted);
+    k_pj_eval<<<152 * 16, 128, 0, st>>>(sorted, q.count, q.capacity, pval);
+}
+
+}  // namespace napg

@@ -182,6 +182,38 @@ napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st) {
     return NAPG_OK;
 }
 
+// P-value job queue of one run (see pjobs.cuh)
+struct PJobBufs {
+    PJobQueue q{};
+    PJob *sorted = nullptr;
+    int32_t *offs = nullptr, *cursor = nullptr;
+};
+
+static napg_status pjobs_setup(napg_ctx *ctx, Workspace &ws, cudaStream_t st, int64_t capacity, bool want,
+                               PJobBufs &b) {
+    b = PJobBufs();
+    if (!want || capacity <= 0) return NAPG_OK;
+    if (capacity > INT32_MAX - 1) return fail(ctx, NAPG_E_UNSUPPORTED, "too many pairs in one call");
+    napg_status st_ = NAPG_OK;
+    b.q.jobs = (PJob *)ws_get(ctx, ws, Workspace::kPjJobs, sizeof(PJob) * (size_t)capacity, &st_);
+    b.sorted = (PJob *)ws_get(ctx, ws, Workspace::kPjSorted, sizeof(PJob) * (size_t)capacity, &st_);
+    int32_t *meta = (int32_t *)ws_get(ctx, ws, Workspace::kPjMeta, sizeof(int32_t) * (1 + 3 * kPjBins), &st_);
+    if (st_) return st_;
+    b.q.count = meta;
+    b.q.hist = meta + 1;
+    b.offs = meta + 1 + kPjBins;
+    b.cursor = meta + 1 + 2 * kPjBins;
+    b.q.capacity = (int32_t)capacity;
+    NAPG_CU(ctx, cudaMemsetAsync(meta, 0, sizeof(int32_t) * (1 + kPjBins), st));
+    return NAPG_OK;
+}
+
+static void pjobs_run(napg_ctx *ctx, const PJobBufs &b, double *pval, cudaStream_t st) {
+    if (!b.q.jobs || !pval) return;
+    Stage s_(ctx->trace, st, "pvalues");
+    launch_pjobs_eval(b.q, b.sorted, b.offs, b.cursor, pval, st);
+}
+
 // A pair whose centred sum falls to rel_tol x its raw sum (about the column's
 // in-context mean) is recomputed exactly by the two-pass rescue: for the FP64
 // form only true degeneracy (a constant column/group) reaches 1e-9; for the
@@ -318,8 +350,11 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
             { Stage s_(ctx->trace, st, "shift_fp64"); launch_shift_values(c.X, c.dtype, S, S_pad, d_va, na, obsA, W, shift, xs, st); }
             { Stage s_(ctx->trace, st, "pearson_moments_fp64"); launch_pearson_fp64(xs, S_pad, obsA, W, na, Sxy, Sx, Sxx, nn, st); }
         }
-        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq};
+        PJobBufs pj;
+        NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
+        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq, pj.q};
         { Stage s_(ctx->trace, st, "finalize_pearson"); launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st); }
+        pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, 0, st); }
     } else if (t == NAPG_ANOVA || t == NAPG_TTEST) {
         const int64_t rb = (int64_t)R * nb;
@@ -337,25 +372,34 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
             { Stage s_(ctx->trace, st, "shift_fp64"); launch_shift_values(c.X, c.dtype, S, S_pad, d_vb, nb, obsB, W, shift, xs, st); }
             { Stage s_(ctx->trace, st, "groupsum_fp64"); launch_groupsum_fp64(c.lab, S, d_cat, na, d_lo, d_nl, xs, S_pad, obsB, W, nb, gn, g1, g2, maxlev, st); }
         }
+        PJobBufs pj;
+        NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
         GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? kMixedRelTol : kPlainRelTol,
-                   vsq};
+                   vsq, pj.q};
         { Stage s_(ctx->trace, st, "finalize_groups"); launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st); }
+        pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, maxlev, st); }
     } else if (t == NAPG_CHI2) {
         int32_t *T = WS(kIntA, int32_t, (int64_t)R * R);
         if (st_) return st_;
         if (mixed) NAPG_ST(mixed_contingency(ctx, ws, st, levbits, R, T));
         else { Stage s_(ctx->trace, st, "contingency_popc"); launch_contingency(levbits, W, R, T, st); }
-        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2};
+        PJobBufs pj;
+        NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
+        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2, pj.q};
         { Stage s_(ctx->trace, st, "finalize_chi2"); launch_finalize_chi2(f, a.stat, a.pval, a.n, st); }
+        pjobs_run(ctx, pj, a.pval, st);
     } else if (t == NAPG_SPEARMAN) {
         NAPG_ST(ensure_presort(ctx, st));
         int64_t *q = WS(kMomA, int64_t, (int64_t)na * nb * 4);
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
         { Stage s_(ctx->trace, st, "spearman_rank"); launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st); }
-        SpearmanFin f{q, na, nb, symmetric ? 1 : 0};
+        PJobBufs pj;
+        NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
+        SpearmanFin f{q, na, nb, symmetric ? 1 : 0, pj.q};
         { Stage s_(ctx->trace, st, "finalize_spearman"); launch_finalize_spearman(f, a.stat, a.pval, a.n, st); }
+        pjobs_run(ctx, pj, a.pval, st);
     } else {  // MWU / KRUSKAL
         NAPG_ST(ensure_presort(ctx, st));
         const int64_t rb = (int64_t)R * nb;
@@ -366,8 +410,11 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
         { Stage s_(ctx->trace, st, "rank_groups"); launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st); }
-        RankGroupFin f{rsum, rcnt, tie, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.mwu_mode, a.opt.mwu_continuity};
+        PJobBufs pj;
+        NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr && t == NAPG_KRUSKAL, pj));
+        RankGroupFin f{rsum, rcnt, tie, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.mwu_mode, a.opt.mwu_continuity, pj.q};
         { Stage s_(ctx->trace, st, "finalize_rankgroups"); launch_finalize_rankgroups(f, a.stat, a.pval, a.n, flags, counter, st); }
+        pjobs_run(ctx, pj, a.pval, st);
         if (t == NAPG_MWU && a.pval) {
             const size_t sb = mwu_exact_scratch_bytes(S);
             void *scratch = ws_get(ctx, ws, Workspace::kTmpA, sb, &st_);

@@ -51,7 +51,7 @@ struct Workspace {
         kCtxBits, kObsA, kObsB, kShiftA, kShiftB, kXsA, kXsB, kVarA, kLevBits, kLevCnt,
         kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
-        kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kNumSlots
+        kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -129,6 +129,11 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
 napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st);
 
 // ---- kernel launchers (defined in the .cu files) ---------------------------
+}  // namespace napg
+#include "pjobs.cuh"
+namespace napg {
+void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
+                       cudaStream_t st);
 // prep
 void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int64_t W, double missing,
                          const uint8_t *vtype_dev, const int32_t *nlev_dev, const int32_t *catrow_dev,
@@ -157,6 +162,7 @@ struct PearsonFin {
     const double *Sxy, *Sx, *Sxx; const int32_t *nn; const double *shift; int32_t nv;
     double rel_tol;      // ill-conditioned when a centred sum <= rel_tol x its raw sum
     const double *vsq;   // mixed form: Sxx holds sum (x~^2 - v) m; add v n back (NULL: plain)
+    PJobQueue q;         // p-value jobs (q.jobs NULL: no p-values wanted)
 };
 void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout,
                              int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -165,12 +171,14 @@ struct GroupFin {
     const int32_t *levoff, *nlev, *present; int32_t na, nb; int32_t test; int32_t welch;
     double rel_tol;
     const double *vsq;   // mixed form: g2 holds sum (x~^2 - v); add v n_g back (NULL: plain)
+    PJobQueue q;
 };
 void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout,
                             int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
 struct Chi2Fin {
     const int32_t *T; int32_t R; const int32_t *levoff_a, *nlev_a, *levoff_b, *nlev_b;
     const int32_t *present; int32_t na, nb; int32_t symmetric; int32_t yates;
+    PJobQueue q;
 };
 void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
 // exact rescue of pairs whose moments are degenerate (constant columns/groups)
@@ -200,11 +208,12 @@ void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *c
                         const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
                         const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int32_t total_rows,
                         int64_t *rsum, int32_t *rcnt, int64_t *tie_term, cudaStream_t st);
-struct SpearmanFin { const int64_t *q; int32_t na, nb; int32_t symmetric; };
+struct SpearmanFin { const int64_t *q; int32_t na, nb; int32_t symmetric; PJobQueue pq; };
 void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
 struct RankGroupFin {
     const int64_t *rsum; const int32_t *rcnt; const int64_t *tie_term; int32_t total_rows;
     const int32_t *levoff, *nlev, *present; int32_t na, nb; int32_t test; int32_t mwu_mode; int32_t mwu_cc;
+    PJobQueue q;
 };
 void launch_finalize_rankgroups(const RankGroupFin &f, double *stat, double *pval, int32_t *nout,
                                 int32_t *flag_list, int32_t *flag_count, cudaStream_t st);

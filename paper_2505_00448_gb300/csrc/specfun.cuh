@@ -110,7 +110,7 @@ __device__ __forceinline__ double lgamma_shift(double small, double big) {
 }
 
 // x^a y^b / B(a,b) with x + y = 1
-__device__ double beta_prefactor(double a, double b, double x, double y) {
+static __device__ double beta_prefactor(double a, double b, double x, double y) {
     if (a >= 10.0 && b >= 10.0) {
         const double lam = (x <= 0.5) ? ((a + b) * x - a) : (b - (a + b) * y);
         const double e = -a * rlog1(lam / a) - b * rlog1(-lam / b)
@@ -146,7 +146,7 @@ constexpr int kMaxIter = 200000;
 constexpr double kTiny = 1e-300;
 
 // value of 1/(1 + d1/(1 + d2/(1 + ...)))
-__device__ double cf_plain(double a, double b, double x) {
+static __device__ double cf_plain(double a, double b, double x) {
     double f = kTiny, C = kTiny, D = 0.0;
     for (int n = 1; n < kMaxIter; ++n) {
         const double an = (n == 1) ? 1.0 : cf_d(a, b, x, n - 1);
@@ -163,7 +163,7 @@ __device__ double cf_plain(double a, double b, double x) {
 }
 
 // the same value through the even part 1/(1 + d1 - d1 d2/(1 + d2 + d3 - d3 d4/(...)))
-__device__ double cf_even(double a, double b, double x, double y) {
+static __device__ double cf_even(double a, double b, double x, double y) {
     double f = cf_one_plus_odd(a, b, y, 0);
     f = (fabs(f) < kTiny) ? kTiny : f;
     double C = f, D = 0.0;
@@ -183,13 +183,13 @@ __device__ double cf_even(double a, double b, double x, double y) {
     return 1.0 / f;
 }
 
-__device__ double ibeta_lower(double a, double b, double x, double y) {
+static __device__ double ibeta_lower(double a, double b, double x, double y) {
     const double cf = (a >= b) ? cf_even(a, b, x, y) : cf_plain(a, b, x);
     return beta_prefactor(a, b, x, y) / a * cf;
 }
 
 // regularized I_x(a,b) with x + y = 1 supplied
-__device__ double ibeta(double a, double b, double x, double y) {
+static __device__ double ibeta(double a, double b, double x, double y) {
     if (!(a > 0.0) || !(b > 0.0) || isnan(x) || isnan(y)) return nan("");
     if (x <= 0.0) return 0.0;
     if (y <= 0.0) return 1.0;
@@ -204,7 +204,7 @@ __device__ __forceinline__ double gamma_prefactor(double a, double x) {
 }
 
 // regularized upper incomplete gamma Q(a, x)
-__device__ double gamma_q(double a, double x) {
+static __device__ double gamma_q(double a, double x) {
     if (!(a > 0.0) || isnan(x)) return nan("");
     if (x <= 0.0) return 1.0;
     if (isinf(x)) return 0.0;
