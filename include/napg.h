@@ -217,6 +217,31 @@ napg_status napg_trace_read(napg_ctx *ctx, char *buf, size_t cap);
 /* Number of kernels this process has launched through the library so far. */
 uint64_t napg_kernel_launches(void);
 
+/* ------------------------------------------------------- allocation-free --
+ * All-pairs Pearson r, p and n in the plain FP64 form for a small matrix that is
+ * already on the GPU, without allocating any memory. (The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, such as code
+ * running inside a framework whose own allocator owns the device memory, a
+ * process with a hard device-memory cap, or a latency-critical path that must
+ * not block in the allocator.)
+ *   X          device, n_vars x n_samples doubles, row-major (one row per variable)
+ *   missing    the sentinel; NaN means "missing iff NaN"
+ *   r, p       device, n_vars x n_vars doubles, row-major (either may be NULL)
+ *   n          device, n_vars x n_vars int32 co-observed counts (may be NULL)
+ *   stream     cudaStream_t to run on (NULL: the default stream)
+ * Work space is one fixed 24 MiB array inside the library, held by every GPU
+ * that loads the library until the process exits; the call allocates nothing.
+ * Limits: 1 <= n_vars <= 256 and 1 <= n_samples <= 8192; larger requests return
+ * NAPG_E_UNSUPPORTED without touching the GPU.
+ * The first call on each device looks up the array's device address; make that
+ * first call before capturing any stream. All calls share the array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and give
+ * wrong results; serialize them. The call returns after its results are written
+ * (it reads a status word back), with NAPG_E_NONFINITE if a non-missing value is
+ * +-inf or NaN, NAPG_E_ARG for bad arguments and NAPG_E_CUDA on a CUDA error. */
+napg_status napg_pearson_fp64_noalloc(const double *X, int32_t n_vars, int32_t n_samples, double missing,
+                                      double *r, double *p, int32_t *n, void *stream);
+
 /* Library version string. */
 const char *napg_version(void);
 

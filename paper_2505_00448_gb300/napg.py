@@ -29,7 +29,7 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_serve_start",
            "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version", "napg_trace_enable",
-           "napg_trace_read", "napg_kernel_launches"]
+           "napg_trace_read", "napg_kernel_launches", "napg_pearson_fp64_noalloc"]
 
 
 class Options(C.Structure):
@@ -82,6 +82,8 @@ def _load():
     L.napg_trace_read.restype = C.c_int
     L.napg_kernel_launches.argtypes = []
     L.napg_kernel_launches.restype = C.c_uint64
+    L.napg_pearson_fp64_noalloc.argtypes = [p, i32, i32, d, p, p, p, p]
+    L.napg_pearson_fp64_noalloc.restype = C.c_int
     return L
 
 
