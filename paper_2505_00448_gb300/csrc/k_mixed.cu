@@ -49,6 +49,7 @@ struct UmmaParams {
     int rowsA, rowsB;          // valid rows of A and B
     int tilesA, tilesB;        // tile counts along A rows and B rows
     int triangle;              // 1: only tiles with I <= J
+    int a_fastest;             // full grids: 1 = consecutive CTAs step through A tiles (share the B tile)
     int nkb;                   // K-blocks
     int chunk;                 // K-blocks per drain chunk
     double *out_drain[2];      // drained sums, row-major [rowsA][ld]
@@ -62,10 +63,18 @@ struct UmmaParams {
     uint32_t *err;
 };
 
-__device__ __forceinline__ void tile_coords(int t, int tilesB, int triangle, int &I, int &J) {
+// Full grids: the operand with more planes should be the one the concurrently
+// resident CTAs share, so that each wave streams it from HBM about once.
+__device__ __forceinline__ void tile_coords(int t, int tilesA, int tilesB, int triangle, int a_fastest, int &I,
+                                            int &J) {
     if (!triangle) {
-        I = t / tilesB;
-        J = t - I * tilesB;
+        if (a_fastest) {
+            J = t / tilesA;
+            I = t - J * tilesA;
+        } else {
+            I = t / tilesB;
+            J = t - I * tilesB;
+        }
         return;
     }
     int i = 0;
@@ -106,7 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int I, J;
-    tile_coords(blockIdx.x, P.tilesB, P.triangle, I, J);
+    tile_coords(blockIdx.x, P.tilesA, P.tilesB, P.triangle, P.a_fastest, I, J);
     const int nchunks = NDRAIN ? (P.nkb + P.chunk - 1) / P.chunk : 1;
 
     if (threadIdx.x == 0) {
@@ -123,66 +132,78 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
-        if (lane == 0) {
+        // The whole warp runs the loop (uniform control flow); lane 0 issues.
+        const uint32_t leader = lane == 0;
+        if (leader) {
             for (int p = 0; p < NA; ++p) prefetch_tmap(&P.mapA[p]);
             for (int p = 0; p < NB; ++p) prefetch_tmap(&P.mapB[p]);
-            int issued = 0;
-            for (int kb = 0; kb < P.nkb; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
-                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                uint8_t *st = smem + s * STAGE_BYTES;
-                for (int p = 0; p < NA; ++p) tma_load_2d(st + p * A_BYTES, &P.mapA[p], &full[s], kb * kKB, I * kTM);
-                for (int p = 0; p < NB; ++p)
-                    tma_load_2d(st + NA * A_BYTES + p * B_BYTES, &P.mapB[p], &full[s], kb * kKB, J * N);
-                issued = kb + 1;
-            }
-            // our own copies must have landed before the CTA tears down
-            for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
         }
+        int issued = 0;
+        for (int kb = 0; kb < P.nkb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
+            mbar_arrive_expect_tx_by(&full[s], STAGE_BYTES, leader);
+            uint8_t *st = smem + s * STAGE_BYTES;
+#pragma unroll
+            for (int p = 0; p < NA; ++p)
+                tma_load_2d_by(st + p * A_BYTES, &P.mapA[p], &full[s], kb * kKB, I * kTM, leader);
+#pragma unroll
+            for (int p = 0; p < NB; ++p)
+                tma_load_2d_by(st + NA * A_BYTES + p * B_BYTES, &P.mapB[p], &full[s], kb * kKB, J * N, leader);
+            issued = kb + 1;
+        }
+        // our own copies must have landed before the CTA tears down
+        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+            mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            int kb = 0;
-            bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                const int b = c & 1;
-                if (NDRAIN && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
-                fence_after_sync();
-                const int kb_end = NDRAIN ? min(P.nkb, (c + 1) * P.chunk) : P.nkb;
-                const int kb_chunk0 = kb;
-                for (; kb < kb_end; ++kb) {
-                    const int s = kb % STAGES;
-                    if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
-                    fence_after_sync();
-                    const uint32_t sbase = smem_u32(smem + s * STAGE_BYTES);
+        // Whole warp in the loop, lane 0 issues. Descriptors are the stage's base
+        // descriptor plus precomputed offsets (start address in 16-byte units in
+        // the low bits; shared addresses stay below 2^18 so no carry leaves them).
+        const uint32_t leader = lane == 0;
+        uint32_t aoff[NP], boff[NP], tcol[NP], drained[NP], first[NP];
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k) {
-#pragma unroll
-                        for (int q = 0; q < NP; ++q) {
-                            const Prod pr = P.prod[q];
-                            const uint64_t ad = sdesc_sw128(sbase + pr.a * A_BYTES + k * 32);
-                            const uint64_t bd = sdesc_sw128(sbase + NA * A_BYTES + pr.b * B_BYTES + k * 32);
-                            uint32_t col, acc;
-                            if (pr.acc < 0) {
-                                col = (uint32_t)(-1 - pr.acc) * N;
-                                acc = (kb == 0 && k == 0 && pr.first) ? 0u : 1u;
-                            } else {
-                                col = RESC + (b * ND + pr.acc) * N;
-                                acc = (kb == kb_chunk0 && k == 0 && pr.first) ? 0u : 1u;
-                            }
-                            mma_f16(tbase + col, ad, bd, IDESC, acc);
-                        }
-                    }
-                    mma_commit(&empty[s]);      // frees the stage once these MMAs are done
-                }
-                if (!ok) break;
-                mma_commit(&tfull[b]);          // chunk (and, last, the resident sums) ready
-            }
-            mma_commit(mdone);
-            mbar_wait(mdone, 0, P.err);
+        for (int q = 0; q < NP; ++q) {
+            const Prod pr = P.prod[q];
+            aoff[q] = (uint32_t)(pr.a * A_BYTES) >> 4;
+            boff[q] = (uint32_t)(NA * A_BYTES + pr.b * B_BYTES) >> 4;
+            drained[q] = pr.acc >= 0;
+            tcol[q] = pr.acc < 0 ? (uint32_t)(-1 - pr.acc) * N : (uint32_t)(RESC + pr.acc * N);
+            first[q] = pr.first;
         }
+        const uint64_t dbase = sdesc_sw128(smem_u32(smem));
+        int kb = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int b = c & 1;
+            if (NDRAIN && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
+            fence_after_sync();
+            const int kb_end = NDRAIN ? min(P.nkb, (c + 1) * P.chunk) : P.nkb;
+            const int kb_chunk0 = kb;
+            const uint32_t cbuf = (uint32_t)(b * ND * N);
+            for (; kb < kb_end; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+                fence_after_sync();
+                const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
+#pragma unroll
+                for (int k = 0; k < kKB / 16; ++k) {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const uint64_t ad = ds + (uint64_t)(aoff[q] + 2 * k);
+                        const uint64_t bd = ds + (uint64_t)(boff[q] + 2 * k);
+                        const uint32_t col = drained[q] ? tcol[q] + cbuf : tcol[q];
+                        const bool restart = first[q] && k == 0 && (drained[q] ? kb == kb_chunk0 : kb == 0);
+                        mma_f16_by(tbase + col, ad, bd, IDESC, restart ? 0u : 1u, leader);
+                    }
+                }
+                mma_commit_by(&empty[s], leader);      // frees the stage once these MMAs are done
+            }
+            if (!ok) break;
+            mma_commit_by(&tfull[b], leader);          // chunk (and, last, the resident sums) ready
+        }
+        mma_commit_by(mdone, leader);
+        mbar_wait(mdone, 0, P.err);
     } else {
         // ---------------------------------------------------------- epilogue
         const int ew = warp - 2;               // 0..7
@@ -190,14 +211,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
         const int half = ew >> 2;              // which half of the columns
         const int row = q * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-        float hi[ND][HC];
-        float lo[ND][FF ? HC : 1];
+        // running sums: FF = float-float pairs packed two columns per register pair
+        constexpr int H2 = HC / 2;
+        uint64_t hi[ND][H2];
+        uint64_t lo[ND][FF ? H2 : 1];
 #pragma unroll
         for (int d = 0; d < ND; ++d)
 #pragma unroll
-            for (int k = 0; k < HC; ++k) {
-                hi[d][k] = 0.f;
-                if (FF) lo[d][FF ? k : 0] = 0.f;
+            for (int k = 0; k < H2; ++k) {
+                hi[d][k] = 0ull;
+                if (FF) lo[d][FF ? k : 0] = 0ull;
             }
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
@@ -213,18 +236,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
                         tmem_ld16(tbase + lane_addr + RESC + (b * ND + d) * N + half * HC + g * 16, r);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const float v = __uint_as_float(r[k]);
-                            if (FF) {
-                                // TwoSum: exact error of hi + v kept in lo
-                                const float s = hi[d][g * 16 + k] + v;
-                                const float bb = s - hi[d][g * 16 + k];
-                                const float e = (hi[d][g * 16 + k] - (s - bb)) + (v - bb);
-                                hi[d][g * 16 + k] = s;
-                                lo[d][FF ? g * 16 + k : 0] += e;
-                            } else {
-                                hi[d][g * 16 + k] += v;
-                            }
+                        for (int k = 0; k < 8; ++k) {
+                            const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+                            if (FF) two_sum2(hi[d][g * 8 + k], lo[d][FF ? g * 8 + k : 0], v);
+                            else hi[d][g * 8 + k] = add2(hi[d][g * 8 + k], v);
                         }
                     }
                 }
@@ -248,12 +263,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
                     tmem_ld16(tbase + lane_addr + rr * N + half * HC + g * 16, r);
                     tmem_ld_wait();
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
+                    for (int k = 0; k < 8; ++k) {
+                        const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
 #pragma unroll
                         for (int dd = 0; dd < ND; ++dd)
                             if (dd == d) {
-                                if (FF) lo[dd][FF ? g * 16 + k : 0] += __uint_as_float(r[k]);
-                                else hi[dd][g * 16 + k] += __uint_as_float(r[k]);
+                                if (FF) lo[dd][FF ? g * 8 + k : 0] = add2(lo[dd][FF ? g * 8 + k : 0], v);
+                                else hi[dd][g * 8 + k] = add2(hi[dd][g * 8 + k], v);
                             }
                     }
                 }
@@ -279,14 +295,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 #pragma unroll
                 for (int d = 0; d < ND; ++d) {
 #pragma unroll
-                    for (int k = 0; k < HC; ++k) {
-                        const int col = J * N + half * HC + k;
-                        if (row_ok && col < P.rowsB) {
-                            double v = (double)hi[d][k];
-                            if (FF) v += (double)lo[d][FF ? k : 0];
-                            const int e = (P.expA[d] ? (int)P.expA[d][gi] : 0) + (P.expB[d] ? (int)P.expB[d][col] : 0);
-                            P.out_drain[d][P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col] =
-                                ldexp(v, -e);
+                    for (int k = 0; k < H2; ++k) {
+                        float h0, h1, l0 = 0.f, l1 = 0.f;
+                        unpk2(hi[d][k], h0, h1);
+                        if (FF) unpk2(lo[d][FF ? k : 0], l0, l1);
+#pragma unroll
+                        for (int e2 = 0; e2 < 2; ++e2) {
+                            const int col = J * N + half * HC + 2 * k + e2;
+                            if (row_ok && col < P.rowsB) {
+                                const double v = (double)(e2 ? h1 : h0) + (double)(e2 ? l1 : l0);
+                                const int e = (P.expA[d] ? (int)P.expA[d][gi] : 0) +
+                                              (P.expB[d] ? (int)P.expB[d][col] : 0);
+                                P.out_drain[d][P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col] =
+                                    ldexp(v, -e);
+                            }
                         }
                     }
                 }
@@ -297,6 +319,197 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
     __syncthreads();
     fence_after_sync();
     if (warp == 1) tmem_dealloc(tbase, TCOLS);
+}
+
+// --------------------------------------------------- stacked contraction --
+//
+// A 0/1 plane (observed mask or one-hot levels) against the five planes M, Xh,
+// Xl, Dh, Dl of kSV B variables stacked into one operand of N = 5 kSV rows:
+// one MMA per 16 samples reads the A tile once for all five sums (five separate
+// N = kSV products would read it five times, more shared-memory traffic than
+// the tensor core's operand path carries). All five blocks of the accumulator
+// restart every chunk and are drained: counts as exact integers, the hi sums by
+// TwoSum into float-float running sums, the lo sums into the low parts.
+constexpr int kSV = 48;            // B variables per tile
+constexpr int kSN = 5 * kSV;       // MMA N
+constexpr int kSPerThread = kSV / 2;
+
+struct StackParams {
+    CUtensorMap mapA;              // 0/1 plane, box 64 x 128
+    CUtensorMap mapB[5];           // M, Xh, Xl, Dh, Dl of the B variables, box 64 x kSV
+    int rowsA, rowsB;              // valid rows of A and B
+    int tilesA, tilesB;
+    int nkb, chunk;                // K-blocks, K-blocks per drain
+    int32_t *out_n;                // counts      [rowsA][ld] (or transposed)
+    double *out_s1, *out_s2;       // sum x~, sum (x~^2 - v)
+    int64_t ld;
+    int out_transpose;
+    const int8_t *exp1, *exp2;     // per-B-row scale exponents of X~ and D
+    uint32_t *err;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_constant__ StackParams P) {
+    constexpr int A_BYTES = kTM * kKB * 2;
+    constexpr int BP_BYTES = kSV * kKB * 2;
+    constexpr int STAGE_BYTES = A_BYTES + 5 * BP_BYTES;
+    static_assert(BP_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "8-row swizzle atoms stay 1024-B aligned");
+    constexpr uint32_t IDESC = idesc_f16_f32(kTM, kSN);
+    constexpr int BUF = 256;       // tensor-memory columns per accumulator buffer (kSN used)
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *mdone = tempty + 2;
+    uint32_t *tslot = (uint32_t *)(mdone + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // consecutive CTAs step through A tiles and share the (five-plane) B tile
+    const int J = blockIdx.x / P.tilesA, I = blockIdx.x - J * P.tilesA;
+    const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
+        mbar_init(mdone, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        const uint32_t leader = lane == 0;
+        if (leader) {
+            prefetch_tmap(&P.mapA);
+            for (int p = 0; p < 5; ++p) prefetch_tmap(&P.mapB[p]);
+        }
+        int issued = 0;
+        for (int kb = 0; kb < P.nkb; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
+            mbar_arrive_expect_tx_by(&full[s], STAGE_BYTES, leader);
+            uint8_t *st = smem + s * STAGE_BYTES;
+            tma_load_2d_by(st, &P.mapA, &full[s], kb * kKB, I * kTM, leader);
+#pragma unroll
+            for (int p = 0; p < 5; ++p)
+                tma_load_2d_by(st + A_BYTES + p * BP_BYTES, &P.mapB[p], &full[s], kb * kKB, J * kSV, leader);
+            issued = kb + 1;
+        }
+        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+            mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        const uint32_t leader = lane == 0;
+        const uint64_t dbase = sdesc_sw128(smem_u32(smem));
+        int kb = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int b = c & 1;
+            if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
+            fence_after_sync();
+            const int kb_end = min(P.nkb, (c + 1) * P.chunk);
+            const int kb_chunk0 = kb;
+            const uint32_t dcol = tbase + (uint32_t)(b * BUF);
+            for (; kb < kb_end; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+                fence_after_sync();
+                const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
+#pragma unroll
+                for (int k = 0; k < kKB / 16; ++k)
+                    mma_f16_by(dcol, ds + (uint64_t)(2 * k), ds + (uint64_t)((A_BYTES >> 4) + 2 * k), IDESC,
+                               (kb == kb_chunk0 && k == 0) ? 0u : 1u, leader);
+                mma_commit_by(&empty[s], leader);
+            }
+            if (!ok) break;
+            mma_commit_by(&tfull[b], leader);
+        }
+        mma_commit_by(mdone, leader);
+        mbar_wait(mdone, 0, P.err);
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int ew = warp - 2;               // 0..7
+        const int q = warp & 3;                // TMEM lane quadrant this warp may access
+        const int h = ew >> 2;                 // which half of the kSV variables
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        constexpr int K2 = kSPerThread / 2;
+        int32_t cnt[kSPerThread];
+        uint64_t s1h[K2], s1l[K2], s2h[K2], s2l[K2];    // packed float-float sums
+#pragma unroll
+        for (int k = 0; k < kSPerThread; ++k) cnt[k] = 0;
+#pragma unroll
+        for (int k = 0; k < K2; ++k) s1h[k] = s1l[k] = s2h[k] = s2l[k] = 0ull;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(&tfull[b], (c >> 1) & 1, P.err)) { ok = false; break; }
+            fence_after_sync();
+            const uint32_t col0 = tbase + lane_addr + (uint32_t)(b * BUF + h * kSPerThread);
+#pragma unroll
+            for (int p = 0; p < 5; ++p) {
+                uint32_t r[kSPerThread];
+#pragma unroll
+                for (int g = 0; g < kSPerThread / 8; ++g) {
+                    uint32_t t8[8];
+                    tmem_ld8(col0 + (uint32_t)(p * kSV + g * 8), t8);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) r[g * 8 + k] = t8[k];
+                }
+                tmem_ld_wait();
+                if (p == 0) {
+#pragma unroll
+                    for (int k = 0; k < kSPerThread; ++k) cnt[k] += (int32_t)__uint_as_float(r[k]);   // exact integers
+                } else {
+#pragma unroll
+                    for (int k = 0; k < K2; ++k) {
+                        const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+                        if (p == 1) two_sum2(s1h[k], s1l[k], v);
+                        else if (p == 2) s1l[k] = add2(s1l[k], v);
+                        else if (p == 3) two_sum2(s2h[k], s2l[k], v);
+                        else s2l[k] = add2(s2l[k], v);
+                    }
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        if (ok) {
+            const int gi = I * kTM + row;
+            if (gi < P.rowsA) {
+#pragma unroll
+                for (int k = 0; k < K2; ++k) {
+                    float a0, a1, b0, b1, c0, c1, d0, d1;
+                    unpk2(s1h[k], a0, a1);
+                    unpk2(s1l[k], b0, b1);
+                    unpk2(s2h[k], c0, c1);
+                    unpk2(s2l[k], d0, d1);
+#pragma unroll
+                    for (int e2 = 0; e2 < 2; ++e2) {
+                        const int col = J * kSV + h * kSPerThread + 2 * k + e2;
+                        if (col < P.rowsB) {
+                            const int64_t o = P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col;
+                            P.out_n[o] = cnt[2 * k + e2];
+                            P.out_s1[o] = ldexp((double)(e2 ? a1 : a0) + (double)(e2 ? b1 : b0), -(int)P.exp1[col]);
+                            P.out_s2[o] = ldexp((double)(e2 ? c1 : c0) + (double)(e2 ? d1 : d0), -(int)P.exp2[col]);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(tbase, 512);
 }
 
 // ------------------------------------------------------------ plane prep --
@@ -464,6 +677,20 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
     return NAPG_OK;
 }
 
+static napg_status launch_stacked(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
+    constexpr int STAGES = 4;
+    constexpr int STAGE_BYTES = kTM * kKB * 2 + 5 * kSV * kKB * 2;
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    auto kern = k_umma_stacked<STAGES>;
+    NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int tiles = P.tilesA * P.tilesB;
+    if (tiles == 0) return NAPG_OK;
+    count_launch();
+    kern<<<tiles, kThreads, smem, st>>>(P);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
 struct ContPlanes {
     __half *M, *Xh, *Xl, *Dh, *Dl;
     int8_t *sexp, *texp;        // per-row scale exponents of X~ and D
@@ -559,33 +786,23 @@ napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const i
         Stage s_(ctx->trace, st, "pearson_moments_tc");
         NAPG_ST((launch_umma<128, 2, 2, 4, 1, 1, true, 3>(ctx, P, T * (T + 1) / 2, st)));
     }
-    // P2: all ordered tiles, N = 64, the mask as the single A operand against
-    // M, X~ and D of the B rows: n = M M^T (resident, exact), and
-    // sum_s m_i x~_j = Sx[j][i], sum_s m_i d_j = D[j][i] (hi drained, lo resident),
-    // written transposed (which also makes the stores coalesced).
+    // P2: all ordered (A tile, B tile) pairs, the mask as A against the stacked
+    // planes of kSV B variables: n = M M^T, sum_s m_i x~_j = Sx[j][i] and
+    // sum_s m_i d_j = D[j][i], written transposed (coalesced stores).
     {
-        constexpr int N2 = 64;
-        UmmaParams<1, 5, 5> P{};
-        if (!make_map(&P.mapA[0], cp.M, cp.rows_pad, cp.S_pad, kTM))
+        StackParams P{};
+        if (!make_map(&P.mapA, cp.M, cp.rows_pad, cp.S_pad, kTM))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
         for (int k = 0; k < 5; ++k)
-            if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, N2))
+            if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, kSV))
                 return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        P.prod[0] = {0, 0, -1, 0};   // M M  -> n (resident 0, integer)
-        P.prod[1] = {0, 1, 0, 0};    // M Xh -> Sx^T hi (drained 0)
-        P.prod[2] = {0, 2, -2, 0};   // M Xl -> lo (resident 1)
-        P.prod[3] = {0, 3, 1, 0};    // M Dh -> D^T hi (drained 1)
-        P.prod[4] = {0, 4, -3, 0};   // M Dl -> lo (resident 2)
-        const int TJ = (nv + N2 - 1) / N2;
-        P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = TJ; P.triangle = 0;
+        P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = (nv + kSV - 1) / kSV;
         P.nkb = nkb; P.chunk = kChunkOther;
-        P.out_drain[0] = Sx; P.out_drain[1] = Sxx; P.ld = nv;
-        P.out_res = nn; P.res_sym = 0; P.out_transpose = 1;
-        P.res_into[1] = 0; P.res_into[2] = 1; P.err = ctx->dev_err;
-        P.expB[0] = cp.sexp; P.expB[1] = cp.texp;
+        P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
+        P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST((launch_umma<N2, 1, 5, 5, 2, 3, true, 3>(ctx, P, T * TJ, st)));
+        NAPG_ST(launch_stacked(ctx, P, st));
     }
     return NAPG_OK;
 }
@@ -598,26 +815,18 @@ napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const 
     __half *H = nullptr;
     int64_t hrows = 0, S_pad = 0;
     NAPG_ST(prep_onehot(ctx, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
-    constexpr int N = 64;
-    UmmaParams<1, 5, 5> P{};
-    if (!make_map(&P.mapA[0], H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+    StackParams P{};
+    if (!make_map(&P.mapA, H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
     const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
     for (int k = 0; k < 5; ++k)
-        if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, N))
+        if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, kSV))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-    P.prod[0] = {0, 0, -1, 0};   // H M  -> n_g (resident 0)
-    P.prod[1] = {0, 1, 0, 0};    // H Xh -> S1 hi (drained 0)
-    P.prod[2] = {0, 2, -2, 0};   // H Xl -> S1 lo (resident 1)
-    P.prod[3] = {0, 3, 1, 0};    // H Dh -> S2 - v n_g, hi (drained 1)
-    P.prod[4] = {0, 4, -3, 0};   // H Dl -> lo (resident 2)
-    const int TI = (int)(hrows / kTM), TJ = (int)((nb + N - 1) / N);
-    P.rowsA = R; P.rowsB = nb; P.tilesA = TI; P.tilesB = TJ; P.triangle = 0;
+    P.rowsA = R; P.rowsB = nb; P.tilesA = (int)(hrows / kTM); P.tilesB = (nb + kSV - 1) / kSV;
     P.nkb = (int)(S_pad / kKB); P.chunk = kChunkOther;
-    P.out_drain[0] = g1; P.out_drain[1] = g2; P.ld = nb;
-    P.out_res = gn; P.res_sym = 0; P.res_into[1] = 0; P.res_into[2] = 1; P.err = ctx->dev_err;
-    P.expB[0] = cp.sexp; P.expB[1] = cp.texp;
+    P.out_n = gn; P.out_s1 = g1; P.out_s2 = g2; P.ld = nb; P.out_transpose = 0;
+    P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
     Stage s_(ctx->trace, st, "groupsum_tc");
-    return launch_umma<N, 1, 5, 5, 2, 3, true, 3>(ctx, P, TI * TJ, st);
+    return launch_stacked(ctx, P, st);
 }
 
 napg_status mixed_contingency(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,

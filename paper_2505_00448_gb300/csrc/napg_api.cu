@@ -655,6 +655,33 @@ napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
     return NAPG_OK;
 }
 
+napg_status napg_debug_pvalues(napg_ctx *ctx, int32_t kind, const double *s, const double *a, const double *b,
+                               int64_t count, double *p) {
+    if (!ctx || count < 0 || kind < 0 || kind > 6) return NAPG_E_ARG;
+    if (count == 0) return NAPG_OK;
+    if (!s || !p || (kind != 4 && !a) || ((kind == 2 || kind == 5) && !b)) return NAPG_E_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t bytes = sizeof(double) * (size_t)count;
+    double *d = nullptr;
+    NAPG_CU(ctx, cudaMalloc(&d, 4 * bytes));
+    double *ds = d, *da = d + count, *db = d + 2 * count, *dp = d + 3 * count;
+    cudaError_t e = cudaMemcpyAsync(ds, s, bytes, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && a) e = cudaMemcpyAsync(da, a, bytes, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(db, b, bytes, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) {
+        launch_debug_pvalues(kind, ds, a ? da : ds, b ? db : ds, count, dp, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "napg_debug_pvalues");
+    return NAPG_OK;
+}
+
 napg_status napg_debug_integers(napg_ctx *ctx, int32_t test, const uint8_t *sample_mask, int32_t a, int32_t b,
                                 int64_t *out, int64_t cap, int64_t *written) {
     if (!ctx || !out || !written) return NAPG_E_ARG;

@@ -134,6 +134,8 @@ napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st);
 namespace napg {
 void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
                        cudaStream_t st);
+void launch_debug_pvalues(int32_t kind, const double *s, const double *a, const double *b, int64_t count, double *p,
+                          cudaStream_t st);
 // prep
 void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int64_t W, double missing,
                          const uint8_t *vtype_dev, const int32_t *nlev_dev, const int32_t *catrow_dev,

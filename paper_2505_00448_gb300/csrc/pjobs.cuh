@@ -7,6 +7,8 @@
 
 #include <cstdint>
 
+#include "specfun.cuh"
+
 namespace napg {
 
 enum PJobKind : int32_t { kPjCorr = 0, kPjT = 1, kPjF = 2, kPjChi2 = 3 };
@@ -15,11 +17,11 @@ struct PJob {
     double s;       // statistic (r, t, F or chi2)
     double a, b;    // n (corr); df (t); d1, d2 (F); df (chi2)
     int64_t idx;    // output index
-    int32_t kind;
+    int32_t kind;   // PJobKind in bits 0-7, key in bits 8 and up once queued
     int32_t mirror; // > 0: also write at the transposed index of an mirror x mirror matrix
 };
 
-constexpr int kPjBins = 128;
+constexpr int kPjBins = 160;
 
 struct PJobQueue {
     PJob *jobs;         // appended by the finalize kernels
@@ -36,7 +38,9 @@ __device__ __forceinline__ int log_bucket(double v) {
     return e < 0 ? 0 : (e > 31 ? 31 : e);
 }
 
-// key: 4 families (beta direct, beta swapped, gamma series, gamma fraction) x 32 buckets
+// key: 5 families x 32 buckets: beta fraction direct / swapped (by the quantity
+// that sets the fraction's length), beta large-a expansion (by 2b), gamma series,
+// gamma fraction. The branch tests mirror sf::ibeta and sf::gamma_q.
 __device__ __forceinline__ int pjob_key(const PJob &j) {
     double a = 0, b = 0, x = 0, y = 0;
     switch (j.kind) {
@@ -45,18 +49,31 @@ __device__ __forceinline__ int pjob_key(const PJob &j) {
         case kPjF: { const double den = j.b + j.a * j.s; a = 0.5 * j.b; b = 0.5 * j.a; x = j.b / den; y = j.a * j.s / den; } break;
         default: {
             const double ga = 0.5 * j.a, gx = 0.5 * j.s;
-            return (gx < ga + 1.0 ? 64 : 96) + log_bucket(gx < ga + 1.0 ? gx : ga / (gx + 1e-300) * 32.0);
+            return (gx < ga + 1.0 ? 96 : 128) + log_bucket(gx < ga + 1.0 ? gx : ga / (gx + 1e-300) * 32.0);
         }
     }
+    if (sf::ibeta_large_a_applies(a, b, x)) return 64 + min(31, (int)(2.0 * b));
     const bool swapped = x > (a + 1.0) / (a + b + 2.0);
     return (swapped ? 32 : 0) + log_bucket(swapped ? b * x : a * y);
 }
 
-__device__ __forceinline__ void pjob_push(const PJobQueue &q, const PJob &j) {
+// Appends a job. Lanes of a warp that push together take their slots with one
+// atomic, and lanes with equal keys add to the histogram with one atomic (all
+// Pearson jobs near the null share a key). The key is kept in the job's kind
+// word (bits 8 and up) for the scatter.
+__device__ __forceinline__ void pjob_push(const PJobQueue &q, PJob j) {
     const int k = pjob_key(j);
-    const int slot = atomicAdd(q.count, 1);
+    j.kind |= k << 8;
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(q.count, __popc(act));
+    base = __shfl_sync(act, base, leader);
+    const int slot = base + __popc(act & ((1u << lane) - 1u));
     if (slot < q.capacity) q.jobs[slot] = j;
-    atomicAdd(&q.hist[k], 1);
+    const unsigned same = __match_any_sync(act, k);
+    if (lane == __ffs(same) - 1) atomicAdd(&q.hist[k], __popc(same));
 }
 
 }  // namespace napg

@@ -13,9 +13,13 @@
 //    Stirling remainder Delta(.) (DLMF 5.11.1, Bernoulli series) and
 //    rlog1(z) = z - log(1+z), which keeps full precision for large degrees of
 //    freedom.
+//  * For a >= 20, b <= 32 (integer or half-integer) and x >= 1/2, an
+//    expansion of the integrand in w = -ln t around the Gamma(b) limit
+//    (the idea of DiDonato & Morris's large-a expansion, derived in full at
+//    ibeta_large_a): a few terms in 1/T^2 replace about sqrt(a) fraction steps.
 //  * Q(a,x): series of DLMF 8.7.1 for x < a+1, Legendre's continued fraction
 //    (DLMF 8.9.2, even part) otherwise, with the same scaled prefactor.
-// CUDA's own lgamma/log/log1p/exp/erfc/sqrt are called, never re-implemented.
+// CUDA's own lgamma/log/log1p/exp/erfc/erfcx/sqrt are called, never re-implemented.
 #pragma once
 
 #include <math.h>
@@ -25,7 +29,7 @@ namespace sf {
 
 // log Gamma(k/2), k = 1..40, from Gamma(n) = (n-1)! and
 // Gamma(n + 1/2) = (2n)! sqrt(pi) / (4^n n!) (evaluated to 40 digits, rounded).
-__constant__ double kLogGammaHalf[40] = {
+static __constant__ double kLogGammaHalf[40] = {
     0.5723649429247001,
     0.0,
     -0.12078223763524522,
@@ -75,11 +79,10 @@ __device__ __forceinline__ double lgamma_fast(double a) {
     return lgamma(a);
 }
 
-__device__ __forceinline__ double stirling_rem(double a) {
-    // Delta(a) = lgamma(a) - ((a - 1/2) log a - a + log(2 pi)/2)
-    if (a < 10.0) return lgamma_fast(a) - ((a - 0.5) * log(a) - a + 0.91893853320467274178);
-    const double inv = 1.0 / a, q = inv * inv;
-    // Bernoulli terms B_{2k} / (2k (2k-1) a^{2k-1}), k = 1..6
+// Delta(a) = lgamma(a) - ((a - 1/2) log a - a + log(2 pi)/2) for a >= 10 from
+// inv = 1/a: Bernoulli terms B_{2k} / (2k (2k-1) a^{2k-1}), k = 1..6
+__device__ __forceinline__ double stirling_series(double inv) {
+    const double q = inv * inv;
     double s = -691.0 / 360360.0;
     s = s * q + 1.0 / 1188.0;
     s = s * q - 1.0 / 1680.0;
@@ -87,6 +90,11 @@ __device__ __forceinline__ double stirling_rem(double a) {
     s = s * q - 1.0 / 360.0;
     s = s * q + 1.0 / 12.0;
     return s * inv;
+}
+
+__device__ __forceinline__ double stirling_rem(double a) {
+    if (a < 10.0) return lgamma_fast(a) - ((a - 0.5) * log(a) - a + 0.91893853320467274178);
+    return stirling_series(1.0 / a);
 }
 
 __device__ __forceinline__ double rlog1(double z) {
@@ -184,8 +192,115 @@ static __device__ double cf_even(double a, double b, double x, double y) {
 }
 
 static __device__ double ibeta_lower(double a, double b, double x, double y) {
+    const double pf = beta_prefactor(a, b, x, y);
+    if (pf == 0.0) return 0.0;   // underflowed: the (bounded) fraction cannot lift it
     const double cf = (a >= b) ? cf_even(a, b, x, y) : cf_plain(a, b, x);
-    return beta_prefactor(a, b, x, y) / a * cf;
+    return pf / a * cf;
+}
+
+// k e_k = (-1)^(k+1) zeta(2k) / (2 pi)^(2k), k = 1..20: the Taylor coefficients
+// of (d/ds) s log(sinh(w/2)/(w/2)) in s = w^2 (B_2k = (-1)^(k+1) 2 (2k)! zeta(2k)
+// / (2 pi)^(2k)); evaluated to 40 digits, rounded.
+static __constant__ double kSinhLogCoef[20] = {
+    4.1666666666666667e-2, -6.9444444444444444e-4, 1.6534391534391534e-5, -4.1335978835978836e-7,
+    1.0438378493934049e-8, -2.6420950693437466e-10, 6.6912682653423394e-12, -1.6948401481612914e-13,
+    4.2930310281389223e-15, -1.0874343492790309e-16, 2.7545014141801148e-18, -6.9772323429062617e-20,
+    1.7673535198147337e-21, -4.4767587135187734e-23, 1.1339762261688415e-24, -2.8723953344361012e-26,
+    7.2758623780743245e-28, -1.8429974703326551e-29, 4.6683671285475223e-31, -1.182511207850315e-32};
+
+// The expansion below applies to I_x(a,b) with a large, b a moderate integer or
+// half-integer and x >= 1/2 (the p-values of t, F and r near the null, where the
+// continued fraction needs about sqrt(a) steps).
+__device__ __forceinline__ bool ibeta_large_a_applies(double a, double b, double x) {
+    return x >= 0.5 && a >= 20.0 && b <= 32.0 && b <= a && 2.0 * b == floor(2.0 * b);
+}
+
+// I_x(a,b) for large a. With t = e^-w the integrand of I_x is
+// e^{-T w} w^{b-1} phi(w), T = a + (b-1)/2, phi(w) = (sinh(w/2)/(w/2))^{b-1}
+// (even in w). Expanding phi = sum_k g_k w^{2k} and integrating term by term
+// from w0 = -ln x gives
+//   I_x(a,b) = M sum_k g_k (b)_{2k} Q(b+2k, u) / T^{2k},  u = T w0,
+//   M = Gamma(a+b) / (Gamma(a) T^b) = 1 + O(1/T^2),
+// an expansion in 1/T^2 (and, in the tail, a convergent series in (w0/2pi)^2).
+// phi = exp((b-1) sum_k e_k w^{2k}) gives g_n = ((b-1)/n) sum_{k<=n} k e_k g_{n-k}.
+// Q(b+j, u) climbs from Q(1/2,u) = erfc(sqrt u) or Q(1,u) = e^-u by
+// Q(s+1,u) = Q(s,u) + e^-u u^s / Gamma(s+1); the ladder is kept scaled by e^u
+// (erfcx) so that it does not underflow before the final product.
+// 2/m, m = 1..160 (entry 0 unused): 1/s for the half-integer steps s = m/2 of
+// the ladder below, correctly rounded
+static __constant__ double kInvHalf[161] = {
+    0.0, 2.0, 1.0, 0.6666666666666666, 0.5, 0.4, 0.3333333333333333, 0.2857142857142857,
+    0.25, 0.2222222222222222, 0.2, 0.18181818181818182, 0.16666666666666666, 0.15384615384615385, 0.14285714285714285, 0.13333333333333333,
+    0.125, 0.11764705882352941, 0.1111111111111111, 0.10526315789473684, 0.1, 0.09523809523809523, 0.09090909090909091, 0.08695652173913043,
+    0.08333333333333333, 0.08, 0.07692307692307693, 0.07407407407407407, 0.07142857142857142, 0.06896551724137931, 0.06666666666666667, 0.06451612903225806,
+    0.0625, 0.06060606060606061, 0.058823529411764705, 0.05714285714285714, 0.05555555555555555, 0.05405405405405406, 0.05263157894736842, 0.05128205128205128,
+    0.05, 0.04878048780487805, 0.047619047619047616, 0.046511627906976744, 0.045454545454545456, 0.044444444444444446, 0.043478260869565216, 0.0425531914893617,
+    0.041666666666666664, 0.04081632653061224, 0.04, 0.0392156862745098, 0.038461538461538464, 0.03773584905660377, 0.037037037037037035, 0.03636363636363636,
+    0.03571428571428571, 0.03508771929824561, 0.034482758620689655, 0.03389830508474576, 0.03333333333333333, 0.03278688524590164, 0.03225806451612903, 0.031746031746031744,
+    0.03125, 0.03076923076923077, 0.030303030303030304, 0.029850746268656716, 0.029411764705882353, 0.028985507246376812, 0.02857142857142857, 0.028169014084507043,
+    0.027777777777777776, 0.0273972602739726, 0.02702702702702703, 0.02666666666666667, 0.02631578947368421, 0.025974025974025976, 0.02564102564102564, 0.02531645569620253,
+    0.025, 0.024691358024691357, 0.024390243902439025, 0.024096385542168676, 0.023809523809523808, 0.023529411764705882, 0.023255813953488372, 0.022988505747126436,
+    0.022727272727272728, 0.02247191011235955, 0.022222222222222223, 0.02197802197802198, 0.021739130434782608, 0.021505376344086023, 0.02127659574468085, 0.021052631578947368,
+    0.020833333333333332, 0.020618556701030927, 0.02040816326530612, 0.020202020202020204, 0.02, 0.019801980198019802, 0.0196078431372549, 0.019417475728155338,
+    0.019230769230769232, 0.01904761904761905, 0.018867924528301886, 0.018691588785046728, 0.018518518518518517, 0.01834862385321101, 0.01818181818181818, 0.018018018018018018,
+    0.017857142857142856, 0.017699115044247787, 0.017543859649122806, 0.017391304347826087, 0.017241379310344827, 0.017094017094017096, 0.01694915254237288, 0.01680672268907563,
+    0.016666666666666666, 0.01652892561983471, 0.01639344262295082, 0.016260162601626018, 0.016129032258064516, 0.016, 0.015873015873015872, 0.015748031496062992,
+    0.015625, 0.015503875968992248, 0.015384615384615385, 0.015267175572519083, 0.015151515151515152, 0.015037593984962405, 0.014925373134328358, 0.014814814814814815,
+    0.014705882352941176, 0.014598540145985401, 0.014492753623188406, 0.014388489208633094, 0.014285714285714285, 0.014184397163120567, 0.014084507042253521, 0.013986013986013986,
+    0.013888888888888888, 0.013793103448275862, 0.0136986301369863, 0.013605442176870748, 0.013513513513513514, 0.013422818791946308, 0.013333333333333334, 0.013245033112582781,
+    0.013157894736842105, 0.013071895424836602, 0.012987012987012988, 0.012903225806451613, 0.01282051282051282, 0.012738853503184714, 0.012658227848101266, 0.012578616352201259,
+    0.0125};
+
+static __device__ double ibeta_large_a(double a, double b, double x, double y) {
+    const double T = a + 0.5 * (b - 1.0);
+    const double u = -T * ((x <= 0.5) ? log(x) : log1p(-y));
+    // the result is below the smallest subnormal: p <= 2 e^-u u^(b+41)
+    if (u > 700.0 && u - (b + 41.0) * log(u) > 760.0) return 0.0;
+    // log M from the Stirling forms of log Gamma(a+b) and log Gamma(a)
+    const double inv_a = 1.0 / a;
+    const double logM = (a + b - 0.5) * log1p(b * inv_a) - b * log1p((b - 1.0) * 0.5 * inv_a) - b
+                        + stirling_series(1.0 / (a + b)) - stirling_series(inv_a);
+    int m;             // 2 s
+    double Q, th;      // Q = e^u Q(s,u), th = u^s / Gamma(s+1)
+    if (b == floor(b)) {
+        m = 2; Q = 1.0; th = u;
+    } else {
+        const double su = sqrt(u);
+        m = 1; Q = erfcx(su); th = su * 1.1283791670955125739;   // sqrt(u) / Gamma(3/2)
+    }
+    const int mb = (int)(2.0 * b);
+    while (m < mb) {
+        Q += th;
+        m += 2;
+        th *= u * kInvHalf[m];
+    }
+    const double beta = b - 1.0, invT2 = 1.0 / (T * T);
+    double g[21];
+    g[0] = 1.0;
+    double sum = Q, poch = 1.0, pw = 1.0;
+    int small = 0;
+#pragma unroll
+    for (int k = 1; k <= 20; ++k) {
+        Q += th; m += 2; th *= u * kInvHalf[m];
+        Q += th; m += 2; th *= u * kInvHalf[m];
+        poch *= (b + (double)(2 * k - 2)) * (b + (double)(2 * k - 1));
+        pw *= invT2;
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 1; i <= k; ++i) acc = fma(kSinhLogCoef[i - 1], g[k - i], acc);
+        g[k] = beta * acc * (1.0 / (double)k);
+        const double term = g[k] * poch * pw * Q;
+        sum += term;
+        // two consecutive negligible terms (a single g_k can vanish for some b)
+        if (fabs(term) <= 1e-17 * fabs(sum)) {
+            if (++small == 2) break;
+        } else {
+            small = 0;
+        }
+    }
+    const double e = logM - u;
+    if (e > -700.0) return exp(e) * sum;
+    return exp(e + log(sum));
 }
 
 // regularized I_x(a,b) with x + y = 1 supplied
@@ -193,6 +308,7 @@ static __device__ double ibeta(double a, double b, double x, double y) {
     if (!(a > 0.0) || !(b > 0.0) || isnan(x) || isnan(y)) return nan("");
     if (x <= 0.0) return 0.0;
     if (y <= 0.0) return 1.0;
+    if (ibeta_large_a_applies(a, b, x)) return ibeta_large_a(a, b, x, y);
     if (x > (a + 1.0) / (a + b + 2.0)) return 1.0 - ibeta_lower(b, a, y, x);
     return ibeta_lower(a, b, x, y);
 }
@@ -217,6 +333,8 @@ static __device__ double gamma_q(double a, double x) {
         }
         return 1.0 - gamma_prefactor(a, x) / a * sum;
     }
+    const double pf = gamma_prefactor(a, x);
+    if (pf == 0.0) return 0.0;
     double f = kTiny, C = kTiny, D = 0.0;
     for (int n = 1; n < kMaxIter; ++n) {
         const double an = (n == 1) ? 1.0 : -(double)(n - 1) * ((double)(n - 1) - a);
@@ -230,7 +348,7 @@ static __device__ double gamma_q(double a, double x) {
         f *= del;
         if (fabs(del - 1.0) < 1e-15) break;
     }
-    return gamma_prefactor(a, x) * f;
+    return pf * f;
 }
 
 // two-sided p of Student t with df degrees of freedom

@@ -27,7 +27,7 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 
 # every symbol include/napg.h declares
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync",
-           "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_serve_start",
+           "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_debug_pvalues", "napg_serve_start",
            "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version", "napg_trace_enable",
            "napg_trace_read", "napg_kernel_launches", "napg_pearson_fp64_noalloc"]
 
@@ -66,6 +66,8 @@ def _load():
     L.napg_run_batch.restype = C.c_int
     L.napg_debug_integers.argtypes = [p, i32, p, i32, i32, p, i64, p]
     L.napg_debug_integers.restype = C.c_int
+    L.napg_debug_pvalues.argtypes = [p, i32, p, p, p, i64, p]
+    L.napg_debug_pvalues.restype = C.c_int
     L.napg_serve_start.argtypes = [p, C.c_size_t, i32]
     L.napg_serve_start.restype = C.c_int
     L.napg_serve_submit.argtypes = [p, p, p]
@@ -248,6 +250,18 @@ class Context:
         m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
         self._check(lib.napg_debug_integers(self.h, t, _ptr(m), int(a), int(b), _ptr(out), len(out), C.byref(w)))
         return out[:w.value].copy()
+
+    PVALUE_KINDS = {"corr": 0, "t": 1, "f": 2, "chi2": 3, "norm": 4, "ibeta": 5, "gamma_q": 6}
+
+    def debug_pvalues(self, kind, s, a=None, b=None):
+        """The device p-value functions on given values (host float64 arrays)."""
+        k = self.PVALUE_KINDS[kind] if isinstance(kind, str) else int(kind)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        a = None if a is None else np.ascontiguousarray(np.broadcast_to(a, s.shape), dtype=np.float64)
+        b = None if b is None else np.ascontiguousarray(np.broadcast_to(b, s.shape), dtype=np.float64)
+        out = np.empty_like(s)
+        self._check(lib.napg_debug_pvalues(self.h, k, _ptr(s), _ptr(a), _ptr(b), s.size, _ptr(out)))
+        return out
 
 
 def version() -> str:
