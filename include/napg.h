@@ -119,6 +119,13 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
                              int64_t n_samples, int32_t samples_major, double missing,
                              const uint8_t *var_type, const int32_t *n_levels);
 
+/* Marks the context's derived data stale: the FP16 planes kept from the last
+ * run without a sample context (reused by the next run on the same continuous
+ * variables) and the presort of the continuous variables (Sec. 3.5.3: sorted once
+ * per feature). The next run rebuilds what it needs; buffers are kept for reuse.
+ * Errors: NAPG_E_ARG (NULL context). */
+napg_status napg_release_cache(napg_ctx *ctx);
+
 /* Runs one test over all pairs vars_a x vars_b of the loaded cohort.
  *   test         napg_test.
  *   opt          options, or NULL for the defaults.

@@ -9,6 +9,11 @@
 namespace napg {
 
 __device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000000000000LL); }
+
+// Mixed form: the planes carry 22 bits relative to each row's largest value;
+// over few co-observed samples the centred sums can cancel without the errors
+// averaging out, so such pairs are recomputed exactly (cheap at that size).
+constexpr int32_t kMixedMinN = 64;
 __device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 
 __device__ __forceinline__ void put(double *stat, double *pval, int32_t *nout, int64_t idx, double s, double p,
@@ -39,11 +44,14 @@ __global__ void k_finalize_pearson(PearsonFin f, double *stat, double *pval, int
             const double sxx = f.vsq ? f.Sxx[ij] + f.vsq[i] * nd : f.Sxx[ij];
             const double syy = f.vsq ? f.Sxx[ji] + f.vsq[j] * nd : f.Sxx[ji];
             const double cxx = sxx - sx * sx / nd, cyy = syy - sy * sy / nd, cxy = sxy - sx * sy / nd;
-            if (!(cxx > f.rel_tol * sxx) || !(cyy > f.rel_tol * syy)) {
+            if (!(cxx > f.rel_tol * sxx) || !(cyy > f.rel_tol * syy) || (f.vsq && n < kMixedMinN)) {
                 const int q = atomicAdd(nflag, 1);
                 flags[q] = (int32_t)ij;
             } else {
-                r = cxy / (sqrt(cxx) * sqrt(cyy));
+                // a variable against itself: r = 1 exactly, as the two-pass
+                // definition gives (its centred cross sum is its sum of squares)
+                const bool same = f.vars ? f.vars[i] == f.vars[j] : i == j;
+                r = same ? 1.0 : cxy / (sqrt(cxx) * sqrt(cyy));
                 r = fmin(1.0, fmax(-1.0, r));
                 if (n <= 2) p = dnan();
                 else if (fabs(r) >= 1.0) p = 0.0;
@@ -102,7 +110,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     ssb += ng * (mg - gm) * (mg - gm);
                     ssw += s2 - f.g1[idx] * mg;
                 }
-                if (!(ssw > f.rel_tol * raw)) {
+                if (!(ssw > f.rel_tol * raw) || (f.vsq && n < kMixedMinN)) {
                     flags[atomicAdd(nflag, 1)] = (int32_t)t;
                 } else {
                     const double d1 = (double)(k - 1), d2 = (double)(n - k);
@@ -118,7 +126,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 const double r0 = f.g2[i0] + (f.vsq ? f.vsq[j] * (double)n0 : 0.0);
                 const double r1 = f.g2[i1] + (f.vsq ? f.vsq[j] * (double)n1 : 0.0);
                 const double q0 = r0 - f.g1[i0] * m0, q1 = r1 - f.g1[i1] * m1;
-                if (!(q0 > f.rel_tol * r0) || !(q1 > f.rel_tol * r1)) {
+                if (!(q0 > f.rel_tol * r0) || !(q1 > f.rel_tol * r1) || (f.vsq && n < kMixedMinN)) {
                     flags[atomicAdd(nflag, 1)] = (int32_t)t;
                 } else if (f.welch) {
                     const double e0 = q0 / (double)(n0 - 1) / (double)n0, e1 = q1 / (double)(n1 - 1) / (double)n1;
@@ -222,7 +230,9 @@ __global__ void k_finalize_spearman(SpearmanFin f, double *stat, double *pval, i
             const __int128 da = (__int128)n * q[2] - K * K;
             const __int128 db = (__int128)n * q[3] - K * K;
             if (da > 0 && db > 0) {
-                r = (double)num / (sqrt((double)da) * sqrt((double)db));
+                // identical or reversed rankings (|rho| = 1) decided exactly in integers
+                if (da == db && (num == da || num == -da)) r = num > 0 ? 1.0 : -1.0;
+                else r = (double)num / (sqrt((double)da) * sqrt((double)db));
                 r = fmin(1.0, fmax(-1.0, r));
                 if (n <= 2) p = dnan();
                 else if (fabs(r) >= 1.0) p = 0.0;
@@ -356,7 +366,7 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
                     const double dx = xval(r, (int64_t)va * r.S + k) - mx, dy = xval(r, (int64_t)vb * r.S + k) - my;
                     sxx += dx * dx; syy += dy * dy; sxy += dx * dy;
                 }
-                s = fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
+                s = (va == vb) ? 1.0 : fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
                 p = (n <= 2) ? dnan() : sf::corr_p(s, (double)n);
             }
             put(stat, pval, nout, t, s, p, (int32_t)n);
@@ -503,7 +513,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                     sxx += dx * dx; syy += dy * dy; sxy += dx * dy;
                 }
                 sxx = block_reduce(sxx, 0, sh); syy = block_reduce(syy, 0, sh); sxy = block_reduce(sxy, 0, sh);
-                s = fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
+                s = (va == vb) ? 1.0 : fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
                 if (threadIdx.x == 0) p = (ni <= 2) ? dnan() : sf::corr_p(s, n);
             }
             if (threadIdx.x == 0) {

@@ -697,10 +697,10 @@ struct ContPlanes {
     int64_t rows_pad, S_pad;
 };
 
-static napg_status prep_cont_planes(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev,
-                                    int32_t nv, const uint32_t *obsv, int first_slot, double *shift, double *vsq,
-                                    ContPlanes &cp) {
-    Cohort &c = ctx->coh;
+static napg_status prep_cont_planes(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st,
+                                    const int32_t *vars_dev, int32_t nv, const uint32_t *obsv, int first_slot,
+                                    double *shift, double *vsq, ContPlanes &cp,
+                                    const std::vector<int32_t> *cache_vars) {
     cp.S_pad = ((c.S + kKB - 1) / kKB) * kKB;
     cp.rows_pad = ((nv + kTM - 1) / kTM) * kTM;
     const size_t plane = sizeof(__half) * (size_t)cp.rows_pad * (size_t)cp.S_pad;
@@ -712,25 +712,39 @@ static napg_status prep_cont_planes(napg_ctx *ctx, Workspace &ws, cudaStream_t s
     }
     cp.M = pl[0]; cp.Xh = pl[1]; cp.Xl = pl[2]; cp.Dh = pl[3]; cp.Dl = pl[4];
     cp.sexp = (int8_t *)ws_get(ctx, ws, Workspace::kExp, 2 * (size_t)cp.rows_pad, &st_);
+    double *pshift = (double *)ws_get(ctx, ws, Workspace::kPlShift, sizeof(double) * (size_t)nv, &st_);
+    double *pvsq = (double *)ws_get(ctx, ws, Workspace::kPlVsq, sizeof(double) * (size_t)nv, &st_);
     if (st_) return st_;
     cp.texp = cp.sexp + cp.rows_pad;
-    Stage s_(ctx->trace, st, "planes_f16");
-    count_launch();
-    if (c.dtype == NAPG_F32)
-        k_planes_cont<float><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const float *)c.X, c.S, cp.S_pad, vars_dev, nv,
-                                                                    obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl,
-                                                                    shift, vsq, cp.sexp, cp.texp);
-    else
-        k_planes_cont<double><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const double *)c.X, c.S, cp.S_pad, vars_dev, nv,
-                                                                     obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl,
-                                                                     shift, vsq, cp.sexp, cp.texp);
-    NAPG_CU(ctx, cudaGetLastError());
+    Workspace::PlaneKey &key = ws.plane_key;
+    const bool hit = cache_vars && first_slot == Workspace::kTmpA && key.valid && key.gen == c.gen &&
+                     key.vars == *cache_vars;
+    if (!hit) {
+        key.valid = false;
+        Stage s_(ctx->trace, st, "planes_f16");
+        count_launch();
+        if (c.dtype == NAPG_F32)
+            k_planes_cont<float><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const float *)c.X, c.S, cp.S_pad, vars_dev,
+                                                                        nv, obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh,
+                                                                        cp.Dl, pshift, pvsq, cp.sexp, cp.texp);
+        else
+            k_planes_cont<double><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const double *)c.X, c.S, cp.S_pad,
+                                                                         vars_dev, nv, obsv, c.W, cp.M, cp.Xh, cp.Xl,
+                                                                         cp.Dh, cp.Dl, pshift, pvsq, cp.sexp, cp.texp);
+        NAPG_CU(ctx, cudaGetLastError());
+        if (cache_vars && first_slot == Workspace::kTmpA) {
+            key.valid = true;
+            key.gen = c.gen;
+            key.vars = *cache_vars;
+        }
+    }
+    NAPG_CU(ctx, cudaMemcpyAsync(shift, pshift, sizeof(double) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
+    NAPG_CU(ctx, cudaMemcpyAsync(vsq, pvsq, sizeof(double) * (size_t)nv, cudaMemcpyDeviceToDevice, st));
     return NAPG_OK;
 }
 
-static napg_status prep_onehot(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
-                               int slot, __half **H, int64_t &rows_pad, int64_t &S_pad) {
-    Cohort &c = ctx->coh;
+static napg_status prep_onehot(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
+                               int32_t R, int slot, __half **H, int64_t &rows_pad, int64_t &S_pad) {
     S_pad = ((c.S + kKB - 1) / kKB) * kKB;
     rows_pad = ((R + kTM - 1) / kTM) * kTM;
     napg_status st_ = NAPG_OK;
@@ -752,11 +766,11 @@ static napg_status prep_onehot(napg_ctx *ctx, Workspace &ws, cudaStream_t st, co
 constexpr int kChunkSxy = 1;
 constexpr int kChunkOther = 4;
 
-napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
+napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
-                          double *vsq) {
+                          double *vsq, const std::vector<int32_t> *cache_vars) {
     ContPlanes cp;
-    NAPG_ST(prep_cont_planes(ctx, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp));
+    NAPG_ST(prep_cont_planes(ctx, c, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp, cache_vars));
     const int nkb = (int)(cp.S_pad / kKB);
     const int T = (int)(cp.rows_pad / kTM);
     // P1: triangle tiles, N = 128, Sxy only. The hi*hi product alone is
@@ -807,14 +821,14 @@ napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const i
     return NAPG_OK;
 }
 
-napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                            const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn, double *g1,
-                           double *g2, double *shift, double *vsq) {
+                           double *g2, double *shift, double *vsq, const std::vector<int32_t> *cache_vars) {
     ContPlanes cp;
-    NAPG_ST(prep_cont_planes(ctx, ws, st, vars_b_dev, nb, obsb, Workspace::kTmpA, shift, vsq, cp));
+    NAPG_ST(prep_cont_planes(ctx, c, ws, st, vars_b_dev, nb, obsb, Workspace::kTmpA, shift, vsq, cp, cache_vars));
     __half *H = nullptr;
     int64_t hrows = 0, S_pad = 0;
-    NAPG_ST(prep_onehot(ctx, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+    NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
     StackParams P{};
     if (!make_map(&P.mapA, H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
     const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
@@ -829,11 +843,11 @@ napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const 
     return launch_stacked(ctx, P, st);
 }
 
-napg_status mixed_contingency(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                               int32_t *T) {
     __half *H = nullptr;
     int64_t hrows = 0, S_pad = 0;
-    NAPG_ST(prep_onehot(ctx, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+    NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
     UmmaParams<1, 1, 1> P{};
     if (!make_map(&P.mapA[0], H, hrows, S_pad, kTM) || !make_map(&P.mapB[0], H, hrows, S_pad, 128))
         return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");

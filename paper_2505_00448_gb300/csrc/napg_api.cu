@@ -2,12 +2,18 @@
 // per-test pipelines (bitmasks -> contraction or rank kernel -> finalize ->
 // exact rescue), all ordered on one CUDA stream.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
 
 #include "napg_internal.cuh"
 
 namespace napg {
+
+uint64_t next_cohort_gen() {
+    static std::atomic<uint64_t> g{0};
+    return ++g;
+}
 
 napg_status fail(napg_ctx *ctx, napg_status code, const std::string &msg) {
     if (ctx) ctx->err = msg;
@@ -23,6 +29,7 @@ napg_status cuda_fail(napg_ctx *ctx, cudaError_t e, const char *what) {
 void *ws_get(napg_ctx *ctx, Workspace &ws, int slot, size_t bytes, napg_status *st) {
     bytes = ((std::max<size_t>(bytes, 16) + 255) / 256) * 256;
     if (ws.cap[slot] >= bytes) return ws.ptr[slot];
+    if (Workspace::plane_slot(slot)) ws.plane_key.valid = false;
     if (ws.ptr[slot]) {
         cudaFree(ws.ptr[slot]);
         ws.ptr[slot] = nullptr;
@@ -50,10 +57,12 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static void free_cohort(Cohort &c) {
-    void *ptrs[] = {c.X, c.obs, c.lab, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
+void free_cohort(Cohort &c) {
+    void *ptrs[] = {c.X, c.obs, c.lab, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, c.cont_vars_dev};
+    if (c.owns) {
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
     c = Cohort();
 }
 
@@ -78,8 +87,8 @@ struct HostLists {
     int32_t R = 0, maxlev = 0;
 };
 
-static napg_status check_vars(napg_ctx *ctx, const RunArgs &a, bool *symmetric) {
-    const Cohort &c = ctx->coh;
+napg_status check_run_vars(napg_ctx *ctx, const RunArgs &a, bool *symmetric) {
+    const Cohort &c = a.coh ? *a.coh : ctx->coh;
     const int t = a.test;
     if (t < NAPG_PEARSON || t > NAPG_KRUSKAL) return fail(ctx, NAPG_E_ARG, "unknown test");
     if (a.na < 0 || a.nb < 0 || (a.na > 0 && !a.va)) return fail(ctx, NAPG_E_ARG, "bad variable list");
@@ -151,33 +160,35 @@ __global__ void k_gather_block(const double *sstat, const double *sp, const int3
 
 // ------------------------------------------------------------ run pipeline --
 
-napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st) {
-    Cohort &c = ctx->coh;
+// Presort of every continuous variable of `c`: stream-ordered, no host
+// synchronisation; the arrays are allocated (or grown) only when too small, so a
+// run whose sizes were seen before makes no allocation (graph capture relies on it).
+napg_status ensure_presort(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st) {
     if (c.sorted || c.n_cont == 0) {
         c.sorted = true;
         return NAPG_OK;
     }
     const int64_t nc = c.n_cont, S = c.S, W = c.W;
-    NAPG_CU(ctx, cudaMalloc(&c.perm, sizeof(int32_t) * nc * S));
-    NAPG_CU(ctx, cudaMalloc(&c.pos, sizeof(int32_t) * nc * S));
-    NAPG_CU(ctx, cudaMalloc(&c.nobs, sizeof(int32_t) * nc));
-    NAPG_CU(ctx, cudaMalloc(&c.tie, sizeof(uint32_t) * nc * W));
-    NAPG_CU(ctx, cudaMalloc(&c.gsw, sizeof(int32_t) * nc * W));
-    NAPG_CU(ctx, cudaMalloc(&c.gew, sizeof(int32_t) * nc * W));
-    std::vector<int32_t> cv;
-    for (int64_t v = 0; v < c.F; ++v)
-        if (c.vtype[v] == 0) cv.push_back((int32_t)v);
-    int32_t *dcv = nullptr;
-    NAPG_CU(ctx, cudaMalloc(&dcv, sizeof(int32_t) * cv.size()));
-    NAPG_CU(ctx, cudaMemcpyAsync(dcv, cv.data(), sizeof(int32_t) * cv.size(), cudaMemcpyHostToDevice, st));
+    if (c.presort_cap < S) {
+        if (!c.owns) return fail(ctx, NAPG_E_ARG, "presort arrays of a borrowed cohort are too small");
+        void *old[] = {c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew};
+        for (void *p : old)
+            if (p) cudaFree(p);
+        const int64_t Wc = (S + 31) / 32;
+        NAPG_CU(ctx, cudaMalloc(&c.perm, sizeof(int32_t) * nc * S));
+        NAPG_CU(ctx, cudaMalloc(&c.pos, sizeof(int32_t) * nc * S));
+        NAPG_CU(ctx, cudaMalloc(&c.nobs, sizeof(int32_t) * nc));
+        NAPG_CU(ctx, cudaMalloc(&c.tie, sizeof(uint32_t) * nc * Wc));
+        NAPG_CU(ctx, cudaMalloc(&c.gsw, sizeof(int32_t) * nc * Wc));
+        NAPG_CU(ctx, cudaMalloc(&c.gew, sizeof(int32_t) * nc * Wc));
+        c.presort_cap = S;
+    }
     const size_t tb = presort_tmp_bytes(S, (int32_t)nc);
-    void *tmp = nullptr;
-    NAPG_CU(ctx, cudaMalloc(&tmp, tb));
-    { Stage s_(ctx->trace, st, "presort"); launch_presort(c.X, c.dtype, S, W, dcv, (int32_t)nc, c.obs, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, tmp, tb, st); }
+    napg_status st_ = NAPG_OK;
+    void *tmp = ws_get(ctx, ws, Workspace::kPresortTmp, tb, &st_);
+    if (st_) return st_;
+    { Stage s_(ctx->trace, st, "presort"); launch_presort(c.X, c.dtype, S, W, c.cont_vars_dev, (int32_t)nc, c.obs, c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, tmp, tb, st); }
     NAPG_CU(ctx, cudaGetLastError());
-    NAPG_CU(ctx, cudaStreamSynchronize(st));
-    cudaFree(tmp);
-    cudaFree(dcv);
     c.sorted = true;
     return NAPG_OK;
 }
@@ -214,6 +225,38 @@ static void pjobs_run(napg_ctx *ctx, const PJobBufs &b, double *pval, cudaStream
     launch_pjobs_eval(b.q, b.sorted, b.offs, b.cursor, pval, st);
 }
 
+// Host lists of one run, concatenated as they are staged on the device:
+// [va | vb | crow_a | crow_b | catrow | nlev | levoff] with their offsets.
+void var_lists(const Cohort &c, const RunArgs &a, bool symmetric, std::vector<int32_t> &va,
+               std::vector<int32_t> &vb, std::vector<int32_t> &catrow, std::vector<int32_t> &nlev,
+               std::vector<int32_t> &levoff, int32_t &R, int32_t &maxlev, std::vector<int32_t> &all,
+               std::vector<size_t> &off) {
+    const int t = a.test;
+    const int32_t na = a.na, nb = symmetric ? a.na : a.nb;
+    va.assign(a.va, a.va + a.na);
+    if (!symmetric) vb.assign(a.vb, a.vb + a.nb);
+    else vb = va;
+    std::vector<int32_t> crow_a(na), crow_b(nb);
+    for (int i = 0; i < na; ++i) crow_a[i] = c.cont_index[va[i]];
+    for (int i = 0; i < nb; ++i) crow_b[i] = c.cont_index[vb[i]];
+    R = 0;
+    maxlev = 0;
+    catrow.clear();
+    nlev.clear();
+    levoff.clear();
+    if (t != NAPG_PEARSON && t != NAPG_SPEARMAN) level_lists(c, va, catrow, nlev, levoff, R, maxlev);
+    DevInts di;
+    di.add(va);
+    di.add(vb);
+    di.add(crow_a);
+    di.add(crow_b);
+    di.add(catrow);
+    di.add(nlev);
+    di.add(levoff);
+    all = di.all;
+    off = di.off;
+}
+
 // A pair whose centred sum falls to rel_tol x its raw sum (about the column's
 // in-context mean) is recomputed exactly by the two-pass rescue: for the FP64
 // form only true degeneracy (a constant column/group) reaches 1e-9; for the
@@ -223,10 +266,10 @@ constexpr double kPlainRelTol = 1e-9;
 constexpr double kMixedRelTol = 0.25;
 
 napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a) {
-    Cohort &c = ctx->coh;
+    Cohort &c = a.coh ? *a.coh : ctx->coh;
     if (!c.loaded) return fail(ctx, NAPG_E_ARG, "no cohort loaded");
     bool symmetric = false;
-    NAPG_ST(check_vars(ctx, a, &symmetric));
+    NAPG_ST(check_run_vars(ctx, a, &symmetric));
     const int t = a.test;
     const int64_t S = c.S, W = c.W, S_pad = ((S + 31) / 32) * 32;
     const bool mixed = a.opt.precision == NAPG_MIXED;
@@ -289,24 +332,23 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
     launch_ctx_bits(mask_dev, S, W, ctxw, st);
 
     // variable lists on the device: [va | vb | crow_a | crow_b | catrow | nlev | levoff]
-    std::vector<int32_t> va(a.va, a.va + a.na), vb;
-    if (!symmetric) vb.assign(a.vb, a.vb + a.nb);
-    else vb = va;
-    std::vector<int32_t> crow_a(na), crow_b(nb);
-    for (int i = 0; i < na; ++i) crow_a[i] = c.cont_index[va[i]];
-    for (int i = 0; i < nb; ++i) crow_b[i] = c.cont_index[vb[i]];
-    std::vector<int32_t> catrow, nlev, levoff;
+    std::vector<int32_t> va, vb, catrow, nlev, levoff;
     int32_t R = 0, maxlev = 0;
-    if (t != NAPG_PEARSON && t != NAPG_SPEARMAN) level_lists(c, va, catrow, nlev, levoff, R, maxlev);
-    DevInts di;
-    const size_t i_va = di.add(va), i_vb = di.add(vb), i_ca = di.add(crow_a), i_cb = di.add(crow_b);
-    const size_t i_cat = di.add(catrow), i_nl = di.add(nlev), i_lo = di.add(levoff);
-    int32_t *dints = WS(kVarsDev, int32_t, di.all.size() + 1);
-    if (st_) return st_;
-    NAPG_CU(ctx, cudaMemcpyAsync(dints, di.all.data(), sizeof(int32_t) * di.all.size(), cudaMemcpyHostToDevice, st));
-    const int32_t *d_va = dints + di.off[i_va], *d_vb = dints + di.off[i_vb];
-    const int32_t *d_ca = dints + di.off[i_ca], *d_cb = dints + di.off[i_cb];
-    const int32_t *d_cat = dints + di.off[i_cat], *d_nl = dints + di.off[i_nl], *d_lo = dints + di.off[i_lo];
+    std::vector<int32_t> all_ints;
+    std::vector<size_t> off;
+    var_lists(c, a, symmetric, va, vb, catrow, nlev, levoff, R, maxlev, all_ints, off);
+    enum { i_va, i_vb, i_ca, i_cb, i_cat, i_nl, i_lo };
+    const int32_t *dints = a.dints;
+    const size_t *doff = a.dints ? a.dints_off : off.data();
+    if (!dints) {
+        int32_t *d = WS(kVarsDev, int32_t, all_ints.size() + 1);
+        if (st_) return st_;
+        NAPG_CU(ctx, cudaMemcpyAsync(d, all_ints.data(), sizeof(int32_t) * all_ints.size(), cudaMemcpyHostToDevice, st));
+        dints = d;
+    }
+    const int32_t *d_va = dints + doff[i_va], *d_vb = dints + doff[i_vb];
+    const int32_t *d_ca = dints + doff[i_ca], *d_cb = dints + doff[i_cb];
+    const int32_t *d_cat = dints + doff[i_cat], *d_nl = dints + doff[i_nl], *d_lo = dints + doff[i_lo];
 
     // effective observed bits (observed AND in context)
     uint32_t *obsA = WS(kObsA, uint32_t, (int64_t)na * W);
@@ -343,7 +385,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         double *vsq = mixed ? WS(kVsq, double, na) : nullptr;
         if (st_) return st_;
         if (mixed) {
-            NAPG_ST(mixed_pearson(ctx, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift, vsq));
+            NAPG_ST(mixed_pearson(ctx, c, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift, vsq, (a.mask || a.no_plane_cache) ? nullptr : &va));
         } else {
             double *xs = WS(kXsA, double, (int64_t)na * S_pad);
             if (st_) return st_;
@@ -352,7 +394,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
-        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq, pj.q};
+        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq, pj.q, d_va};
         { Stage s_(ctx->trace, st, "finalize_pearson"); launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, 0, st); }
@@ -365,7 +407,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         double *vsq = mixed ? WS(kVsq, double, nb) : nullptr;
         if (st_) return st_;
         if (mixed) {
-            NAPG_ST(mixed_groupsum(ctx, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift, vsq));
+            NAPG_ST(mixed_groupsum(ctx, c, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift, vsq, (a.mask || a.no_plane_cache) ? nullptr : &vb));
         } else {
             double *xs = WS(kXsB, double, (int64_t)nb * S_pad);
             if (st_) return st_;
@@ -382,7 +424,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
     } else if (t == NAPG_CHI2) {
         int32_t *T = WS(kIntA, int32_t, (int64_t)R * R);
         if (st_) return st_;
-        if (mixed) NAPG_ST(mixed_contingency(ctx, ws, st, levbits, R, T));
+        if (mixed) NAPG_ST(mixed_contingency(ctx, c, ws, st, levbits, R, T));
         else { Stage s_(ctx->trace, st, "contingency_popc"); launch_contingency(levbits, W, R, T, st); }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
@@ -390,7 +432,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         { Stage s_(ctx->trace, st, "finalize_chi2"); launch_finalize_chi2(f, a.stat, a.pval, a.n, st); }
         pjobs_run(ctx, pj, a.pval, st);
     } else if (t == NAPG_SPEARMAN) {
-        NAPG_ST(ensure_presort(ctx, st));
+        NAPG_ST(ensure_presort(ctx, c, ws, st));
         int64_t *q = WS(kMomA, int64_t, (int64_t)na * nb * 4);
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
@@ -401,7 +443,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         { Stage s_(ctx->trace, st, "finalize_spearman"); launch_finalize_spearman(f, a.stat, a.pval, a.n, st); }
         pjobs_run(ctx, pj, a.pval, st);
     } else {  // MWU / KRUSKAL
-        NAPG_ST(ensure_presort(ctx, st));
+        NAPG_ST(ensure_presort(ctx, c, ws, st));
         const int64_t rb = (int64_t)R * nb;
         int64_t *rsum = WS(kMomA, int64_t, rb);
         int32_t *rcnt = WS(kIntA, int32_t, rb);
@@ -417,7 +459,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         pjobs_run(ctx, pj, a.pval, st);
         if (t == NAPG_MWU && a.pval) {
             const size_t sb = mwu_exact_scratch_bytes(S);
-            void *scratch = ws_get(ctx, ws, Workspace::kTmpA, sb, &st_);
+            void *scratch = ws_get(ctx, ws, Workspace::kTmpG, sb, &st_);
             if (st_) return st_;
             if (!a.stat) return fail(ctx, NAPG_E_ARG, "exact Mann-Whitney p needs the stat buffer");
             Stage s_(ctx->trace, st, "mwu_exact");
@@ -426,6 +468,37 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         }
     }
     NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
+// Outputs: device pointers are written in place; host ones through workspace
+// buffers copied back before returning.
+napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape) {
+    const int64_t cnt = (int64_t)a.na * (symmetric_shape ? a.na : a.nb);
+    double *hs = a.stat, *hp = a.pval;
+    int32_t *hn = a.n;
+    const bool ds = !hs || is_device_ptr(hs), dp = !hp || is_device_ptr(hp), dn = !hn || is_device_ptr(hn);
+    napg_status st_ = NAPG_OK;
+    if (!ds) a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
+    if (!dp) a.pval = (double *)ws_get(ctx, ws, Workspace::kOutP, sizeof(double) * cnt, &st_);
+    if (!dn) a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_);
+    if (st_) return st_;
+    // exact Mann-Whitney p reads the statistic back: give it a buffer if none
+    if (a.test == NAPG_MWU && a.pval && !a.stat) {
+        a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
+        if (st_) return st_;
+        hs = nullptr;
+    }
+    NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
+    NAPG_ST(run_on_stream(ctx, ws, st, a));
+    if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!ds || !dp || !dn) {
+        NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        NAPG_CU(ctx, cudaStreamSynchronize(st));
+        if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    }
     return NAPG_OK;
 }
 
@@ -487,6 +560,7 @@ void napg_destroy(napg_ctx *ctx) {
     if (ctx->serve) napg_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    free_batch(ctx);
     free_cohort(ctx->coh);
     free_ws(ctx->ws);
     if (ctx->dev_err) cudaFree(ctx->dev_err);
@@ -502,6 +576,14 @@ napg_status napg_sync(napg_ctx *ctx) {
     NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
     NAPG_CU(ctx, cudaStreamSynchronize(ctx->stream));
     if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    return NAPG_OK;
+}
+
+napg_status napg_release_cache(napg_ctx *ctx) {
+    if (!ctx) return NAPG_E_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->ws.plane_key.valid = false;
+    ctx->coh.sorted = false;
     return NAPG_OK;
 }
 
@@ -584,38 +666,15 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
         free_cohort(ctx->coh);
         return fail(ctx, NAPG_E_LABEL, "a categorical value is not an integer in [0, c)");
     }
+    if (c.n_cont > 0) {
+        std::vector<int32_t> cv;
+        for (int64_t v = 0; v < c.F; ++v)
+            if (c.vtype[v] == 0) cv.push_back((int32_t)v);
+        NAPG_CU(ctx, cudaMalloc(&c.cont_vars_dev, sizeof(int32_t) * cv.size()));
+        NAPG_CU(ctx, cudaMemcpy(c.cont_vars_dev, cv.data(), sizeof(int32_t) * cv.size(), cudaMemcpyHostToDevice));
+    }
+    c.gen = next_cohort_gen();
     c.loaded = true;
-    return NAPG_OK;
-}
-
-// Outputs: device pointers are written in place; host ones through workspace
-// buffers copied back before returning.
-static napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape) {
-    const int64_t cnt = (int64_t)a.na * (symmetric_shape ? a.na : a.nb);
-    double *hs = a.stat, *hp = a.pval;
-    int32_t *hn = a.n;
-    const bool ds = !hs || is_device_ptr(hs), dp = !hp || is_device_ptr(hp), dn = !hn || is_device_ptr(hn);
-    napg_status st_ = NAPG_OK;
-    if (!ds) a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
-    if (!dp) a.pval = (double *)ws_get(ctx, ws, Workspace::kOutP, sizeof(double) * cnt, &st_);
-    if (!dn) a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_);
-    if (st_) return st_;
-    // exact Mann-Whitney p reads the statistic back: give it a buffer if none
-    if (a.test == NAPG_MWU && a.pval && !a.stat) {
-        a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
-        if (st_) return st_;
-        hs = nullptr;
-    }
-    NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
-    NAPG_ST(run_on_stream(ctx, ws, st, a));
-    if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
-    if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
-    if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
-    if (!ds || !dp || !dn) {
-        NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        NAPG_CU(ctx, cudaStreamSynchronize(st));
-        if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
-    }
     return NAPG_OK;
 }
 
@@ -646,13 +705,19 @@ napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
                            const uint8_t *const *sample_masks, const int32_t *vars_a, int32_t n_a,
                            const int32_t *vars_b, int32_t n_b, double *const *stat, double *const *pval,
                            int32_t *const *n) {
-    if (!ctx || n_ctx < 0 || (n_ctx > 0 && !sample_masks)) return NAPG_E_ARG;
-    for (int32_t k = 0; k < n_ctx; ++k) {
-        napg_status s = napg_run(ctx, test, opt, sample_masks[k], vars_a, n_a, vars_b, n_b, stat ? stat[k] : nullptr,
-                                 pval ? pval[k] : nullptr, n ? n[k] : nullptr);
-        if (s != NAPG_OK) return s;
-    }
-    return NAPG_OK;
+    if (!ctx || n_ctx < 0) return NAPG_E_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    RunArgs a{};
+    a.test = test;
+    if (opt) a.opt = *opt;
+    else napg_default_options(&a.opt);
+    a.va = vars_a;
+    a.na = n_a;
+    a.vb = vars_b;
+    a.nb = vars_b ? n_b : n_a;
+    return run_batch(ctx, a, n_ctx, sample_masks, stat, pval, n);
 }
 
 napg_status napg_debug_pvalues(napg_ctx *ctx, int32_t kind, const double *s, const double *a, const double *b,

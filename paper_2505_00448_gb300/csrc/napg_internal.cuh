@@ -27,6 +27,7 @@ struct Cohort {
     int32_t dtype = NAPG_F64;
     double missing = 0.0;
     bool loaded = false;
+    uint64_t gen = 0;                    // unique per load (keys derived data)
     void *X = nullptr;                   // F x S values (input dtype)
     uint32_t *obs = nullptr;             // F x W observed bits (no context applied)
     uint8_t *lab = nullptr;              // n_cat x S labels (kMissingLabel = missing)
@@ -43,6 +44,9 @@ struct Cohort {
     uint32_t *tie = nullptr;             // n_cont x W: bit p set when position p starts a tie group
     int32_t *gsw = nullptr;              // n_cont x W: start of the group open at word w's first position
     int32_t *gew = nullptr;              // n_cont x W: first group start after word w (or nobs)
+    int64_t presort_cap = 0;             // samples the presort arrays hold (per variable)
+    int32_t *cont_vars_dev = nullptr;    // the continuous variable ids (device), for the presort
+    bool owns = true;                    // false: arrays borrowed (freed by their owner)
 };
 
 // Grow-only named device buffers; a run asks for capacity and gets a pointer.
@@ -51,10 +55,20 @@ struct Workspace {
         kCtxBits, kObsA, kObsB, kShiftA, kShiftB, kXsA, kXsB, kVarA, kLevBits, kLevCnt,
         kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
-        kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kNumSlots
+        kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kPlShift, kPlVsq,
+        kPresortTmp, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
+    // The FP16 planes in kTmpA..kTmpE (with kExp, kPlShift, kPlVsq) describe the
+    // variables `vars` of cohort generation `gen` without a sample context; a
+    // later run on the same list reuses them. Cleared when a slot is reallocated.
+    struct PlaneKey {
+        bool valid = false;
+        uint64_t gen = 0;
+        std::vector<int32_t> vars;
+    } plane_key;
+    static bool plane_slot(int s) { return (s >= kTmpA && s <= kTmpE) || s == kExp || s == kPlShift || s == kPlVsq; }
     size_t total() const {
         size_t t = 0;
         for (int i = 0; i < kNumSlots; ++i) t += cap[i];
@@ -63,6 +77,7 @@ struct Workspace {
 };
 
 struct ServeState;   // serving loop (serve.cu)
+struct BatchState;   // batched contexts (batch.cu)
 
 // Stage timing with CUDA events (napg_trace_*).
 struct Tracer {
@@ -78,6 +93,7 @@ struct Tracer {
 // counts every kernel launch made by the library
 void count_launch(uint64_t k = 1);
 uint64_t launches_so_far();
+void uncount_launches(uint64_t k);
 
 // RAII: records an event pair around a stage when tracing is on
 struct Stage {
@@ -100,6 +116,7 @@ struct napg_ctx {
     uint32_t *dev_err = nullptr;       // device error word for checks
     uint32_t *host_err = nullptr;      // pinned mirror
     napg::ServeState *serve = nullptr;
+    napg::BatchState *batch = nullptr;
     napg::Tracer trace;
     std::mutex mu;                     // guards cohort/workspace use from the serving threads
 };
@@ -116,6 +133,12 @@ bool is_device_ptr(const void *p);
 struct RunArgs {
     int32_t test;
     napg_options opt;
+    Cohort *coh;              // cohort to run on (NULL: the context's)
+    bool no_plane_cache;      // never reuse FP16 planes across runs
+    // variable lists already on the device, as run_on_stream would stage them
+    // ([va | vb | crow_a | crow_b | catrow | nlev | levoff]); NULL: stage them
+    const int32_t *dints;
+    const size_t *dints_off;
     const uint8_t *mask;      // host or device (mask_on_device tells)
     bool mask_on_device;
     const int32_t *va;        // host
@@ -126,7 +149,18 @@ struct RunArgs {
     int32_t *n;
 };
 napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a);
-napg_status ensure_presort(napg_ctx *ctx, cudaStream_t st);
+void free_cohort(Cohort &c);
+uint64_t next_cohort_gen();
+napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape);
+napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uint8_t *const *masks,
+                      double *const *stat, double *const *pval, int32_t *const *n);
+void free_batch(napg_ctx *ctx);
+napg_status check_run_vars(napg_ctx *ctx, const RunArgs &a, bool *symmetric);
+void var_lists(const Cohort &c, const RunArgs &a, bool symmetric, std::vector<int32_t> &va,
+               std::vector<int32_t> &vb, std::vector<int32_t> &catrow, std::vector<int32_t> &nlev,
+               std::vector<int32_t> &levoff, int32_t &R, int32_t &maxlev, std::vector<int32_t> &all,
+               std::vector<size_t> &off);
+napg_status ensure_presort(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st);
 
 // ---- kernel launchers (defined in the .cu files) ---------------------------
 }  // namespace napg
@@ -165,6 +199,7 @@ struct PearsonFin {
     double rel_tol;      // ill-conditioned when a centred sum <= rel_tol x its raw sum
     const double *vsq;   // mixed form: Sxx holds sum (x~^2 - v) m; add v n back (NULL: plain)
     PJobQueue q;         // p-value jobs (q.jobs NULL: no p-values wanted)
+    const int32_t *vars; // variable ids of the rows (NULL: rows are distinct variables)
 };
 void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout,
                              int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -227,13 +262,16 @@ void launch_fill_nan(double *p, int64_t count, cudaStream_t st);
 
 // mixed precision (tcgen05) path
 struct MixedPlan;
-napg_status mixed_pearson(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
+// cache_vars: host copy of the variable list when the run has no sample context
+// (the planes may then be reused by the next run on the same list), else NULL
+napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn,
-                          double *shift_out, double *vsq_out);
-napg_status mixed_groupsum(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+                          double *shift_out, double *vsq_out, const std::vector<int32_t> *cache_vars);
+napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                            const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn,
-                           double *g1, double *g2, double *shift_out, double *vsq_out);
-napg_status mixed_contingency(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
+                           double *g1, double *g2, double *shift_out, double *vsq_out,
+                           const std::vector<int32_t> *cache_vars);
+napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
                               int32_t R, int32_t *T);
 
 }  // namespace napg

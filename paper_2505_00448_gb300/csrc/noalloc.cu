@@ -133,7 +133,7 @@ extern "C" napg_status napg_pearson_fp64_noalloc(const double *X, int32_t n_vars
         q.hist = pl.pj_meta + 1;
         q.capacity = (int32_t)pl.pairs;
     }
-    PearsonFin f{pl.Sxy, pl.Sx, pl.Sxx, pl.nn, pl.shift, n_vars, 1e-9, nullptr, q};
+    PearsonFin f{pl.Sxy, pl.Sx, pl.Sxx, pl.nn, pl.shift, n_vars, 1e-9, nullptr, q, nullptr};
     launch_finalize_pearson(f, r, p, n, pl.flags, pl.counter, st);
     RescueArgs rsc{X, NAPG_F64, S, pl.W, pl.ctxw, pl.obs, nullptr, nullptr, pl.vars, nullptr, n_vars, n_vars,
                    NAPG_PEARSON, 1, nullptr, nullptr, nullptr};

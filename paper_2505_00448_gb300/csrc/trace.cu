@@ -10,6 +10,8 @@ static std::atomic<uint64_t> g_launches{0};
 
 void count_launch(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 uint64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+// launches recorded into a CUDA graph run later, when the graph is launched
+void uncount_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
 static cudaEvent_t take_event(Tracer &t) {
     if (!t.pool.empty()) {

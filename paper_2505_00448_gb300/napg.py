@@ -26,7 +26,7 @@ E_ARG, E_OOM, E_CUDA, E_LABEL, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED, E_BUSY = r
 MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 
 # every symbol include/napg.h declares
-EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync",
+EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync", "napg_release_cache",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_debug_pvalues", "napg_serve_start",
            "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version", "napg_trace_enable",
            "napg_trace_read", "napg_kernel_launches", "napg_pearson_fp64_noalloc"]
@@ -58,6 +58,8 @@ def _load():
     L.napg_last_error.restype = C.c_char_p
     L.napg_sync.argtypes = [p]
     L.napg_sync.restype = C.c_int
+    L.napg_release_cache.argtypes = [p]
+    L.napg_release_cache.restype = C.c_int
     L.napg_load_cohort.argtypes = [p, p, i32, i64, i64, i32, d, p, p]
     L.napg_load_cohort.restype = C.c_int
     L.napg_run.argtypes = [p, i32, p, p, p, i32, p, i32, p, p, p]
@@ -215,6 +217,10 @@ class Context:
             self.sync()
         return {"stat": stat, "p": p, "n": n}
 
+    def release_cache(self):
+        """Mark the cached planes and presort stale (the next run rebuilds them)."""
+        self._check(lib.napg_release_cache(self.h))
+
     def trace(self, on=True):
         self._check(lib.napg_trace_enable(self.h, 1 if on else 0))
 
@@ -224,23 +230,38 @@ class Context:
         self._check(lib.napg_trace_read(self.h, buf, len(buf)))
         return json.loads(buf.value.decode())
 
-    def run_batch(self, test, masks, vars_a, vars_b=None, **opt):
-        """One test for several sample contexts (list of uint8 masks); returns a list of dicts (numpy)."""
+    def run_batch(self, test, masks, vars_a, vars_b=None, out="numpy", outputs=None, sync=True, **opt):
+        """One test for several sample contexts (a list of uint8 masks, host or
+        device; None = every sample). Returns a list of dict(stat, p, n): numpy
+        arrays (out="numpy"), or device tensors (out="cuda": the batch runs as one
+        captured CUDA graph, stream-ordered; synchronised unless sync=False).
+        `outputs` may supply the per-context dict buffers to write."""
+        torch = self.torch
         t = TESTS[test] if isinstance(test, str) else int(test)
         va, vb = _i32(vars_a), _i32(vars_b)
         na = len(va)
         nb = na if vb is None else len(vb)
         o = options(**opt)
         ms = [np.ascontiguousarray(m, dtype=np.uint8) if isinstance(m, np.ndarray) else m for m in masks]
-        outs = [{"stat": np.empty((na, nb)), "p": np.empty((na, nb)), "n": np.empty((na, nb), np.int32)}
-                for _ in ms]
         K = len(ms)
-        mp = (C.c_void_p * K)(*[_ptr(m) for m in ms])
-        sp = (C.c_void_p * K)(*[_ptr(r["stat"]) for r in outs])
-        pp = (C.c_void_p * K)(*[_ptr(r["p"]) for r in outs])
-        npp = (C.c_void_p * K)(*[_ptr(r["n"]) for r in outs])
+        if outputs is not None:
+            outs = outputs
+        elif out == "numpy":
+            outs = [{"stat": np.empty((na, nb)), "p": np.empty((na, nb)), "n": np.empty((na, nb), np.int32)}
+                    for _ in range(K)]
+        else:
+            dev = torch.device("cuda", self.device)
+            outs = [{"stat": torch.empty((na, nb), dtype=torch.float64, device=dev),
+                     "p": torch.empty((na, nb), dtype=torch.float64, device=dev),
+                     "n": torch.empty((na, nb), dtype=torch.int32, device=dev)} for _ in range(K)]
+        mp = (C.c_void_p * max(K, 1))(*[_ptr(m) for m in ms])
+        sp = (C.c_void_p * max(K, 1))(*[_ptr(r.get("stat")) for r in outs])
+        pp = (C.c_void_p * max(K, 1))(*[_ptr(r.get("p")) for r in outs])
+        npp = (C.c_void_p * max(K, 1))(*[_ptr(r.get("n")) for r in outs])
         self._check(lib.napg_run_batch(self.h, t, C.byref(o), K, mp, _ptr(va), na, _ptr(vb),
                                        0 if vb is None else nb, sp, pp, npp))
+        if out != "numpy" and sync:
+            self.sync()
         return outs
 
     def debug_integers(self, test, a, b, mask=None):

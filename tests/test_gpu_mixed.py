@@ -116,3 +116,38 @@ def test_mixed_counts_exact_beyond_2_16(napg):
     gp = c.run("chi2", [1, 2], out="numpy", precision="fp64")
     assert np.array_equal(gm["stat"], gp["stat"])
     c.close()
+
+
+def test_plane_cache_reuse_and_invalidation(napg):
+    """Planes built by one unmasked run are reused by the next run on the same
+    variables; a masked run, another variable list and a new cohort rebuild them."""
+    rng = np.random.default_rng(31)
+    coh = synth.small_cohort(205, n_cont=150, n_cat=12, S=2500 + 3, miss=0.25, dtype=np.float32)
+    coh2 = synth.small_cohort(206, n_cont=150, n_cat=12, S=2500 + 3, miss=0.25, dtype=np.float32)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    va, cats = coh["cont"], coh["cat"]
+    r1 = c.run("pearson", va, out="numpy", precision="mixed")
+    c.trace(True)
+    c.trace_read()
+    g = c.run("anova", cats, va, out="numpy", precision="mixed")          # same continuous list: reused
+    stages = c.trace_read().get("stages", {})
+    assert "planes_f16" not in stages, stages
+    c.trace(False)
+    compare("anova", g, oracle_run("anova", coh, cats, va), stat_tol=("effect", 1e-6))
+    r2 = c.run("pearson", va, out="numpy", precision="mixed")
+    for k in ("stat", "p", "n"):
+        assert np.array_equal(r1[k], r2[k], equal_nan=True)
+    mask = (rng.random(coh["X"].shape[1]) < 0.6).astype(np.uint8)
+    compare("pearson", c.run("pearson", va, mask=mask, out="numpy", precision="mixed"),
+            oracle_run("pearson", coh, va, mask=mask), stat_tol=("abs", 1e-6))
+    sub = va[::2]
+    compare("pearson", c.run("pearson", sub, out="numpy", precision="mixed"), oracle_run("pearson", coh, sub),
+            stat_tol=("abs", 1e-6))
+    r3 = c.run("pearson", va, out="numpy", precision="mixed")
+    for k in ("stat", "p", "n"):
+        assert np.array_equal(r1[k], r3[k], equal_nan=True)
+    c.load_cohort(coh2["X"], coh2["vtype"], coh2["nlev"], coh2["missing"])
+    compare("pearson", c.run("pearson", va, out="numpy", precision="mixed"), oracle_run("pearson", coh2, va),
+            stat_tol=("abs", 1e-6))
+    c.close()
