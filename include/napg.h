@@ -209,7 +209,9 @@ typedef struct {
 } napg_request;
 
 /* Starts the serving loop: `slots` concurrent requests (1..64) within
- * `mem_budget` bytes of work memory (0 = 80% of the free device memory).
+ * `mem_budget` bytes of work memory (0 = 80% of the free device memory). Builds
+ * the presort of the continuous variables first (shared by the slots). While
+ * serving, napg_load_cohort and napg_release_cache return NAPG_E_BUSY.
  * Errors: NAPG_E_ARG, NAPG_E_BUSY (already started), NAPG_E_OOM, NAPG_E_CUDA. */
 napg_status napg_serve_start(napg_ctx *ctx, size_t mem_budget, int32_t slots);
 
@@ -225,6 +227,16 @@ napg_status napg_serve_poll(napg_ctx *ctx, uint64_t ticket, int32_t *done, doubl
 
 /* Drains the queue, waits for running requests and stops the loop. */
 napg_status napg_serve_stop(napg_ctx *ctx);
+
+/* The admission policy of the serving loop on its own (host only, no GPU):
+ * queued requests in arrival order with device-memory estimates est[q] and
+ * waiting times age_ms[q]; slots holding slot_mem[k] bytes, busy if
+ * slot_busy[k]. Each idle slot takes the first queued request whose estimate
+ * fits next to the memory of the other slots (a slot keeps what it holds);
+ * a request waiting 200 ms or more is not overtaken. assign[k] receives the
+ * queue index given to slot k, or -1. Errors: NAPG_E_ARG. */
+napg_status napg_serve_plan(const uint64_t *est, const double *age_ms, int32_t nq, const uint64_t *slot_mem,
+                            const int32_t *slot_busy, int32_t nslots, uint64_t budget, int32_t *assign);
 
 /* ----------------------------------------------------------------- tracing --
  * With tracing on, every stage of a run (bitmasks, contraction, finalize, ...)

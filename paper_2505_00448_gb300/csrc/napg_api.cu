@@ -582,6 +582,7 @@ napg_status napg_sync(napg_ctx *ctx) {
 napg_status napg_release_cache(napg_ctx *ctx) {
     if (!ctx) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serve) return fail(ctx, NAPG_E_BUSY, "the serving loop reads the presort");
     ctx->ws.plane_key.valid = false;
     ctx->coh.sorted = false;
     return NAPG_OK;
@@ -591,6 +592,7 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
                              int32_t samples_major, double missing, const uint8_t *var_type, const int32_t *n_levels) {
     if (!ctx) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->serve) return fail(ctx, NAPG_E_BUSY, "stop the serving loop before loading a cohort");
     ctx->err.clear();
     if (!X || !var_type || !n_levels || n_vars <= 0 || n_samples <= 0 || (dtype != NAPG_F32 && dtype != NAPG_F64))
         return fail(ctx, NAPG_E_ARG, "bad cohort arguments");

@@ -7,6 +7,7 @@ ImportError when it is missing: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import time
 import math
 import os
 
@@ -28,7 +29,7 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 # every symbol include/napg.h declares
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync", "napg_release_cache",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_debug_pvalues", "napg_serve_start",
-           "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_version", "napg_trace_enable",
+           "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_serve_plan", "napg_version", "napg_trace_enable",
            "napg_trace_read", "napg_kernel_launches", "napg_pearson_fp64_noalloc"]
 
 
@@ -78,6 +79,8 @@ def _load():
     L.napg_serve_poll.restype = C.c_int
     L.napg_serve_stop.argtypes = [p]
     L.napg_serve_stop.restype = C.c_int
+    L.napg_serve_plan.argtypes = [p, p, i32, p, p, i32, C.c_uint64, p]
+    L.napg_serve_plan.restype = C.c_int
     L.napg_version.argtypes = []
     L.napg_version.restype = C.c_char_p
     L.napg_trace_enable.argtypes = [p, i32]
@@ -264,6 +267,54 @@ class Context:
             self.sync()
         return outs
 
+    # ------------------------------------------------------------ serving --
+    def serve_start(self, mem_budget=0, slots=4):
+        """Start the request loop on the resident cohort (`slots` concurrent requests)."""
+        self._serve_out = {}
+        self._check(lib.napg_serve_start(self.h, int(mem_budget), int(slots)))
+
+    def serve_submit(self, test, vars_a, vars_b=None, mask=None, **opt):
+        """Queue one request; returns its ticket. Outputs are host arrays kept until done."""
+        t = TESTS[test] if isinstance(test, str) else int(test)
+        va, vb = _i32(vars_a), _i32(vars_b)
+        na = len(va)
+        nb = na if vb is None else len(vb)
+        outs = {"stat": np.empty((na, nb)), "p": np.empty((na, nb)), "n": np.empty((na, nb), np.int32)}
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        r = Request()
+        r.test = t
+        r.opt = options(**opt)
+        r.sample_mask = _ptr(m)
+        r.vars_a = _ptr(va)
+        r.n_a = na
+        r.vars_b = _ptr(vb)
+        r.n_b = 0 if vb is None else nb
+        r.stat = _ptr(outs["stat"])
+        r.pval = _ptr(outs["p"])
+        r.n = _ptr(outs["n"])
+        tk = C.c_uint64()
+        self._check(lib.napg_serve_submit(self.h, C.byref(r), C.byref(tk)))
+        self._serve_out[tk.value] = outs
+        return tk.value
+
+    def serve_poll(self, ticket):
+        """(done, latency_ms, status, outputs-or-None); a finished ticket is reported once."""
+        done, lat, st = C.c_int32(), C.c_double(), C.c_int32()
+        self._check(lib.napg_serve_poll(self.h, C.c_uint64(ticket), C.byref(done), C.byref(lat), C.byref(st)))
+        if not done.value:
+            return False, None, None, None
+        return True, lat.value, st.value, self._serve_out.pop(ticket, None)
+
+    def serve_wait(self, ticket, poll_s=2e-4):
+        while True:
+            d, lat, st, out = self.serve_poll(ticket)
+            if d:
+                return lat, st, out
+            time.sleep(poll_s)
+
+    def serve_stop(self):
+        self._check(lib.napg_serve_stop(self.h))
+
     def debug_integers(self, test, a, b, mask=None):
         t = TESTS[test] if isinstance(test, str) else int(test)
         out = np.zeros(4 + 2 * 64 + 64 * 64, np.int64)
@@ -283,6 +334,20 @@ class Context:
         out = np.empty_like(s)
         self._check(lib.napg_debug_pvalues(self.h, k, _ptr(s), _ptr(a), _ptr(b), s.size, _ptr(out)))
         return out
+
+
+def serve_plan(est, age_ms, slot_mem, slot_busy, budget):
+    """The serving loop's admission policy on given numbers (host only): the
+    queue index each slot would take (-1 = none)."""
+    e = np.ascontiguousarray(est, dtype=np.uint64)
+    a = np.ascontiguousarray(age_ms, dtype=np.float64)
+    m = np.ascontiguousarray(slot_mem, dtype=np.uint64)
+    b = np.ascontiguousarray(slot_busy, dtype=np.int32)
+    out = np.empty(len(m), np.int32)
+    rc = lib.napg_serve_plan(_ptr(e), _ptr(a), len(e), _ptr(m), _ptr(b), len(m), int(budget), _ptr(out))
+    if rc:
+        raise NapgError(rc, "napg_serve_plan")
+    return out
 
 
 def version() -> str:
