@@ -670,7 +670,8 @@ static void mwu_pair(const orc_cohort *c, int64_t a, int64_t j, orc_scratch *w,
 /* Sec. 3.5.8: Kruskal-Wallis H over the present levels with tie-averaged ranks
  * and the tie correction C = 1 - sum(t^3 - t)/(n^3 - n); p from chi2(k-1).
  * H0 = 12/(n(n+1)) * sum_g n_g (Rbar_g - (n+1)/2)^2 (the centred form of the
- * textbook 12/(n(n+1)) sum R_g^2/n_g - 3(n+1)). Readings: k < 2 -> NaN;
+ * textbook 12/(n(n+1)) sum R_g^2/n_g - 3(n+1)), the centred group sums formed
+ * exactly from the integer doubled ranks. Readings: k < 2 -> NaN;
  * C == 0 (all tied) -> NaN. */
 static void kruskal_pair(const orc_cohort *c, int64_t a, int64_t j, orc_scratch *w,
                          double *st, double *p, int32_t *nn) {
@@ -682,14 +683,17 @@ static void kruskal_pair(const orc_cohort *c, int64_t a, int64_t j, orc_scratch 
     int64_t T = 0;
     doubled_ranks(w->y, n, w->r2, w->buf, &T);
     int L = c->nlev[a];
-    double R[ORC_MAXLEV];
-    for (int g = 0; g < L; ++g) R[g] = 0.0;
-    for (int64_t q = 0; q < n; ++q) R[(int)w->x[q]] += 0.5 * (double)w->r2[q];
+    /* per level, the doubled rank sum and its centred value
+     * D_g = sum 2R - n_g (n+1) = 2 n_g (Rbar_g - (n+1)/2), exact in int64, so
+     * n_g (Rbar_g - (n+1)/2)^2 = D_g^2 / (4 n_g) carries no cancellation */
+    int64_t S2[ORC_MAXLEV];
+    for (int g = 0; g < L; ++g) S2[g] = 0;
+    for (int64_t q = 0; q < n; ++q) S2[(int)w->x[q]] += w->r2[q];
     double nd = (double)n, h0 = 0.0;
     for (int g = 0; g < L; ++g) {
         if (!present[g]) continue;
-        double d = R[g] / (double)ng[g] - 0.5 * (nd + 1.0);
-        h0 += (double)ng[g] * d * d;
+        const double D = (double)(S2[g] - ng[g] * (n + 1));
+        h0 += D * D / (4.0 * (double)ng[g]);
     }
     h0 *= 12.0 / (nd * (nd + 1.0));
     double C = 1.0 - (double)T / (nd * nd * nd - nd);
