@@ -262,14 +262,22 @@ __device__ __forceinline__ int32_t prefix_at(const Side &sd, int32_t x) {
     return sd.P[w] + __popc(sd.B[w] & ((1u << l) - 1u));
 }
 
-__device__ __forceinline__ int64_t rank2_at(const Side &sd, int32_t p) {
-    const int w = p >> 5, l = p & 31;
-    const uint32_t le = (l == 31) ? 0xffffffffu : ((1u << (l + 1)) - 1u);
-    const uint32_t tw = sd.T[w];
-    const uint32_t m_le = tw & le, m_gt = tw & ~le;
-    const int32_t gs = m_le ? (w * 32 + 31 - __clz(m_le)) : sd.GS[w];
-    const int32_t ge = m_gt ? (w * 32 + __ffs(m_gt) - 1) : sd.GE[w];
-    return (int64_t)prefix_at(sd, gs) + (int64_t)prefix_at(sd, ge) + 1;
+// Doubled rank 2R = P(gs) + P(ge) + 1 of the position at bit l of word w, from
+// that word's tie-start bits Tw, co-observed bits Bw and prefix Pw; pgs / pge are
+// P at the bounds of the group open across the word's start / end (the side's
+// GS / GE after bounds_to_prefix). Below 2^31 for any S.
+__device__ __forceinline__ uint32_t rank2_word(uint32_t Tw, uint32_t Bw, int32_t Pw, int32_t pgs, int32_t pge,
+                                               int l) {
+    const uint32_t le = (l == 31) ? 0xffffffffu : ((2u << l) - 1u);
+    const uint32_t m_le = Tw & le, m_gt = Tw & ~le;
+    const int32_t a = m_le ? Pw + __popc(Bw & ((1u << (31 - __clz(m_le))) - 1u)) : pgs;
+    const int32_t b = m_gt ? Pw + __popc(Bw & ((1u << (__ffs(m_gt) - 1)) - 1u)) : pge;
+    return (uint32_t)(a + b + 1);
+}
+
+__device__ __forceinline__ uint32_t rank2_at(const Side &sd, int32_t p) {
+    const int w = p >> 5;
+    return rank2_word(sd.T[w], sd.B[w], sd.P[w], sd.GS[w], sd.GE[w], p & 31);
 }
 
 // Build B over the column's sorted positions from the co-observed sample bits,
@@ -288,20 +296,36 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
         if (lane == 0) sd.B[w] = bits;
     }
     __syncthreads();
-    // exclusive scan of popc(B[w]) over w = 0..W (W+1 entries), block-wide
+    // exclusive scan of popc(B[w]) over w = 0..W (W+1 entries), block-wide:
+    // per-thread chunks, then warp 0 scans the per-thread totals by shuffles
     const int per = (W + 1 + blockDim.x - 1) / blockDim.x;
     const int w0 = threadIdx.x * per, w1 = min(W + 1, w0 + per);
     int c = 0;
     for (int w = w0; w < w1; ++w) c += __popc(sd.B[w]);
     scan_tmp[threadIdx.x] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int t = 0; t < (int)blockDim.x; ++t) { const int v = scan_tmp[t]; scan_tmp[t] = run; run += v; }
+    if (warp == 0) {
+        const int k = blockDim.x >> 5;          // totals per lane (blockDim.x <= 1024)
+        int v[32];
+        int tot = 0;
+        for (int i = 0; i < k; ++i) { v[i] = scan_tmp[lane * k + i]; tot += v[i]; }
+        int incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int run = incl - tot;
+        for (int i = 0; i < k; ++i) { scan_tmp[lane * k + i] = run; run += v[i]; }
     }
     __syncthreads();
     int run = scan_tmp[threadIdx.x];
     for (int w = w0; w < w1; ++w) { sd.P[w] = run; run += __popc(sd.B[w]); }
+    __syncthreads();
+    // group bounds (positions) -> co-observed prefix counts at them, in place
+    for (int w = threadIdx.x; w <= W; w += blockDim.x) {
+        sd.GS[w] = prefix_at(sd, sd.GS[w]);
+        sd.GE[w] = prefix_at(sd, sd.GE[w]);
+    }
     __syncthreads();
 }
 
@@ -340,22 +364,27 @@ __device__ Side carve_side(unsigned char *&cur, int W) {
 
 // ----------------------------------------------------------------- Spearman --
 // One CTA per pair. out4[pair] = {n, sum A*B, sum A^2, sum B^2}, A = 2Rx, B = 2Ry.
-__global__ void __launch_bounds__(256) k_spearman(RankData rd, const int32_t *__restrict__ crow_a,
+__global__ void __launch_bounds__(1024) k_spearman(RankData rd, const int32_t *__restrict__ crow_a,
                                                   const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
                                                   const uint32_t *__restrict__ obs_b, int32_t na, int32_t nb,
                                                   int32_t symmetric, int64_t *__restrict__ out4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t scan_tmp[256];
-    __shared__ int64_t red[8];
+    __shared__ int32_t scan_tmp[1024];
+    __shared__ int64_t red[32];
     const int W = (int)rd.W;
     // pair index
     int64_t pid = blockIdx.x;
     int a, b;
     if (symmetric) {
-        // upper triangle including the diagonal, row-major
-        int64_t t = pid, i = 0;
-        while (t >= (int64_t)na - i) { t -= na - i; ++i; }
-        a = (int)i; b = (int)(i + t);
+        // upper triangle including the diagonal, row-major: row i starts at
+        // i (2 na - i + 1) / 2; closed form, then an exact integer fix-up
+        const int64_t nv = na;
+        int64_t i = (int64_t)((2.0 * nv + 1.0 - sqrt((2.0 * nv + 1.0) * (2.0 * nv + 1.0) - 8.0 * (double)pid)) / 2.0);
+        if (i < 0) i = 0;
+        if (i > nv - 1) i = nv - 1;
+        while (i > 0 && i * (2 * nv - i + 1) / 2 > pid) --i;
+        while ((i + 1) * (2 * nv - i) / 2 <= pid) ++i;
+        a = (int)i; b = (int)(i + (pid - i * (2 * nv - i + 1) / 2));
     } else {
         a = (int)(pid / nb); b = (int)(pid - (int64_t)a * nb);
     }
@@ -372,18 +401,27 @@ __global__ void __launch_bounds__(256) k_spearman(RankData rd, const int32_t *__
     const int32_t *pos_j = rd.pos + (int64_t)cj * rd.S;
     build_side(si, perm_i, co, W, scan_tmp);
     build_side(sj, perm_j, co, W, scan_tmp);
-    int64_t sab = 0, saa = 0, sbb = 0, cnt = 0;
-    for (int p = threadIdx.x; p < si.n; p += blockDim.x) {
-        if (!((si.B[p >> 5] >> (p & 31)) & 1u)) continue;
-        const int s = perm_i[p];
-        const int q = pos_j[s];
-        const int64_t A = rank2_at(si, p), B = rank2_at(sj, q);
-        sab += A * B; saa += A * A; sbb += B * B; ++cnt;
+    uint64_t sab = 0, saa = 0, sbb = 0;
+    int64_t cnt = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // each warp takes one word of 32 sorted positions of column i at a time
+    for (int w = warp; w < ((si.n + 31) >> 5); w += nwarps) {
+        const uint32_t Bw = si.B[w];
+        if (Bw == 0u) continue;
+        const uint32_t Tw = si.T[w];
+        const int32_t Pw = si.P[w], pgs = si.GS[w], pge = si.GE[w];
+        if ((Bw >> lane) & 1u) {
+            const int s = perm_i[w * 32 + lane];
+            const int q = pos_j[s];
+            const uint32_t A = rank2_word(Tw, Bw, Pw, pgs, pge, lane), B = rank2_at(sj, q);
+            // 32 x 32 -> 64-bit products (exact)
+            sab += (uint64_t)A * B; saa += (uint64_t)A * A; sbb += (uint64_t)B * B; ++cnt;
+        }
     }
     const int64_t t0 = block_sum64(cnt, red);
-    const int64_t t1 = block_sum64(sab, red);
-    const int64_t t2 = block_sum64(saa, red);
-    const int64_t t3 = block_sum64(sbb, red);
+    const int64_t t1 = block_sum64((int64_t)sab, red);
+    const int64_t t2 = block_sum64((int64_t)saa, red);
+    const int64_t t3 = block_sum64((int64_t)sbb, red);
     if (threadIdx.x == 0) {
         int64_t *o = out4 + 4 * ((int64_t)a * nb + b);
         o[0] = t0; o[1] = t1; o[2] = t2; o[3] = t3;
@@ -394,6 +432,11 @@ static size_t rank_smem_bytes(int64_t W, int sides, bool with_co) {
     return (size_t)(W + 1) * 4 * (5 * sides + (with_co ? 1 : 0));
 }
 
+// Threads per pair: the per-pair arrays grow with S; once fewer than four
+// 256-thread CTAs fit in an SM's shared memory, one 1024-thread CTA per pair
+// keeps 32 warps resident instead.
+static int rank_threads(size_t smem) { return smem > (size_t)56 * 1024 ? 1024 : 256; }
+
 void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b, const uint32_t *obs_a,
                            const uint32_t *obs_b, int32_t na, int32_t nb, int32_t symmetric, int64_t *out4,
                            cudaStream_t st) {
@@ -402,27 +445,30 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
     const size_t smem = rank_smem_bytes(rd.W, 2, true);
     cudaFuncSetAttribute(k_spearman, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    k_spearman<<<(unsigned)pairs, 256, smem, st>>>(rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric, out4);
+    k_spearman<<<(unsigned)pairs, rank_threads(smem), smem, st>>>(rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric,
+                                                                  out4);
 }
 
 // ------------------------------------------------------------ MWU / Kruskal --
 // One CTA per (categorical a, continuous j): per level g the count n_g and the
 // sum of doubled ranks S_g, plus the tie term sum (t^3 - t) over co-observed
 // tie groups. Per-level sums use shared-memory 64-bit atomics.
-__global__ void __launch_bounds__(256) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
+__global__ void __launch_bounds__(1024) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
                                                      const int32_t *__restrict__ catrow_a, const int32_t *__restrict__ nlev_a,
                                                      const int32_t *__restrict__ levoff_a, int32_t na,
                                                      const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
                                                      const uint32_t *__restrict__ obs_b, int32_t nb, int64_t *__restrict__ rsum,
                                                      int32_t *__restrict__ rcnt, int64_t *__restrict__ tie_term) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t scan_tmp[256];
-    __shared__ int64_t red[8];
-    __shared__ unsigned long long lsum[kMaxLevels];
-    __shared__ int lcnt[kMaxLevels];
+    __shared__ int32_t scan_tmp[1024];
+    __shared__ int64_t red[32];
     const int W = (int)rd.W;
     const int a = (int)(blockIdx.x / nb), j = (int)(blockIdx.x - (int64_t)a * nb);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned char *cur = smem_raw;
+    // per-warp level sums and counts (dynamic: one table per warp of the block)
+    unsigned long long *lsum = (unsigned long long *)cur; cur += (size_t)nwarp * kMaxLevels * 8;
+    int *lcnt = (int *)cur; cur += (size_t)nwarp * kMaxLevels * 4;
     uint32_t *co = (uint32_t *)cur; cur += (W + 1) * 4;
     Side sj = carve_side(cur, W);
     const uint32_t *oa = obs_a + (int64_t)a * W, *ob = obs_b + (int64_t)j * W;
@@ -430,35 +476,56 @@ __global__ void __launch_bounds__(256) k_rank_groups(RankData rd, const uint8_t 
     const int cj = crow_b[j];
     load_side_static(sj, rd, cj, W);
     const int c = nlev_a[a];
-    for (int g = threadIdx.x; g < kMaxLevels; g += blockDim.x) { lsum[g] = 0ull; lcnt[g] = 0; }
+    for (int i = threadIdx.x; i < nwarp * kMaxLevels; i += blockDim.x) {
+        lsum[i] = 0ull;
+        lcnt[i] = 0;
+    }
     __syncthreads();
     const int32_t *perm_j = rd.perm + (int64_t)cj * rd.S;
     build_side(sj, perm_j, co, W, scan_tmp);
     const uint8_t *la = lab + (int64_t)catrow_a[a] * rd.S;
     int64_t tsum = 0;
-    for (int p = threadIdx.x; p < sj.n; p += blockDim.x) {
-        const int w = p >> 5, l = p & 31;
-        if ((sj.T[w] >> l) & 1u) {
+    // each warp takes one word of 32 sorted positions at a time
+    const int nwarps = blockDim.x >> 5;
+    const int nwj = (sj.n + 31) >> 5;
+    for (int w0 = 0; w0 < nwj; w0 += nwarps) {
+        const int w = w0 + warp;               // warps past the end still join the warp-wide steps
+        const bool inw = w < nwj;
+        const uint32_t Bw = inw ? sj.B[w] : 0u, Tw = inw ? sj.T[w] : 0u;
+        const int32_t Pw = inw ? sj.P[w] : 0, pgs = inw ? sj.GS[w] : 0, pge = inw ? sj.GE[w] : 0;
+        const int p = w * 32 + lane;
+        if (inw && p < sj.n && ((Tw >> lane) & 1u)) {
             // group starting at p: co-observed size t = P(ge) - P(p)
-            const uint32_t le = (l == 31) ? 0xffffffffu : ((1u << (l + 1)) - 1u);
-            const uint32_t m_gt = sj.T[w] & ~le;
-            const int32_t ge = m_gt ? (w * 32 + __ffs(m_gt) - 1) : sj.GE[w];
-            const int64_t t = (int64_t)prefix_at(sj, ge) - prefix_at(sj, p);
+            const uint32_t le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+            const uint32_t m_gt = Tw & ~le;
+            const int32_t pge_here = m_gt ? Pw + __popc(Bw & ((1u << (__ffs(m_gt) - 1)) - 1u)) : pge;
+            const int64_t t = (int64_t)pge_here - (Pw + __popc(Bw & ((1u << lane) - 1u)));
             tsum += t * t * t - t;
         }
-        if (!((sj.B[w] >> l) & 1u)) continue;
-        const int s = perm_j[p];
-        const int g = la[s];
-        const int64_t r2 = rank2_at(sj, p);
-        atomicAdd(&lsum[g], (unsigned long long)r2);
-        atomicAdd(&lcnt[g], 1);
+        const bool on = inw && ((Bw >> lane) & 1u);
+        int g = kMaxLevels;                    // no level
+        uint32_t r2 = 0;
+        if (on) {
+            g = la[perm_j[p]];
+            r2 = rank2_word(Tw, Bw, Pw, pgs, pge, lane);
+        }
+        // lanes with the same level add their doubled ranks (a warp's sum fits 32 bits)
+        const unsigned same = __match_any_sync(0xffffffffu, g);
+        const uint32_t sum = __reduce_add_sync(same, r2);
+        if (on && lane == __ffs(same) - 1) {
+            lsum[warp * kMaxLevels + g] += sum;   // distinct levels per leader: no conflict
+            lcnt[warp * kMaxLevels + g] += __popc(same);
+        }
     }
     const int64_t T = block_sum64(tsum, red);
     __syncthreads();
     const int off = levoff_a[a];
     for (int g = threadIdx.x; g < c; g += blockDim.x) {
-        rsum[(int64_t)(off + g) * nb + j] = (int64_t)lsum[g];
-        rcnt[(int64_t)(off + g) * nb + j] = lcnt[g];
+        unsigned long long su = 0;
+        int cn = 0;
+        for (int k = 0; k < nwarp; ++k) { su += lsum[k * kMaxLevels + g]; cn += lcnt[k * kMaxLevels + g]; }
+        rsum[(int64_t)(off + g) * nb + j] = (int64_t)su;
+        rcnt[(int64_t)(off + g) * nb + j] = cn;
     }
     if (threadIdx.x == 0) tie_term[(int64_t)a * nb + j] = T;
 }
@@ -470,11 +537,13 @@ void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *c
     (void)total_rows;
     const int64_t pairs = (int64_t)na * nb;
     if (pairs == 0) return;
-    const size_t smem = rank_smem_bytes(rd.W, 1, true);
+    const size_t side = rank_smem_bytes(rd.W, 1, true);
+    const int threads = rank_threads(side);
+    const size_t smem = side + (size_t)(threads / 32) * kMaxLevels * 12;
     cudaFuncSetAttribute(k_rank_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    k_rank_groups<<<(unsigned)pairs, 256, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b,
-                                                      nb, rsum, rcnt, tie_term);
+    k_rank_groups<<<(unsigned)pairs, threads, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a,
+                                                           obs_b, nb, rsum, rcnt, tie_term);
 }
 
 // ------------------------------------------------------ exact Mann-Whitney --

@@ -270,3 +270,27 @@ def test_sentinel_and_samples_major(napg):
     compare("pearson", c.run("pearson", va, out="numpy"), oracle_run("pearson", coh, va))
     compare("kruskal", c.run("kruskal", coh["cat"], va, out="numpy"), oracle_run("kruskal", coh, coh["cat"], va))
     c.close()
+
+
+def test_rank_tests_many_samples(napg):
+    """80,000 samples: the per-pair rank arrays no longer leave room for four
+    256-thread blocks per SM, so each pair runs as one 1024-thread block; rank
+    sums stay bit-exact and the statistics match the oracle."""
+    rng = np.random.default_rng(17)
+    coh = synth.small_cohort(111, n_cont=6, n_cat=4, S=80_000 + 13, miss=0.3, ties=True, lev_lo=2, lev_hi=5,
+                             binary_cats=2)
+    c = ctx_for(napg, coh)
+    cats, conts = coh["cat"], coh["cont"]
+    compare("spearman", c.run("spearman", conts, out="numpy"), oracle_run("spearman", coh, conts))
+    mask = (rng.random(coh["X"].shape[1]) < 0.5).astype(np.uint8)
+    compare("spearman", c.run("spearman", conts, mask=mask, out="numpy"),
+            oracle_run("spearman", coh, conts, mask=mask))
+    compare("kruskal", c.run("kruskal", cats, conts, out="numpy"), oracle_run("kruskal", coh, cats, conts))
+    compare("mwu", c.run("mwu", cats[:2], conts, mwu_mode="asymptotic", out="numpy"),
+            oracle_run("mwu", coh, cats[:2], conts, mwu_mode=2))
+    Xd = coh["X"].astype(np.float64)
+    for test, a, b in (("spearman", conts[0], conts[3]), ("kruskal", cats[3], conts[1]), ("mwu", cats[0], conts[5])):
+        got = c.debug_integers(test, int(a), int(b))
+        ref = O.pair_ints(test, Xd, NAN, coh["vtype"], coh["nlev"], int(a), int(b))
+        assert np.array_equal(got, ref), (test, got, ref)
+    c.close()
