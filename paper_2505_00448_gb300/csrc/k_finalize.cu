@@ -55,7 +55,7 @@ __global__ void k_finalize_pearson(PearsonFin f, double *stat, double *pval, int
                 r = fmin(1.0, fmax(-1.0, r));
                 if (n <= 2) p = dnan();
                 else if (fabs(r) >= 1.0) p = 0.0;
-                else if (f.q.jobs) { pjob_push(f.q, PJob{r, nd, 0.0, ij, kPjCorr, (int32_t)nv}); p = dnan(); }
+                else if (f.q.jobs) p = pjob_push_p(f.q, PJob{r, nd, 0.0, ij, kPjCorr, (int32_t)nv});
             }
         }
         put(stat, pval, nout, ij, r, p, n);       // p of a queued job is written by the evaluation
@@ -115,7 +115,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 } else {
                     const double d1 = (double)(k - 1), d2 = (double)(n - k);
                     s = (ssb / d1) / (ssw / d2);
-                    if (f.q.jobs) pjob_push(f.q, PJob{s, d1, d2, t, kPjF, 0});
+                    if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, d1, d2, t, kPjF, 0});
                 }
             }
         } else {  // two-sample t (levels 0 and 1)
@@ -133,12 +133,12 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     const double se2 = e0 + e1;
                     s = (m0 - m1) / sqrt(se2);
                     const double nu = se2 * se2 / (e0 * e0 / (double)(n0 - 1) + e1 * e1 / (double)(n1 - 1));
-                    if (f.q.jobs) pjob_push(f.q, PJob{s, nu, 0.0, t, kPjT, 0});
+                    if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, nu, 0.0, t, kPjT, 0});
                 } else {
                     const double df = (double)(n - 2);
                     const double sp2 = (q0 + q1) / df;
                     s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
-                    if (f.q.jobs) pjob_push(f.q, PJob{s, df, 0.0, t, kPjT, 0});
+                    if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, df, 0.0, t, kPjT, 0});
                 }
             }
         }
@@ -236,7 +236,7 @@ __global__ void k_finalize_spearman(SpearmanFin f, double *stat, double *pval, i
                 r = fmin(1.0, fmax(-1.0, r));
                 if (n <= 2) p = dnan();
                 else if (fabs(r) >= 1.0) p = 0.0;
-                else if (f.pq.jobs) pjob_push(f.pq, PJob{r, (double)n, 0.0, t, kPjCorr, f.symmetric ? f.nb : 0});
+                else if (f.pq.jobs) p = pjob_push_p(f.pq, PJob{r, (double)n, 0.0, t, kPjCorr, f.symmetric ? f.nb : 0});
             }
         }
         put(stat, pval, nout, t, r, p, (int32_t)n);

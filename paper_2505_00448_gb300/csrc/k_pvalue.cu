@@ -27,15 +27,16 @@ __global__ void k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t cap
     }
 }
 
-__global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capacity, double *pval) {
+__global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capacity, double *pval,
+                          const double *bgrat) {
     const int32_t n = min(*count, capacity);
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const PJob j = sorted[t];
         double p;
         switch (j.kind & 0xff) {
-            case kPjCorr: p = sf::corr_p(j.s, j.a); break;
-            case kPjT: p = sf::t_two_sided(j.s, j.a); break;
-            case kPjF: p = sf::f_sf(j.s, j.a, j.b); break;
+            case kPjCorr: p = sf::corr_p(j.s, j.a, bgrat); break;
+            case kPjT: p = sf::t_two_sided(j.s, j.a, bgrat); break;
+            case kPjF: p = sf::f_sf(j.s, j.a, j.b, bgrat); break;
             default: p = sf::chi2_sf(j.s, j.a); break;
         }
         pval[j.idx] = p;
@@ -52,21 +53,32 @@ void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t 
     count_launch(3);
     k_pj_scan<<<1, 32, 0, st>>>(q.hist, offs, cursor);
     k_pj_scatter<<<152 * 8, 256, 0, st>>>(q.jobs, q.count, q.capacity, offs, cursor, sorted);
-    k_pj_eval<<<152 * 16, 128, 0, st>>>(sorted, q.count, q.capacity, pval);
+    k_pj_eval<<<152 * 16, 128, 0, st>>>(sorted, q.count, q.capacity, pval, q.bgrat);
+}
+
+// the table of expansion coefficients c_k(b), 2b = 1..64 (one thread per row)
+__global__ void k_bgrat_table(double *tab) {
+    const int r = threadIdx.x;
+    if (r < sf::kBgratRows) sf::bgrat_coefs(0.5 * (double)(r + 1), tab + r * sf::kBgratTerms);
+}
+
+void launch_bgrat_table(double *tab, cudaStream_t st) {
+    count_launch();
+    k_bgrat_table<<<1, sf::kBgratRows, 0, st>>>(tab);
 }
 
 // p-values of caller-supplied statistics (kinds as napg_debug_pvalues)
 __global__ void k_debug_pvalues(int32_t kind, const double *s, const double *a, const double *b, int64_t count,
-                                double *p) {
+                                double *p, const double *bgrat) {
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
         double v;
         switch (kind) {
-            case 0: v = sf::corr_p(s[t], a[t]); break;
-            case 1: v = sf::t_two_sided(s[t], a[t]); break;
-            case 2: v = sf::f_sf(s[t], a[t], b[t]); break;
+            case 0: v = sf::corr_p(s[t], a[t], bgrat); break;
+            case 1: v = sf::t_two_sided(s[t], a[t], bgrat); break;
+            case 2: v = sf::f_sf(s[t], a[t], b[t], bgrat); break;
             case 3: v = sf::chi2_sf(s[t], a[t]); break;
             case 4: v = sf::norm_sf(s[t]); break;
-            case 5: v = sf::ibeta(a[t], b[t], s[t], 1.0 - s[t]); break;
+            case 5: v = sf::ibeta(a[t], b[t], s[t], 1.0 - s[t], bgrat); break;
             default: v = sf::gamma_q(a[t], s[t]); break;
         }
         p[t] = v;
@@ -74,11 +86,11 @@ __global__ void k_debug_pvalues(int32_t kind, const double *s, const double *a, 
 }
 
 void launch_debug_pvalues(int32_t kind, const double *s, const double *a, const double *b, int64_t count, double *p,
-                          cudaStream_t st) {
+                          const double *bgrat, cudaStream_t st) {
     if (count <= 0) return;
     count_launch();
     const int64_t blocks = std::min<int64_t>((count + 127) / 128, 152 * 16);
-    k_debug_pvalues<<<(unsigned)blocks, 128, 0, st>>>(kind, s, a, b, count, p);
+    k_debug_pvalues<<<(unsigned)blocks, 128, 0, st>>>(kind, s, a, b, count, p, bgrat);
 }
 
 }  // namespace napg

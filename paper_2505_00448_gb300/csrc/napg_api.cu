@@ -30,6 +30,7 @@ void *ws_get(napg_ctx *ctx, Workspace &ws, int slot, size_t bytes, napg_status *
     bytes = ((std::max<size_t>(bytes, 16) + 255) / 256) * 256;
     if (ws.cap[slot] >= bytes) return ws.ptr[slot];
     if (Workspace::plane_slot(slot)) ws.plane_key.valid = false;
+    if (slot == Workspace::kBgrat) ws.bgrat_ready = false;
     if (ws.ptr[slot]) {
         cudaFree(ws.ptr[slot]);
         ws.ptr[slot] = nullptr;
@@ -216,6 +217,15 @@ static napg_status pjobs_setup(napg_ctx *ctx, Workspace &ws, cudaStream_t st, in
     b.cursor = meta + 1 + 2 * kPjBins;
     b.q.capacity = (int32_t)capacity;
     NAPG_CU(ctx, cudaMemsetAsync(meta, 0, sizeof(int32_t) * (1 + kPjBins), st));
+    // expansion coefficients of the large-parameter incomplete beta, once per workspace
+    double *tab = (double *)ws_get(ctx, ws, Workspace::kBgrat, sizeof(double) * sf::kBgratRows * sf::kBgratTerms, &st_);
+    if (st_) return st_;
+    if (!ws.bgrat_ready) {
+        launch_bgrat_table(tab, st);
+        NAPG_CU(ctx, cudaGetLastError());
+        ws.bgrat_ready = true;
+    }
+    b.q.bgrat = tab;
     return NAPG_OK;
 }
 
@@ -733,13 +743,15 @@ napg_status napg_debug_pvalues(napg_ctx *ctx, int32_t kind, const double *s, con
     cudaStream_t st = ctx->stream;
     const size_t bytes = sizeof(double) * (size_t)count;
     double *d = nullptr;
-    NAPG_CU(ctx, cudaMalloc(&d, 4 * bytes));
-    double *ds = d, *da = d + count, *db = d + 2 * count, *dp = d + 3 * count;
+    const size_t tab = sizeof(double) * sf::kBgratRows * sf::kBgratTerms;
+    NAPG_CU(ctx, cudaMalloc(&d, 4 * bytes + tab));
+    double *ds = d, *da = d + count, *db = d + 2 * count, *dp = d + 3 * count, *dt = d + 4 * count;
+    launch_bgrat_table(dt, st);
     cudaError_t e = cudaMemcpyAsync(ds, s, bytes, cudaMemcpyDefault, st);
     if (e == cudaSuccess && a) e = cudaMemcpyAsync(da, a, bytes, cudaMemcpyDefault, st);
     if (e == cudaSuccess && b) e = cudaMemcpyAsync(db, b, bytes, cudaMemcpyDefault, st);
     if (e == cudaSuccess) {
-        launch_debug_pvalues(kind, ds, a ? da : ds, b ? db : ds, count, dp, st);
+        launch_debug_pvalues(kind, ds, a ? da : ds, b ? db : ds, count, dp, dt, st);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(p, dp, bytes, cudaMemcpyDefault, st);

@@ -56,7 +56,7 @@ struct Workspace {
         kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
         kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kPlShift, kPlVsq,
-        kPresortTmp, kNumSlots
+        kPresortTmp, kBgrat, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -68,6 +68,7 @@ struct Workspace {
         uint64_t gen = 0;
         std::vector<int32_t> vars;
     } plane_key;
+    bool bgrat_ready = false;   // kBgrat holds the p-value expansion coefficients
     static bool plane_slot(int s) { return (s >= kTmpA && s <= kTmpE) || s == kExp || s == kPlShift || s == kPlVsq; }
     size_t total() const {
         size_t t = 0;
@@ -168,8 +169,9 @@ napg_status ensure_presort(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
 namespace napg {
 void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
                        cudaStream_t st);
+void launch_bgrat_table(double *tab, cudaStream_t st);
 void launch_debug_pvalues(int32_t kind, const double *s, const double *a, const double *b, int64_t count, double *p,
-                          cudaStream_t st);
+                          const double *bgrat, cudaStream_t st);
 // prep
 void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int64_t W, double missing,
                          const uint8_t *vtype_dev, const int32_t *nlev_dev, const int32_t *catrow_dev,

@@ -21,13 +21,14 @@ struct PJob {
     int32_t mirror; // > 0: also write at the transposed index of an mirror x mirror matrix
 };
 
-constexpr int kPjBins = 160;
+constexpr int kPjBins = 288;
 
 struct PJobQueue {
     PJob *jobs;         // appended by the finalize kernels
     int32_t *count;     // number of jobs
     int32_t *hist;      // [kPjBins] jobs per key
     int32_t capacity;
+    const double *bgrat;   // sf::bgrat_coefs rows for 2b = 1..64 (NULL: formed per job)
 };
 
 // bucket of log2(v + 1) clipped to [0, 31]
@@ -38,29 +39,38 @@ __device__ __forceinline__ int log_bucket(double v) {
     return e < 0 ? 0 : (e > 31 ? 31 : e);
 }
 
-// key: 5 families x 32 buckets: beta fraction direct / swapped (by the quantity
-// that sets the fraction's length), beta large-a expansion (by 2b), gamma series,
-// gamma fraction. The branch tests mirror sf::ibeta and sf::gamma_q.
+// the incomplete-beta parameters (a, b) and argument (x, y = 1 - x) of a job's
+// p-value; false for the chi-squared (incomplete gamma) kind
+__device__ __forceinline__ bool pjob_beta(const PJob &j, double &a, double &b, double &x, double &y) {
+    switch (j.kind & 0xff) {
+        case kPjCorr: a = 0.5 * (j.a - 2.0); b = 0.5; y = j.s * j.s; x = 1.0 - y; return true;
+        case kPjT: { const double t2 = j.s * j.s; a = 0.5 * j.a; b = 0.5; x = j.a / (j.a + t2); y = t2 / (j.a + t2); } return true;
+        case kPjF: { const double den = j.b + j.a * j.s; a = 0.5 * j.b; b = 0.5 * j.a; x = j.b / den; y = j.a * j.s / den; } return true;
+        default: return false;
+    }
+}
+
+// key: beta continued fraction direct / swapped (32 buckets each, by the
+// quantity that sets the fraction's length), gamma series / fraction (32 each),
+// and the beta large-a expansion (160 buckets: 2b up to 20, then 8 octaves of
+// a y, which sets u = -T ln x and with it the branches and the term count).
+// The branch tests mirror sf::ibeta and sf::gamma_q.
 __device__ __forceinline__ int pjob_key(const PJob &j) {
     double a = 0, b = 0, x = 0, y = 0;
-    switch (j.kind) {
-        case kPjCorr: a = 0.5 * (j.a - 2.0); b = 0.5; y = j.s * j.s; x = 1.0 - y; break;
-        case kPjT: { const double t2 = j.s * j.s; a = 0.5 * j.a; b = 0.5; x = j.a / (j.a + t2); y = t2 / (j.a + t2); } break;
-        case kPjF: { const double den = j.b + j.a * j.s; a = 0.5 * j.b; b = 0.5 * j.a; x = j.b / den; y = j.a * j.s / den; } break;
-        default: {
-            const double ga = 0.5 * j.a, gx = 0.5 * j.s;
-            return (gx < ga + 1.0 ? 96 : 128) + log_bucket(gx < ga + 1.0 ? gx : ga / (gx + 1e-300) * 32.0);
-        }
+    if (!pjob_beta(j, a, b, x, y)) {
+        const double ga = 0.5 * j.a, gx = 0.5 * j.s;
+        return (gx < ga + 1.0 ? 64 : 96) + log_bucket(gx < ga + 1.0 ? gx : ga / (gx + 1e-300) * 32.0);
     }
-    if (sf::ibeta_large_a_applies(a, b, x)) return 64 + min(31, (int)(2.0 * b));
+    if (sf::ibeta_large_a_applies(a, b, x))
+        return 128 + (min(20, (int)(2.0 * b)) - 1) * 8 + min(7, log_bucket(a * y) >> 1);
     const bool swapped = x > (a + 1.0) / (a + b + 2.0);
     return (swapped ? 32 : 0) + log_bucket(swapped ? b * x : a * y);
 }
 
 // Appends a job. Lanes of a warp that push together take their slots with one
-// atomic, and lanes with equal keys add to the histogram with one atomic (all
-// Pearson jobs near the null share a key). The key is kept in the job's kind
-// word (bits 8 and up) for the scatter.
+// atomic, and lanes with equal keys add to the histogram with one atomic (many
+// jobs share a key). The key is kept in the job's kind word (bits 8 and up) for
+// the scatter.
 __device__ __forceinline__ void pjob_push(const PJobQueue &q, PJob j) {
     const int k = pjob_key(j);
     j.kind |= k << 8;
@@ -74,6 +84,15 @@ __device__ __forceinline__ void pjob_push(const PJobQueue &q, PJob j) {
     if (slot < q.capacity) q.jobs[slot] = j;
     const unsigned same = __match_any_sync(act, k);
     if (lane == __ffs(same) - 1) atomicAdd(&q.hist[k], __popc(same));
+}
+
+// Queues the job and returns NaN (its p-value is written by the evaluation), or
+// returns the p-value 0 at once when it certainly underflows (sf::ibeta_underflows).
+__device__ __forceinline__ double pjob_push_p(const PJobQueue &q, const PJob &j) {
+    double a, b, x, y;
+    if (pjob_beta(j, a, b, x, y) && isfinite(j.s) && sf::ibeta_underflows(a, b, y)) return 0.0;
+    pjob_push(q, j);
+    return __longlong_as_double(0x7ff8000000000000LL);
 }
 
 }  // namespace napg

@@ -208,6 +208,13 @@ static __constant__ double kSinhLogCoef[20] = {
     1.7673535198147337e-21, -4.4767587135187734e-23, 1.1339762261688415e-24, -2.8723953344361012e-26,
     7.2758623780743245e-28, -1.8429974703326551e-29, 4.6683671285475223e-31, -1.182511207850315e-32};
 
+// I_x(a,b) is below the smallest subnormal when a >= 20, b <= 32 and a y >= 2000:
+// then -a ln x >= a y >= 2000 while the remaining factor of the integral,
+// Gamma(a+b) / (Gamma(a+1) Gamma(b)) max(1, y^(b-1)), stays far below e^1200.
+__device__ __forceinline__ bool ibeta_underflows(double a, double b, double y) {
+    return a >= 20.0 && b <= 32.0 && a * y >= 2000.0;
+}
+
 // The expansion below applies to I_x(a,b) with a large, b a moderate integer or
 // half-integer and x >= 1/2 (the p-values of t, F and r near the null, where the
 // continued fraction needs about sqrt(a) steps).
@@ -251,15 +258,55 @@ static __constant__ double kInvHalf[161] = {
     0.013157894736842105, 0.013071895424836602, 0.012987012987012988, 0.012903225806451613, 0.01282051282051282, 0.012738853503184714, 0.012658227848101266, 0.012578616352201259,
     0.0125};
 
-static __device__ double ibeta_large_a(double a, double b, double x, double y) {
+// c_k(b) = g_k (b)_{2k}, k = 1..20: the coefficients of the expansion below for
+// one b (row 2b - 1 of a table of kBgratRows rows), by the recurrence for g_k
+constexpr int kBgratTerms = 20, kBgratRows = 64;
+
+__device__ __forceinline__ void bgrat_coefs(double b, double *c) {
+    const double beta = b - 1.0;
+    double g[kBgratTerms + 1];
+    g[0] = 1.0;
+    double poch = 1.0;
+#pragma unroll
+    for (int k = 1; k <= kBgratTerms; ++k) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 1; i <= k; ++i) acc = fma(kSinhLogCoef[i - 1], g[k - i], acc);
+        g[k] = beta * acc * (1.0 / (double)k);
+        poch *= (b + (double)(2 * k - 2)) * (b + (double)(2 * k - 1));
+        c[k - 1] = g[k] * poch;
+    }
+}
+
+// log M for b = 1/2: log Gamma(T + 3/4) - log Gamma(T - 1/4) - (1/2) log T
+// = -sum_m 2 B_{2m+1}(3/4) / (2m (2m+1) T^{2m}) (DLMF 5.11.8; the odd powers
+// cancel because 3/4 + 1/4 = 1); six terms reach 1e-20 at T = 20.
+__device__ __forceinline__ double log_m_half(double invT2) {
+    double s = -0.0067123894890149434408;
+    s = fma(s, invT2, 0.0024090290069580078125);
+    s = fma(s, invT2, -0.00132083892822265625);
+    s = fma(s, invT2, 0.0012410481770833333333);
+    s = fma(s, invT2, -0.00244140625);
+    s = fma(s, invT2, 0.015625);
+    return s * invT2;
+}
+
+// coef: the table row c_k(b) (see bgrat_coefs), or NULL to form it here
+static __device__ double ibeta_large_a(double a, double b, double x, double y, const double *coef) {
     const double T = a + 0.5 * (b - 1.0);
     const double u = -T * ((x <= 0.5) ? log(x) : log1p(-y));
     // the result is below the smallest subnormal: p <= 2 e^-u u^(b+41)
     if (u > 700.0 && u - (b + 41.0) * log(u) > 760.0) return 0.0;
-    // log M from the Stirling forms of log Gamma(a+b) and log Gamma(a)
-    const double inv_a = 1.0 / a;
-    const double logM = (a + b - 0.5) * log1p(b * inv_a) - b * log1p((b - 1.0) * 0.5 * inv_a) - b
-                        + stirling_series(1.0 / (a + b)) - stirling_series(inv_a);
+    const double invT2 = 1.0 / (T * T);
+    double logM;
+    if (b == 0.5) {
+        logM = log_m_half(invT2);
+    } else {
+        // log M from the Stirling forms of log Gamma(a+b) and log Gamma(a)
+        const double inv_a = 1.0 / a;
+        logM = (a + b - 0.5) * log1p(b * inv_a) - b * log1p((b - 1.0) * 0.5 * inv_a) - b
+               + stirling_series(1.0 / (a + b)) - stirling_series(inv_a);
+    }
     int m;             // 2 s
     double Q, th;      // Q = e^u Q(s,u), th = u^s / Gamma(s+1)
     if (b == floor(b)) {
@@ -274,24 +321,22 @@ static __device__ double ibeta_large_a(double a, double b, double x, double y) {
         m += 2;
         th *= u * kInvHalf[m];
     }
-    const double beta = b - 1.0, invT2 = 1.0 / (T * T);
-    double g[21];
-    g[0] = 1.0;
-    double sum = Q, poch = 1.0, pw = 1.0;
+    double cbuf[kBgratTerms];
+    const double *c = coef;
+    if (!c) {
+        bgrat_coefs(b, cbuf);
+        c = cbuf;
+    }
+    double sum = Q, pw = 1.0;
     int small = 0;
 #pragma unroll
-    for (int k = 1; k <= 20; ++k) {
+    for (int k = 1; k <= kBgratTerms; ++k) {
         Q += th; m += 2; th *= u * kInvHalf[m];
         Q += th; m += 2; th *= u * kInvHalf[m];
-        poch *= (b + (double)(2 * k - 2)) * (b + (double)(2 * k - 1));
         pw *= invT2;
-        double acc = 0.0;
-#pragma unroll
-        for (int i = 1; i <= k; ++i) acc = fma(kSinhLogCoef[i - 1], g[k - i], acc);
-        g[k] = beta * acc * (1.0 / (double)k);
-        const double term = g[k] * poch * pw * Q;
+        const double term = c[k - 1] * pw * Q;
         sum += term;
-        // two consecutive negligible terms (a single g_k can vanish for some b)
+        // two consecutive negligible terms (a single c_k can vanish for some b)
         if (fabs(term) <= 1e-17 * fabs(sum)) {
             if (++small == 2) break;
         } else {
@@ -303,12 +348,15 @@ static __device__ double ibeta_large_a(double a, double b, double x, double y) {
     return exp(e + log(sum));
 }
 
-// regularized I_x(a,b) with x + y = 1 supplied
-static __device__ double ibeta(double a, double b, double x, double y) {
+// regularized I_x(a,b) with x + y = 1 supplied; bgrat: table of c_k(b) rows
+// for 2b = 1..kBgratRows (or NULL)
+static __device__ double ibeta(double a, double b, double x, double y, const double *bgrat = nullptr) {
     if (!(a > 0.0) || !(b > 0.0) || isnan(x) || isnan(y)) return nan("");
     if (x <= 0.0) return 0.0;
     if (y <= 0.0) return 1.0;
-    if (ibeta_large_a_applies(a, b, x)) return ibeta_large_a(a, b, x, y);
+    if (ibeta_underflows(a, b, y)) return 0.0;
+    if (ibeta_large_a_applies(a, b, x))
+        return ibeta_large_a(a, b, x, y, bgrat ? bgrat + ((int)(2.0 * b) - 1) * kBgratTerms : nullptr);
     if (x > (a + 1.0) / (a + b + 2.0)) return 1.0 - ibeta_lower(b, a, y, x);
     return ibeta_lower(a, b, x, y);
 }
@@ -352,27 +400,27 @@ static __device__ double gamma_q(double a, double x) {
 }
 
 // two-sided p of Student t with df degrees of freedom
-__device__ __forceinline__ double t_two_sided(double t, double df) {
+__device__ __forceinline__ double t_two_sided(double t, double df, const double *bgrat = nullptr) {
     if (isnan(t) || !(df > 0.0)) return nan("");
     if (isinf(t)) return 0.0;
     const double t2 = t * t;
-    return ibeta(0.5 * df, 0.5, df / (df + t2), t2 / (df + t2));
+    return ibeta(0.5 * df, 0.5, df / (df + t2), t2 / (df + t2), bgrat);
 }
 
 // p of a correlation coefficient with n observations: I_{1-r^2}((n-2)/2, 1/2)
-__device__ __forceinline__ double corr_p(double r, double n) {
+__device__ __forceinline__ double corr_p(double r, double n, const double *bgrat = nullptr) {
     if (isnan(r) || n <= 2.0) return nan("");
     if (fabs(r) >= 1.0) return 0.0;
-    return ibeta(0.5 * (n - 2.0), 0.5, (1.0 - r) * (1.0 + r), r * r);
+    return ibeta(0.5 * (n - 2.0), 0.5, (1.0 - r) * (1.0 + r), r * r, bgrat);
 }
 
 // survival function of F(d1, d2)
-__device__ __forceinline__ double f_sf(double F, double d1, double d2) {
+__device__ __forceinline__ double f_sf(double F, double d1, double d2, const double *bgrat = nullptr) {
     if (isnan(F) || !(d1 > 0.0) || !(d2 > 0.0)) return nan("");
     if (isinf(F)) return 0.0;
     if (F <= 0.0) return 1.0;
     const double den = d2 + d1 * F;
-    return ibeta(0.5 * d2, 0.5 * d1, d2 / den, d1 * F / den);
+    return ibeta(0.5 * d2, 0.5 * d1, d2 / den, d1 * F / den, bgrat);
 }
 
 __device__ __forceinline__ double chi2_sf(double x, double df) {
