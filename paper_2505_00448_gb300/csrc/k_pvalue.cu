@@ -17,13 +17,27 @@ __global__ void k_pj_scan(const int32_t *hist, int32_t *offs, int32_t *cursor) {
     }
 }
 
+// Lanes of a warp with the same key take consecutive slots with one atomic
+// (most jobs share a few keys, so per-job atomics would serialise).
 __global__ void k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t capacity, const int32_t *offs,
                              int32_t *cursor, PJob *sorted) {
     const int32_t n = min(*count, capacity);
-    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const PJob j = jobs[t];
-        const int k = j.kind >> 8;
-        sorted[offs[k] + atomicAdd(&cursor[k], 1)] = j;
+    const int lane = threadIdx.x & 31;
+    const int32_t stride = gridDim.x * blockDim.x;
+    for (int32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n; t0 += stride) {   // warp-uniform
+        const int32_t t = t0 + lane;
+        PJob j;
+        int k = kPjBins;                     // no job
+        if (t < n) {
+            j = jobs[t];
+            k = j.kind >> 8;
+        }
+        const unsigned same = __match_any_sync(0xffffffffu, k);
+        const int leader = __ffs(same) - 1;
+        int base = 0;
+        if (lane == leader && k < kPjBins) base = atomicAdd(&cursor[k], __popc(same));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (k < kPjBins) sorted[offs[k] + base + __popc(same & ((1u << lane) - 1u))] = j;
     }
 }
 
