@@ -331,12 +331,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 // restart every chunk and are drained: counts as exact integers, the hi sums by
 // TwoSum into float-float running sums, the lo sums into the low parts.
 constexpr int kSV = 48;            // B variables per tile
-constexpr int kSN = 5 * kSV;       // MMA N
 constexpr int kSPerThread = kSV / 2;
+constexpr int kSGroup = 16;        // A tiles per rasterisation group
 
 struct StackParams {
     CUtensorMap mapA;              // 0/1 plane, box 64 x 128
-    CUtensorMap mapB[5];           // M, Xh, Xl, Dh, Dl of the B variables, box 64 x kSV
+    CUtensorMap mapB[5];           // M, Xh, Xl, Dh[, Dl] of the B variables, box 64 x kSV
     int rowsA, rowsB;              // valid rows of A and B
     int tilesA, tilesB;
     int nkb, chunk;                // K-blocks, K-blocks per drain
@@ -348,12 +348,18 @@ struct StackParams {
     uint32_t *err;
 };
 
-template <int STAGES>
+// NPL planes stacked (M, Xh, Xl, Dh, Dl: 5). Dropping Dl is not an option for the
+// group sums either: the FP16 rounding of the centred squares leaves ~2^-12 /
+// sqrt(n) relative error on the within-group sum, which at n of a few hundred and
+// F well above 1 moves the F statistic's effect-scale value by more than 1e-6.
+template <int NPL, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_constant__ StackParams P) {
     constexpr int A_BYTES = kTM * kKB * 2;
     constexpr int BP_BYTES = kSV * kKB * 2;
-    constexpr int STAGE_BYTES = A_BYTES + 5 * BP_BYTES;
+    constexpr int STAGE_BYTES = A_BYTES + NPL * BP_BYTES;
+    constexpr int kSN = NPL * kSV;    // MMA N
     static_assert(BP_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "8-row swizzle atoms stay 1024-B aligned");
+    static_assert(kSN % 16 == 0 && kSN <= 256, "N");
     constexpr uint32_t IDESC = idesc_f16_f32(kTM, kSN);
     constexpr int BUF = 256;       // tensor-memory columns per accumulator buffer (kSN used)
 
@@ -367,8 +373,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
     uint32_t *tslot = (uint32_t *)(mdone + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // consecutive CTAs step through A tiles and share the (five-plane) B tile
-    const int J = blockIdx.x / P.tilesA, I = blockIdx.x - J * P.tilesA;
+    // grouped rasterisation: within a group of kSGroup A tiles, consecutive CTAs
+    // step through the A tiles of the group, then the B tiles, so a wave of
+    // resident CTAs covers a block of both operands and streams each from HBM
+    // about once
+    int I, J;
+    {
+        const int per_group = kSGroup * P.tilesB;
+        const int g = blockIdx.x / per_group, r = blockIdx.x - g * per_group;
+        const int gsz = min(kSGroup, P.tilesA - g * kSGroup);
+        J = r / gsz;
+        I = g * kSGroup + (r - J * gsz);
+    }
     const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;
 
     if (threadIdx.x == 0) {
@@ -388,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
         const uint32_t leader = lane == 0;
         if (leader) {
             prefetch_tmap(&P.mapA);
-            for (int p = 0; p < 5; ++p) prefetch_tmap(&P.mapB[p]);
+            for (int p = 0; p < NPL; ++p) prefetch_tmap(&P.mapB[p]);
         }
         int issued = 0;
         for (int kb = 0; kb < P.nkb; ++kb) {
@@ -398,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             uint8_t *st = smem + s * STAGE_BYTES;
             tma_load_2d_by(st, &P.mapA, &full[s], kb * kKB, I * kTM, leader);
 #pragma unroll
-            for (int p = 0; p < 5; ++p)
+            for (int p = 0; p < NPL; ++p)
                 tma_load_2d_by(st + A_BYTES + p * BP_BYTES, &P.mapB[p], &full[s], kb * kKB, J * kSV, leader);
             issued = kb + 1;
         }
@@ -454,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             fence_after_sync();
             const uint32_t col0 = tbase + lane_addr + (uint32_t)(b * BUF + h * kSPerThread);
 #pragma unroll
-            for (int p = 0; p < 5; ++p) {
+            for (int p = 0; p < NPL; ++p) {
                 uint32_t r[kSPerThread];
 #pragma unroll
                 for (int g = 0; g < kSPerThread / 8; ++g) {
@@ -677,11 +693,12 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
     return NAPG_OK;
 }
 
+template <int NPL>
 static napg_status launch_stacked(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
-    constexpr int STAGES = 4;
-    constexpr int STAGE_BYTES = kTM * kKB * 2 + 5 * kSV * kKB * 2;
+    constexpr int STAGES = NPL == 5 ? 4 : 5;
+    constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * kSV * kKB * 2;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    auto kern = k_umma_stacked<STAGES>;
+    auto kern = k_umma_stacked<NPL, STAGES>;
     NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int tiles = P.tilesA * P.tilesB;
     if (tiles == 0) return NAPG_OK;
@@ -816,7 +833,7 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_stacked(ctx, P, st));
+        NAPG_ST(launch_stacked<5>(ctx, P, st));
     }
     return NAPG_OK;
 }
@@ -840,7 +857,7 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     P.out_n = gn; P.out_s1 = g1; P.out_s2 = g2; P.ld = nb; P.out_transpose = 0;
     P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
     Stage s_(ctx->trace, st, "groupsum_tc");
-    return launch_stacked(ctx, P, st);
+    return launch_stacked<5>(ctx, P, st);
 }
 
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
