@@ -312,6 +312,295 @@ def load_traffic(kernel):
         return None
 
 
+# ------------------------------------------------------------ serve workload --
+
+def serve_requests(coh, rng, count):
+    """Random requests of the serving workload: test, mask, variable subset."""
+    S = coh["X"].shape[1]
+    cont, cat = coh["cont"], coh["cat"]
+    out = []
+    for _ in range(count):
+        test = ["pearson", "spearman", "chi2", "kruskal"][int(rng.integers(0, 4))]
+        frac = rng.uniform(0.05, 0.8)
+        mask = (rng.random(S) < frac).astype(np.uint8)
+        k = int(rng.integers(50, 2001))
+        if test in ("pearson", "spearman"):
+            va, vb = np.sort(rng.choice(cont, k, replace=False)), None
+            pairs = k * (k - 1) // 2
+        elif test == "chi2":
+            va, vb = np.sort(rng.choice(cat, k, replace=False)), None
+            pairs = k * (k - 1) // 2
+        else:
+            va = np.sort(rng.choice(cat, k // 2, replace=False))
+            vb = np.sort(rng.choice(cont, k - k // 2, replace=False))
+            pairs = len(va) * len(vb)
+        out.append((test, va, vb, mask, pairs))
+    return out
+
+
+def serve_main(args, world, rank, local_rank):
+    """Request loop on the resident config-5 cohort; one replica per GPU."""
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    device = local_rank if world > 1 else 0
+    torch.cuda.set_device(device)
+    from paper_2505_00448_gb300 import napg
+    coh = synth.config5()
+    prec = args.precision
+    ctx = napg.Context(device)
+    ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    rng = np.random.default_rng(5 + rank)
+    slots = 4
+    t0 = time.perf_counter()
+    ctx.serve_start(0, slots)
+    t_start = time.perf_counter() - t0
+    # warm-up, then the single-request service time (one request in flight at a time)
+    for test, va, vb, m, _ in serve_requests(coh, rng, 4):
+        ctx.serve_wait(ctx.serve_submit(test, va, vb, mask=m, precision=prec))
+    single = []
+    for test, va, vb, m, pairs in serve_requests(coh, rng, 12):
+        lat, st, _ = ctx.serve_wait(ctx.serve_submit(test, va, vb, mask=m, precision=prec))
+        single.append(lat)
+    mu = 1000.0 / statistics.mean(single)          # requests per second, one at a time
+    launches0 = napg.kernel_launches()
+    clocks = ClockSampler(device)
+    clocks.start()
+    sweep = []
+    for f in (0.25, 0.5, 0.75, 0.9, 1.1, 1.5):
+        lam = f * mu
+        reqs = serve_requests(coh, rng, args.serve_requests)
+        gaps = rng.exponential(1.0 / lam, len(reqs))
+        pending = {}
+        lat = []
+        pairs_done = 0
+        t_begin = time.perf_counter()
+        t_next = t_begin
+        i = 0
+        while i < len(reqs) or pending:
+            now = time.perf_counter()
+            while i < len(reqs) and now >= t_next:
+                test, va, vb, m, pairs = reqs[i]
+                pending[ctx.serve_submit(test, va, vb, mask=m, precision=prec)] = pairs
+                t_next += gaps[i]
+                i += 1
+            for tk in list(pending):
+                d, l, st, _ = ctx.serve_poll(tk)
+                if d:
+                    lat.append(l)
+                    pairs_done += pending.pop(tk)
+            time.sleep(2e-4)
+        wall = time.perf_counter() - t_begin
+        lat.sort()
+        sweep.append({"load": f, "lambda_per_s": lam, "requests": len(lat), "wall_s": wall,
+                      "p50_ms": statistics.median(lat), "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                      "pairs_per_s": pairs_done / wall})
+    clk = clocks.stop()
+    launches = napg.kernel_launches() - launches0
+    ctx.serve_stop()
+    ctx.close()
+    sat = max(sweep, key=lambda r: r["pairs_per_s"])
+    value = sat["pairs_per_s"]
+    if dist:
+        t = torch.tensor([value], device=torch.device("cuda", device))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        value = float(t.item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.serve_requests,
+                "warmup": 4, "ms_per_step": statistics.mean(single), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f16x2-split/f32-acc/f64" if prec == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": "serving loop: resident 100,000-sample x 10,000-variable cohort (8,000 "
+                           "continuous FP32, 2,000 categorical 2-8 levels, 35% MCAR); Poisson requests, each a "
+                           "random test (Pearson, Spearman, chi-squared, Kruskal-Wallis), mask of 5-80% of the "
+                           "samples and 50-2,000 variables; value = pairs/s at the best rate of the sweep",
+                           "precision": prec, "slots": slots, "serve_start_s": t_start,
+                           "single_request_ms_mean": statistics.mean(single),
+                           "capacity_req_per_s": mu, "sweep": sweep},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ batch workload --
+
+def batch_main(args, world, rank, local_rank):
+    """256 sample contexts per test in one napg_run_batch call each (replicas per GPU)."""
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    device = local_rank if world > 1 else 0
+    torch.cuda.set_device(device)
+    from paper_2505_00448_gb300 import napg
+    coh = synth.config4()
+    masks = coh["contexts"]
+    K, S = masks.shape
+    tests = [("pearson", coh["cont"]), ("chi2", coh["cat"])]
+    desc = ("batched contexts: 256 sample subsets (500-20,000 of 20,000 samples, log-uniform sizes, random "
+            "condition masks) of a 1,600 continuous FP32 + 400 categorical (2-6 levels) cohort, 25% MCAR; "
+            "per context all-pairs Pearson + chi-squared; one napg_run_batch call (one captured CUDA graph) per test")
+    prec = args.precision
+    ctx = napg.Context(device)
+    stream = ctx.stream
+    torch.cuda.set_stream(stream)
+    ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    dev = torch.device("cuda", device)
+    dmask = torch.from_numpy(masks).to(dev)
+    mlist = [dmask[k] for k in range(K)]
+    outs = {}
+    for test, va in tests:
+        n = len(va)
+        outs[test] = [{"stat": torch.empty((n, n), dtype=torch.float64, device=dev),
+                       "p": torch.empty((n, n), dtype=torch.float64, device=dev),
+                       "n": torch.empty((n, n), dtype=torch.int32, device=dev)} for _ in range(K)]
+
+    def step():
+        ctx.release_cache()
+        for test, va in tests:
+            ctx.run_batch(test, mlist, va, out="cuda", outputs=outs[test], sync=False, precision=prec)
+
+    t_first = time.perf_counter()
+    step()                               # sizing run + capture of both graphs
+    torch.cuda.synchronize()
+    t_first = time.perf_counter() - t_first
+    for _ in range(args.warmup - 1):
+        step()
+    torch.cuda.synchronize()
+    launches0 = napg.kernel_launches()
+    clocks = ClockSampler(device)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    per_step = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        per_step.append((a, b))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = napg.kernel_launches() - launches0
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    step_ms = sorted(a.elapsed_time(b) for a, b in per_step)
+    pairs_ctx = {t: len(va) * (len(va) - 1) // 2 for t, va in tests}
+    pairs_step = K * sum(pairs_ctx.values())
+    value = world * pairs_step / (ms_step / 1000.0)
+
+    # accuracy of the timed outputs on a few contexts (random pairs) against the oracle
+    accuracy = None
+    if rank == 0 and args.accuracy_pairs > 0:
+        from oracle import oracle as O
+        rng = np.random.default_rng(7)
+        X = coh["X"].astype(np.float64)
+        accuracy = {}
+        for test, va in tests:
+            worst, worst_p, n_ok, cnt = 0.0, 0.0, True, 0
+            for k in rng.choice(K, size=3, replace=False):
+                ia = rng.integers(0, len(va), args.accuracy_pairs // 3)
+                ib = rng.integers(0, len(va), args.accuracy_pairs // 3)
+                st, pv, nn = O.run_pairs(test, X, coh["missing"], coh["vtype"], coh["nlev"], va[ia], va[ib],
+                                         ctx=masks[k], validate=False)
+                gs = outs[test][k]["stat"].cpu().numpy()[ia, ib]
+                gp = outs[test][k]["p"].cpu().numpy()[ia, ib]
+                gn = outs[test][k]["n"].cpu().numpy()[ia, ib]
+                fin = np.isfinite(st) & np.isfinite(gs)
+                d = np.abs(gs - st)[fin] if test == "pearson" else (np.abs(gs - st) / np.maximum(np.abs(st), 1e-300))[fin]
+                worst = max(worst, float(d.max(initial=0.0)))
+                pok = np.isfinite(pv) & (pv > 1e-300) & np.isfinite(gp)
+                if pok.any():
+                    worst_p = max(worst_p, float((np.abs(gp[pok] - pv[pok]) / pv[pok]).max()))
+                n_ok = n_ok and bool(np.array_equal(gn, nn))
+                cnt += len(ia)
+            accuracy[test] = {"pairs": cnt, "contexts": 3, "stat_error": worst,
+                              "stat_metric": "max |d r|" if test == "pearson" else "max rel d stat",
+                              "p_rel_error_max": worst_p, "n_exact": n_ok}
+
+    # end to end through the public API with host buffers: cohort and masks in, outputs out
+    e2e = None
+    if not args.no_e2e:
+        host_outs = {t: [{"stat": np.empty((len(va), len(va))), "p": np.empty((len(va), len(va))),
+                          "n": np.empty((len(va), len(va)), np.int32)} for _ in range(K)] for t, va in tests}
+        hmasks = [masks[k] for k in range(K)]
+        h2d = coh["X"].nbytes + masks.nbytes
+        d2h = sum(sum(a.nbytes for a in o.values()) for v in host_outs.values() for o in v)
+        ctx2 = napg.Context(device)
+        times = []
+        for k in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx2.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+            for test, va in tests:
+                ctx2.run_batch(test, hmasks, va, out="numpy", outputs=host_outs[test], precision=prec)
+            times.append(time.perf_counter() - t0)
+        ctx2.close()
+        e2e = {"value": world * pairs_step / statistics.mean(times[1:] or times), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1000 * statistics.mean(times[1:] or times),
+               "path": "host outputs: per-context loop (the graph path takes device outputs)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        rng = np.random.default_rng(11)
+        X = coh["X"].astype(np.float64)
+        sizes = masks.sum(axis=1)
+        est, desc_s = 0.0, []
+        for test, va in tests:
+            # cost per pair is about proportional to the context size: time random
+            # pairs on 3 contexts and scale by the batch's total samples
+            per_sample = []
+            for k in rng.choice(K, size=3, replace=False):
+                m = 2000 if test == "pearson" else 1000
+                pa, pb = rng.choice(va, m), rng.choice(va, m)
+                t0 = time.perf_counter()
+                O.run_pairs(test, X, coh["missing"], coh["vtype"], coh["nlev"], pa, pb, ctx=masks[k], validate=False)
+                dt = time.perf_counter() - t0
+                per_sample.append(dt / (m * sizes[k]))
+                desc_s.append(f"{test}: {m} pairs in context {k} ({sizes[k]} samples) {dt:.2f}s")
+            est += statistics.mean(per_sample) * pairs_ctx[test] * float(sizes.sum())
+        cpu = {"value": pairs_step / est, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+               "sample": "; ".join(desc_s) + "; extrapolated by pairs x total context samples"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f16x2-split/f32-acc/f64" if prec == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": desc, "precision": prec, "contexts": int(K), "pairs_per_step": pairs_step,
+                           "context_samples_total": int(masks.sum()),
+                           "l2": "cohort (160 MB) and outputs (13.9 GB) larger than L2: no flush between steps",
+                           "first_call_s": t_first, "step_ms_p50": statistics.median(step_ms),
+                           "step_ms_p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
+                "roofline": None, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk, "accuracy_vs_oracle": accuracy}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 # -------------------------------------------------------------------- main --
 
 def main():
