@@ -591,7 +591,7 @@ def batch_main(args, world, rank, local_rank):
                 "config": {"workload": desc, "precision": prec, "contexts": int(K), "pairs_per_step": pairs_step,
                            "context_samples_total": int(masks.sum()),
                            "l2": "cohort (160 MB) and outputs (13.9 GB) larger than L2: no flush between steps",
-                           "first_call_s": t_first, "step_ms_p50": statistics.median(step_ms),
+                           "first_call_s": t_first, "autotuned": ctx.tune_read(), "step_ms_p50": statistics.median(step_ms),
                            "step_ms_p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))]},
                 "roofline": None, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk, "accuracy_vs_oracle": accuracy}
@@ -802,7 +802,8 @@ def main():
                            "per_test_ms": {t: statistics.median(v) for t, v in per_test_ms.items()},
                            "per_test_pairs_per_s": {t: pair_count(t, va, vb) / (statistics.median(per_test_ms[t]) / 1e3)
                                                     for t, va, vb in tests},
-                           "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()}},
+                           "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()},
+                           "autotuned": ctx.tune_read()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator}
         print(json.dumps(line), flush=True)

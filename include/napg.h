@@ -248,6 +248,17 @@ napg_status napg_serve_plan(const uint64_t *est, const double *age_ms, int32_t n
 napg_status napg_trace_enable(napg_ctx *ctx, int32_t on);
 napg_status napg_trace_read(napg_ctx *ctx, char *buf, size_t cap);
 
+/* Autotuner (on by default): the first run of a problem shape times each
+ * launch-shape candidate of its tunable kernels once (the B-tile width of the
+ * stacked tensor contractions, threads per pair of the rank kernels) and keeps
+ * the fastest for the context; candidates give identical results. Runs being
+ * captured into a CUDA graph use the choice recorded for the nearest shape.
+ * napg_tune_read writes the records as JSON
+ *   [{"kind": K, "rows_a": A, "rows_b": B, "k": L, "choice": C, "ms": [...]}, ...]
+ * Errors: NAPG_E_ARG (NULL context, buffer too small). */
+napg_status napg_tune_enable(napg_ctx *ctx, int32_t on);
+napg_status napg_tune_read(napg_ctx *ctx, char *buf, size_t cap);
+
 /* Number of kernels this process has launched through the library so far. */
 uint64_t napg_kernel_launches(void);
 

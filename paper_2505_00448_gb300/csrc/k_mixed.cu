@@ -330,13 +330,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 // the tensor core's operand path carries). All five blocks of the accumulator
 // restart every chunk and are drained: counts as exact integers, the hi sums by
 // TwoSum into float-float running sums, the lo sums into the low parts.
-constexpr int kSV = 48;            // B variables per tile
-constexpr int kSPerThread = kSV / 2;
+// SV = B variables per tile (a multiple of 16: the epilogue's two halves read
+// 8-column groups); the autotuner picks 32 or 48 per shape.
 constexpr int kSGroup = 16;        // A tiles per rasterisation group
 
 struct StackParams {
     CUtensorMap mapA;              // 0/1 plane, box 64 x 128
-    CUtensorMap mapB[5];           // M, Xh, Xl, Dh[, Dl] of the B variables, box 64 x kSV
+    CUtensorMap mapB[5];           // M, Xh, Xl, Dh[, Dl] of the B variables, box 64 x SV
     int rowsA, rowsB;              // valid rows of A and B
     int tilesA, tilesB;
     int nkb, chunk;                // K-blocks, K-blocks per drain
@@ -352,8 +352,11 @@ struct StackParams {
 // group sums either: the FP16 rounding of the centred squares leaves ~2^-12 /
 // sqrt(n) relative error on the within-group sum, which at n of a few hundred and
 // F well above 1 moves the F statistic's effect-scale value by more than 1e-6.
-template <int NPL, int STAGES>
+template <int NPL, int SV, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_constant__ StackParams P) {
+    constexpr int kSV = SV;
+    constexpr int kSPerThread = SV / 2;
+    static_assert(SV % 16 == 0, "SV");
     constexpr int A_BYTES = kTM * kKB * 2;
     constexpr int BP_BYTES = kSV * kKB * 2;
     constexpr int STAGE_BYTES = A_BYTES + NPL * BP_BYTES;
@@ -693,12 +696,12 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
     return NAPG_OK;
 }
 
-template <int NPL>
-static napg_status launch_stacked(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
-    constexpr int STAGES = NPL == 5 ? 4 : 5;
-    constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * kSV * kKB * 2;
+template <int NPL, int SV>
+static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
+    constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * SV * kKB * 2;
+    constexpr int STAGES = (220 * 1024) / STAGE_BYTES > 6 ? 6 : (220 * 1024) / STAGE_BYTES;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    auto kern = k_umma_stacked<NPL, STAGES>;
+    auto kern = k_umma_stacked<NPL, SV, STAGES>;
     NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int tiles = P.tilesA * P.tilesB;
     if (tiles == 0) return NAPG_OK;
@@ -706,6 +709,26 @@ static napg_status launch_stacked(napg_ctx *ctx, const StackParams &P, cudaStrea
     kern<<<tiles, kThreads, smem, st>>>(P);
     NAPG_CU(ctx, cudaGetLastError());
     return NAPG_OK;
+}
+
+// B-tile widths the autotuner chooses from (every width gives the same sums:
+// each output accumulates the same products in the same order and drains)
+constexpr int kStackWidths[2] = {48, 32};
+
+// A x stacked B planes with the B-tile width chosen by the autotuner for this
+// shape (the tensor maps of the B planes are encoded for that width)
+static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *const *pb, int64_t rows_b_pad,
+                                  int64_t S_pad, int kind, cudaStream_t st) {
+    auto run = [&](int choice) -> napg_status {
+        const int sv = kStackWidths[choice];
+        for (int k = 0; k < 5; ++k)
+            if (!make_map(&P.mapB[k], pb[k], rows_b_pad, S_pad, sv))
+                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        P.tilesB = (P.rowsB + sv - 1) / sv;
+        return sv == 48 ? launch_stacked_sv<5, 48>(ctx, P, st) : launch_stacked_sv<5, 32>(ctx, P, st);
+    };
+    const TuneKey key{kind, P.rowsA, P.rowsB, P.nkb};
+    return tuned_launch(ctx, key, 2, run, st);
 }
 
 struct ContPlanes {
@@ -825,15 +848,12 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         if (!make_map(&P.mapA, cp.M, cp.rows_pad, cp.S_pad, kTM))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
-        for (int k = 0; k < 5; ++k)
-            if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, kSV))
-                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = (nv + kSV - 1) / kSV;
+        P.rowsA = nv; P.rowsB = nv; P.tilesA = T;
         P.nkb = nkb; P.chunk = kChunkOther;
         P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_stacked<5>(ctx, P, st));
+        NAPG_ST(launch_stacked(ctx, P, pb, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
     }
     return NAPG_OK;
 }
@@ -849,15 +869,12 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     StackParams P{};
     if (!make_map(&P.mapA, H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
     const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
-    for (int k = 0; k < 5; ++k)
-        if (!make_map(&P.mapB[k], pb[k], cp.rows_pad, cp.S_pad, kSV))
-            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-    P.rowsA = R; P.rowsB = nb; P.tilesA = (int)(hrows / kTM); P.tilesB = (nb + kSV - 1) / kSV;
+    P.rowsA = R; P.rowsB = nb; P.tilesA = (int)(hrows / kTM);
     P.nkb = (int)(S_pad / kKB); P.chunk = kChunkOther;
     P.out_n = gn; P.out_s1 = g1; P.out_s2 = g2; P.ld = nb; P.out_transpose = 0;
     P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
     Stage s_(ctx->trace, st, "groupsum_tc");
-    return launch_stacked<5>(ctx, P, st);
+    return launch_stacked(ctx, P, pb, cp.rows_pad, cp.S_pad, kTuneStackOneHot, st);
 }
 
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,

@@ -437,16 +437,18 @@ static size_t rank_smem_bytes(int64_t W, int sides, bool with_co) {
 // keeps 32 warps resident instead.
 static int rank_threads(size_t smem) { return smem > (size_t)56 * 1024 ? 1024 : 256; }
 
+int rank_threads_default(int64_t W, bool groups) { return rank_threads(rank_smem_bytes(W, groups ? 1 : 2, true)); }
+
 void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b, const uint32_t *obs_a,
                            const uint32_t *obs_b, int32_t na, int32_t nb, int32_t symmetric, int64_t *out4,
-                           cudaStream_t st) {
+                           cudaStream_t st, int threads) {
     const int64_t pairs = symmetric ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
     if (pairs == 0) return;
     const size_t smem = rank_smem_bytes(rd.W, 2, true);
     cudaFuncSetAttribute(k_spearman, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
-    k_spearman<<<(unsigned)pairs, rank_threads(smem), smem, st>>>(rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric,
-                                                                  out4);
+    k_spearman<<<(unsigned)pairs, threads > 0 ? threads : rank_threads(smem), smem, st>>>(
+        rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric, out4);
 }
 
 // ------------------------------------------------------------ MWU / Kruskal --
@@ -533,12 +535,12 @@ __global__ void __launch_bounds__(1024) k_rank_groups(RankData rd, const uint8_t
 void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a, const int32_t *nlev_a,
                         const int32_t *levoff_a, int32_t na, const int32_t *crow_b, const uint32_t *obs_a,
                         const uint32_t *obs_b, int32_t nb, int32_t total_rows, int64_t *rsum, int32_t *rcnt,
-                        int64_t *tie_term, cudaStream_t st) {
+                        int64_t *tie_term, cudaStream_t st, int threads_req) {
     (void)total_rows;
     const int64_t pairs = (int64_t)na * nb;
     if (pairs == 0) return;
     const size_t side = rank_smem_bytes(rd.W, 1, true);
-    const int threads = rank_threads(side);
+    const int threads = threads_req > 0 ? threads_req : rank_threads(side);
     const size_t smem = side + (size_t)(threads / 32) * kMaxLevels * 12;
     cudaFuncSetAttribute(k_rank_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();

@@ -446,7 +446,16 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         int64_t *q = WS(kMomA, int64_t, (int64_t)na * nb * 4);
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
-        { Stage s_(ctx->trace, st, "spearman_rank"); launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st); }
+        {
+            Stage s_(ctx->trace, st, "spearman_rank");
+            const int t0 = rank_threads_default(W, false), cand[2] = {t0, t0 == 256 ? 1024 : 256};
+            auto run = [&](int c) -> napg_status {
+                launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st, cand[c]);
+                NAPG_CU(ctx, cudaGetLastError());
+                return NAPG_OK;
+            };
+            NAPG_ST(tuned_launch(ctx, TuneKey{kTuneSpearman, na, nb, W}, 2, run, st));
+        }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
         SpearmanFin f{q, na, nb, symmetric ? 1 : 0, pj.q};
@@ -461,7 +470,17 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         int32_t *flags = WS(kFlagList, int32_t, (int64_t)na * nb + 1);
         if (st_) return st_;
         RankData rd{c.perm, c.pos, c.nobs, c.tie, c.gsw, c.gew, S, W};
-        { Stage s_(ctx->trace, st, "rank_groups"); launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st); }
+        {
+            Stage s_(ctx->trace, st, "rank_groups");
+            const int t0 = rank_threads_default(W, true), cand[2] = {t0, t0 == 256 ? 1024 : 256};
+            auto run = [&](int cc) -> napg_status {
+                launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st,
+                                   cand[cc]);
+                NAPG_CU(ctx, cudaGetLastError());
+                return NAPG_OK;
+            };
+            NAPG_ST(tuned_launch(ctx, TuneKey{kTuneRankGroups, na, nb, W}, 2, run, st));
+        }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr && t == NAPG_KRUSKAL, pj));
         RankGroupFin f{rsum, rcnt, tie, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.mwu_mode, a.opt.mwu_continuity, pj.q};

@@ -5,6 +5,8 @@
 
 #include <cstdint>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -77,6 +79,25 @@ struct Workspace {
     }
 };
 
+// ---- autotuner (tune.cu)
+enum TuneKind : int { kTuneStackMask = 1, kTuneStackOneHot = 2, kTuneSpearman = 3, kTuneRankGroups = 4 };
+struct TuneKey {
+    int kind;
+    int64_t a, b, c;    // rows of A, rows of B, K length (shape of the problem)
+    bool operator<(const TuneKey &o) const {
+        if (kind != o.kind) return kind < o.kind;
+        if (a != o.a) return a < o.a;
+        if (b != o.b) return b < o.b;
+        return c < o.c;
+    }
+};
+struct TuneRec { int choice; std::vector<float> ms; };
+struct Tuner {
+    std::mutex mu;
+    bool on = true;
+    std::map<TuneKey, TuneRec> best;
+};
+
 struct ServeState;   // serving loop (serve.cu)
 struct BatchState;   // batched contexts (batch.cu)
 
@@ -119,6 +140,7 @@ struct napg_ctx {
     napg::ServeState *serve = nullptr;
     napg::BatchState *batch = nullptr;
     napg::Tracer trace;
+    napg::Tuner tune;
     std::mutex mu;                     // guards cohort/workspace use from the serving threads
 };
 
@@ -153,6 +175,9 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
 void free_cohort(Cohort &c);
 uint64_t next_cohort_gen();
 napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape);
+// runs run(choice) with the launch shape the autotuner picks for `key`
+napg_status tuned_launch(napg_ctx *ctx, const TuneKey &key, int ncand, const std::function<napg_status(int)> &run,
+                         cudaStream_t st);
 napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uint8_t *const *masks,
                       double *const *stat, double *const *pval, int32_t *const *n);
 void free_batch(napg_ctx *ctx);
@@ -242,11 +267,12 @@ struct RankData {
 };
 void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b,
                            const uint32_t *obs_a, const uint32_t *obs_b, int32_t na, int32_t nb,
-                           int32_t symmetric, int64_t *out4, cudaStream_t st);
+                           int32_t symmetric, int64_t *out4, cudaStream_t st, int threads = 0);
+int rank_threads_default(int64_t W, bool groups);
 void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a,
                         const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
                         const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int32_t total_rows,
-                        int64_t *rsum, int32_t *rcnt, int64_t *tie_term, cudaStream_t st);
+                        int64_t *rsum, int32_t *rcnt, int64_t *tie_term, cudaStream_t st, int threads = 0);
 struct SpearmanFin { const int64_t *q; int32_t na, nb; int32_t symmetric; PJobQueue pq; };
 void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
 struct RankGroupFin {

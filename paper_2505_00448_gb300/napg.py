@@ -30,7 +30,7 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync", "napg_release_cache",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_debug_pvalues", "napg_serve_start",
            "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_serve_plan", "napg_version", "napg_trace_enable",
-           "napg_trace_read", "napg_kernel_launches", "napg_pearson_fp64_noalloc"]
+           "napg_trace_read", "napg_kernel_launches", "napg_tune_enable", "napg_tune_read", "napg_pearson_fp64_noalloc"]
 
 
 class Options(C.Structure):
@@ -81,6 +81,10 @@ def _load():
     L.napg_serve_stop.restype = C.c_int
     L.napg_serve_plan.argtypes = [p, p, i32, p, p, i32, C.c_uint64, p]
     L.napg_serve_plan.restype = C.c_int
+    L.napg_tune_enable.argtypes = [p, i32]
+    L.napg_tune_enable.restype = C.c_int
+    L.napg_tune_read.argtypes = [p, p, C.c_size_t]
+    L.napg_tune_read.restype = C.c_int
     L.napg_version.argtypes = []
     L.napg_version.restype = C.c_char_p
     L.napg_trace_enable.argtypes = [p, i32]
@@ -223,6 +227,16 @@ class Context:
     def release_cache(self):
         """Mark the cached planes and presort stale (the next run rebuilds them)."""
         self._check(lib.napg_release_cache(self.h))
+
+    def tune(self, on=True):
+        """Enable or disable the launch-shape autotuner (on by default)."""
+        self._check(lib.napg_tune_enable(self.h, 1 if on else 0))
+
+    def tune_read(self):
+        import json
+        buf = C.create_string_buffer(1 << 16)
+        self._check(lib.napg_tune_read(self.h, buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def trace(self, on=True):
         self._check(lib.napg_trace_enable(self.h, 1 if on else 0))

@@ -151,3 +151,35 @@ def test_plane_cache_reuse_and_invalidation(napg):
     compare("pearson", c.run("pearson", va, out="numpy", precision="mixed"), oracle_run("pearson", coh2, va),
             stat_tol=("abs", 1e-6))
     c.close()
+
+
+def test_autotuner_keeps_results_identical(napg):
+    """Launch shapes picked by the autotuner change timing only: outputs with
+    tuning off, on the tuning run and on a later run are bit-identical."""
+    coh = synth.small_cohort(207, n_cont=140, n_cat=10, S=6000 + 5, miss=0.2, dtype=np.float32, ties=True)
+    outs = []
+    for tune_on in (False, True, True):
+        c = outs_ctx = napg.Context(0)
+        c.tune(tune_on)
+        c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+        r = {}
+        r["pearson"] = c.run("pearson", coh["cont"], out="numpy", precision="mixed")
+        r["anova"] = c.run("anova", coh["cat"], coh["cont"], out="numpy", precision="mixed")
+        r["spearman"] = c.run("spearman", coh["cont"], out="numpy")
+        r["kruskal"] = c.run("kruskal", coh["cat"], coh["cont"], out="numpy")
+        if tune_on:
+            again = c.run("pearson", coh["cont"], out="numpy", precision="mixed")
+            for k in ("stat", "p", "n"):
+                assert np.array_equal(again[k], r["pearson"][k], equal_nan=True)
+            recs = c.tune_read()
+            kinds = {x["kind"] for x in recs}
+            assert {"stacked_mask", "stacked_onehot", "spearman_threads", "rank_groups_threads"} <= kinds, recs
+            assert all(len(x["ms"]) == 2 and min(x["ms"]) > 0 for x in recs), recs
+        else:
+            assert c.tune_read() == []
+        outs.append(r)
+        c.close()
+    for r in outs[1:]:
+        for t in outs[0]:
+            for k in ("stat", "p", "n"):
+                assert np.array_equal(outs[0][t][k], r[t][k], equal_nan=True), (t, k)
