@@ -44,6 +44,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2505_00448_gb300 import dist as D  # noqa: E402
 from paper_2505_00448_gb300 import synth  # noqa: E402
 
 METRIC = "var-pairs/s per test, mixed-precision vs plain FP64 GPU at |dr|<=1e-6; p99 ms"
@@ -404,10 +405,7 @@ def serve_main(args, world, rank, local_rank):
     ctx.close()
     sat = max(sweep, key=lambda r: r["pairs_per_s"])
     value = sat["pairs_per_s"]
-    if dist:
-        t = torch.tensor([value], device=torch.device("cuda", device))
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        value = float(t.item())
+    value = D.sum_over_ranks(value, dist)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.serve_requests,
                 "warmup": 4, "ms_per_step": statistics.mean(single), "higher_is_better": True, "scaling": "weak",
@@ -498,14 +496,11 @@ def batch_main(args, world, rank, local_rank):
     clk = clocks.stop()
     launches = napg.kernel_launches() - launches0
     ms_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = D.max_over_ranks(ms_step, dist)      # the slowest rank sets the time
     step_ms = sorted(a.elapsed_time(b) for a, b in per_step)
     pairs_ctx = {t: len(va) * (len(va) - 1) // 2 for t, va in tests}
     pairs_step = K * sum(pairs_ctx.values())
-    value = world * pairs_step / (ms_step / 1000.0)
+    value = D.weak_scaling_value(pairs_step, ms_step / 1000.0, world)
 
     # accuracy of the timed outputs on a few contexts (random pairs) against the oracle
     accuracy = None
@@ -623,9 +618,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local_rank = D.env_ranks()
 
     if args.impl == "reference":
         if rank != 0:
@@ -726,15 +719,12 @@ def main():
     trace = ctx.trace_read()
     ctx.trace(False)
     ms_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = D.max_over_ranks(ms_step, dist)      # the slowest rank sets the time
     per_test_ms = {t: [pe[t][0].elapsed_time(pe[t][1]) for pe in step_events] for t, _, _ in tests}
     first, last = tests[0][0], tests[-1][0]
     step_ms = sorted(pe[first][0].elapsed_time(pe[last][1]) for pe in step_events)
     pairs_step = sum(pair_count(t, va, vb) for t, va, vb in tests)
-    value = world * pairs_step / (ms_step / 1000.0)
+    value = D.weak_scaling_value(pairs_step, ms_step / 1000.0, world)
 
     # e2e through the public API with host buffers: upload + run + download per step
     e2e = None
