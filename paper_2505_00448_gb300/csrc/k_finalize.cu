@@ -156,61 +156,104 @@ void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32
 }
 
 // -------------------------------------------------------------- chi-squared --
-__global__ void k_finalize_chi2(Chi2Fin f, double *stat, double *pval, int32_t *nout) {
-    const int64_t total = (int64_t)f.na * f.nb;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int a = (int)(t / f.nb), b = (int)(t - (int64_t)a * f.nb);
-        if (f.symmetric && b < a) continue;     // filled from (b, a)
-        const int ca = f.nlev_a[a], cb = f.nlev_b[b];
-        const int oa = f.levoff_a[a], ob = f.levoff_b[b];
-        int32_t row[kMaxLevels], col[kMaxLevels];
-        int64_t n = 0;
-        for (int g = 0; g < ca; ++g) row[g] = 0;
-        for (int h = 0; h < cb; ++h) col[h] = 0;
-        for (int g = 0; g < ca; ++g)
-            for (int h = 0; h < cb; ++h) {
-                const int32_t o = f.T[(int64_t)(oa + g) * f.R + (ob + h)];
-                row[g] += o;
-                col[h] += o;
-                n += o;
-            }
-        int ka = 0, kb = 0;
-        bool empty = (n == 0);
-        for (int g = 0; g < ca; ++g)
-            if (f.present[oa + g]) { ++ka; if (row[g] == 0) empty = true; }
-        for (int h = 0; h < cb; ++h)
-            if (f.present[ob + h]) { ++kb; if (col[h] == 0) empty = true; }
-        double s = dnan(), p = dnan();
-        if (!empty) {
-            const bool yates = f.yates && ka == 2 && kb == 2;
-            double chi = 0.0;
-            const double nd = (double)n;
-            for (int g = 0; g < ca; ++g) {
-                if (!f.present[oa + g]) continue;
-                for (int h = 0; h < cb; ++h) {
-                    if (!f.present[ob + h]) continue;
-                    const double E = (double)row[g] * (double)col[h] / nd;
-                    double d = fabs((double)f.T[(int64_t)(oa + g) * f.R + (ob + h)] - E);
-                    if (yates) d = (d > 0.5) ? d - 0.5 : 0.0;
-                    chi += d * d / E;
-                }
-            }
-            s = chi;
-            const int df = (ka - 1) * (kb - 1);
-            if (df > 0 && f.q.jobs) pjob_push(f.q, PJob{chi, (double)df, 0.0, t, kPjChi2, f.symmetric ? f.nb : 0});
-        }
-        put(stat, pval, nout, t, s, p, (int32_t)n);
-        if (f.symmetric && a != b) put(stat, pval, nout, (int64_t)b * f.nb + a, s, p, (int32_t)n);
-    }
+// One thread per pair (the upper triangle only, for symmetric calls). Each cell
+// contributes (O - E)^2 / E = (n O - r c)^2 / (n r c): the centred numerator is
+// exact in integers and the reciprocals of n and of the margins are formed once,
+// so no cell divides. MAXC bounds the levels per variable: tables up to 16 x 16
+// keep their margins in registers (fully unrolled, predicated loops); larger
+// ones run the same body without unrolling.
+#define NAPG_CHI2_KERNEL(NAME, MAXC, UNROLL) \
+__global__ void NAME(Chi2Fin f, double *stat, double *pval, int32_t *nout) { \
+    const int64_t nn = f.na; \
+    const int64_t total = f.symmetric ? nn * (nn + 1) / 2 : (int64_t)f.na * f.nb; \
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; \
+         t += (int64_t)gridDim.x * blockDim.x) { \
+        int a, b; \
+        if (f.symmetric) { \
+            int64_t i = (int64_t)((2.0 * nn + 1.0 - sqrt((2.0 * nn + 1.0) * (2.0 * nn + 1.0) - 8.0 * (double)t)) / 2.0); \
+            if (i < 0) i = 0; \
+            if (i > nn - 1) i = nn - 1; \
+            while (i > 0 && i * (2 * nn - i + 1) / 2 > t) --i; \
+            while ((i + 1) * (2 * nn - i) / 2 <= t) ++i; \
+            a = (int)i; \
+            b = (int)(i + (t - i * (2 * nn - i + 1) / 2)); \
+        } else { \
+            a = (int)(t / f.nb); \
+            b = (int)(t - (int64_t)a * f.nb); \
+        } \
+        const int64_t ab = (int64_t)a * f.nb + b; \
+        const int ca = f.nlev_a[a], cb = f.nlev_b[b]; \
+        const int oa = f.levoff_a[a], ob = f.levoff_b[b]; \
+        const int32_t *Tb = f.T + (int64_t)oa * f.R + ob; \
+        int32_t row[MAXC], col[MAXC]; \
+UNROLL \
+        for (int g = 0; g < MAXC; ++g) { row[g] = 0; col[g] = 0; } \
+        int64_t n = 0; \
+UNROLL \
+        for (int g = 0; g < MAXC; ++g) { \
+            if (g >= ca) break; \
+UNROLL \
+            for (int h = 0; h < MAXC; ++h) { \
+                if (h >= cb) break; \
+                const int32_t o = Tb[(int64_t)g * f.R + h]; \
+                row[g] += o; \
+                col[h] += o; \
+                n += o; \
+            } \
+        } \
+        int ka = 0, kb = 0; \
+        bool empty = (n == 0); \
+UNROLL \
+        for (int g = 0; g < MAXC; ++g) \
+            if (g < ca && f.present[oa + g]) { ++ka; if (row[g] == 0) empty = true; } \
+UNROLL \
+        for (int h = 0; h < MAXC; ++h) \
+            if (h < cb && f.present[ob + h]) { ++kb; if (col[h] == 0) empty = true; } \
+        double s = dnan(), p = dnan(); \
+        if (!empty) { \
+            const bool yates = f.yates && ka == 2 && kb == 2; \
+            const double nd = (double)n, inv_n = 1.0 / nd; \
+            double icol[MAXC]; \
+UNROLL \
+            for (int h = 0; h < MAXC; ++h) icol[h] = (h < cb && col[h] > 0) ? 1.0 / (double)col[h] : 0.0; \
+            double chi = 0.0; \
+UNROLL \
+            for (int g = 0; g < MAXC; ++g) { \
+                if (g >= ca) break; \
+                if (!f.present[oa + g]) continue; \
+                const double irow = 1.0 / (double)row[g]; \
+                double acc = 0.0; \
+UNROLL \
+                for (int h = 0; h < MAXC; ++h) { \
+                    if (h >= cb) break; \
+                    if (!f.present[ob + h]) continue; \
+                    const int64_t D = n * (int64_t)Tb[(int64_t)g * f.R + h] - (int64_t)row[g] * col[h];   /* exact */ \
+                    double d = fabs((double)D); \
+                    if (yates) d = fmax(d - 0.5 * nd, 0.0);      /* |O - E| - 1/2, times n */ \
+                    acc += d * d * icol[h]; \
+                } \
+                chi += acc * irow; \
+            } \
+            s = chi * inv_n; \
+            const int df = (ka - 1) * (kb - 1); \
+            if (df > 0 && f.q.jobs) pjob_push(f.q, PJob{s, (double)df, 0.0, ab, kPjChi2, f.symmetric ? f.nb : 0}); \
+        } \
+        put(stat, pval, nout, ab, s, p, (int32_t)n); \
+        if (f.symmetric && a != b) put(stat, pval, nout, (int64_t)b * f.nb + a, s, p, (int32_t)n); \
+    } \
 }
 
+NAPG_CHI2_KERNEL(k_finalize_chi2_small, 16, _Pragma("unroll"))
+NAPG_CHI2_KERNEL(k_finalize_chi2_large, kMaxLevels, _Pragma("unroll 1"))
+#undef NAPG_CHI2_KERNEL
+
 void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st) {
-    const int64_t total = (int64_t)f.na * f.nb;
+    const int64_t total = f.symmetric ? (int64_t)f.na * (f.na + 1) / 2 : (int64_t)f.na * f.nb;
     if (total == 0) return;
     const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
     count_launch();
-    k_finalize_chi2<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
+    if (f.maxc <= 16) k_finalize_chi2_small<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
+    else k_finalize_chi2_large<<<blocks, 128, 0, st>>>(f, stat, pval, nout);
 }
 
 // ----------------------------------------------------------------- Spearman --

@@ -438,7 +438,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         else { Stage s_(ctx->trace, st, "contingency_popc"); launch_contingency(levbits, W, R, T, st); }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
-        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2, pj.q};
+        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2, pj.q, maxlev};
         { Stage s_(ctx->trace, st, "finalize_chi2"); launch_finalize_chi2(f, a.stat, a.pval, a.n, st); }
         pjobs_run(ctx, pj, a.pval, st);
     } else if (t == NAPG_SPEARMAN) {

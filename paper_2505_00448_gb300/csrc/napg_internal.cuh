@@ -243,6 +243,7 @@ struct Chi2Fin {
     const int32_t *T; int32_t R; const int32_t *levoff_a, *nlev_a, *levoff_b, *nlev_b;
     const int32_t *present; int32_t na, nb; int32_t symmetric; int32_t yates;
     PJobQueue q;
+    int32_t maxc;        // most levels of any variable in the call
 };
 void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
 // exact rescue of pairs whose moments are degenerate (constant columns/groups)
