@@ -559,7 +559,7 @@ static void anova_pair(const orc_cohort *c, int64_t a, int64_t j, orc_scratch *w
     *nn = (int32_t)n;
     if (empty || k < 2 || n - k < 1) { *st = NAN; *p = NAN; return; }
     int L = c->nlev[a];
-    double sum[ORC_MAXLEV], mean[ORC_MAXLEV], first[ORC_MAXLEV];
+    double sum[ORC_MAXLEV], first[ORC_MAXLEV];
     int constant[ORC_MAXLEV], seen[ORC_MAXLEV];
     for (int g = 0; g < L; ++g) { sum[g] = 0.0; constant[g] = 1; seen[g] = 0; first[g] = 0.0; }
     double gm = 0.0;
@@ -570,16 +570,24 @@ static void anova_pair(const orc_cohort *c, int64_t a, int64_t j, orc_scratch *w
     }
     gm /= (double)n;
     int all_const = 1;
-    for (int g = 0; g < L; ++g) if (present[g]) { mean[g] = sum[g] / (double)ng[g]; all_const &= constant[g]; }
+    for (int g = 0; g < L; ++g) if (present[g]) all_const &= constant[g];
     if (all_const) {
         int differ = 0; double ref = NAN;
         for (int g = 0; g < L; ++g) if (present[g]) { if (isnan(ref)) ref = first[g]; else if (first[g] != ref) differ = 1; }
         if (differ) { *st = INFINITY; *p = 0.0; } else { *st = NAN; *p = NAN; }
         return;
     }
+    /* F does not change when every y moves by one constant: the sums of
+     * squares are formed from y - gm (the two-pass form), so that a large
+     * common offset does not swamp group-mean differences far below it. */
+    double dsum[ORC_MAXLEV], dmean[ORC_MAXLEV], dgm = 0.0;
+    for (int g = 0; g < L; ++g) dsum[g] = 0.0;
+    for (int64_t q = 0; q < n; ++q) { double d = w->y[q] - gm; dsum[(int)w->x[q]] += d; dgm += d; }
+    dgm /= (double)n;
+    for (int g = 0; g < L; ++g) if (present[g]) dmean[g] = dsum[g] / (double)ng[g];
     double ssb = 0.0, ssw = 0.0;
-    for (int g = 0; g < L; ++g) if (present[g]) ssb += (double)ng[g] * (mean[g] - gm) * (mean[g] - gm);
-    for (int64_t q = 0; q < n; ++q) { int g = (int)w->x[q]; double d = w->y[q] - mean[g]; ssw += d * d; }
+    for (int g = 0; g < L; ++g) if (present[g]) ssb += (double)ng[g] * (dmean[g] - dgm) * (dmean[g] - dgm);
+    for (int64_t q = 0; q < n; ++q) { int g = (int)w->x[q]; double d = (w->y[q] - gm) - dmean[g]; ssw += d * d; }
     double d1 = (double)(k - 1), d2 = (double)(n - k);
     double F = (ssb / d1) / (ssw / d2);
     *st = F;
@@ -603,10 +611,17 @@ static void ttest_pair(const orc_cohort *c, int64_t a, int64_t j, orc_scratch *w
         else                { if (n1 == 0) f1 = v; else if (v != f1) c1 = 0; s1 += v; ++n1; }
     }
     if (n0 < 2 || n1 < 2 || n < 3) { *st = NAN; *p = NAN; return; }
-    double m0 = s0 / (double)n0, m1 = s1 / (double)n1;
+    /* t does not change when every y moves by one constant: means and sums of
+     * squares are formed from y - (overall mean), as for the F statistic. */
+    double gm = (s0 + s1) / (double)n, d0 = 0.0, d1 = 0.0;
+    for (int64_t q = 0; q < n; ++q) {
+        double d = w->y[q] - gm;
+        if (w->x[q] == 0.0) d0 += d; else d1 += d;
+    }
+    double m0 = d0 / (double)n0, m1 = d1 / (double)n1;
     double q0 = 0.0, q1 = 0.0;
     for (int64_t q = 0; q < n; ++q) {
-        double v = w->y[q];
+        double v = w->y[q] - gm;
         if (w->x[q] == 0.0) q0 += (v - m0) * (v - m0); else q1 += (v - m1) * (v - m1);
     }
     if (c0) q0 = 0.0;

@@ -30,6 +30,10 @@ MUTANTS = {
     "deletion_one_sided": ("if (observed(c, va, s) && observed(c, vb, s)) {", "if (observed(c, va, s)) {"),
     "transposed_operand": ("y[n] = c->X[vb * c->S + s];", "y[n] = c->X[va * c->S + s];"),
     "context_ignored": ("if (c->ctx && !c->ctx[s]) return 0;", ""),
+    "anova_uncentred": ("{ double d = w->y[q] - gm; dsum[(int)w->x[q]] += d; dgm += d; }",
+                        "{ double d = w->y[q]; dsum[(int)w->x[q]] += d; dgm += d; }"),
+    "ttest_uncentred": ("double gm = (s0 + s1) / (double)n, d0 = 0.0, d1 = 0.0;",
+                        "double gm = 0.0, d0 = 0.0, d1 = 0.0;"),
 }
 
 

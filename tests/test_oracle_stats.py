@@ -237,6 +237,44 @@ def test_welch_equals_student_for_equal_group_sizes():
     assert tw[0, 0] == pytest.approx(ts[0, 0], rel=1e-14)
 
 
+def test_anova_t_large_offset_against_exact_rationals():
+    """F and t are shift-invariant; with a common offset 10^4 times the spread and
+    group means 10^-5 spread apart, the oracle still matches F and t^2 computed
+    in exact rational arithmetic (the inputs are multiples of 2^-8)."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(21)
+    n = 3000
+    lab = rng.integers(0, 3, n).astype(float)
+    y = 57403.0 + np.round(rng.normal(size=n) * 7.5 * 256) / 256
+    y[lab == 1] += 2.0 ** -8                       # a mean shift far below the offset
+    X = np.array([lab, lab % 2, y])
+    vt = np.array([1, 1, 0], np.uint8)
+    nl = np.array([3, 2, 0], np.int32)
+    F, _, _ = O.run("anova", X, NAN, vt, nl, [0], [2])
+    g = [[Fr(v) for v in y[lab == k]] for k in range(3)]
+    tot = [v for gg in g for v in gg]
+    m = sum(tot) / len(tot)
+    mg = [sum(gg) / len(gg) for gg in g]
+    ssb = sum(len(gg) * (mk - m) ** 2 for gg, mk in zip(g, mg))
+    ssw = sum((v - mk) ** 2 for gg, mk in zip(g, mg) for v in gg)
+    F_exact = (ssb / 2) / (ssw / (n - 3))
+    assert abs(F[0, 0] - float(F_exact)) <= 1e-13 * float(F_exact)
+    lab2 = lab % 2
+    h = [[Fr(v) for v in y[lab2 == k]] for k in range(2)]
+    mh = [sum(hh) / len(hh) for hh in h]
+    vh = [sum((v - mk) ** 2 for v in hh) / (len(hh) - 1) for hh, mk in zip(h, mh)]
+    for welch in (1, 0):
+        t, _, _ = O.run("ttest", X, NAN, vt, nl, [1], [2], welch=welch)
+        if welch:
+            se2 = vh[0] / len(h[0]) + vh[1] / len(h[1])
+        else:
+            sp2 = (vh[0] * (len(h[0]) - 1) + vh[1] * (len(h[1]) - 1)) / (n - 2)
+            se2 = sp2 * (Fr(1, len(h[0])) + Fr(1, len(h[1])))
+        t2 = (mh[0] - mh[1]) ** 2 / se2
+        assert math.copysign(1.0, t[0, 0]) == (1.0 if mh[0] > mh[1] else -1.0)
+        assert abs(t[0, 0] ** 2 - float(t2)) <= 1e-13 * float(t2)
+
+
 def test_anova_t_edge_rules():
     lab = np.array([0, 0, 0, 1, 1, 1, 2, 2], float)
     x_const_diff = np.array([1, 1, 1, 2, 2, 2, 3, 3], float)
