@@ -313,6 +313,46 @@ def load_traffic(kernel):
         return None
 
 
+def latency_config1(napg, device, reps=100, warm=10):
+    """Config 1 (200 x 1,000, plain FP64 Pearson): p50 / p99 of one call over
+    `reps` calls after `warm`, device time by CUDA events and host wall time."""
+    import torch
+    coh = synth.config1()
+    ctx = napg.Context(device)
+    st = ctx.stream
+    ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    va = coh["cont"]
+    n = len(va)
+    dev = torch.device("cuda", device)
+    out = {"stat": torch.empty((n, n), dtype=torch.float64, device=dev),
+           "p": torch.empty((n, n), dtype=torch.float64, device=dev),
+           "n": torch.empty((n, n), dtype=torch.int32, device=dev)}
+    dev_ms, wall_ms = [], []
+    for k in range(warm + reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a.record(st)
+        ctx.run("pearson", va, outputs=out, sync=False)
+        b.record(st)
+        b.synchronize()
+        t1 = time.perf_counter()
+        if k >= warm:
+            dev_ms.append(a.elapsed_time(b))
+            wall_ms.append(1000.0 * (t1 - t0))
+    ctx.close()
+    dev_ms.sort()
+    wall_ms.sort()
+    q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))]
+    pairs = n * (n - 1) // 2
+    return {"workload": "200 continuous x 1,000 samples, FP64, 20% MCAR; all-pairs Pearson, plain FP64 form",
+            "reps": reps, "warmup": warm, "pairs": pairs,
+            "device_ms_p50": q(dev_ms, 0.5), "device_ms_p99": q(dev_ms, 0.99),
+            "wall_ms_p50": q(wall_ms, 0.5), "wall_ms_p99": q(wall_ms, 0.99),
+            "pairs_per_s_p50": pairs / (q(wall_ms, 0.5) / 1000.0)}
+
+
 # ------------------------------------------------------------ serve workload --
 
 def serve_requests(coh, rng, count):
@@ -631,7 +671,8 @@ def main():
                 samples.append(r)
         v = statistics.mean(r["value"] for r in samples)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * sum(pair_count(t, va, vb) for t, va, vb in tests) / v, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": desc, "reference": "plain FP64 CPU oracle (oracle/napg_oracle.c)"},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": samples[0]["cores"], "kind": "oracle",
@@ -779,6 +820,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(coh, tests, budget_s=args.cpu_budget)
+    latency = latency_config1(napg, device) if (rank == 0 and args.workload == "mixed" and args.scale == 1.0) else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -795,7 +837,7 @@ def main():
                            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()},
                            "autotuned": ctx.tune_read()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator}
+                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator, "latency_config1": latency}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
