@@ -92,6 +92,34 @@ def test_config1_full(napg):
     c.close()
 
 
+@pytest.mark.parametrize("S", [31, 33, 257, 1007])
+def test_pearson_fp64_sample_split(napg, S):
+    """Few variables: the plain FP64 moments split the sample axis over a cluster
+    of CTAs (up to 8, at least one 32-sample word each); every split size agrees
+    with the oracle, and repeated calls are bit-identical."""
+    coh = synth.small_cohort(110 + S, n_cont=70, n_cat=0, S=S, miss=0.2, offset=50.0)
+    c = ctx_for(napg, coh)
+    for nv in (1, 2, 33, 70):
+        va = coh["cont"][:nv]
+        g = c.run("pearson", va, out="numpy")
+        compare("pearson", g, oracle_run("pearson", coh, va))
+        g2 = c.run("pearson", va, out="numpy")
+        for k in ("stat", "p", "n"):
+            assert np.array_equal(g[k], g2[k], equal_nan=True)
+    c.close()
+
+
+@pytest.mark.parametrize("levels", [(2, 4), (5, 16), (17, 64)])
+def test_anova_fp64_level_counts(napg, levels):
+    """The plain FP64 group sums at each level-count class (up to 4, 16, 64)."""
+    coh = synth.small_cohort(120 + levels[1], n_cont=9, n_cat=6, S=2000 + 5, miss=0.2, lev_lo=levels[0],
+                             lev_hi=levels[1])
+    c = ctx_for(napg, coh)
+    cats, conts = coh["cat"], coh["cont"]
+    compare("anova", c.run("anova", cats, conts, out="numpy"), oracle_run("anova", coh, cats, conts))
+    c.close()
+
+
 # ----------------------------------------------------------------- Spearman --
 
 def test_spearman_parity_and_rank_sums(napg):
