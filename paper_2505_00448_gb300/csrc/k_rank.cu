@@ -281,8 +281,10 @@ __device__ __forceinline__ uint32_t rank2_at(const Side &sd, int32_t p) {
 }
 
 // Build B over the column's sorted positions from the co-observed sample bits,
-// then the exclusive word prefix P. Every thread of the block must call it.
-__device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uint32_t *co, int W, int32_t *scan_tmp) {
+// then the exclusive word prefix P; with lab_s, also gather the labels la[perm[p]]
+// of the co-observed positions into lab_s[p]. Every thread of the block must call it.
+__device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uint32_t *co, int W, int32_t *scan_tmp,
+                           const uint8_t *__restrict__ la = nullptr, uint8_t *lab_s = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nw = (sd.n + 31) >> 5;
     for (int w = warp; w <= W; w += nwarps) {
@@ -291,6 +293,8 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
         if (w < nw && p < sd.n) {
             const int s = perm[p];
             b = (co[s >> 5] >> (s & 31)) & 1u;
+            // the label of a co-observed position, in sorted order (others are never read)
+            if (lab_s && b) lab_s[p] = la[s];
         }
         const uint32_t bits = __ballot_sync(0xffffffffu, b);
         if (lane == 0) sd.B[w] = bits;
@@ -306,16 +310,19 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
     __syncthreads();
     if (warp == 0) {
         const int k = blockDim.x >> 5;          // totals per lane (blockDim.x <= 1024)
-        int v[32];
         int tot = 0;
-        for (int i = 0; i < k; ++i) { v[i] = scan_tmp[lane * k + i]; tot += v[i]; }
+        for (int i = 0; i < k; ++i) tot += scan_tmp[lane * k + i];
         int incl = tot;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
         int run = incl - tot;
-        for (int i = 0; i < k; ++i) { scan_tmp[lane * k + i] = run; run += v[i]; }
+        for (int i = 0; i < k; ++i) {
+            const int v = scan_tmp[lane * k + i];
+            scan_tmp[lane * k + i] = run;
+            run += v;
+        }
     }
     __syncthreads();
     int run = scan_tmp[threadIdx.x];
@@ -364,7 +371,7 @@ __device__ Side carve_side(unsigned char *&cur, int W) {
 
 // ----------------------------------------------------------------- Spearman --
 // One CTA per pair. out4[pair] = {n, sum A*B, sum A^2, sum B^2}, A = 2Rx, B = 2Ry.
-__global__ void __launch_bounds__(1024) k_spearman(RankData rd, const int32_t *__restrict__ crow_a,
+__global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t *__restrict__ crow_a,
                                                   const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
                                                   const uint32_t *__restrict__ obs_b, int32_t na, int32_t nb,
                                                   int32_t symmetric, int64_t *__restrict__ out4) {
@@ -437,6 +444,10 @@ static size_t rank_smem_bytes(int64_t W, int sides, bool with_co) {
 // keeps 32 warps resident instead.
 static int rank_threads(size_t smem) { return smem > (size_t)56 * 1024 ? 1024 : 256; }
 
+// Dynamic shared memory a rank CTA may take (below the 227 KB opt-in limit, with
+// room for the static scan buffers).
+constexpr size_t kRankSmemCap = 210 * 1024;
+
 int rank_threads_default(int64_t W, bool groups) { return rank_threads(rank_smem_bytes(W, groups ? 1 : 2, true)); }
 
 void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b, const uint32_t *obs_a,
@@ -454,8 +465,24 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
 // ------------------------------------------------------------ MWU / Kruskal --
 // One CTA per (categorical a, continuous j): per level g the count n_g and the
 // sum of doubled ranks S_g, plus the tie term sum (t^3 - t) over co-observed
-// tie groups. Per-level sums use shared-memory 64-bit atomics.
-__global__ void __launch_bounds__(1024) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
+// tie groups. The walk visits j's sorted positions a word (32 positions) per warp
+// at a time. With CMAX levels at most (2, 4 or 8), every lane adds into its own
+// slot per level, (1 << 40) + 2R as one 64-bit word (sum in the low 40 bits,
+// count above: the totals stay below 2^40 and 2^24 for any S the rank tests
+// take), and the slots are summed at the end. With CMAX = 0 (up to kMaxLevels
+// levels) lanes of one level are grouped by match_any and their leader adds
+// into the warp's table. SLAB: the labels are gathered into shared memory in
+// sorted order while the co-observed bits are built (otherwise the walk reads
+// them from the cohort).
+constexpr int kPackShift = 40;
+
+template <int CMAX>
+__host__ __device__ constexpr size_t rank_group_table_bytes(int nwarp) {
+    return CMAX ? (size_t)nwarp * CMAX * 32 * 8 : (size_t)nwarp * kMaxLevels * 12;
+}
+
+template <int CMAX, bool SLAB>
+__global__ void __launch_bounds__(1024, 2) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
                                                      const int32_t *__restrict__ catrow_a, const int32_t *__restrict__ nlev_a,
                                                      const int32_t *__restrict__ levoff_a, int32_t na,
                                                      const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
@@ -468,29 +495,35 @@ __global__ void __launch_bounds__(1024) k_rank_groups(RankData rd, const uint8_t
     const int a = (int)(blockIdx.x / nb), j = (int)(blockIdx.x - (int64_t)a * nb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned char *cur = smem_raw;
-    // per-warp level sums and counts (dynamic: one table per warp of the block)
-    unsigned long long *lsum = (unsigned long long *)cur; cur += (size_t)nwarp * kMaxLevels * 8;
-    int *lcnt = (int *)cur; cur += (size_t)nwarp * kMaxLevels * 4;
+    // CMAX > 0: acc[(warp * CMAX + g) * 32 + lane]; CMAX = 0: lsum / lcnt[warp * kMaxLevels + g]
+    unsigned long long *acc = (unsigned long long *)cur;
+    unsigned long long *lsum = acc;
+    int *lcnt = (int *)(cur + (size_t)nwarp * kMaxLevels * 8);
+    cur += rank_group_table_bytes<CMAX>(nwarp);
     uint32_t *co = (uint32_t *)cur; cur += (W + 1) * 4;
     Side sj = carve_side(cur, W);
+    uint8_t *lab_s = SLAB ? (uint8_t *)cur : nullptr;   // (W + 1) * 32 bytes
     const uint32_t *oa = obs_a + (int64_t)a * W, *ob = obs_b + (int64_t)j * W;
     for (int w = threadIdx.x; w < W; w += blockDim.x) co[w] = oa[w] & ob[w];
     const int cj = crow_b[j];
     load_side_static(sj, rd, cj, W);
     const int c = nlev_a[a];
-    for (int i = threadIdx.x; i < nwarp * kMaxLevels; i += blockDim.x) {
-        lsum[i] = 0ull;
-        lcnt[i] = 0;
+    if (CMAX) {
+        for (int i = threadIdx.x; i < nwarp * CMAX * 32; i += blockDim.x) acc[i] = 0ull;
+    } else {
+        for (int i = threadIdx.x; i < nwarp * kMaxLevels; i += blockDim.x) {
+            lsum[i] = 0ull;
+            lcnt[i] = 0;
+        }
     }
     __syncthreads();
     const int32_t *perm_j = rd.perm + (int64_t)cj * rd.S;
-    build_side(sj, perm_j, co, W, scan_tmp);
     const uint8_t *la = lab + (int64_t)catrow_a[a] * rd.S;
+    build_side(sj, perm_j, co, W, scan_tmp, SLAB ? la : nullptr, lab_s);
     int64_t tsum = 0;
-    // each warp takes one word of 32 sorted positions at a time
-    const int nwarps = blockDim.x >> 5;
     const int nwj = (sj.n + 31) >> 5;
-    for (int w0 = 0; w0 < nwj; w0 += nwarps) {
+#pragma unroll 1
+    for (int w0 = 0; w0 < nwj; w0 += nwarp) {
         const int w = w0 + warp;               // warps past the end still join the warp-wide steps
         const bool inw = w < nwj;
         const uint32_t Bw = inw ? sj.B[w] : 0u, Tw = inw ? sj.T[w] : 0u;
@@ -508,44 +541,87 @@ __global__ void __launch_bounds__(1024) k_rank_groups(RankData rd, const uint8_t
         int g = kMaxLevels;                    // no level
         uint32_t r2 = 0;
         if (on) {
-            g = la[perm_j[p]];
+            g = SLAB ? lab_s[p] : la[perm_j[p]];
             r2 = rank2_word(Tw, Bw, Pw, pgs, pge, lane);
         }
-        // lanes with the same level add their doubled ranks (a warp's sum fits 32 bits)
-        const unsigned same = __match_any_sync(0xffffffffu, g);
-        const uint32_t sum = __reduce_add_sync(same, r2);
-        if (on && lane == __ffs(same) - 1) {
-            lsum[warp * kMaxLevels + g] += sum;   // distinct levels per leader: no conflict
-            lcnt[warp * kMaxLevels + g] += __popc(same);
+        if (CMAX) {
+            if (on) acc[(warp * CMAX + g) * 32 + lane] += (1ull << kPackShift) + r2;
+        } else {
+            // lanes with the same level add their doubled ranks (a warp's sum fits 32 bits)
+            const unsigned same = __match_any_sync(0xffffffffu, g);
+            const uint32_t sum = __reduce_add_sync(same, r2);
+            if (on && lane == __ffs(same) - 1) {
+                lsum[warp * kMaxLevels + g] += sum;   // distinct levels per leader: no conflict
+                lcnt[warp * kMaxLevels + g] += __popc(same);
+            }
         }
     }
-    const int64_t T = block_sum64(tsum, red);
+    const int64_t T = block_sum64(tsum, red);   // has barriers: the tables are complete after it
     __syncthreads();
     const int off = levoff_a[a];
-    for (int g = threadIdx.x; g < c; g += blockDim.x) {
-        unsigned long long su = 0;
-        int cn = 0;
-        for (int k = 0; k < nwarp; ++k) { su += lsum[k * kMaxLevels + g]; cn += lcnt[k * kMaxLevels + g]; }
-        rsum[(int64_t)(off + g) * nb + j] = (int64_t)su;
-        rcnt[(int64_t)(off + g) * nb + j] = cn;
+    if (CMAX) {
+        // warp g sums level g over warps (per lane), then over lanes
+        if (warp < c) {
+            unsigned long long v = 0;
+            for (int k = 0; k < nwarp; ++k) v += acc[(k * CMAX + warp) * 32 + lane];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) {
+                rsum[(int64_t)(off + warp) * nb + j] = (int64_t)(v & ((1ull << kPackShift) - 1ull));
+                rcnt[(int64_t)(off + warp) * nb + j] = (int32_t)(v >> kPackShift);
+            }
+        }
+    } else {
+        for (int g2 = threadIdx.x; g2 < c; g2 += blockDim.x) {
+            unsigned long long su = 0;
+            int cn = 0;
+            for (int k = 0; k < nwarp; ++k) { su += lsum[k * kMaxLevels + g2]; cn += lcnt[k * kMaxLevels + g2]; }
+            rsum[(int64_t)(off + g2) * nb + j] = (int64_t)su;
+            rcnt[(int64_t)(off + g2) * nb + j] = cn;
+        }
     }
     if (threadIdx.x == 0) tie_term[(int64_t)a * nb + j] = T;
 }
 
+template <int CMAX, bool SLAB>
+static void launch_rank_groups_t(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a,
+                                 const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
+                                 const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int64_t *rsum,
+                                 int32_t *rcnt, int64_t *tie_term, int threads, size_t smem, cudaStream_t st) {
+    auto kern = k_rank_groups<CMAX, SLAB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    count_launch();
+    kern<<<(unsigned)((int64_t)na * nb), threads, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a,
+                                                              obs_b, nb, rsum, rcnt, tie_term);
+}
+
 void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a, const int32_t *nlev_a,
                         const int32_t *levoff_a, int32_t na, const int32_t *crow_b, const uint32_t *obs_a,
-                        const uint32_t *obs_b, int32_t nb, int32_t total_rows, int64_t *rsum, int32_t *rcnt,
+                        const uint32_t *obs_b, int32_t nb, int32_t max_levels, int64_t *rsum, int32_t *rcnt,
                         int64_t *tie_term, cudaStream_t st, int threads_req) {
-    (void)total_rows;
     const int64_t pairs = (int64_t)na * nb;
     if (pairs == 0) return;
     const size_t side = rank_smem_bytes(rd.W, 1, true);
     const int threads = threads_req > 0 ? threads_req : rank_threads(side);
-    const size_t smem = side + (size_t)(threads / 32) * kMaxLevels * 12;
-    cudaFuncSetAttribute(k_rank_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    count_launch();
-    k_rank_groups<<<(unsigned)pairs, threads, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a,
-                                                           obs_b, nb, rsum, rcnt, tie_term);
+    const int cmax = max_levels <= 2 ? 2 : max_levels <= 4 ? 4 : max_levels <= 8 ? 8 : 0;
+    const int nwarp = threads / 32;
+    const size_t tables = cmax == 2 ? rank_group_table_bytes<2>(nwarp)
+                        : cmax == 4 ? rank_group_table_bytes<4>(nwarp)
+                        : cmax == 8 ? rank_group_table_bytes<8>(nwarp) : rank_group_table_bytes<0>(nwarp);
+    const size_t labs = (size_t)(rd.W + 1) * 32;
+    const bool slab = side + tables + labs <= kRankSmemCap;
+    const size_t smem = side + tables + (slab ? labs : 0);
+#define NAPG_RG(C)                                                                                                  \
+    (slab ? launch_rank_groups_t<C, true>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b, nb, rsum,   \
+                                          rcnt, tie_term, threads, smem, st)                                        \
+          : launch_rank_groups_t<C, false>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b, nb, rsum,  \
+                                           rcnt, tie_term, threads, smem, st))
+    switch (cmax) {
+        case 2: NAPG_RG(2); break;
+        case 4: NAPG_RG(4); break;
+        case 8: NAPG_RG(8); break;
+        default: NAPG_RG(0); break;
+    }
+#undef NAPG_RG
 }
 
 // ------------------------------------------------------ exact Mann-Whitney --

@@ -474,7 +474,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
             Stage s_(ctx->trace, st, "rank_groups");
             const int t0 = rank_threads_default(W, true), cand[2] = {t0, t0 == 256 ? 1024 : 256};
             auto run = [&](int cc) -> napg_status {
-                launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, R, rsum, rcnt, tie, st,
+                launch_rank_groups(rd, c.lab, d_cat, d_nl, d_lo, na, d_cb, obsA, obsB, nb, maxlev, rsum, rcnt, tie, st,
                                    cand[cc]);
                 NAPG_CU(ctx, cudaGetLastError());
                 return NAPG_OK;

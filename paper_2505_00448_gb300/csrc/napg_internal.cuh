@@ -272,7 +272,7 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
 int rank_threads_default(int64_t W, bool groups);
 void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a,
                         const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
-                        const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int32_t total_rows,
+                        const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int32_t max_levels,
                         int64_t *rsum, int32_t *rcnt, int64_t *tie_term, cudaStream_t st, int threads = 0);
 struct SpearmanFin { const int64_t *q; int32_t na, nb; int32_t symmetric; PJobQueue pq; };
 void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);

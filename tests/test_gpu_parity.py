@@ -243,6 +243,40 @@ def test_mwu_kruskal_parity_and_rank_sums(napg):
     c.close()
 
 
+@pytest.mark.parametrize("levels", [(2, 2), (3, 4), (5, 8), (9, 20)])
+def test_kruskal_level_classes(napg, levels):
+    """Rank sums per level through each level-count class of the rank kernel (per
+    level warp reductions up to 8 levels, the last level from the totals; lane
+    grouping above), bit-exact, with the statistics against the oracle."""
+    coh = synth.small_cohort(130 + levels[1], n_cont=7, n_cat=6, S=2000 + 7, miss=0.25, ties=True,
+                             lev_lo=levels[0], lev_hi=levels[1])
+    c = ctx_for(napg, coh)
+    cats, conts = coh["cat"], coh["cont"]
+    compare("kruskal", c.run("kruskal", cats, conts, out="numpy"), oracle_run("kruskal", coh, cats, conts))
+    Xd = coh["X"].astype(np.float64)
+    for a, j in ((cats[0], conts[0]), (cats[5], conts[6])):
+        got = c.debug_integers("kruskal", int(a), int(j))
+        ref = O.pair_ints("kruskal", Xd, NAN, coh["vtype"], coh["nlev"], int(a), int(j))
+        assert np.array_equal(got, ref), (got, ref)
+    c.close()
+
+
+def test_rank_groups_labels_from_cohort(napg):
+    """150,000 samples: the sorted labels no longer fit beside the per-pair rank
+    arrays in shared memory, so the walk reads them from the cohort."""
+    coh = synth.small_cohort(140, n_cont=3, n_cat=3, S=150_000 + 3, miss=0.3, ties=True, lev_lo=2, lev_hi=6,
+                             binary_cats=1)
+    c = ctx_for(napg, coh)
+    cats, conts = coh["cat"], coh["cont"]
+    compare("kruskal", c.run("kruskal", cats, conts, out="numpy"), oracle_run("kruskal", coh, cats, conts))
+    compare("mwu", c.run("mwu", cats[:1], conts, mwu_mode="asymptotic", out="numpy"),
+            oracle_run("mwu", coh, cats[:1], conts, mwu_mode=2))
+    Xd = coh["X"].astype(np.float64)
+    got = c.debug_integers("kruskal", int(cats[2]), int(conts[1]))
+    assert np.array_equal(got, O.pair_ints("kruskal", Xd, NAN, coh["vtype"], coh["nlev"], int(cats[2]), int(conts[1])))
+    c.close()
+
+
 def test_mwu_exact_mode(napg):
     """Small groups without ties: exact p by the product form vs the oracle's
     Mann-Whitney recurrence."""
