@@ -54,8 +54,13 @@ UNIT = "var-pairs/s"
 # ------------------------------------------------------------------ workload --
 
 def make_workload(name, scale=1.0):
+    if name == "small-pearson":
+        coh = synth.small_pearson_cohort()
+        tests = [("pearson", coh["cont"], None)]
+        desc = "200 continuous x 1,000 samples, FP64, 20% MCAR; all-pairs Pearson, plain FP64 form"
+        return coh, tests, desc
     if name == "ranks":
-        coh = synth.config2() if scale == 1.0 else synth.config2(n_cont=max(32, int(1000 * scale)),
+        coh = synth.rank_cohort() if scale == 1.0 else synth.rank_cohort(n_cont=max(32, int(1000 * scale)),
                                                                    n_cat=max(8, int(200 * scale)))
         cat = coh["cat"]
         bins = cat[coh["nlev"][cat] == 2]
@@ -64,7 +69,7 @@ def make_workload(name, scale=1.0):
         desc = ("rank cohort: 1,000 continuous (1-decimal ties, 30% MCAR + block losses) + 200 categorical "
                 "(2-8 levels) x 10,000 samples, FP64; Spearman + Mann-Whitney + Kruskal-Wallis")
     else:
-        coh = synth.config3() if scale == 1.0 else synth.config3(n_cont=max(64, int(4000 * scale)),
+        coh = synth.mixed_cohort() if scale == 1.0 else synth.mixed_cohort(n_cont=max(64, int(4000 * scale)),
                                                                    n_cat=max(16, int(1000 * scale)))
         cat = coh["cat"]
         bins = cat[coh["nlev"][cat] == 2]
@@ -251,6 +256,11 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
             R = int(coh["nlev"][va].sum())
             Tt = -(-R // 128)
             work["contingency_tc"] = ("tensor", 1.0 * S * na * (na + 1) / 2, Tt * (Tt + 1) / 2 * nkb * 4 * 2.0 * 128 * 128 * 16)
+        if test == "pearson":
+            work["pearson_moments_fp64"] = ("fp64", 12.0 * S * na * (na + 1) / 2, None)
+        if test in ("anova", "ttest") and vb is not None:
+            w = work.get("groupsum_fp64", ("fp64", 0.0, None))
+            work["groupsum_fp64"] = ("fp64", w[1] + 6.0 * S * na * len(vb), None)
         if test == "spearman":
             work["spearman_rank"] = ("hbm", 16.25 * S * na * (na + 1) / 2, None)
         if test in ("mwu", "kruskal"):
@@ -276,6 +286,11 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
         elif bound == "hbm":
             e.update(achieved=alg / secs / 1e9, peak=hbm_peak, unit="GB/s",
                      peak_source="measured HBM copy (MEASURED_PEAKS)")
+        elif bound == "fp64":
+            # plain FP64 moments on the CUDA cores: 152 SMs x 2 FP64 FMA per clock x
+            # 2.07 GHz = 1.26 TFLOP/s nominal (1.25 TFLOP/s stated for GB300)
+            e.update(bound="alu", achieved=alg / secs / 1e9, peak=1250.0, unit="GFLOP/s",
+                     peak_source="nominal FP64 rate (152 SMs x 4 flops/clock x 2.07 GHz)")
         else:
             # FP64-pipe bound: the pipe's share is what ncu reports for this kernel
             # (profiles/pvalues_mixed_cohort.md); the job count is not known here
@@ -313,11 +328,11 @@ def load_traffic(kernel):
         return None
 
 
-def latency_config1(napg, device, reps=100, warm=10):
-    """Config 1 (200 x 1,000, plain FP64 Pearson): p50 / p99 of one call over
+def latency_small_pearson(napg, device, reps=100, warm=10):
+    """The 200 x 1,000 Pearson cohort (plain FP64): p50 / p99 of one call over
     `reps` calls after `warm`, device time by CUDA events and host wall time."""
     import torch
-    coh = synth.config1()
+    coh = synth.small_pearson_cohort()
     ctx = napg.Context(device)
     st = ctx.stream
     ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
@@ -390,7 +405,7 @@ def serve_main(args, world, rank, local_rank):
     device = local_rank if world > 1 else 0
     torch.cuda.set_device(device)
     from paper_2505_00448_gb300 import napg
-    coh = synth.config5()
+    coh = synth.serving_cohort()
     prec = args.precision
     ctx = napg.Context(device)
     ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
@@ -477,7 +492,7 @@ def batch_main(args, world, rank, local_rank):
     device = local_rank if world > 1 else 0
     torch.cuda.set_device(device)
     from paper_2505_00448_gb300 import napg
-    coh = synth.config4()
+    coh = synth.context_cohort()
     masks = coh["contexts"]
     K, S = masks.shape
     tests = [("pearson", coh["cont"]), ("chi2", coh["cat"])]
@@ -645,7 +660,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "ranks", "batch", "serve"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "ranks", "batch", "serve", "small-pearson"])
     ap.add_argument("--serve-requests", type=int, default=40, help="requests per arrival rate (serve workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -715,7 +730,8 @@ def main():
         outs[test] = {"stat": torch.empty((na, nb), dtype=torch.float64, device=dev),
                       "p": torch.empty((na, nb), dtype=torch.float64, device=dev),
                       "n": torch.empty((na, nb), dtype=torch.int32, device=dev)}
-    prec = args.precision
+    # the small Pearson cohort is the plain FP64 form by definition
+    prec = "fp64" if args.workload == "small-pearson" else args.precision
 
     def step(per_test_events=None):
         # every step builds its own derived data (planes, presort) once and
@@ -820,7 +836,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(coh, tests, budget_s=args.cpu_budget)
-    latency = latency_config1(napg, device) if (rank == 0 and args.workload == "mixed" and args.scale == 1.0) else None
+    latency = latency_small_pearson(napg, device) if (rank == 0 and args.workload == "mixed" and args.scale == 1.0) else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -837,7 +853,7 @@ def main():
                            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()},
                            "autotuned": ctx.tune_read()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator, "latency_config1": latency}
+                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator, "latency_small_pearson": latency}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

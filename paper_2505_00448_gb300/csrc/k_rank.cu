@@ -301,31 +301,30 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
     }
     __syncthreads();
     // exclusive scan of popc(B[w]) over w = 0..W (W+1 entries), block-wide:
-    // per-thread chunks, then warp 0 scans the per-thread totals by shuffles
+    // per-thread chunks, then a warp-shuffle scan of the chunk totals with one
+    // total per warp carried through shared memory
     const int per = (W + 1 + blockDim.x - 1) / blockDim.x;
     const int w0 = threadIdx.x * per, w1 = min(W + 1, w0 + per);
     int c = 0;
     for (int w = w0; w < w1; ++w) c += __popc(sd.B[w]);
-    scan_tmp[threadIdx.x] = c;
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) scan_tmp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const int k = blockDim.x >> 5;          // totals per lane (blockDim.x <= 1024)
-        int tot = 0;
-        for (int i = 0; i < k; ++i) tot += scan_tmp[lane * k + i];
-        int incl = tot;
+        const int t = lane < nwarps ? scan_tmp[lane] : 0;
+        int ti = t;
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
+            const int y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
         }
-        int run = incl - tot;
-        for (int i = 0; i < k; ++i) {
-            const int v = scan_tmp[lane * k + i];
-            scan_tmp[lane * k + i] = run;
-            run += v;
-        }
+        if (lane < nwarps) scan_tmp[32 + lane] = ti - t;    // exclusive offset of each warp
     }
     __syncthreads();
-    int run = scan_tmp[threadIdx.x];
+    int run = scan_tmp[32 + warp] + incl - c;
     for (int w = w0; w < w1; ++w) { sd.P[w] = run; run += __popc(sd.B[w]); }
     __syncthreads();
     // group bounds (positions) -> co-observed prefix counts at them, in place
@@ -376,8 +375,8 @@ __global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t
                                                   const uint32_t *__restrict__ obs_b, int32_t na, int32_t nb,
                                                   int32_t symmetric, int64_t *__restrict__ out4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t scan_tmp[1024];
-    __shared__ int64_t red[32];
+    __shared__ int32_t scan_tmp[64];
+    __shared__ int64_t red4[32][4];
     const int W = (int)rd.W;
     // pair index
     int64_t pid = blockIdx.x;
@@ -425,13 +424,24 @@ __global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t
             sab += (uint64_t)A * B; saa += (uint64_t)A * A; sbb += (uint64_t)B * B; ++cnt;
         }
     }
-    const int64_t t0 = block_sum64(cnt, red);
-    const int64_t t1 = block_sum64((int64_t)sab, red);
-    const int64_t t2 = block_sum64((int64_t)saa, red);
-    const int64_t t3 = block_sum64((int64_t)sbb, red);
-    if (threadIdx.x == 0) {
-        int64_t *o = out4 + 4 * ((int64_t)a * nb + b);
-        o[0] = t0; o[1] = t1; o[2] = t2; o[3] = t3;
+    // the four sums over the block: shuffles within each warp, one total per warp
+    // through shared memory, then warp 0 (lane k of the result holds sum k)
+    int64_t v4[4] = {cnt, (int64_t)sab, (int64_t)saa, (int64_t)sbb};
+    for (int k = 0; k < 4; ++k)
+        for (int o = 16; o > 0; o >>= 1) v4[k] += __shfl_down_sync(0xffffffffu, v4[k], o);
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) red4[warp][k] = v4[k];
+    __syncthreads();
+    if (warp == 0) {
+        int64_t t[4];
+        for (int k = 0; k < 4; ++k) {
+            t[k] = lane < nwarps ? red4[lane][k] : 0;
+            for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+        }
+        if (lane == 0) {
+            int64_t *o = out4 + 4 * ((int64_t)a * nb + b);
+            o[0] = t[0]; o[1] = t[1]; o[2] = t[2]; o[3] = t[3];
+        }
     }
 }
 
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(1024, 2) k_rank_groups(RankData rd, const uint
                                                      const uint32_t *__restrict__ obs_b, int32_t nb, int64_t *__restrict__ rsum,
                                                      int32_t *__restrict__ rcnt, int64_t *__restrict__ tie_term) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t scan_tmp[1024];
+    __shared__ int32_t scan_tmp[64];
     __shared__ int64_t red[32];
     const int W = (int)rd.W;
     const int a = (int)(blockIdx.x / nb), j = (int)(blockIdx.x - (int64_t)a * nb);

@@ -94,7 +94,7 @@ def assemble(cont_X, cat_X, cat_nlev, dtype):
             "cont": np.arange(Fc, dtype=np.int32), "cat": np.arange(Fc, Fc + Fg, dtype=np.int32)}
 
 
-def config1():
+def small_pearson_cohort():
     """200 continuous x 1,000 samples, FP64, 20% MCAR."""
     rng = rng_for(1)
     z = factor_scores(rng, 200, 1000)
@@ -105,7 +105,7 @@ def config1():
     return assemble(X, None, None, np.float64)
 
 
-def config2(n_cont=1000, n_cat=200, S=10_000):
+def rank_cohort(n_cont=1000, n_cat=200, S=10_000):
     """Rank-test cohort: tied continuous columns with block losses + categoricals."""
     rng = rng_for(2)
     z = np.round(factor_scores(rng, n_cont, S), 1)
@@ -120,7 +120,7 @@ def config2(n_cont=1000, n_cat=200, S=10_000):
     return assemble(z, cat, nlev, np.float64)
 
 
-def config3(n_cont=4000, n_cat=1000, S=50_000):
+def mixed_cohort(n_cont=4000, n_cat=1000, S=50_000):
     """Mixed-type FP32 cohort with large offsets and heavy tails."""
     rng = rng_for(3)
     half = n_cont // 2
@@ -138,7 +138,7 @@ def config3(n_cont=4000, n_cat=1000, S=50_000):
     return assemble(X, cat, nlev, np.float32)
 
 
-def config4(n_cont=1600, n_cat=400, S=20_000, n_ctx=256):
+def context_cohort(n_cont=1600, n_cat=400, S=20_000, n_ctx=256):
     """Cohort plus n_ctx sample contexts (uint8 masks) of uneven size."""
     rng = rng_for(4)
     z = factor_scores(rng, n_cont, S)
@@ -158,7 +158,7 @@ def config4(n_cont=1600, n_cat=400, S=20_000, n_ctx=256):
     return coh
 
 
-def config5(n_cont=8000, n_cat=2000, S=100_000):
+def serving_cohort(n_cont=8000, n_cat=2000, S=100_000):
     """Serving cohort, 35% MCAR."""
     rng = rng_for(5)
     X = np.empty((n_cont + n_cat, S), np.float32)

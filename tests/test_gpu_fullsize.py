@@ -17,10 +17,11 @@ MIXED_BAR = {"pearson": ("abs", 1e-6), "anova": ("effect", 1e-6), "ttest": ("eff
 _COHORTS = {}
 
 
-def cohort(k):
-    """Each config generated once per session (config 3 and 5 take tens of seconds)."""
+def cohort(name):
+    """Each cohort generated once per session (the mixed and serving cohorts take tens of seconds)."""
+    k = name
     if k not in _COHORTS:
-        coh = getattr(synth, f"config{k}")()
+        coh = getattr(synth, name)()
         coh["X64"] = coh["X"] if coh["X"].dtype == np.float64 else coh["X"].astype(np.float64)
         _COHORTS[k] = coh
     return _COHORTS[k]
@@ -48,8 +49,8 @@ def sampled(test, coh, g, va, vb, rng, k, mask=None, bar=None, **kw):
     compare(test, got, ref, stat_tol=bar)
 
 
-def test_config1_full(napg):
-    coh = cohort(1)
+def test_small_pearson_full(napg):
+    coh = cohort("small_pearson_cohort")
     c = napg.Context(0)
     c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
     va = coh["cont"]
@@ -58,9 +59,9 @@ def test_config1_full(napg):
     c.close()
 
 
-def test_config2_ranks_full_size(napg):
+def test_rank_cohort_full_size(napg):
     rng = np.random.default_rng(2)
-    coh = cohort(2)
+    coh = cohort("rank_cohort")
     c = napg.Context(0)
     c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
     cat, cont = coh["cat"], coh["cont"]
@@ -72,9 +73,9 @@ def test_config2_ranks_full_size(napg):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_config3_mixed_cohort_full_size(napg, precision):
+def test_mixed_cohort_full_size(napg, precision):
     rng = np.random.default_rng(3)
-    coh = cohort(3)
+    coh = cohort("mixed_cohort")
     c = napg.Context(0)
     c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
     cat, cont = coh["cat"], coh["cont"]
@@ -88,9 +89,9 @@ def test_config3_mixed_cohort_full_size(napg, precision):
     c.close()
 
 
-def test_config4_batch_full_size(napg):
+def test_context_batch_full_size(napg):
     rng = np.random.default_rng(4)
-    coh = cohort(4)
+    coh = cohort("context_cohort")
     masks = coh["contexts"]
     c = napg.Context(0)
     c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
@@ -103,9 +104,9 @@ def test_config4_batch_full_size(napg):
     c.close()
 
 
-def test_config5_cohort_requests(napg):
+def test_serving_cohort_requests(napg):
     rng = np.random.default_rng(5)
-    coh = cohort(5)
+    coh = cohort("serving_cohort")
     c = napg.Context(0)
     c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
     S = coh["X"].shape[1]

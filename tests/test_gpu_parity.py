@@ -84,8 +84,8 @@ def test_pearson_offsets_and_empty_context(napg):
     c.close()
 
 
-def test_config1_full(napg):
-    coh = synth.config1()
+def test_small_pearson_full(napg):
+    coh = synth.small_pearson_cohort()
     c = ctx_for(napg, coh)
     va = coh["cont"]
     compare("pearson", c.run("pearson", va, out="numpy"), oracle_run("pearson", coh, va))
