@@ -228,7 +228,7 @@ def sampled_accuracy(coh, tests, outs, k, seed=123):
 def stage_rooflines(stage_ms, steps, coh, tests, peaks):
     """Roofline entry per traced stage: algorithmic work of the stage per step
     (the per-unit figures of the hot-path table: 12 S flops per Pearson pair,
-    6 S per group-sum pair, S increments per contingency pair, 16.25 S / 9.125 S
+    6 S per group-sum pair (issued: the one-hot rows against the B planes), S increments per contingency pair, 16.25 S / 9.125 S
     bytes per rank pair, bytes streamed by the plane builder, FP64 operations per
     p-value) divided by the stage's device time, against the measured peak."""
     S = coh["X"].shape[1]
@@ -249,7 +249,12 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
             work["planes_f16"][1] += na * (esz * S + S / 8 + 10.0 * S_pad)
         if test in ("anova", "ttest") and vb is not None:
             R = int(coh["nlev"][va].sum())
-            issued = -(-R // 128) * -(-len(vb) // 48) * nkb * 4 * 2.0 * 128 * 240 * 16
+            if test == "anova":
+                # level rows x (count, two sum planes) + observed rows x two square planes
+                issued = 2.0 * 128 * -(-R // 128) * 3 * len(vb) * S_pad + 2.0 * 128 * -(-na // 128) * 2 * len(vb) * S_pad
+            else:
+                # level rows x all five planes
+                issued = 2.0 * 128 * -(-R // 128) * 5 * len(vb) * S_pad
             w = work.get("groupsum_tc", ("tensor", 0.0, 0.0))
             work["groupsum_tc"] = ("tensor", w[1] + 6.0 * S * na * len(vb), w[2] + issued)
         if test == "chi2":

@@ -98,17 +98,23 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 for (int g = 0; g < c; ++g) {
                     const int64_t idx = (int64_t)(off + g) * f.nb + j;
                     s1 += f.g1[idx];
-                    raw += f.g2[idx] + (f.vsq ? f.vsq[j] * (double)f.gn[idx] : 0.0);
+                    if (!f.g2tot) raw += f.g2[idx] + (f.vsq ? f.vsq[j] * (double)f.gn[idx] : 0.0);
                 }
+                // sum of squares over all co-observed samples: per level, or one total
+                if (f.g2tot) raw = f.g2tot[t] + (f.vsq ? f.vsq[j] * (double)n : 0.0);
                 const double gm = s1 / (double)n;
-                double ssb = 0.0, ssw = 0.0;
+                double ssb = 0.0, ssw = f.g2tot ? raw : 0.0;
                 for (int g = 0; g < c; ++g) {
                     if (!f.present[off + g]) continue;
                     const int64_t idx = (int64_t)(off + g) * f.nb + j;
                     const double ng = (double)f.gn[idx], mg = f.g1[idx] / ng;
-                    const double s2 = f.g2[idx] + (f.vsq ? f.vsq[j] * ng : 0.0);
                     ssb += ng * (mg - gm) * (mg - gm);
-                    ssw += s2 - f.g1[idx] * mg;
+                    if (f.g2tot) {
+                        ssw -= f.g1[idx] * mg;
+                    } else {
+                        const double s2 = f.g2[idx] + (f.vsq ? f.vsq[j] * ng : 0.0);
+                        ssw += s2 - f.g1[idx] * mg;
+                    }
                 }
                 if (!(ssw > f.rel_tol * raw) || (f.vsq && n < kMixedMinN)) {
                     flags[atomicAdd(nflag, 1)] = (int32_t)t;

@@ -348,12 +348,18 @@ struct StackParams {
     uint32_t *err;
 };
 
-// NPL planes stacked (M, Xh, Xl, Dh, Dl: 5). Dropping Dl is not an option for the
-// group sums either: the FP16 rounding of the centred squares leaves ~2^-12 /
-// sqrt(n) relative error on the within-group sum, which at n of a few hundred and
-// F well above 1 moves the F statistic's effect-scale value by more than 1e-6.
-template <int NPL, int SV, int STAGES>
+// NPL planes stacked, playing the roles ROLE0, ROLE0 + 1, ... of the list (M,
+// Xh, Xl, Dh, Dl): all five (counts and both sums), the first three (counts and
+// sum x~) or the last two (sum of centred squares alone). Dropping Dl is not an
+// option for the group sums: the FP16 rounding of the centred squares leaves
+// ~2^-12 / sqrt(n) relative error on the within-group sum, which at n of a few
+// hundred and F well above 1 moves the F statistic's effect-scale value by more
+// than 1e-6.
+template <int NPL, int SV, int STAGES, int ROLE0>
 __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_constant__ StackParams P) {
+    constexpr bool kHasN = ROLE0 == 0;
+    constexpr bool kHasS1 = ROLE0 <= 1 && ROLE0 + NPL > 1;
+    constexpr bool kHasS2 = ROLE0 + NPL > 3;
     constexpr int kSV = SV;
     constexpr int kSPerThread = SV / 2;
     static_assert(SV % 16 == 0, "SV");
@@ -483,16 +489,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
                     for (int k = 0; k < 8; ++k) r[g * 8 + k] = t8[k];
                 }
                 tmem_ld_wait();
-                if (p == 0) {
+                const int role = ROLE0 + p;
+                if (role == 0) {
 #pragma unroll
                     for (int k = 0; k < kSPerThread; ++k) cnt[k] += (int32_t)__uint_as_float(r[k]);   // exact integers
                 } else {
 #pragma unroll
                     for (int k = 0; k < K2; ++k) {
                         const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
-                        if (p == 1) two_sum2(s1h[k], s1l[k], v);
-                        else if (p == 2) s1l[k] = add2(s1l[k], v);
-                        else if (p == 3) two_sum2(s2h[k], s2l[k], v);
+                        if (role == 1) two_sum2(s1h[k], s1l[k], v);
+                        else if (role == 2) s1l[k] = add2(s1l[k], v);
+                        else if (role == 3) two_sum2(s2h[k], s2l[k], v);
                         else s2l[k] = add2(s2l[k], v);
                     }
                 }
@@ -516,9 +523,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
                         const int col = J * kSV + h * kSPerThread + 2 * k + e2;
                         if (col < P.rowsB) {
                             const int64_t o = P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col;
-                            P.out_n[o] = cnt[2 * k + e2];
-                            P.out_s1[o] = ldexp((double)(e2 ? a1 : a0) + (double)(e2 ? b1 : b0), -(int)P.exp1[col]);
-                            P.out_s2[o] = ldexp((double)(e2 ? c1 : c0) + (double)(e2 ? d1 : d0), -(int)P.exp2[col]);
+                            if (kHasN) P.out_n[o] = cnt[2 * k + e2];
+                            if (kHasS1)
+                                P.out_s1[o] = ldexp((double)(e2 ? a1 : a0) + (double)(e2 ? b1 : b0), -(int)P.exp1[col]);
+                            if (kHasS2)
+                                P.out_s2[o] = ldexp((double)(e2 ? c1 : c0) + (double)(e2 ? d1 : d0), -(int)P.exp2[col]);
                         }
                     }
                 }
@@ -696,12 +705,12 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
     return NAPG_OK;
 }
 
-template <int NPL, int SV>
+template <int NPL, int SV, int ROLE0>
 static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
     constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * SV * kKB * 2;
     constexpr int STAGES = (220 * 1024) / STAGE_BYTES > 6 ? 6 : (220 * 1024) / STAGE_BYTES;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    auto kern = k_umma_stacked<NPL, SV, STAGES>;
+    auto kern = k_umma_stacked<NPL, SV, STAGES, ROLE0>;
     NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int tiles = P.tilesA * P.tilesB;
     if (tiles == 0) return NAPG_OK;
@@ -711,21 +720,28 @@ static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaSt
     return NAPG_OK;
 }
 
-// B-tile widths the autotuner chooses from (every width gives the same sums:
-// each output accumulates the same products in the same order and drains)
-constexpr int kStackWidths[2] = {48, 32};
+// B-tile widths the autotuner chooses from, per plane set (every width gives the
+// same sums: each output accumulates the same products in the same order and
+// drains); MMA N = planes x width stays a multiple of 16 and at most 256
+enum StackPlanes { kStackAll = 0, kStackNS1 = 1, kStackS2 = 2 };
+constexpr int kStackWidths[3][2] = {{48, 32}, {64, 48}, {64, 48}};
+constexpr int kStackPlaneCount[3] = {5, 3, 2};
+constexpr int kStackRole0[3] = {0, 0, 3};
 
 // A x stacked B planes with the B-tile width chosen by the autotuner for this
-// shape (the tensor maps of the B planes are encoded for that width)
-static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *const *pb, int64_t rows_b_pad,
+// shape (the tensor maps of the B planes are encoded for that width); pb holds
+// the planes of the set in role order
+static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *const *pb, int set, int64_t rows_b_pad,
                                   int64_t S_pad, int kind, cudaStream_t st) {
     auto run = [&](int choice) -> napg_status {
-        const int sv = kStackWidths[choice];
-        for (int k = 0; k < 5; ++k)
+        const int sv = kStackWidths[set][choice];
+        for (int k = 0; k < kStackPlaneCount[set]; ++k)
             if (!make_map(&P.mapB[k], pb[k], rows_b_pad, S_pad, sv))
                 return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         P.tilesB = (P.rowsB + sv - 1) / sv;
-        return sv == 48 ? launch_stacked_sv<5, 48>(ctx, P, st) : launch_stacked_sv<5, 32>(ctx, P, st);
+        if (set == kStackAll) return sv == 48 ? launch_stacked_sv<5, 48, 0>(ctx, P, st) : launch_stacked_sv<5, 32, 0>(ctx, P, st);
+        if (set == kStackNS1) return sv == 64 ? launch_stacked_sv<3, 64, 0>(ctx, P, st) : launch_stacked_sv<3, 48, 0>(ctx, P, st);
+        return sv == 64 ? launch_stacked_sv<2, 64, 3>(ctx, P, st) : launch_stacked_sv<2, 48, 3>(ctx, P, st);
     };
     const TuneKey key{kind, P.rowsA, P.rowsB, P.nkb};
     return tuned_launch(ctx, key, 2, run, st);
@@ -853,14 +869,15 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_stacked(ctx, P, pb, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
+        NAPG_ST(launch_stacked(ctx, P, pb, kStackAll, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
     }
     return NAPG_OK;
 }
 
 napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                            const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn, double *g1,
-                           double *g2, double *shift, double *vsq, const std::vector<int32_t> *cache_vars) {
+                           double *g2, double *shift, double *vsq, const std::vector<int32_t> *cache_vars,
+                           const uint32_t *obsa, int32_t na, double *g2tot) {
     ContPlanes cp;
     NAPG_ST(prep_cont_planes(ctx, c, ws, st, vars_b_dev, nb, obsb, Workspace::kTmpA, shift, vsq, cp, cache_vars));
     __half *H = nullptr;
@@ -868,13 +885,37 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
     StackParams P{};
     if (!make_map(&P.mapA, H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-    const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
     P.rowsA = R; P.rowsB = nb; P.tilesA = (int)(hrows / kTM);
     P.nkb = (int)(S_pad / kKB); P.chunk = kChunkOther;
     P.out_n = gn; P.out_s1 = g1; P.out_s2 = g2; P.ld = nb; P.out_transpose = 0;
     P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
+    if (!g2tot) {
+        const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
+        Stage s_(ctx->trace, st, "groupsum_tc");
+        return launch_stacked(ctx, P, pb, kStackAll, cp.rows_pad, cp.S_pad, kTuneStackOneHot, st);
+    }
+    // One-way ANOVA needs the centred squares summed over all co-observed
+    // samples only (SSW = sum x~^2 - sum_g S1_g^2 / n_g): the level rows take
+    // the count and sum planes, and each categorical's observed row alone takes
+    // the square planes
+    {
+        const void *pb[3] = {cp.M, cp.Xh, cp.Xl};
+        P.out_s2 = nullptr;
+        Stage s_(ctx->trace, st, "groupsum_tc");
+        NAPG_ST(launch_stacked(ctx, P, pb, kStackNS1, cp.rows_pad, cp.S_pad, kTuneStackOneHotNS1, st));
+    }
+    __half *O = nullptr;
+    int64_t orows = 0;
+    NAPG_ST(prep_onehot(ctx, c, ws, st, obsa, na, Workspace::kTmpG, &O, orows, S_pad));
+    StackParams Q{};
+    if (!make_map(&Q.mapA, O, orows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+    Q.rowsA = na; Q.rowsB = nb; Q.tilesA = (int)(orows / kTM);
+    Q.nkb = (int)(S_pad / kKB); Q.chunk = kChunkOther;
+    Q.out_n = nullptr; Q.out_s1 = nullptr; Q.out_s2 = g2tot; Q.ld = nb; Q.out_transpose = 0;
+    Q.exp1 = cp.sexp; Q.exp2 = cp.texp; Q.err = ctx->dev_err;
+    const void *qb[2] = {cp.Dh, cp.Dl};
     Stage s_(ctx->trace, st, "groupsum_tc");
-    return launch_stacked(ctx, P, pb, cp.rows_pad, cp.S_pad, kTuneStackOneHot, st);
+    return launch_stacked(ctx, Q, qb, kStackS2, cp.rows_pad, cp.S_pad, kTuneStackSquares, st);
 }
 
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,

@@ -416,8 +416,12 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         double *shift = WS(kShiftB, double, nb);
         double *vsq = mixed ? WS(kVsq, double, nb) : nullptr;
         if (st_) return st_;
+        // mixed-form ANOVA: the centred squares summed per (a, j) over all levels
+        double *g2tot = (mixed && t == NAPG_ANOVA) ? WS(kMomC, double, (int64_t)na * nb) : nullptr;
+        if (st_) return st_;
         if (mixed) {
-            NAPG_ST(mixed_groupsum(ctx, c, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift, vsq, (a.mask || a.no_plane_cache) ? nullptr : &vb));
+            NAPG_ST(mixed_groupsum(ctx, c, ws, st, levbits, R, d_vb, nb, obsB, gn, g1, g2, shift, vsq,
+                                   (a.mask || a.no_plane_cache) ? nullptr : &vb, obsA, na, g2tot));
         } else {
             double *xs = WS(kXsB, double, (int64_t)nb * S_pad);
             if (st_) return st_;
@@ -427,7 +431,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
         GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? kMixedRelTol : kPlainRelTol,
-                   vsq, pj.q};
+                   vsq, pj.q, g2tot};
         { Stage s_(ctx->trace, st, "finalize_groups"); launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, maxlev, st); }

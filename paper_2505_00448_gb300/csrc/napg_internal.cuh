@@ -80,7 +80,8 @@ struct Workspace {
 };
 
 // ---- autotuner (tune.cu)
-enum TuneKind : int { kTuneStackMask = 1, kTuneStackOneHot = 2, kTuneSpearman = 3, kTuneRankGroups = 4 };
+enum TuneKind : int { kTuneStackMask = 1, kTuneStackOneHot = 2, kTuneSpearman = 3, kTuneRankGroups = 4,
+                      kTuneStackOneHotNS1 = 5, kTuneStackSquares = 6 };
 struct TuneKey {
     int kind;
     int64_t a, b, c;    // rows of A, rows of B, K length (shape of the problem)
@@ -236,6 +237,8 @@ struct GroupFin {
     double rel_tol;
     const double *vsq;   // mixed form: g2 holds sum (x~^2 - v); add v n_g back (NULL: plain)
     PJobQueue q;
+    const double *g2tot; // ANOVA, mixed form: [na][nb] sum (x~^2 - v) over all co-observed samples
+                         // (then g2 is not read); NULL: per-level g2
 };
 void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout,
                             int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -299,7 +302,8 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
 napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                            const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn,
                            double *g1, double *g2, double *shift_out, double *vsq_out,
-                           const std::vector<int32_t> *cache_vars);
+                           const std::vector<int32_t> *cache_vars,
+                           const uint32_t *obsa = nullptr, int32_t na = 0, double *g2tot = nullptr);
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
                               int32_t R, int32_t *T);
 

@@ -17,6 +17,8 @@ static const char *kind_name(int k) {
         case kTuneStackOneHot: return "stacked_onehot";
         case kTuneSpearman: return "spearman_threads";
         case kTuneRankGroups: return "rank_groups_threads";
+        case kTuneStackOneHotNS1: return "stacked_onehot_counts_sums";
+        case kTuneStackSquares: return "stacked_observed_squares";
         default: return "unknown";
     }
 }

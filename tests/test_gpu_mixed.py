@@ -165,6 +165,8 @@ def test_autotuner_keeps_results_identical(napg):
         r = {}
         r["pearson"] = c.run("pearson", coh["cont"], out="numpy", precision="mixed")
         r["anova"] = c.run("anova", coh["cat"], coh["cont"], out="numpy", precision="mixed")
+        bins = coh["cat"][coh["nlev"][coh["cat"]] == 2]
+        r["ttest"] = c.run("ttest", bins, coh["cont"], out="numpy", precision="mixed")
         r["spearman"] = c.run("spearman", coh["cont"], out="numpy")
         r["kruskal"] = c.run("kruskal", coh["cat"], coh["cont"], out="numpy")
         if tune_on:
@@ -173,7 +175,10 @@ def test_autotuner_keeps_results_identical(napg):
                 assert np.array_equal(again[k], r["pearson"][k], equal_nan=True)
             recs = c.tune_read()
             kinds = {x["kind"] for x in recs}
-            assert {"stacked_mask", "stacked_onehot", "spearman_threads", "rank_groups_threads"} <= kinds, recs
+            # ANOVA: level rows x (count, sum) planes and observed rows x square
+            # planes; the t-test: level rows x all five planes
+            assert {"stacked_mask", "stacked_onehot", "stacked_onehot_counts_sums", "stacked_observed_squares",
+                    "spearman_threads", "rank_groups_threads"} <= kinds, recs
             assert all(len(x["ms"]) == 2 and min(x["ms"]) > 0 for x in recs), recs
         else:
             assert c.tune_read() == []
