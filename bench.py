@@ -661,7 +661,8 @@ def batch_main(args, world, rank, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=30,
+                    help="timed steps (the default keeps the timed region near a second, for clock samples)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -686,7 +687,7 @@ def main():
         coh, tests, desc = make_workload(args.workload, args.scale)
         samples = []
         for k in range(args.warmup + args.steps):
-            r = oracle_sample(coh, tests, budget_s=max(4.0, 60.0 / (args.warmup + args.steps)), seed=k)
+            r = oracle_sample(coh, tests, budget_s=max(1.5, 60.0 / (args.warmup + args.steps)), seed=k)
             if k >= args.warmup:
                 samples.append(r)
         v = statistics.mean(r["value"] for r in samples)
