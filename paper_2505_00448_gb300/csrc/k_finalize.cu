@@ -24,52 +24,80 @@ __device__ __forceinline__ void put(double *stat, double *pval, int32_t *nout, i
 }
 
 // ------------------------------------------------------------------ Pearson --
-__global__ void k_finalize_pearson(PearsonFin f, double *stat, double *pval, int32_t *nout, int32_t *flags,
-                                   int32_t *nflag) {
-    const int64_t nv = f.nv;
-    const int64_t total = nv * (nv + 1) / 2;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        // t -> (i, j), i <= j, row-major over the upper triangle
-        int64_t i = (int64_t)((2.0 * nv + 1.0 - sqrt((2.0 * nv + 1.0) * (2.0 * nv + 1.0) - 8.0 * (double)t)) / 2.0);
-        while (i > 0 && i * (2 * nv - i + 1) / 2 > t) --i;
-        while ((i + 1) * (2 * nv - i) / 2 <= t) ++i;
-        const int64_t j = i + (t - i * (2 * nv - i + 1) / 2);
-        const int64_t ij = i * nv + j, ji = j * nv + i;
-        const int32_t n = f.nn[ij];
-        double r = dnan(), p = dnan();
-        if (n > 1) {
-            const double nd = (double)n;
-            const double sx = f.Sx[ij], sy = f.Sx[ji], sxy = f.Sxy[ij];
-            const double sxx = f.vsq ? f.Sxx[ij] + f.vsq[i] * nd : f.Sxx[ij];
-            const double syy = f.vsq ? f.Sxx[ji] + f.vsq[j] * nd : f.Sxx[ji];
-            const double cxx = sxx - sx * sx / nd, cyy = syy - sy * sy / nd, cxy = sxy - sx * sy / nd;
-            if (!(cxx > f.rel_tol * sxx) || !(cyy > f.rel_tol * syy) || (f.vsq && n < kMixedMinN)) {
-                const int q = atomicAdd(nflag, 1);
-                flags[q] = (int32_t)ij;
-            } else {
-                // a variable against itself: r = 1 exactly, as the two-pass
-                // definition gives (its centred cross sum is its sum of squares)
-                const bool same = f.vars ? f.vars[i] == f.vars[j] : i == j;
-                r = same ? 1.0 : cxy / (sqrt(cxx) * sqrt(cyy));
-                r = fmin(1.0, fmax(-1.0, r));
-                if (n <= 2) p = dnan();
-                else if (fabs(r) >= 1.0) p = 0.0;
-                else if (f.q.jobs) p = pjob_push_p(f.q, PJob{r, nd, 0.0, ij, kPjCorr, (int32_t)nv});
-            }
+// One CTA per upper-triangle tile (I <= J) of 32 x 32 pairs. The (j, i) sums
+// come from the mirrored tile, read row by row and transposed in shared memory,
+// and the (j, i) outputs go back the same way, so every global access runs
+// along a row.
+constexpr int kFinT = 32;
+
+__global__ void __launch_bounds__(256) k_finalize_pearson(PearsonFin f, double *stat, double *pval, int32_t *nout,
+                                                          int32_t *flags, int32_t *nflag) {
+    const int nv = f.nv;
+    const int T = (nv + kFinT - 1) / kFinT;
+    int t = blockIdx.x, I = 0;
+    while (t >= T - I) { t -= T - I; ++I; }
+    const int J = I + t;
+    __shared__ double m_sx[kFinT][kFinT + 1], m_sxx[kFinT][kFinT + 1];   // mirrored tile (rows j, columns i)
+    __shared__ double o_r[kFinT][kFinT + 1], o_p[kFinT][kFinT + 1];      // outputs by (i, j) for the mirror
+    __shared__ int32_t o_n[kFinT][kFinT + 1];
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int i0 = I * kFinT, j0 = J * kFinT;
+    for (int ry = ly; ry < kFinT; ry += 8) {
+        const int j = j0 + ry, i = i0 + lx;
+        if (j < nv && i < nv) {
+            m_sx[ry][lx] = f.Sx[(int64_t)j * nv + i];
+            m_sxx[ry][lx] = f.Sxx[(int64_t)j * nv + i];
         }
-        put(stat, pval, nout, ij, r, p, n);       // p of a queued job is written by the evaluation
-        put(stat, pval, nout, ji, r, p, n);
+    }
+    __syncthreads();
+    for (int ry = ly; ry < kFinT; ry += 8) {
+        const int i = i0 + ry, j = j0 + lx;
+        double r = dnan(), p = dnan();
+        int32_t n = 0;
+        if (i < nv && j < nv && (I != J || i <= j)) {
+            const int64_t ij = (int64_t)i * nv + j;
+            n = f.nn[ij];
+            if (n > 1) {
+                const double nd = (double)n, inv_n = 1.0 / nd;
+                const double sx = f.Sx[ij], sy = m_sx[lx][ry], sxy = f.Sxy[ij];
+                const double sxx = f.vsq ? f.Sxx[ij] + f.vsq[i] * nd : f.Sxx[ij];
+                const double syy = f.vsq ? m_sxx[lx][ry] + f.vsq[j] * nd : m_sxx[lx][ry];
+                const double cxx = sxx - sx * sx * inv_n, cyy = syy - sy * sy * inv_n, cxy = sxy - sx * sy * inv_n;
+                if (!(cxx > f.rel_tol * sxx) || !(cyy > f.rel_tol * syy) || (f.vsq && n < kMixedMinN)) {
+                    const int q = atomicAdd(nflag, 1);
+                    flags[q] = (int32_t)ij;
+                } else {
+                    // a variable against itself: r = 1 exactly, as the two-pass
+                    // definition gives (its centred cross sum is its sum of squares)
+                    const bool same = f.vars ? f.vars[i] == f.vars[j] : i == j;
+                    r = same ? 1.0 : cxy / sqrt(cxx * cyy);
+                    r = fmin(1.0, fmax(-1.0, r));
+                    if (n <= 2) p = dnan();
+                    else if (fabs(r) >= 1.0) p = 0.0;
+                    else if (f.q.jobs) p = pjob_push_p(f.q, PJob{r, nd, 0.0, ij, kPjCorr, (int32_t)nv});
+                }
+            }
+            put(stat, pval, nout, ij, r, p, n);       // p of a queued job is written by the evaluation
+        }
+        o_r[ry][lx] = r;
+        o_p[ry][lx] = p;
+        o_n[ry][lx] = n;
+    }
+    __syncthreads();
+    // the mirrored outputs (j, i), i < j: row j of the (J, I) tile
+    for (int ry = ly; ry < kFinT; ry += 8) {
+        const int j = j0 + ry, i = i0 + lx;
+        if (i < nv && j < nv && (I != J || i < j))
+            put(stat, pval, nout, (int64_t)j * nv + i, o_r[lx][ry], o_p[lx][ry], o_n[lx][ry]);
     }
 }
 
 void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout, int32_t *flag_list,
                              int32_t *flag_count, cudaStream_t st) {
-    const int64_t total = (int64_t)f.nv * (f.nv + 1) / 2;
-    if (total == 0) return;
-    const unsigned blocks = (unsigned)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    if (f.nv == 0) return;
+    const int64_t T = (f.nv + kFinT - 1) / kFinT;
     count_launch();
-    k_finalize_pearson<<<blocks, 128, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
+    k_finalize_pearson<<<(unsigned)(T * (T + 1) / 2), 256, 0, st>>>(f, stat, pval, nout, flag_list, flag_count);
 }
 
 // --------------------------------------------------- ANOVA / Welch / Student --
