@@ -558,90 +558,176 @@ __device__ __forceinline__ int scale_exp(double maxabs) {
 // and in the finalize step (which adds v n back), so they are FP32 values; x - c
 // keeps 24 bits relative to itself (exact when x and c are within a factor of
 // two), and the planes keep 22.
+// Four consecutive values x[s0 .. s0+3] (zero past S): one 16-byte load (two for
+// FP64) when the row is 16-byte aligned and the four are inside it.
 template <typename T>
-__global__ void k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad, const int32_t *__restrict__ vars,
-                              int32_t nv, const uint32_t *__restrict__ obsv, int64_t W, __half *Pm, __half *Pxh,
-                              __half *Pxl, __half *Pdh, __half *Pdl, double *shift, double *vsq, int8_t *sexp,
-                              int8_t *texp) {
+__device__ __forceinline__ void load4(const T *__restrict__ x, int64_t s0, int64_t S, bool aligned, T (&v)[4]) {
+    if (aligned && s0 + 4 <= S) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 f = *reinterpret_cast<const float4 *>(x + s0);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else {
+            const double2 a = *reinterpret_cast<const double2 *>(x + s0);
+            const double2 b = *reinterpret_cast<const double2 *>(x + s0 + 2);
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = s0 + k < S ? x[s0 + k] : T(0);
+    }
+}
+
+// STAGE: the row and its observed bits are first copied to shared memory (one
+// read from HBM; the three passes then read shared memory), for rows that fit.
+// Every pass takes four samples per thread and step.
+template <typename T, bool STAGE>
+__global__ void __launch_bounds__(1024) k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad,
+                                                      const int32_t *__restrict__ vars, int32_t nv,
+                                                      const uint32_t *__restrict__ obsv, int64_t W, __half *Pm,
+                                                      __half *Pxh, __half *Pxl, __half *Pdh, __half *Pdl,
+                                                      double *shift, double *vsq, int8_t *sexp, int8_t *texp) {
+    extern __shared__ __align__(16) unsigned char pl_smem[];
     const int i = blockIdx.x;
     const int64_t base = (int64_t)i * S_pad;
-    const __half z = __float2half(0.f);
+    // the planes are written four samples (8 bytes) per thread and step (S_pad is
+    // a multiple of 64, so every row starts 128-byte aligned)
+    uint2 *m4 = reinterpret_cast<uint2 *>(Pm + base), *xh4 = reinterpret_cast<uint2 *>(Pxh + base),
+          *xl4 = reinterpret_cast<uint2 *>(Pxl + base), *dh4 = reinterpret_cast<uint2 *>(Pdh + base),
+          *dl4 = reinterpret_cast<uint2 *>(Pdl + base);
+    const int64_t n4 = S_pad / 4;
     if (i >= nv) {
-        for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
-            Pm[base + s] = z; Pxh[base + s] = z; Pxl[base + s] = z; Pdh[base + s] = z; Pdl[base + s] = z;
-        }
+        const uint2 z4 = make_uint2(0u, 0u);
+        for (int64_t q = threadIdx.x; q < n4; q += blockDim.x) { m4[q] = z4; xh4[q] = z4; xl4[q] = z4; dh4[q] = z4; dl4[q] = z4; }
         return;
     }
     const T *x = X + (int64_t)vars[i] * S;
     const uint32_t *ob = obsv + (int64_t)i * W;
-    __shared__ float red[32];
+    if (STAGE) {
+        T *xs = reinterpret_cast<T *>(pl_smem);
+        uint32_t *obs = reinterpret_cast<uint32_t *>(pl_smem + (size_t)S_pad * sizeof(T));
+        // 16-byte loads, four in flight per thread, when the row is 16-byte aligned
+        int64_t done = 0;
+        if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+            const int64_t nvec = (int64_t)(S * sizeof(T)) / 16;
+            const uint4 *xv = reinterpret_cast<const uint4 *>(x);
+            uint4 *sv = reinterpret_cast<uint4 *>(xs);
+#pragma unroll 4
+            for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) sv[q] = xv[q];
+            done = nvec * (int64_t)(16 / sizeof(T));
+        }
+        for (int64_t s = done + threadIdx.x; s < S; s += blockDim.x) xs[s] = x[s];
+        for (int64_t w = threadIdx.x; w < W; w += blockDim.x) obs[w] = ob[w];
+        __syncthreads();
+        x = xs;
+        ob = obs;
+    }
+    __shared__ float red[4][32];
     __shared__ int redc[32];
-    __shared__ float bc[4];
-    __shared__ int cnt_s;
-    auto block_red = [&](float v, int c, int op, float *out_v, int *out_c) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const float w = __shfl_down_sync(0xffffffffu, v, o);
-            v = op ? fmaxf(v, w) : v + w;
-            c += __shfl_down_sync(0xffffffffu, c, o);
-        }
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) { red[threadIdx.x >> 5] = v; redc[threadIdx.x >> 5] = c; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float tv = 0.f;
-            int tc = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { tv = op ? fmaxf(tv, red[w]) : tv + red[w]; tc += redc[w]; }
-            *out_v = tv;
-            if (out_c) *out_c = tc;
-        }
-        __syncthreads();
-    };
-    // T = double input: x - c is formed in FP64 then rounded (FP32 data: exact ops)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const bool al = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+    const int64_t nq = (S + 3) / 4;
+    // pass 1: the shift c = mean of the observed values (FP32)
     float s1 = 0.f;
     int cn = 0;
-    for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
-        if ((ob[s >> 5] >> (s & 31)) & 1u) { s1 += (float)x[s]; ++cn; }
-    block_red(s1, cn, 0, &bc[0], &cnt_s);
-    const int cnt = cnt_s;
-    const float c = cnt > 0 ? bc[0] / (float)cnt : 0.f;
-    float s2 = 0.f, mx = 0.f;
-    for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
-        if ((ob[s >> 5] >> (s & 31)) & 1u) {
-            const float d = (float)(x[s] - (T)c);
-            s2 = fmaf(d, d, s2);
-            mx = fmaxf(mx, fabsf(d));
-        }
-    block_red(s2, 0, 0, &bc[1], nullptr);
-    block_red(mx, 0, 1, &bc[2], nullptr);
-    const float v = cnt > 0 ? bc[1] / (float)cnt : 0.f;
-    float md = 0.f;
-    for (int64_t s = threadIdx.x; s < S; s += blockDim.x)
-        if ((ob[s >> 5] >> (s & 31)) & 1u) {
-            const float d = (float)(x[s] - (T)c);
-            md = fmaxf(md, fabsf(fmaf(d, d, -v)));
-        }
-    block_red(md, 0, 1, &bc[3], nullptr);
-    const int es = scale_exp((double)bc[2]), et = scale_exp((double)bc[3]);
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int64_t s0 = 4 * q;
+        const uint32_t obits = (ob[s0 >> 5] >> (s0 & 31)) & 0xfu;
+        if (!obits) continue;
+        T xv[4];
+        load4(x, s0, S, al, xv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if ((obits >> k) & 1u) { s1 += (float)xv[k]; ++cn; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        cn += __shfl_down_sync(0xffffffffu, cn, o);
+    }
+    if (lane == 0) { red[0][warp] = s1; redc[warp] = cn; }
+    __syncthreads();
+    float tot = 0.f;
+    int cnt = 0;
+    for (int k = 0; k < nw; ++k) { tot += red[0][k]; cnt += redc[k]; }   // every thread, same order
+    const float c = cnt > 0 ? tot / (float)cnt : 0.f;
+    __syncthreads();
+    // pass 2: v = mean (x - c)^2, the largest |x - c| and the range of (x - c)^2,
+    // which bounds |(x - c)^2 - v| (the square planes' scale)
+    float s2 = 0.f, mx = 0.f, sqmax = 0.f, sqmin = 3.0e38f;
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int64_t s0 = 4 * q;
+        const uint32_t obits = (ob[s0 >> 5] >> (s0 & 31)) & 0xfu;
+        if (!obits) continue;
+        T xv[4];
+        load4(x, s0, S, al, xv);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if ((obits >> k) & 1u) {
+                const float d = (float)(xv[k] - (T)c);
+                const float sq = d * d;
+                s2 = fmaf(d, d, s2);
+                mx = fmaxf(mx, fabsf(d));
+                sqmax = fmaxf(sqmax, sq);
+                sqmin = fminf(sqmin, sq);
+            }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        sqmax = fmaxf(sqmax, __shfl_down_sync(0xffffffffu, sqmax, o));
+        sqmin = fminf(sqmin, __shfl_down_sync(0xffffffffu, sqmin, o));
+    }
+    if (lane == 0) { red[0][warp] = s2; red[1][warp] = mx; red[2][warp] = sqmax; red[3][warp] = sqmin; }
+    __syncthreads();
+    float ts2 = 0.f, tmx = 0.f, tmax = 0.f, tmin = 3.0e38f;
+    for (int k = 0; k < nw; ++k) {
+        ts2 += red[0][k];
+        tmx = fmaxf(tmx, red[1][k]);
+        tmax = fmaxf(tmax, red[2][k]);
+        tmin = fminf(tmin, red[3][k]);
+    }
+    const float v = cnt > 0 ? ts2 / (float)cnt : 0.f;
+    const float md = cnt > 0 ? fmaxf(tmax - v, v - tmin) : 0.f;
+    const int es = scale_exp((double)tmx), et = scale_exp((double)md);
     if (threadIdx.x == 0) { shift[i] = (double)c; vsq[i] = (double)v; sexp[i] = (int8_t)es; texp[i] = (int8_t)et; }
     const float fs = exp2f((float)es), ft = exp2f((float)et);   // exact powers of two
-    const __half one = __float2half(1.f);
-    for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
-        const bool o = s < S && ((ob[s >> 5] >> (s & 31)) & 1u);
-        if (!o) {
-            Pm[base + s] = z; Pxh[base + s] = z; Pxl[base + s] = z; Pdh[base + s] = z; Pdl[base + s] = z;
-            continue;
+    // pass 3: the planes, four samples per thread and step
+    for (int64_t q = threadIdx.x; q < n4; q += blockDim.x) {
+        const int64_t s0 = 4 * q;
+        const uint32_t obits = s0 < S ? (ob[s0 >> 5] >> (s0 & 31)) & 0xfu : 0u;
+        T xv[4] = {T(0), T(0), T(0), T(0)};
+        if (obits) load4(x, s0, S, al, xv);
+        __align__(8) __half hm[4];
+        __align__(8) __half hxh[4];
+        __align__(8) __half hxl[4];
+        __align__(8) __half hdh[4];
+        __align__(8) __half hdl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t s = s0 + k;
+            const bool o = s < S && ((obits >> k) & 1u);
+            float xt = 0.f;
+            if (o) xt = (float)(xv[k] - (T)c);
+            const float xs = xt * fs;                                  // exact scaling
+            const __half h = __float2half_rn(xs);
+            const __half l = __float2half_rn(xs - __half2float(h));    // the difference is exact in FP32
+            // d = xt^2 - v with the square's rounding error recovered by FMA
+            const float sq = xt * xt;
+            const float sq_err = fmaf(xt, xt, -sq);
+            const float ds = ((sq - v) + sq_err) * ft;
+            const __half dh = __float2half_rn(ds);
+            const __half dl = __float2half_rn(ds - __half2float(dh));
+            const __half z = __float2half(0.f);
+            hm[k] = o ? __float2half(1.f) : z;
+            hxh[k] = o ? h : z;
+            hxl[k] = o ? l : z;
+            hdh[k] = o ? dh : z;
+            hdl[k] = o ? dl : z;
         }
-        const float xt = (float)(x[s] - (T)c);
-        const float xs = xt * fs;                                  // exact scaling
-        const __half h = __float2half_rn(xs);
-        const __half l = __float2half_rn(xs - __half2float(h));    // the difference is exact in FP32
-        // d = xt^2 - v with the square's rounding error recovered by FMA
-        const float sq = xt * xt;
-        const float sq_err = fmaf(xt, xt, -sq);
-        const float ds = ((sq - v) + sq_err) * ft;
-        const __half dh = __float2half_rn(ds);
-        const __half dl = __float2half_rn(ds - __half2float(dh));
-        Pm[base + s] = one; Pxh[base + s] = h; Pxl[base + s] = l; Pdh[base + s] = dh; Pdl[base + s] = dl;
+        m4[q] = *reinterpret_cast<const uint2 *>(hm);
+        xh4[q] = *reinterpret_cast<const uint2 *>(hxh);
+        xl4[q] = *reinterpret_cast<const uint2 *>(hxl);
+        dh4[q] = *reinterpret_cast<const uint2 *>(hdh);
+        dl4[q] = *reinterpret_cast<const uint2 *>(hdl);
     }
 }
 
@@ -726,7 +812,6 @@ static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaSt
 enum StackPlanes { kStackAll = 0, kStackNS1 = 1, kStackS2 = 2 };
 constexpr int kStackWidths[3][2] = {{48, 32}, {64, 48}, {64, 48}};
 constexpr int kStackPlaneCount[3] = {5, 3, 2};
-constexpr int kStackRole0[3] = {0, 0, 3};
 
 // A x stacked B planes with the B-tile width chosen by the autotuner for this
 // shape (the tensor maps of the B planes are encoded for that width); pb holds
@@ -746,6 +831,13 @@ static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *cons
     const TuneKey key{kind, P.rowsA, P.rowsB, P.nkb};
     return tuned_launch(ctx, key, 2, run, st);
 }
+
+// Rows up to this many bytes (values plus observed bits) are staged in shared
+// memory by the plane builder (one 1024-thread CTA per SM).
+constexpr size_t kPlaneStageMax = 220 * 1024;
+
+template <typename T, typename... Rest>
+static const T *kern_x_type(void (*)(const T *, Rest...));
 
 struct ContPlanes {
     __half *M, *Xh, *Xl, *Dh, *Dl;
@@ -778,16 +870,21 @@ static napg_status prep_cont_planes(napg_ctx *ctx, Cohort &c, Workspace &ws, cud
     if (!hit) {
         key.valid = false;
         Stage s_(ctx->trace, st, "planes_f16");
-        count_launch();
-        if (c.dtype == NAPG_F32)
-            k_planes_cont<float><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const float *)c.X, c.S, cp.S_pad, vars_dev,
-                                                                        nv, obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh,
-                                                                        cp.Dl, pshift, pvsq, cp.sexp, cp.texp);
-        else
-            k_planes_cont<double><<<(unsigned)cp.rows_pad, 256, 0, st>>>((const double *)c.X, c.S, cp.S_pad,
-                                                                         vars_dev, nv, obsv, c.W, cp.M, cp.Xh, cp.Xl,
-                                                                         cp.Dh, cp.Dl, pshift, pvsq, cp.sexp, cp.texp);
-        NAPG_CU(ctx, cudaGetLastError());
+        const size_t esz = c.dtype == NAPG_F32 ? sizeof(float) : sizeof(double);
+        const size_t stage_bytes = (size_t)cp.S_pad * esz + (size_t)(c.W + 1) * sizeof(uint32_t);
+        const bool staged = stage_bytes <= kPlaneStageMax;
+        auto launch = [&](auto kern) -> napg_status {
+            if (staged) NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)stage_bytes));
+            count_launch();
+            kern<<<(unsigned)cp.rows_pad, staged ? 1024 : 256, staged ? stage_bytes : 0, st>>>(
+                (decltype(kern_x_type(kern)))c.X, c.S, cp.S_pad, vars_dev, nv, obsv, c.W, cp.M, cp.Xh,
+                cp.Xl, cp.Dh, cp.Dl, pshift, pvsq, cp.sexp, cp.texp);
+            NAPG_CU(ctx, cudaGetLastError());
+            return NAPG_OK;
+        };
+        if (c.dtype == NAPG_F32) NAPG_ST(staged ? launch(k_planes_cont<float, true>) : launch(k_planes_cont<float, false>));
+        else NAPG_ST(staged ? launch(k_planes_cont<double, true>) : launch(k_planes_cont<double, false>));
         if (cache_vars && first_slot == Workspace::kTmpA) {
             key.valid = true;
             key.gen = c.gen;

@@ -186,33 +186,62 @@ void launch_shift_values(const void *X, int32_t dtype, int64_t S, int64_t S_pad,
 // set when sample s is observed (in the context) and has label g. levcnt gets
 // the per-level counts (must be zeroed before). Each warp covers 32 words of one
 // variable and adds its per-level counts with one atomic per level.
+// Level bitmasks of the categorical variables: a thread takes one 32-sample word
+// of one categorical, loads its 32 labels once (eight 32-bit words when the row
+// is 4-byte aligned) and, per level g, forms the word's bits four labels at a
+// time (byte-wise compare, then the four compare results packed into four bits)
+// ANDed with the observed word; adjacent threads store adjacent words of a
+// level row. The in-context level counts are summed per warp, then one atomic
+// per level and warp.
+__device__ __forceinline__ uint32_t bits_eq4(uint32_t labels4, uint32_t g4) {
+    // 0xff in each byte whose label equals g, then bit 7 of each byte moved to
+    // bits 0..3 (byte k -> bit k)
+    const uint32_t m = __vcmpeq4(labels4, g4) & 0x80808080u;
+    return (m * 0x00204081u) >> 28;
+}
+
 __global__ void k_level_bits(const uint8_t *__restrict__ lab, int64_t S, int64_t W,
                              const int32_t *__restrict__ catrow, const int32_t *__restrict__ levoff,
                              const int32_t *__restrict__ nlev, const uint32_t *__restrict__ obsv,
                              uint32_t *__restrict__ levbits, int32_t *__restrict__ levcnt, int i_base) {
     const int i = blockIdx.y + i_base;
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
-    if (w0 >= W) return;
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = nlev[i], off = levoff[i];
     const uint8_t *la = lab + (int64_t)catrow[i] * S;
-    int cnt = 0;                       // lane g accumulates level g (levels <= 64: two passes)
-    int cnt2 = 0;
-    const int64_t w1 = w0 + 32 < W ? w0 + 32 : W;
-    for (int64_t w = w0; w < w1; ++w) {
-        const int64_t s = w * 32 + lane;
-        const uint32_t ob = obsv[(int64_t)i * W + w];
-        const int l = (s < S) ? (int)la[s] : (int)kMissingLabel;
-        for (int g = 0; g < c; ++g) {
-            const uint32_t b = __ballot_sync(0xffffffffu, l == g) & ob;
-            if (lane == (g & 31)) {
-                levbits[(int64_t)(off + g) * W + w] = b;
-                if (g < 32) cnt += __popc(b); else cnt2 += __popc(b);
+    uint32_t L[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) L[k] = 0xffffffffu;   // missing labels past the end
+    uint32_t ob = 0;
+    if (w < W) {
+        ob = obsv[(int64_t)i * W + w];
+        const int64_t s0 = w * 32;
+        if (s0 + 32 <= S && (((uintptr_t)(la + s0)) & 3u) == 0) {
+            const uint32_t *l4 = reinterpret_cast<const uint32_t *>(la + s0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) L[k] = l4[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                uint32_t v = 0;
+                for (int b = 0; b < 4; ++b) {
+                    const int64_t s = s0 + 4 * k + b;
+                    v |= (uint32_t)(s < S ? la[s] : kMissingLabel) << (8 * b);
+                }
+                L[k] = v;
             }
         }
     }
-    if (lane < c && cnt) atomicAdd(&levcnt[off + lane], cnt);
-    if (lane + 32 < c && cnt2) atomicAdd(&levcnt[off + lane + 32], cnt2);
+    for (int g = 0; g < c; ++g) {
+        const uint32_t g4 = 0x01010101u * (uint32_t)g;
+        uint32_t bits = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) bits |= bits_eq4(L[k], g4) << (4 * k);
+        bits &= ob;
+        if (w < W) levbits[(int64_t)(off + g) * W + w] = bits;
+        int cnt = __popc(bits);
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&levcnt[off + g], cnt);
+    }
 }
 
 void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *catrow_dev,
@@ -220,7 +249,7 @@ void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *
                        const uint32_t *obsv, uint32_t *levbits, int32_t *levcnt, cudaStream_t st) {
     if (nv == 0 || W == 0) return;
     for (int i0 = 0; i0 < nv; i0 += 65535) {        // grid.y limit
-        dim3 grid((unsigned)((W + 8 * 32 - 1) / (8 * 32)), (unsigned)std::min(65535, nv - i0));
+        dim3 grid((unsigned)((W + 255) / 256), (unsigned)std::min(65535, nv - i0));
         count_launch();
         k_level_bits<<<grid, 256, 0, st>>>(lab, S, W, catrow_dev, levoff_dev, nlev_dev, obsv, levbits, levcnt, i0);
     }

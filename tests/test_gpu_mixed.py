@@ -71,6 +71,22 @@ def test_mixed_pearson_context_and_ragged(napg):
     c.close()
 
 
+@pytest.mark.parametrize("dtype,S", [(np.float32, 60_000 + 17), (np.float64, 30_000 + 9)])
+def test_mixed_rows_beyond_shared_memory(napg, dtype, S):
+    """Rows too long to stage in shared memory (FP32 above ~56,000 samples, FP64
+    above ~28,000): the plane builder reads them from the cohort, with unaligned
+    row starts (S not a multiple of 4)."""
+    coh = synth.small_cohort(209, n_cont=24, n_cat=6, S=S, miss=0.3, lev_lo=2, lev_hi=5, dtype=dtype, offset=50.0)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    cats, conts = coh["cat"], coh["cont"]
+    compare("pearson", c.run("pearson", conts, out="numpy", precision="mixed"), oracle_run("pearson", coh, conts),
+            stat_tol=("abs", 1e-6))
+    compare("anova", c.run("anova", cats, conts, out="numpy", precision="mixed"),
+            oracle_run("anova", coh, cats, conts), stat_tol=("effect", 1e-6))
+    c.close()
+
+
 @pytest.mark.parametrize("welch", [True, False])
 def test_mixed_anova_ttest(napg, welch):
     coh = synth.small_cohort(203, n_cont=150, n_cat=40, S=2500 + 11, miss=0.2, lev_lo=2, lev_hi=9, binary_cats=12,
