@@ -731,16 +731,22 @@ __global__ void __launch_bounds__(1024) k_planes_cont(const T *__restrict__ X, i
     }
 }
 
-// one-hot level rows from the level bitmasks (zero padding rows/columns)
+// one-hot level rows from the level bitmasks (zero padding rows/columns): a
+// thread writes eight samples (one 16-byte store) from one byte of a bit word
 __global__ void k_planes_onehot(const uint32_t *__restrict__ levbits, int64_t W, int32_t R, int64_t S_pad,
                                 __half *H) {
     const int r = blockIdx.x;
-    const __half one = __float2half(1.f), z = __float2half(0.f);
-    const int64_t base = (int64_t)r * S_pad;
-    for (int64_t s = threadIdx.x; s < S_pad; s += blockDim.x) {
-        const int64_t w = s >> 5;
-        const bool b = r < R && w < W && ((levbits[(int64_t)r * W + w] >> (s & 31)) & 1u);
-        H[base + s] = b ? one : z;
+    uint4 *h8 = reinterpret_cast<uint4 *>(H + (int64_t)r * S_pad);   // S_pad is a multiple of 64
+    const int64_t n8 = S_pad / 8;
+    for (int64_t q = threadIdx.x; q < n8; q += blockDim.x) {
+        const int64_t s0 = 8 * q, w = s0 >> 5;
+        const uint32_t b = (r < R && w < W) ? (levbits[(int64_t)r * W + w] >> (s0 & 31)) & 0xffu : 0u;
+        // FP16 1.0 is 0x3c00; two samples per 32-bit word
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            v[k] = ((b >> (2 * k)) & 1u) * 0x3c00u | (((b >> (2 * k + 1)) & 1u) * 0x3c00u) << 16;
+        h8[q] = make_uint4(v[0], v[1], v[2], v[3]);
     }
 }
 

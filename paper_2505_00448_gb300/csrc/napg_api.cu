@@ -639,7 +639,30 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
     NAPG_CU(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     NAPG_CU(ctx, cudaStreamSynchronize(st));
+    // the previous cohort's value, bit and label buffers are kept for this one
+    // when large enough (no free and allocation per load); nothing uses them now
+    struct Kept { void *p = nullptr; size_t cap = 0; } kx, kobs, klab;
+    if (ctx->coh.owns) {
+        kx = {ctx->coh.X, ctx->coh.x_bytes};
+        kobs = {ctx->coh.obs, ctx->coh.obs_bytes};
+        klab = {ctx->coh.lab, ctx->coh.lab_bytes};
+        ctx->coh.X = nullptr; ctx->coh.obs = nullptr; ctx->coh.lab = nullptr;
+    }
     free_cohort(ctx->coh);
+    auto take = [](Kept &k, size_t need, void **out, size_t *cap) -> cudaError_t {
+        if (k.p && k.cap >= need) {
+            *out = k.p;
+            *cap = k.cap;
+            k.p = nullptr;
+            return cudaSuccess;
+        }
+        *cap = need;
+        return cudaMalloc(out, need);
+    };
+    auto drop_kept = [&]() {
+        for (Kept *k : {&kx, &kobs, &klab})
+            if (k->p) { cudaFree(k->p); k->p = nullptr; }
+    };
     Cohort &c = ctx->coh;
     c.F = n_vars;
     c.S = n_samples;
@@ -660,7 +683,18 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
     }
     const size_t esz = dtype == NAPG_F32 ? 4 : 8;
     const size_t xbytes = esz * (size_t)n_vars * (size_t)n_samples;
-    NAPG_CU(ctx, cudaMalloc(&c.X, xbytes));
+    {
+        const size_t obs_need = sizeof(uint32_t) * (size_t)n_vars * c.W;
+        const size_t lab_need = std::max<size_t>(1, (size_t)c.n_cat * (size_t)n_samples);
+        cudaError_t e1 = take(kx, xbytes, &c.X, &c.x_bytes);
+        cudaError_t e2 = e1 == cudaSuccess ? take(kobs, obs_need, (void **)&c.obs, &c.obs_bytes) : e1;
+        cudaError_t e3 = e2 == cudaSuccess ? take(klab, lab_need, (void **)&c.lab, &c.lab_bytes) : e2;
+        drop_kept();
+        if (e3 != cudaSuccess) {
+            free_cohort(ctx->coh);
+            return cuda_fail(ctx, e3, "cohort allocation");
+        }
+    }
     const bool on_dev = is_device_ptr(X);
     if (!samples_major) {
         NAPG_CU(ctx, cudaMemcpyAsync(c.X, X, xbytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -673,8 +707,6 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
         NAPG_CU(ctx, cudaStreamSynchronize(st));
         cudaFree(tmp);
     }
-    NAPG_CU(ctx, cudaMalloc(&c.obs, sizeof(uint32_t) * (size_t)n_vars * c.W));
-    NAPG_CU(ctx, cudaMalloc(&c.lab, std::max<size_t>(1, (size_t)c.n_cat * (size_t)n_samples)));
     // per-variable tables for the validation kernel
     std::vector<int32_t> tab(2 * n_vars);
     for (int64_t v = 0; v < n_vars; ++v) { tab[v] = c.nlev[v]; tab[n_vars + v] = c.cat_index[v]; }

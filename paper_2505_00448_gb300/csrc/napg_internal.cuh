@@ -49,6 +49,7 @@ struct Cohort {
     int64_t presort_cap = 0;             // samples the presort arrays hold (per variable)
     int32_t *cont_vars_dev = nullptr;    // the continuous variable ids (device), for the presort
     bool owns = true;                    // false: arrays borrowed (freed by their owner)
+    size_t x_bytes = 0, obs_bytes = 0, lab_bytes = 0;   // allocated sizes (napg_load_cohort reuses them)
 };
 
 // Grow-only named device buffers; a run asks for capacity and gets a pointer.

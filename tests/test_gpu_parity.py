@@ -300,6 +300,21 @@ def test_mwu_exact_mode(napg):
 
 # -------------------------------------------------------------- errors --
 
+def test_reloading_cohorts_reuses_buffers(napg):
+    """One context, cohorts loaded one after another (smaller, then larger than
+    the buffers it keeps, FP64 then FP32): every result matches the oracle."""
+    c = napg.Context(0)
+    for seed, nc, nk, S, dt in ((150, 30, 6, 2000 + 3, np.float64), (151, 12, 3, 700 + 1, np.float32),
+                                (152, 40, 8, 3000 + 9, np.float32)):
+        coh = synth.small_cohort(seed, n_cont=nc, n_cat=nk, S=S, miss=0.25, lev_lo=2, lev_hi=5, dtype=dt)
+        c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+        cats, conts = coh["cat"], coh["cont"]
+        compare("pearson", c.run("pearson", conts, out="numpy"), oracle_run("pearson", coh, conts))
+        compare("kruskal", c.run("kruskal", cats, conts, out="numpy"), oracle_run("kruskal", coh, cats, conts))
+        compare("chi2", c.run("chi2", cats, out="numpy"), oracle_run("chi2", coh, cats))
+    c.close()
+
+
 def test_invalid_inputs_are_errors(napg):
     c = napg.Context(0)
     X = np.array([[0, 1, 3.0], [1.0, 2.0, 3.0]])
