@@ -400,7 +400,7 @@ def serve_requests(coh, rng, count):
 
 
 def serve_main(args, world, rank, local_rank):
-    """Request loop on the resident config-5 cohort; one replica per GPU."""
+    """Request loop on the resident serving cohort; one replica per GPU."""
     import torch
     dist = None
     if world > 1:

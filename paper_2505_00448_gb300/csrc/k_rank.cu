@@ -492,7 +492,7 @@ __host__ __device__ constexpr size_t rank_group_table_bytes(int nwarp) {
 }
 
 template <int CMAX, bool SLAB>
-__global__ void __launch_bounds__(1024, 2) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
+__global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
                                                      const int32_t *__restrict__ catrow_a, const int32_t *__restrict__ nlev_a,
                                                      const int32_t *__restrict__ levoff_a, int32_t na,
                                                      const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,

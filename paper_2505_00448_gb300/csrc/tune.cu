@@ -1,9 +1,11 @@
 // Autotuner: picks a launch shape per problem shape by timing the candidates
 // once (CUDA events on the run's own stream) and keeping the fastest for the
 // rest of the context's life. Candidates of one kind give identical results,
-// so the tuning run's outputs stand. While a stream is being captured into a
-// graph nothing can be timed: the choice recorded for the closest shape (same
-// kind and rows, nearest K) is used, else the first candidate.
+// so the tuning run's outputs stand. A shape near a recorded one (same kind, K
+// within 10%, rows within a factor of 4) takes its choice without timing.
+// While a stream is being captured into a graph nothing can be timed: the
+// choice recorded for the closest shape (same kind and rows, nearest K) is
+// used, else the first candidate.
 #include <cstdio>
 #include <cmath>
 
@@ -35,6 +37,7 @@ napg_status tuned_launch(napg_ctx *ctx, const TuneKey &key, int ncand, const std
     {
         std::lock_guard<std::mutex> lk(T.mu);
         auto it = T.best.find(key);
+        auto ld = [](int64_t x, int64_t y) { return std::fabs(std::log((double)(x + 1) / (double)(y + 1))); };
         if (it != T.best.end()) {
             choice = it->second.choice;
         } else if (cs != cudaStreamCaptureStatusNone || !T.on || ncand < 2) {
@@ -42,10 +45,22 @@ napg_status tuned_launch(napg_ctx *ctx, const TuneKey &key, int ncand, const std
             double bestd = 1e300;
             for (auto &kv : T.best)
                 if (kv.first.kind == key.kind && kv.first.a == key.a && kv.first.b == key.b) {
-                    const double d = std::fabs(std::log((double)(kv.first.c + 1) / (double)(key.c + 1)));
+                    const double d = ld(kv.first.c, key.c);
                     if (d < bestd) { bestd = d; choice = kv.second.choice; }
                 }
             if (choice < 0) choice = 0;
+        } else {
+            // a recorded shape of the same kind close to this one (K within 10%,
+            // rows within a factor of 4) decides without timing: a stream of
+            // requests of varied sizes (the serving loop) times a few size
+            // classes, not every request
+            double bestd = 1e300;
+            for (auto &kv : T.best)
+                if (kv.first.kind == key.kind && ld(kv.first.c, key.c) <= 0.1 && ld(kv.first.a, key.a) <= std::log(4.0) &&
+                    ld(kv.first.b, key.b) <= std::log(4.0)) {
+                    const double d = ld(kv.first.a, key.a) + ld(kv.first.b, key.b) + ld(kv.first.c, key.c);
+                    if (d < bestd) { bestd = d; choice = kv.second.choice; }
+                }
         }
     }
     if (choice >= 0) return run(choice);

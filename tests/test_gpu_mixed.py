@@ -204,3 +204,26 @@ def test_autotuner_keeps_results_identical(napg):
         for t in outs[0]:
             for k in ("stat", "p", "n"):
                 assert np.array_equal(outs[0][t][k], r[t][k], equal_nan=True), (t, k)
+
+
+def test_autotuner_near_shapes_reuse_choice(napg):
+    """A shape within a factor of 4 in rows of a recorded one (same K) takes the
+    recorded choice without timing; a far shape is timed; results are those of
+    the untuned run."""
+    coh = synth.small_cohort(208, n_cont=200, n_cat=0, S=4000 + 7, miss=0.2, dtype=np.float32, ties=True)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    ref = napg.Context(0)
+    ref.tune(False)
+    ref.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    cont = coh["cont"]
+    for k, expect in ((100, 1), (130, 1), (60, 1), (20, 2)):
+        g = c.run("spearman", cont[:k], out="numpy")
+        r = ref.run("spearman", cont[:k], out="numpy")
+        for f in ("stat", "p", "n"):
+            assert np.array_equal(g[f], r[f], equal_nan=True)
+        recs = [x for x in c.tune_read() if x["kind"] == "spearman_threads"]
+        assert len(recs) == expect, (k, recs)
+    c.close()
+    ref.close()
+
