@@ -2,7 +2,8 @@
 // once (CUDA events on the run's own stream) and keeping the fastest for the
 // rest of the context's life. Candidates of one kind give identical results,
 // so the tuning run's outputs stand. A shape near a recorded one (same kind, K
-// within 10%, rows within a factor of 4) takes its choice without timing.
+// within a factor of 2, rows within a factor of 4) takes its choice without
+// timing.
 // While a stream is being captured into a graph nothing can be timed: the
 // choice recorded for the closest shape (same kind and rows, nearest K) is
 // used, else the first candidate.
@@ -50,14 +51,14 @@ napg_status tuned_launch(napg_ctx *ctx, const TuneKey &key, int ncand, const std
                 }
             if (choice < 0) choice = 0;
         } else {
-            // a recorded shape of the same kind close to this one (K within 10%,
-            // rows within a factor of 4) decides without timing: a stream of
-            // requests of varied sizes (the serving loop) times a few size
-            // classes, not every request
+            // a recorded shape of the same kind close to this one (K within a
+            // factor of 2, rows within a factor of 4) decides without timing: a
+            // stream of requests or sample contexts of varied sizes times a few
+            // size classes, not every one
             double bestd = 1e300;
             for (auto &kv : T.best)
-                if (kv.first.kind == key.kind && ld(kv.first.c, key.c) <= 0.1 && ld(kv.first.a, key.a) <= std::log(4.0) &&
-                    ld(kv.first.b, key.b) <= std::log(4.0)) {
+                if (kv.first.kind == key.kind && ld(kv.first.c, key.c) <= std::log(2.0) &&
+                    ld(kv.first.a, key.a) <= std::log(4.0) && ld(kv.first.b, key.b) <= std::log(4.0)) {
                     const double d = ld(kv.first.a, key.a) + ld(kv.first.b, key.b) + ld(kv.first.c, key.c);
                     if (d < bestd) { bestd = d; choice = kv.second.choice; }
                 }
