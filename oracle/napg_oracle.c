@@ -916,6 +916,152 @@ int64_t orc_pair_ints(int test, const double *X, int64_t F, int64_t S, double mi
     return m;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Effect sizes (Table 2)                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* One pair's effect sizes, from the test's own statistic on the co-observed
+ * samples (NaN wherever that statistic is NaN):
+ *   Pearson: e1 = r^2.  Spearman: e1 = rho.
+ *   chi-squared: e1 = phi = sqrt(chi2 / n); e2 = Cramer's V =
+ *     sqrt(chi2 / (n (min(k_a, k_b) - 1))) over the present levels, NaN when a
+ *     variable has a single level (Sec. 3.5.4).
+ *   t-test: e1 = Cohen's d = (mean_0 - mean_1) / s, s the pooled SD (Student)
+ *     or sqrt((v_0 + v_1) / 2) (Welch); NaN when s = 0 (Sec. 3.5.5).
+ *   Mann-Whitney: e1 = Pearson's r = |z| / sqrt(n), z = (U_0 - n_0 n_1 / 2) / sigma
+ *     with the tie-corrected sigma and no continuity correction; NaN when sigma = 0.
+ *   ANOVA: e1 = partial eta^2 = SSB / (SSB + SSW) (one-way: the same as eta^2);
+ *     1 when every group is constant and the groups differ (F = inf).
+ *   Kruskal-Wallis: e1 = eta^2 = (H - k + 1) / (n - k); NaN when n <= k (Sec. 3.5.8).
+ * e2 is NaN except for chi-squared. */
+static void effect_pair(const orc_cohort *c, int test, int64_t a, int64_t b, orc_scratch *w,
+                        double *e1, double *e2) {
+    double st, pv;
+    int32_t nn;
+    *e1 = NAN;
+    *e2 = NAN;
+    pick(test)(c, a, b, w, &st, &pv, &nn);
+    if (isnan(st)) return;
+    const double n = (double)nn;
+    switch (test) {
+    case ORC_PEARSON:
+        *e1 = st * st;
+        return;
+    case ORC_SPEARMAN:
+        *e1 = st;
+        return;
+    case ORC_CHI2: {
+        int pa[ORC_MAXLEV], pb[ORC_MAXLEV];
+        int ka = present_levels(c, a, pa), kb = present_levels(c, b, pb);
+        int m = (ka < kb ? ka : kb) - 1;
+        *e1 = sqrt(st / n);
+        if (m >= 1) *e2 = sqrt(st / (n * (double)m));
+        return;
+    }
+    case ORC_TTEST: {
+        int64_t cnt = gather_pair(c, a, b, w->x, w->y);
+        double s0 = 0.0, s1 = 0.0;
+        int64_t n0 = 0, n1 = 0;
+        for (int64_t q = 0; q < cnt; ++q) {
+            if (w->x[q] == 0.0) { s0 += w->y[q]; ++n0; } else { s1 += w->y[q]; ++n1; }
+        }
+        const double m0 = s0 / (double)n0, m1 = s1 / (double)n1;
+        double q0 = 0.0, q1 = 0.0;
+        for (int64_t q = 0; q < cnt; ++q) {
+            if (w->x[q] == 0.0) q0 += (w->y[q] - m0) * (w->y[q] - m0);
+            else q1 += (w->y[q] - m1) * (w->y[q] - m1);
+        }
+        const double v0 = q0 / (double)(n0 - 1), v1 = q1 / (double)(n1 - 1);
+        const double s2 = c->welch ? 0.5 * (v0 + v1) : (q0 + q1) / (double)(n0 + n1 - 2);
+        if (s2 > 0.0) *e1 = (m0 - m1) / sqrt(s2);
+        return;
+    }
+    case ORC_MWU: {
+        int64_t cnt = gather_pair(c, a, b, w->x, w->y);
+        int64_t n0 = 0, n1 = 0, T = 0;
+        for (int64_t q = 0; q < cnt; ++q) { if (w->x[q] == 0.0) ++n0; else ++n1; }
+        doubled_ranks(w->y, cnt, w->r2, w->buf, &T);
+        double R0 = 0.0;
+        for (int64_t q = 0; q < cnt; ++q) if (w->x[q] == 0.0) R0 += 0.5 * (double)w->r2[q];
+        const double U0 = R0 - 0.5 * (double)n0 * (double)(n0 + 1);
+        const double var = (double)n0 * (double)n1 / 12.0 * ((n + 1.0) - (double)T / (n * (n - 1.0)));
+        if (var > 0.0) *e1 = fabs((U0 - 0.5 * (double)n0 * (double)n1) / sqrt(var)) / sqrt(n);
+        return;
+    }
+    case ORC_ANOVA: {
+        if (isinf(st)) { *e1 = 1.0; return; }
+        int present[ORC_MAXLEV], k, empty;
+        int64_t ng[ORC_MAXLEV];
+        int64_t cnt = group_pair(c, a, b, w, present, &k, ng, &empty);
+        int L = c->nlev[a];
+        double gm = 0.0, sum[ORC_MAXLEV];
+        for (int g = 0; g < L; ++g) sum[g] = 0.0;
+        for (int64_t q = 0; q < cnt; ++q) gm += w->y[q];
+        gm /= (double)cnt;
+        for (int64_t q = 0; q < cnt; ++q) sum[(int)w->x[q]] += w->y[q] - gm;
+        double ssb = 0.0, ssw = 0.0;
+        for (int g = 0; g < L; ++g)
+            if (present[g]) ssb += sum[g] * sum[g] / (double)ng[g];
+        for (int64_t q = 0; q < cnt; ++q) {
+            const int g = (int)w->x[q];
+            const double d = (w->y[q] - gm) - sum[g] / (double)ng[g];
+            ssw += d * d;
+        }
+        if (ssb + ssw > 0.0) *e1 = ssb / (ssb + ssw);
+        return;
+    }
+    case ORC_KRUSKAL: {
+        int present[ORC_MAXLEV];
+        int k = present_levels(c, a, present);
+        if (n > (double)k) *e1 = (st - (double)k + 1.0) / (n - (double)k);
+        return;
+    }
+    default:
+        return;
+    }
+}
+
+/* Effect sizes of all pairs, laid out as orc_run's outputs. */
+int orc_effects(int test, const double *X, int64_t F, int64_t S, double miss,
+                const uint8_t *vtype, const int32_t *nlev, const uint8_t *ctx,
+                const int32_t *va, int32_t na, const int32_t *vb, int32_t nb,
+                int welch, int yates, double *e1, double *e2, int nthreads) {
+    orc_cohort c = { X, F, S, miss, vtype, nlev, ctx, welch, yates, 2, 1 };
+    if (!pick(test) || na < 0 || nb < 0) return ORC_E_ARG;
+    int rc = check_vars(&c, test, va, na, vb, nb);
+    if (rc) return rc;
+    rc = orc_validate(X, F, S, miss, vtype, nlev);
+    if (rc) return rc;
+    const int32_t *cols = vb ? vb : va;
+    int64_t ncols = vb ? nb : na;
+    int64_t total = (int64_t)na * ncols;
+    int err = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        orc_scratch w;
+        int ok = alloc_scratch(&w, S) == ORC_OK;
+        if (!ok) {
+#pragma omp atomic write
+            err = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < total; ++q) {
+            if (!ok) continue;
+            double x1, x2;
+            effect_pair(&c, test, va[q / ncols], cols[q % ncols], &w, &x1, &x2);
+            if (e1) e1[q] = x1;
+            if (e2) e2[q] = x2;
+        }
+        free_scratch(&w);
+    }
+    return err ? ORC_E_OOM : ORC_OK;
+}
+
 int orc_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -78,6 +78,9 @@ def lib():
             L.orc_pair_ints.argtypes = [C.c_int, p, i64, i64, d, p, p, p, i32, i32, p, i64]
             L.orc_max_threads.restype = C.c_int
             L.orc_max_threads.argtypes = []
+            L.orc_effects.restype = C.c_int
+            L.orc_effects.argtypes = [C.c_int, p, i64, i64, d, p, p, p, p, i32, p, i32, C.c_int, C.c_int,
+                                      p, p, C.c_int]
             _lib = L
     return _lib
 
@@ -147,6 +150,86 @@ def run_pairs(test, X, missing, vtype, nlev, pairs_a, pairs_b, ctx=None, welch=1
     if rc:
         raise OracleError(rc)
     return stat, pval, nout
+
+
+def effects(test, X, missing, vtype, nlev, vars_a, vars_b=None, ctx=None, welch=1, yates=0, nthreads=0):
+    """Effect sizes of all pairs (Table 2), laid out as run()'s outputs.
+
+    Returns (e1, e2): r^2, rho, phi, Cohen's d, Mann-Whitney r, partial eta^2 or
+    Kruskal-Wallis eta^2 in e1; Cramer's V (chi-squared only, else NaN) in e2.
+    """
+    if isinstance(test, str):
+        test = TEST_NAMES[test]
+    X, F, S, vtype, nlev, ctx = _cohort_arrays(X, vtype, nlev, ctx)
+    va = np.ascontiguousarray(vars_a, dtype=np.int32)
+    vb = None if vars_b is None else np.ascontiguousarray(vars_b, dtype=np.int32)
+    nb = len(va) if vb is None else len(vb)
+    e1 = np.empty((len(va), nb), np.float64)
+    e2 = np.empty((len(va), nb), np.float64)
+    rc = lib().orc_effects(test, _ptr(X), F, S, float(missing), _ptr(vtype), _ptr(nlev), _ptr(ctx),
+                           _ptr(va), len(va), _ptr(vb), 0 if vb is None else len(vb), welch, yates,
+                           _ptr(e1), _ptr(e2), nthreads)
+    if rc:
+        raise OracleError(rc)
+    return e1, e2
+
+
+ADJUST_METHODS = ("bonferroni", "bh", "by")
+
+
+def adjust(p, method, symmetric):
+    """Multiple-testing correction of a p-value matrix (Sec. 3.4).
+
+    The tests are the entries with a p-value (not NaN); in a symmetric matrix
+    (one variable set against itself) each unordered pair i < j is one test and
+    the diagonal is no test (NaN in the result). With m tests and p_(1) <= ... <=
+    p_(m) in ascending order:
+      Bonferroni:         min(1, m p)
+      Benjamini-Hochberg: p_adj_(i) = min over k >= i of (m p_(k)) / k, capped at 1
+      Benjamini-Yekutieli: the same with m replaced by m c(m), c(m) = sum_{k<=m} 1/k
+    (c(m) summed in increasing k). Tied p-values get equal adjusted values.
+    """
+    P = np.array(p, dtype=np.float64)
+    out = np.full(P.shape, np.nan)
+    if symmetric:
+        assert P.shape[0] == P.shape[1]
+        iu = np.triu_indices(P.shape[0], 1)
+        vals = P[iu]
+    else:
+        vals = P.ravel()
+    valid = ~np.isnan(vals)
+    idx = np.nonzero(valid)[0]
+    v = vals[idx]
+    m = len(v)
+    adj = np.full(len(vals), np.nan)
+    if m:
+        if method == "bonferroni":
+            a = np.minimum(1.0, v * float(m))
+        else:
+            scale = float(m)
+            if method == "by":
+                cm = 0.0
+                for k in range(1, m + 1):
+                    cm += 1.0 / k
+                scale = float(m) * cm
+            elif method != "bh":
+                raise ValueError(method)
+            order = np.argsort(v, kind="stable")
+            srt = v[order]
+            a_sorted = np.empty(m)
+            run = np.inf
+            for i in range(m - 1, -1, -1):           # from the largest p down
+                run = min(run, (srt[i] * scale) / float(i + 1))
+                a_sorted[i] = run
+            a = np.empty(m)
+            a[order] = np.minimum(1.0, a_sorted)
+        adj[idx] = a
+    if symmetric:
+        out[iu] = adj
+        out.T[iu] = adj
+    else:
+        out = adj.reshape(P.shape)
+    return out
 
 
 def pair_ints(test, X, missing, vtype, nlev, a, b, ctx=None):

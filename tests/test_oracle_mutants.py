@@ -12,7 +12,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "napg_oracle.c")
-PINS = ["tests/test_oracle_special.py", "tests/test_oracle_stats.py"]
+PINS = ["tests/test_oracle_special.py", "tests/test_oracle_stats.py", "tests/test_oracle_effects.py"]
 
 MUTANTS = {
     "pearson_uncentred_y": ("double dv = v[k] - mv, dw = w[k] - mw;", "double dv = v[k] - mv, dw = w[k];"),
@@ -32,6 +32,13 @@ MUTANTS = {
     "context_ignored": ("if (c->ctx && !c->ctx[s]) return 0;", ""),
     "anova_uncentred": ("{ double d = w->y[q] - gm; dsum[(int)w->x[q]] += d; dgm += d; }",
                         "{ double d = w->y[q]; dsum[(int)w->x[q]] += d; dgm += d; }"),
+    "cramer_v_max_levels": ("int m = (ka < kb ? ka : kb) - 1;", "int m = (ka > kb ? ka : kb) - 1;"),
+    "cohen_d_welch_pooled": ("const double s2 = c->welch ? 0.5 * (v0 + v1) : (q0 + q1) / (double)(n0 + n1 - 2);",
+                             "const double s2 = (q0 + q1) / (double)(n0 + n1 - 2);"),
+    "mwu_r_uncorrected_ties": ("((n + 1.0) - (double)T / (n * (n - 1.0)));\n        if (var > 0.0) *e1",
+                               "((n + 1.0));\n        if (var > 0.0) *e1"),
+    "kruskal_eta_k_off_by_one": ("*e1 = (st - (double)k + 1.0) / (n - (double)k);",
+                                 "*e1 = (st - (double)k) / (n - (double)k);"),
     "ttest_uncentred": ("double gm = (s0 + s1) / (double)n, d0 = 0.0, d1 = 0.0;",
                         "double gm = 0.0, d0 = 0.0, d1 = 0.0;"),
 }
