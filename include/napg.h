@@ -150,6 +150,43 @@ napg_status napg_run(napg_ctx *ctx, int32_t test, const napg_options *opt,
                      const int32_t *vars_b, int32_t n_b, double *stat, double *pval,
                      int32_t *n);
 
+/* napg_run with the effect sizes of Table 2 as two more outputs (n_a x n_b
+ * doubles, row-major, host or device; either may be NULL):
+ *   effect   PEARSON r^2; SPEARMAN rho; CHI2 phi = sqrt(chi2 / n); TTEST Cohen's d
+ *            (mean_0 - mean_1 over the pooled SD for Student, over
+ *            sqrt((v_0 + v_1) / 2) for Welch); MWU Pearson's r = |z| / sqrt(n)
+ *            (z tie-corrected, no continuity correction); ANOVA partial eta^2 =
+ *            SSB / (SSB + SSW); KRUSKAL eta^2 = (H - k + 1) / (n - k).
+ *   effect2  CHI2 Cramer's V = sqrt(chi2 / (n (min(k_a, k_b) - 1))) over the levels
+ *            present in the context; NaN for the other tests.
+ * Each is NaN where the statistic is NaN, and where the paper makes it
+ * undefined (Sec. 3.5.4, 3.5.5, 3.5.8): V with a single level, Welch's d when
+ * both groups are constant, Kruskal-Wallis eta^2 when n <= k.
+ * Errors: as napg_run. */
+napg_status napg_run_ex(napg_ctx *ctx, int32_t test, const napg_options *opt,
+                        const uint8_t *sample_mask, const int32_t *vars_a, int32_t n_a,
+                        const int32_t *vars_b, int32_t n_b, double *stat, double *pval,
+                        int32_t *n, double *effect, double *effect2);
+
+/* Multiple-testing correction (Sec. 3.4). */
+typedef enum { NAPG_ADJ_BONFERRONI = 0, NAPG_ADJ_BH = 1, NAPG_ADJ_BY = 2 } napg_adjust_method;
+
+/* Adjusts a rows x cols p-value matrix (row-major doubles, host or device) into
+ * out (same shape, host or device; may equal p only when both are on the
+ * device). The tests are the entries with a p-value (not NaN); with symmetric != 0
+ * (rows == cols, one variable set against itself) each unordered pair i < j is
+ * one test, both triangles of out get its adjusted value and the diagonal is
+ * NaN (a variable against itself is no test). With m tests and ascending
+ * p_(1) <= ... <= p_(m):
+ *   NAPG_ADJ_BONFERRONI  min(1, m p)
+ *   NAPG_ADJ_BH          Benjamini-Hochberg: min over k >= i of p_(k) m / k, capped at 1
+ *   NAPG_ADJ_BY          Benjamini-Yekutieli: as BH with m c(m), c(m) = sum_{k <= m} 1/k
+ * Entries without a p-value stay NaN. Runs on the context's stream; synchronous.
+ * Errors: NAPG_E_ARG (unknown method, rows != cols for symmetric, NULL pointer),
+ * NAPG_E_OOM, NAPG_E_CUDA. */
+napg_status napg_adjust(napg_ctx *ctx, int32_t method, const double *p, int64_t rows, int64_t cols,
+                        int32_t symmetric, double *out);
+
 /* Runs one test for n_ctx sample contexts with the same variable sets
  * (Sec. 1: per-context association networks). sample_masks[k] is a context mask
  * as in napg_run (host or device); stat[k], pval[k], n[k] are n_a x n_b outputs

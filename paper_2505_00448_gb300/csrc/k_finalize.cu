@@ -119,7 +119,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 if (ng == 0) empty = true;
             }
         }
-        double s = dnan(), p = dnan();
+        double s = dnan(), p = dnan(), es = dnan();
         if (f.test == NAPG_ANOVA) {
             if (!empty && k >= 2 && n - k >= 1) {
                 double s1 = 0.0, raw = 0.0;
@@ -168,15 +168,19 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     s = (m0 - m1) / sqrt(se2);
                     const double nu = se2 * se2 / (e0 * e0 / (double)(n0 - 1) + e1 * e1 / (double)(n1 - 1));
                     if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, nu, 0.0, t, kPjT, 0});
+                    // Cohen's d over the mean of the two variances
+                    es = (m0 - m1) / sqrt(0.5 * (q0 / (double)(n0 - 1) + q1 / (double)(n1 - 1)));
                 } else {
                     const double df = (double)(n - 2);
                     const double sp2 = (q0 + q1) / df;
                     s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
                     if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, df, 0.0, t, kPjT, 0});
+                    es = (m0 - m1) / sqrt(sp2);      // Cohen's d over the pooled SD
                 }
             }
         }
         put(stat, pval, nout, t, s, p, (int32_t)n);
+        if (f.es) f.es[t] = es;
     }
 }
 
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
         const int ia = (int)(t / ncols), ib = (int)(t - (int64_t)ia * ncols);
         const int va = r.va[ia], vb = symmetric ? r.va[ib] : r.vb[ib];
         const uint32_t *oa = r.obs + (int64_t)va * r.W, *ob = r.obs + (int64_t)vb * r.W;
-        double s = dnan(), p = dnan();
+        double s = dnan(), p = dnan(), es = dnan();
         if (r.test == NAPG_PEARSON) {
             double n = 0, sx = 0, sy = 0, mnx = inf, mxx = -inf, mny = inf, mxy = -inf;
             for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
@@ -676,8 +680,10 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                         const double sp2 = (ss[0] + ss[1]) / df;
                         s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
                         p = sf::t_two_sided(s, df);
+                        es = (m0 - m1) / sqrt(sp2);
                     }
                 } else if (cst[0] && cst[1]) {
+                    // Cohen's d undefined: the two variances sum to zero
                     if (mn[0] != mn[1]) { s = mn[0] > mn[1] ? inf : -inf; p = 0.0; }
                 } else {
                     const double e0 = ss[0] / (n0 - 1.0) / n0, e1 = ss[1] / (n1 - 1.0) / n1;
@@ -685,9 +691,11 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                     s = (m0 - m1) / sqrt(se2);
                     const double nu = se2 * se2 / (e0 * e0 / (n0 - 1.0) + e1 * e1 / (n1 - 1.0));
                     p = sf::t_two_sided(s, nu);
+                    es = (m0 - m1) / sqrt(0.5 * (ss[0] / (n0 - 1.0) + ss[1] / (n1 - 1.0)));
                 }
             }
             put(stat, pval, nout, t, s, p, (int32_t)n);
+            if (r.es && r.test == NAPG_TTEST) r.es[t] = es;
         }
         __syncthreads();
     }

@@ -303,6 +303,9 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         double *tp = WS(kUnionP, double, (int64_t)nu * nu);
         int32_t *tn = WS(kUnionN, int32_t, (int64_t)nu * nu + 2 * (nu + a.na + a.nb));
         if (st_) return st_;
+        double *te1 = a.es1 ? WS(kUnionE1, double, (int64_t)nu * nu) : nullptr;
+        double *te2 = a.es2 ? WS(kUnionE2, double, (int64_t)nu * nu) : nullptr;
+        if (st_) return st_;
         RunArgs b = a;
         b.va = uniq.data();
         b.na = nu;
@@ -311,6 +314,8 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         b.stat = ts;
         b.pval = tp;
         b.n = tn;
+        b.es1 = te1;
+        b.es2 = te2;
         NAPG_ST(run_on_stream(ctx, ws, st, b));
         int32_t *dia = tn + (int64_t)nu * nu, *dib = dia + a.na;
         NAPG_CU(ctx, cudaMemcpyAsync(dia, ia.data(), sizeof(int32_t) * a.na, cudaMemcpyHostToDevice, st));
@@ -320,6 +325,12 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         k_gather_block<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, st>>>(
             ts, tp, tn, nu, dia, dib, a.na, a.nb, a.stat, a.pval, a.n);
         NAPG_CU(ctx, cudaGetLastError());
+        if (a.es1 || a.es2) {
+            count_launch();
+            k_gather_block<<<(unsigned)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, st>>>(
+                te1, te2, nullptr, nu, dia, dib, a.na, a.nb, a.es1, a.es2, nullptr);
+            NAPG_CU(ctx, cudaGetLastError());
+        }
         NAPG_CU(ctx, cudaStreamSynchronize(st));   // host vectors ia/ib and uniq go out of scope
         return NAPG_OK;
     }
@@ -384,7 +395,10 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
     prep_stage.end();
 
     RescueArgs rsc{c.X, c.dtype, S, W, ctxw, c.obs, c.lab, d_cat, d_va, symmetric ? nullptr : d_vb, na, nb, t,
-                   a.opt.welch, d_nl, levcnt, d_lo};
+                   a.opt.welch, d_nl, levcnt, d_lo, t == NAPG_TTEST ? a.es1 : nullptr};
+    // Mann-Whitney's per-level counts and tie terms, for its effect size
+    const int32_t *eff_rcnt = nullptr;
+    const int64_t *eff_tie = nullptr;
 
     if (t == NAPG_PEARSON) {
         const int64_t nn2 = (int64_t)na * na;
@@ -431,7 +445,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
         GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? kMixedRelTol : kPlainRelTol,
-                   vsq, pj.q, g2tot};
+                   vsq, pj.q, g2tot, t == NAPG_TTEST ? a.es1 : nullptr};
         { Stage s_(ctx->trace, st, "finalize_groups"); launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, maxlev, st); }
@@ -488,6 +502,8 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr && t == NAPG_KRUSKAL, pj));
         RankGroupFin f{rsum, rcnt, tie, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.mwu_mode, a.opt.mwu_continuity, pj.q};
+        eff_rcnt = rcnt;
+        eff_tie = tie;
         { Stage s_(ctx->trace, st, "finalize_rankgroups"); launch_finalize_rankgroups(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         if (t == NAPG_MWU && a.pval) {
@@ -499,6 +515,11 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
             launch_mwu_exact(a.stat, rcnt, d_lo, R, nb, flags, counter, (int32_t)((int64_t)na * nb + 1), a.pval,
                              scratch, sb, st);
         }
+    }
+    if (a.es1 || a.es2) {
+        Stage s_(ctx->trace, st, "effect_sizes");
+        EffectArgs e{t, na, nb, symmetric ? 1 : 0, a.stat, a.n, levcnt, d_lo, d_nl, eff_rcnt, eff_tie, a.es1, a.es2};
+        launch_effects(e, st);
     }
     NAPG_CU(ctx, cudaGetLastError());
     return NAPG_OK;
@@ -512,10 +533,20 @@ napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunA
     int32_t *hn = a.n;
     const bool ds = !hs || is_device_ptr(hs), dp = !hp || is_device_ptr(hp), dn = !hn || is_device_ptr(hn);
     napg_status st_ = NAPG_OK;
+    double *he1 = a.es1, *he2 = a.es2;
+    const bool de1 = !he1 || is_device_ptr(he1), de2 = !he2 || is_device_ptr(he2);
     if (!ds) a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
     if (!dp) a.pval = (double *)ws_get(ctx, ws, Workspace::kOutP, sizeof(double) * cnt, &st_);
     if (!dn) a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_);
+    if (!de1) a.es1 = (double *)ws_get(ctx, ws, Workspace::kOutE1, sizeof(double) * cnt, &st_);
+    if (!de2) a.es2 = (double *)ws_get(ctx, ws, Workspace::kOutE2, sizeof(double) * cnt, &st_);
     if (st_) return st_;
+    // the effect sizes are formed from the statistic and n
+    if (a.es1 || a.es2) {
+        if (!a.stat) { a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_); hs = nullptr; }
+        if (!a.n) { a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_); hn = nullptr; }
+        if (st_) return st_;
+    }
     // exact Mann-Whitney p reads the statistic back: give it a buffer if none
     if (a.test == NAPG_MWU && a.pval && !a.stat) {
         a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
@@ -527,7 +558,9 @@ napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunA
     if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
-    if (!ds || !dp || !dn) {
+    if (!de1) NAPG_CU(ctx, cudaMemcpyAsync(he1, a.es1, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!de2) NAPG_CU(ctx, cudaMemcpyAsync(he2, a.es2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    if (!ds || !dp || !dn || !de1 || !de2) {
         NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         NAPG_CU(ctx, cudaStreamSynchronize(st));
         if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
@@ -748,6 +781,12 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
 napg_status napg_run(napg_ctx *ctx, int32_t test, const napg_options *opt, const uint8_t *sample_mask,
                      const int32_t *vars_a, int32_t n_a, const int32_t *vars_b, int32_t n_b, double *stat,
                      double *pval, int32_t *n) {
+    return napg_run_ex(ctx, test, opt, sample_mask, vars_a, n_a, vars_b, n_b, stat, pval, n, nullptr, nullptr);
+}
+
+napg_status napg_run_ex(napg_ctx *ctx, int32_t test, const napg_options *opt, const uint8_t *sample_mask,
+                        const int32_t *vars_a, int32_t n_a, const int32_t *vars_b, int32_t n_b, double *stat,
+                        double *pval, int32_t *n, double *effect, double *effect2) {
     if (!ctx) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->err.clear();
@@ -765,7 +804,39 @@ napg_status napg_run(napg_ctx *ctx, int32_t test, const napg_options *opt, const
     a.stat = stat;
     a.pval = pval;
     a.n = n;
+    a.es1 = effect;
+    a.es2 = effect2;
     return run_with_outputs(ctx, ctx->ws, ctx->stream, a, vars_b == nullptr);
+}
+
+napg_status napg_adjust(napg_ctx *ctx, int32_t method, const double *p, int64_t rows, int64_t cols,
+                        int32_t symmetric, double *out) {
+    if (!ctx) return NAPG_E_ARG;
+    if (!p || !out || rows < 0 || cols < 0) return fail(ctx, NAPG_E_ARG, "bad correction arguments");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t bytes = sizeof(double) * (size_t)rows * (size_t)cols;
+    if (bytes == 0) return NAPG_OK;
+    napg_status st_ = NAPG_OK;
+    const bool dp = is_device_ptr(p), dout = is_device_ptr(out);
+    const double *pd = p;
+    double *od = out;
+    if (!dp) {
+        double *b = (double *)ws_get(ctx, ctx->ws, Workspace::kOutP, bytes, &st_);
+        if (st_) return st_;
+        NAPG_CU(ctx, cudaMemcpyAsync(b, p, bytes, cudaMemcpyHostToDevice, st));
+        pd = b;
+    }
+    if (!dout) {
+        od = (double *)ws_get(ctx, ctx->ws, Workspace::kOutE1, bytes, &st_);
+        if (st_) return st_;
+    }
+    NAPG_ST(adjust_pvalues(ctx, ctx->ws, st, method, pd, rows, cols, symmetric, od));
+    if (!dout) NAPG_CU(ctx, cudaMemcpyAsync(out, od, bytes, cudaMemcpyDeviceToHost, st));
+    NAPG_CU(ctx, cudaStreamSynchronize(st));
+    return NAPG_OK;
 }
 
 napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt, int32_t n_ctx,

@@ -59,7 +59,7 @@ struct Workspace {
         kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
         kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kPlShift, kPlVsq,
-        kPresortTmp, kBgrat, kNumSlots
+        kPresortTmp, kBgrat, kUnionE1, kUnionE2, kOutE1, kOutE2, kAdjKeys, kAdjVals, kAdjTmp, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -172,6 +172,8 @@ struct RunArgs {
     int32_t nb;
     double *stat, *pval;      // device buffers (n_a x n_b) or NULL
     int32_t *n;
+    double *es1, *es2;        // effect sizes (device, n_a x n_b) or NULL: Table 2's effect size, and
+                              // Cramer's V for chi-squared (NaN for the other tests)
 };
 napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a);
 void free_cohort(Cohort &c);
@@ -240,6 +242,7 @@ struct GroupFin {
     PJobQueue q;
     const double *g2tot; // ANOVA, mixed form: [na][nb] sum (x~^2 - v) over all co-observed samples
                          // (then g2 is not read); NULL: per-level g2
+    double *es;          // t-test: Cohen's d per pair (NULL: not asked)
 };
 void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout,
                             int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -255,12 +258,26 @@ struct RescueArgs {
     const void *X; int32_t dtype; int64_t S; int64_t W; const uint32_t *ctxw; const uint32_t *obs;
     const uint8_t *lab; const int32_t *catrow; const int32_t *va, *vb; int32_t na, nb; int32_t test;
     int32_t welch; const int32_t *nlev_a; const int32_t *present; const int32_t *levoff;
+    double *es;          // t-test: Cohen's d of the rescued pairs (NULL: not asked)
 };
 void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
                    double *stat, double *pval, int32_t *nout, int32_t symmetric, int32_t max_levels,
                    cudaStream_t st);
 void launch_rescue_serial(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
                           double *stat, double *pval, int32_t *nout, int32_t symmetric, cudaStream_t st);
+// effect sizes from the final statistics (the t-test's Cohen's d comes from the
+// group finalize and the rescue)
+struct EffectArgs {
+    int32_t test, na, nb, symmetric;
+    const double *stat; const int32_t *n;
+    const int32_t *levcnt, *levoff, *nlev;   // in-context level counts, per categorical of vars_a
+    const int32_t *rcnt; const int64_t *tie; // Mann-Whitney: per-level counts [R][nb], tie terms [na][nb]
+    double *es1, *es2;
+};
+void launch_effects(const EffectArgs &e, cudaStream_t st);
+// multiple-testing correction of a p-value matrix (device buffers)
+napg_status adjust_pvalues(napg_ctx *ctx, Workspace &ws, cudaStream_t st, int32_t method, const double *p,
+                           int64_t rows, int64_t cols, int32_t symmetric, double *out);
 // ranks
 void launch_presort(const void *X, int32_t dtype, int64_t S, int64_t W, const int32_t *contvars_dev,
                     int32_t ncont, const uint32_t *obs, int32_t *perm, int32_t *pos, int32_t *nobs,

@@ -30,7 +30,9 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync", "napg_release_cache",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_debug_pvalues", "napg_serve_start",
            "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_serve_plan", "napg_version", "napg_trace_enable",
-           "napg_trace_read", "napg_kernel_launches", "napg_tune_enable", "napg_tune_read", "napg_pearson_fp64_noalloc"]
+           "napg_trace_read", "napg_kernel_launches", "napg_tune_enable", "napg_tune_read", "napg_pearson_fp64_noalloc",
+           "napg_run_ex", "napg_adjust"]
+ADJUST = {"bonferroni": 0, "bh": 1, "by": 2}
 
 
 class Options(C.Structure):
@@ -65,6 +67,10 @@ def _load():
     L.napg_load_cohort.restype = C.c_int
     L.napg_run.argtypes = [p, i32, p, p, p, i32, p, i32, p, p, p]
     L.napg_run.restype = C.c_int
+    L.napg_run_ex.argtypes = [p, i32, p, p, p, i32, p, i32, p, p, p, p, p]
+    L.napg_run_ex.restype = C.c_int
+    L.napg_adjust.argtypes = [p, i32, p, i64, i64, i32, p]
+    L.napg_adjust.restype = C.c_int
     L.napg_run_batch.argtypes = [p, i32, p, i32, p, p, i32, p, i32, p, p, p]
     L.napg_run_batch.restype = C.c_int
     L.napg_debug_integers.argtypes = [p, i32, p, i32, i32, p, i64, p]
@@ -191,12 +197,14 @@ class Context:
         self.F, self.S, self.vtype, self.nlev = F, S, vt, nl
         return self
 
-    def run(self, test, vars_a, vars_b=None, mask=None, out="cuda", outputs=None, sync=True, **opt):
+    def run(self, test, vars_a, vars_b=None, mask=None, out="cuda", outputs=None, sync=True, effects=False, **opt):
         """One test over all pairs vars_a x vars_b (vars_a x vars_a when vars_b is None).
 
         out="cuda": torch tensors on the device (stream-ordered; synchronised unless
         sync=False); out="numpy": host numpy arrays. `outputs` may supply the
-        dict(stat, p, n) buffers to write. Returns dict(stat, p, n).
+        dict(stat, p, n[, effect, effect2]) buffers to write. Returns dict(stat, p, n),
+        plus effect and effect2 (Table 2's effect sizes; Cramer's V for chi-squared)
+        with effects=True.
         """
         torch = self.torch
         t = TESTS[test] if isinstance(test, str) else int(test)
@@ -204,25 +212,53 @@ class Context:
         na = len(va)
         nb = na if vb is None else len(vb)
         o = options(**opt)
+        e1 = e2 = None
         if outputs is not None:
             stat, p, n = outputs.get("stat"), outputs.get("p"), outputs.get("n")
+            e1, e2 = outputs.get("effect"), outputs.get("effect2")
         elif out == "numpy":
             stat = np.empty((na, nb), np.float64)
             p = np.empty((na, nb), np.float64)
             n = np.empty((na, nb), np.int32)
+            if effects:
+                e1, e2 = np.empty((na, nb), np.float64), np.empty((na, nb), np.float64)
         else:
             dev = torch.device("cuda", self.device)
             stat = torch.empty((na, nb), dtype=torch.float64, device=dev)
             p = torch.empty((na, nb), dtype=torch.float64, device=dev)
             n = torch.empty((na, nb), dtype=torch.int32, device=dev)
+            if effects:
+                e1 = torch.empty((na, nb), dtype=torch.float64, device=dev)
+                e2 = torch.empty((na, nb), dtype=torch.float64, device=dev)
         m = None
         if mask is not None:
             m = np.ascontiguousarray(mask, dtype=np.uint8) if isinstance(mask, np.ndarray) else mask
-        self._check(lib.napg_run(self.h, t, C.byref(o), _ptr(m), _ptr(va), na, _ptr(vb), 0 if vb is None else nb,
-                                 _ptr(stat), _ptr(p), _ptr(n)))
+        self._check(lib.napg_run_ex(self.h, t, C.byref(o), _ptr(m), _ptr(va), na, _ptr(vb), 0 if vb is None else nb,
+                                    _ptr(stat), _ptr(p), _ptr(n), _ptr(e1), _ptr(e2)))
         if out != "numpy" and sync:
             self.sync()
-        return {"stat": stat, "p": p, "n": n}
+        res = {"stat": stat, "p": p, "n": n}
+        if e1 is not None or e2 is not None:
+            res["effect"], res["effect2"] = e1, e2
+        return res
+
+    def adjust(self, p, method="bh", symmetric=False, out=None):
+        """Multiple-testing correction (Sec. 3.4) of a p-value matrix (numpy or
+        device tensor): method "bonferroni", "bh" or "by"; symmetric=True for a
+        variable set against itself (each pair i < j one test, NaN diagonal).
+        Returns the adjusted matrix (numpy for numpy input, a device tensor
+        otherwise), or writes `out`."""
+        torch = self.torch
+        mth = ADJUST[method] if isinstance(method, str) else int(method)
+        if isinstance(p, np.ndarray):
+            p = np.ascontiguousarray(p, dtype=np.float64)
+            res = np.empty(p.shape, np.float64) if out is None else out
+        else:
+            p = p.contiguous()
+            res = torch.empty(p.shape, dtype=torch.float64, device=p.device) if out is None else out
+        rows, cols = (int(p.shape[0]), int(p.shape[1])) if len(p.shape) == 2 else (1, int(p.shape[0]))
+        self._check(lib.napg_adjust(self.h, mth, _ptr(p), rows, cols, 1 if symmetric else 0, _ptr(res)))
+        return res
 
     def release_cache(self):
         """Mark the cached planes and presort stale (the next run rebuilds them)."""
