@@ -839,6 +839,35 @@ def main():
 
     roof = kernel_roofline(trace.get("stages", {}), args.steps, coh, tests, peaks)
 
+    # effect sizes and multiple-testing correction after the hot path: the effect
+    # stage per test (28 bytes per pair: statistic and n read, two effect sizes
+    # written) and a Benjamini-Hochberg pass over the first test's p-values
+    post = None
+    if rank == 0 and args.scale == 1.0:
+        eff = {}
+        ctx.trace(True)
+        for test, va, vb in tests:
+            ctx.trace_read()
+            ctx.run(test, va, vb, sync=True, precision=prec, effects=True)
+            stg = ctx.trace_read().get("stages", {}).get("effect_sizes")
+            if stg:
+                pc = pair_count(test, va, vb) if vb is not None else len(va) * len(va)
+                eff[test] = {"ms": stg["ms"], "gb_per_s": 28.0 * pc / (stg["ms"] / 1000.0) / 1e9}
+        ctx.trace(False)
+        p0 = outs[tests[0][0]]["p"]
+        ctx.adjust(p0, "bh", symmetric=tests[0][2] is None)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ctx.adjust(p0, "bh", symmetric=tests[0][2] is None)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        m_tests = pair_count(*tests[0])
+        post = {"effect_sizes": eff, "adjust_bh": {"matrix": list(p0.shape), "tests": m_tests,
+                                                   "ms": a0.elapsed_time(a1),
+                                                   "mtests_per_s": m_tests / (a0.elapsed_time(a1) / 1000.0) / 1e6}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(coh, tests, budget_s=args.cpu_budget)
@@ -859,7 +888,8 @@ def main():
                            "stage_ms_per_step": {k: v["ms"] / args.steps for k, v in trace.get("stages", {}).items()},
                            "autotuned": ctx.tune_read()},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator, "latency_small_pearson": latency}
+                "accuracy_vs_oracle": accuracy, "fp64_plain_gpu": comparator, "latency_small_pearson": latency,
+                "postprocess": post}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
