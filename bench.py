@@ -658,6 +658,74 @@ def batch_main(args, world, rank, local_rank):
 
 # -------------------------------------------------------------------- main --
 
+def paper_sim_main(args, world, rank, local_rank):
+    """The paper's simulated benchmark (Sec. 4.1.1): uniform continuous, c = 4
+    categorical and dichotomous features with 10% missing per feature, on the two
+    lines of its runtime figures (S = 1,000 with F in 250..1,000; F = 1,000 with S
+    in 250..1,000). Every test in the plain FP64 form; device time per call
+    (median of the timed calls after the warm-up ones)."""
+    import torch
+    from paper_2505_00448_gb300 import napg
+    device = local_rank if world > 1 else 0
+    torch.cuda.set_device(device)
+    grid = sorted({(F, 1000) for F in (250, 500, 750, 1000)} | {(1000, S) for S in (250, 500, 750, 1000)})
+    rows = []
+    total_pairs = 0
+    total_ms = 0.0
+    launches0 = napg.kernel_launches()
+    for F, S in grid:
+        coh = synth.paper_simulation(F, S)
+        ctx = napg.Context(device)
+        stream = ctx.stream
+        ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+        tests = [("pearson", coh["cont"], None), ("spearman", coh["cont"], None), ("chi2", coh["cat"], None),
+                 ("ttest", coh["bins"], coh["cont"]), ("mwu", coh["bins"], coh["cont"]),
+                 ("anova", coh["cat"], coh["cont"]), ("kruskal", coh["cat"], coh["cont"])]
+        for test, va, vb in tests:
+            nb = len(va) if vb is None else len(vb)
+            dev = torch.device("cuda", device)
+            out = {"stat": torch.empty((len(va), nb), dtype=torch.float64, device=dev),
+                   "p": torch.empty((len(va), nb), dtype=torch.float64, device=dev),
+                   "n": torch.empty((len(va), nb), dtype=torch.int32, device=dev)}
+            opt = {"mwu_mode": "asymptotic"} if test == "mwu" else {}
+            ms = []
+            for k in range(args.warmup + args.steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.run(test, va, vb, outputs=out, sync=False, precision="fp64", **opt)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= args.warmup:
+                    ms.append(e0.elapsed_time(e1))
+            med = statistics.median(ms)
+            pairs = pair_count(test, va, vb)
+            rows.append({"test": test, "F": F, "S": S, "ms": med, "pairs_per_s": pairs / (med / 1000.0)})
+            total_pairs += pairs
+            total_ms += med
+        ctx.close()
+    launches = napg.kernel_launches() - launches0
+    value = total_pairs / (total_ms / 1000.0)
+    cpu = None
+    if not args.no_cpu_baseline:
+        coh = synth.paper_simulation(1000, 1000)
+        tests = [("pearson", coh["cont"], None), ("spearman", coh["cont"], None), ("chi2", coh["cat"], None),
+                 ("ttest", coh["bins"], coh["cont"]), ("mwu", coh["bins"], coh["cont"]),
+                 ("anova", coh["cat"], coh["cont"]), ("kruskal", coh["cat"], coh["cont"])]
+        cpu = oracle_sample(coh, tests, budget_s=min(args.cpu_budget, 14.0))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "the paper's simulated benchmark: uniform [0,1] continuous, c = 4 categorical "
+                           "and dichotomous features, 10% missing per feature; S = 1,000 with F = 250..1,000 and "
+                           "F = 1,000 with S = 250..1,000; all seven tests, plain FP64 form; one step = every "
+                           "(test, F, S) call once; value = pairs over the summed device times",
+                           "calls": rows},
+                "roofline": None, "cpu_baseline": cpu, "e2e": None, "gpu_launches": int(launches), "clocks": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -666,7 +734,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="mixed", choices=["mixed", "ranks", "batch", "serve", "small-pearson"])
+    ap.add_argument("--workload", default="mixed", choices=["mixed", "ranks", "batch", "serve", "small-pearson",
+                                                             "paper-sim"])
     ap.add_argument("--serve-requests", type=int, default=40, help="requests per arrival rate (serve workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -706,6 +775,8 @@ def main():
         return batch_main(args, world, rank, local_rank)
     if args.workload == "serve":
         return serve_main(args, world, rank, local_rank)
+    if args.workload == "paper-sim":
+        return paper_sim_main(args, world, rank, local_rank)
 
     import torch
     dist = None

@@ -231,3 +231,38 @@ def poisson_requests(rng, n_req, rate_per_s, n_samples, cont_ids, cat_ids, tests
             vb = np.sort(rng.choice(cont_ids, size=min(nv - h, len(cont_ids)), replace=False)).astype(np.int32)
         reqs.append({"t": float(t[k]), "test": test, "mask": mask, "vars_a": va, "vars_b": vb})
     return reqs
+
+
+def paper_simulation(F, S, c=4, miss=0.1, seed=0):
+    """The paper's simulated benchmark data (Sec. 4.1.1): F continuous features
+    with values uniform on [0, 1], F categorical features with labels in
+    {0..c-1} and F dichotomous features (labels {0, 1}), S samples; in every
+    feature exactly round(miss S) samples are missing (NaN) at random positions,
+    and every category of a categorical or dichotomous feature appears at least
+    once among its observed samples (reading: the categories are forced after
+    the missing positions are drawn). Rows: [continuous | categorical |
+    dichotomous]."""
+    rng = rng_for(100 + seed, salt=F * 10007 + S)
+    k = int(round(miss * S))
+    cont = rng.random((F, S))
+    labs = []
+    for levels in (c, 2):
+        out = np.empty((F, S))
+        for v in range(F):
+            lab = rng.integers(0, levels, S).astype(float)
+            miss_pos = rng.choice(S, k, replace=False)
+            keep = np.setdiff1d(np.arange(S), miss_pos)
+            force = rng.choice(keep, levels, replace=False)
+            lab[force] = np.arange(levels)
+            lab[miss_pos] = np.nan
+            out[v] = lab
+        labs.append(out)
+    for v in range(F):
+        cont[v, rng.choice(S, k, replace=False)] = np.nan
+    X = np.concatenate([cont, labs[0], labs[1]])
+    vtype = np.concatenate([np.zeros(F, np.uint8), np.ones(2 * F, np.uint8)])
+    nlev = np.concatenate([np.zeros(F, np.int32), np.full(F, c, np.int32), np.full(F, 2, np.int32)])
+    return {"X": X, "vtype": vtype, "nlev": nlev, "missing": float("nan"),
+            "cont": np.arange(F, dtype=np.int32), "cat": np.arange(F, 2 * F, dtype=np.int32),
+            "bins": np.arange(2 * F, 3 * F, dtype=np.int32)}
+

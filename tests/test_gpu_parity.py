@@ -315,6 +315,21 @@ def test_reloading_cohorts_reuses_buffers(napg):
     c.close()
 
 
+def test_paper_simulation_all_tests(napg):
+    """The paper's simulated benchmark data (uniform values, c = 4 categorical and
+    dichotomous features, exactly 10% missing per feature): every test against
+    the oracle."""
+    coh = synth.paper_simulation(60, 250)
+    c = ctx_for(napg, coh)
+    cont, cat, bins = coh["cont"], coh["cat"], coh["bins"]
+    for test, va, vb, kw in (("pearson", cont, None, {}), ("spearman", cont, None, {}), ("chi2", cat, None, {}),
+                             ("ttest", bins, cont, {}), ("mwu", bins, cont, {"mwu_mode": 2}),
+                             ("anova", cat, cont, {}), ("kruskal", cat, cont, {})):
+        opt = {"mwu_mode": "asymptotic"} if test == "mwu" else {}
+        compare(test, c.run(test, va, vb, out="numpy", **opt), oracle_run(test, coh, va, vb, **kw))
+    c.close()
+
+
 def test_invalid_inputs_are_errors(napg):
     c = napg.Context(0)
     X = np.array([[0, 1, 3.0], [1.0, 2.0, 3.0]])
