@@ -44,18 +44,40 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
+def _run_mutant(name, workdir):
+    """Build the oracle with one planted mistake and run the pins against it;
+    returns (pins' exit status, the end of their output)."""
     old, new = MUTANTS[name]
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation site for {name} not found"
-    mutated = src.replace(old, new)
-    csrc = tmp_path / "mutant.c"
-    csrc.write_text(mutated)
-    so = tmp_path / "libmutant.so"
+    if src.count(old) < 1:
+        return None, f"mutation site for {name} not found"
+    d = os.path.join(workdir, name)
+    os.makedirs(d, exist_ok=True)
+    csrc = os.path.join(d, "mutant.c")
+    with open(csrc, "w") as f:
+        f.write(src.replace(old, new))
+    so = os.path.join(d, "libmutant.so")
     subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-std=c11",
-                    "-o", str(so), str(csrc), "-lm"], check=True)
-    env = dict(os.environ, NAPG_ORACLE_LIB=str(so))
+                    "-o", so, csrc, "-lm"], check=True)
+    env = dict(os.environ, NAPG_ORACLE_LIB=so, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"no pin caught mutant {name}:\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(tmp_path_factory):
+    """Every mutant's pin run, several at a time (each is an independent process)."""
+    from concurrent.futures import ThreadPoolExecutor
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    names = sorted(MUTANTS)
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        results = list(ex.map(lambda n: _run_mutant(n, workdir), names))
+    return dict(zip(names, results))
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, mutant_results):
+    rc, out = mutant_results[name]
+    assert rc is not None, out
+    assert rc != 0, f"no pin caught mutant {name}:\n{out}"
