@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(256) k_pearson_fp64(const double *__restrict__
     while (t >= T - I) { t -= T - I; ++I; }
     const int J = I + t;
     __shared__ union {
-        struct { double xa[kPT][kPK + 1], xb[kPT][kPK + 1]; } st;
+        struct { double xa[kPT][kPK + 1], xb[kPT][kPK + 1], qa[kPT][kPK + 1], qb[kPT][kPK + 1]; } st;
         double part[20][256];
     } u;
     __shared__ int cpart[4][256];
@@ -80,8 +80,12 @@ __global__ void __launch_bounds__(256) k_pearson_fp64(const double *__restrict__
         for (int e = threadIdx.x; e < kPT * kPK; e += 256) {
             const int rr = e / kPK, c = e % kPK;
             const int gi = i0 + rr, gj = j0 + rr;
-            u.st.xa[rr][c] = gi < nv ? xs[(int64_t)gi * S_pad + k0 + c] : 0.0;
-            u.st.xb[rr][c] = gj < nv ? xs[(int64_t)gj * S_pad + k0 + c] : 0.0;
+            const double va = gi < nv ? xs[(int64_t)gi * S_pad + k0 + c] : 0.0;
+            const double vb = gj < nv ? xs[(int64_t)gj * S_pad + k0 + c] : 0.0;
+            u.st.xa[rr][c] = va;
+            u.st.xb[rr][c] = vb;
+            u.st.qa[rr][c] = va * va;      // squares formed once per staged word
+            u.st.qb[rr][c] = vb * vb;
         }
         if (threadIdx.x < kPT) {
             const int gi = i0 + threadIdx.x, gj = j0 + threadIdx.x;
@@ -100,12 +104,12 @@ __global__ void __launch_bounds__(256) k_pearson_fp64(const double *__restrict__
             bool oi[2], oj[2];
             for (int a = 0; a < 2; ++a) {
                 xi[a] = u.st.xa[ty + 16 * a][k];
-                x2i[a] = xi[a] * xi[a];
+                x2i[a] = u.st.qa[ty + 16 * a][k];
                 oi[a] = (mi[a] >> k) & 1u;
             }
             for (int b = 0; b < 2; ++b) {
                 xj[b] = u.st.xb[tx + 16 * b][k];
-                x2j[b] = xj[b] * xj[b];
+                x2j[b] = u.st.qb[tx + 16 * b][k];
                 oj[b] = (mj[b] >> k) & 1u;
             }
             for (int a = 0; a < 2; ++a)
