@@ -82,6 +82,11 @@ typedef struct {
     int32_t mwu_mode;        /* 0 auto (default), 1 exact, 2 asymptotic (Sec. 3.5.6) */
     int32_t mwu_continuity;  /* 1: 0.5 continuity correction in asymptotic mode (default) */
     int32_t debug_checks;    /* 1: extra device-side argument checks */
+    int32_t async_host_outputs; /* 1: napg_run / napg_run_ex return once the work and the
+                                   copies of host outputs are queued (outputs valid after
+                                   napg_sync; one call's copies overlap the next call's
+                                   kernels; pinned host buffers let them run asynchronously);
+                                   0 (default): those calls return with host outputs written */
 } napg_options;
 
 /* Fills *opt with the defaults above. */
@@ -167,6 +172,9 @@ napg_status napg_run_ex(napg_ctx *ctx, int32_t test, const napg_options *opt,
                         const uint8_t *sample_mask, const int32_t *vars_a, int32_t n_a,
                         const int32_t *vars_b, int32_t n_b, double *stat, double *pval,
                         int32_t *n, double *effect, double *effect2);
+
+/* Effect sizes are returned by napg_run_ex only; the batch and serving entry
+ * points return stat, p and n. */
 
 /* Multiple-testing correction (Sec. 3.4). */
 typedef enum { NAPG_ADJ_BONFERRONI = 0, NAPG_ADJ_BH = 1, NAPG_ADJ_BY = 2 } napg_adjust_method;

@@ -527,40 +527,89 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
 
 // Outputs: device pointers are written in place; host ones through workspace
 // buffers copied back before returning.
+napg_status wait_pending_copies(napg_ctx *ctx) {
+    for (int k = 0; k < 2; ++k)
+        if (ctx->copy_used[k]) NAPG_CU(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_copy[k], 0));
+    return NAPG_OK;
+}
+
+// Host outputs are staged in device buffers and copied back. Synchronous by
+// default; with opt.async_host_outputs (the context's own stream and workspace
+// only) the copies go on copy_stream after the run and the call returns: the
+// staging set alternates between calls, and a call first waits (on the device)
+// for the last copy out of the set it is about to overwrite, so one call's
+// copies overlap the next call's kernels.
 napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape) {
     const int64_t cnt = (int64_t)a.na * (symmetric_shape ? a.na : a.nb);
+    const bool async = a.opt.async_host_outputs && &ws == &ctx->ws && st == ctx->stream;
+    const int set = async ? ctx->stage_set : 0;
+    const int sl_stat = set ? Workspace::kOutStatB : Workspace::kOutStat, sl_p = set ? Workspace::kOutPB : Workspace::kOutP,
+              sl_n = set ? Workspace::kOutNB : Workspace::kOutN, sl_e1 = set ? Workspace::kOutE1B : Workspace::kOutE1,
+              sl_e2 = set ? Workspace::kOutE2B : Workspace::kOutE2;
+    if (&ws == &ctx->ws) {
+        // staging set `set` may still be read by an earlier asynchronous copy
+        if (async) {
+            if (ctx->copy_used[set]) NAPG_CU(ctx, cudaStreamWaitEvent(st, ctx->ev_copy[set], 0));
+        } else {
+            NAPG_ST(wait_pending_copies(ctx));
+        }
+    }
     double *hs = a.stat, *hp = a.pval;
     int32_t *hn = a.n;
     const bool ds = !hs || is_device_ptr(hs), dp = !hp || is_device_ptr(hp), dn = !hn || is_device_ptr(hn);
-    napg_status st_ = NAPG_OK;
     double *he1 = a.es1, *he2 = a.es2;
     const bool de1 = !he1 || is_device_ptr(he1), de2 = !he2 || is_device_ptr(he2);
-    if (!ds) a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
-    if (!dp) a.pval = (double *)ws_get(ctx, ws, Workspace::kOutP, sizeof(double) * cnt, &st_);
-    if (!dn) a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_);
-    if (!de1) a.es1 = (double *)ws_get(ctx, ws, Workspace::kOutE1, sizeof(double) * cnt, &st_);
-    if (!de2) a.es2 = (double *)ws_get(ctx, ws, Workspace::kOutE2, sizeof(double) * cnt, &st_);
+    napg_status st_ = NAPG_OK;
+    if (!ds) a.stat = (double *)ws_get(ctx, ws, sl_stat, sizeof(double) * cnt, &st_);
+    if (!dp) a.pval = (double *)ws_get(ctx, ws, sl_p, sizeof(double) * cnt, &st_);
+    if (!dn) a.n = (int32_t *)ws_get(ctx, ws, sl_n, sizeof(int32_t) * cnt, &st_);
+    if (!de1) a.es1 = (double *)ws_get(ctx, ws, sl_e1, sizeof(double) * cnt, &st_);
+    if (!de2) a.es2 = (double *)ws_get(ctx, ws, sl_e2, sizeof(double) * cnt, &st_);
     if (st_) return st_;
     // the effect sizes are formed from the statistic and n
     if (a.es1 || a.es2) {
-        if (!a.stat) { a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_); hs = nullptr; }
-        if (!a.n) { a.n = (int32_t *)ws_get(ctx, ws, Workspace::kOutN, sizeof(int32_t) * cnt, &st_); hn = nullptr; }
+        if (!a.stat) { a.stat = (double *)ws_get(ctx, ws, sl_stat, sizeof(double) * cnt, &st_); hs = nullptr; }
+        if (!a.n) { a.n = (int32_t *)ws_get(ctx, ws, sl_n, sizeof(int32_t) * cnt, &st_); hn = nullptr; }
         if (st_) return st_;
     }
     // exact Mann-Whitney p reads the statistic back: give it a buffer if none
     if (a.test == NAPG_MWU && a.pval && !a.stat) {
-        a.stat = (double *)ws_get(ctx, ws, Workspace::kOutStat, sizeof(double) * cnt, &st_);
+        a.stat = (double *)ws_get(ctx, ws, sl_stat, sizeof(double) * cnt, &st_);
         if (st_) return st_;
         hs = nullptr;
     }
-    NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
+    // an asynchronous call leaves the error word to napg_sync (earlier queued
+    // calls may have set it)
+    if (!async) NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
     NAPG_ST(run_on_stream(ctx, ws, st, a));
+    const bool host_out = !ds || !dp || !dn || !de1 || !de2;
+    if (async && host_out) {
+        if (!ctx->copy_stream) {
+            NAPG_CU(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+            for (int k = 0; k < 2; ++k) {
+                NAPG_CU(ctx, cudaEventCreateWithFlags(&ctx->ev_run[k], cudaEventDisableTiming));
+                NAPG_CU(ctx, cudaEventCreateWithFlags(&ctx->ev_copy[k], cudaEventDisableTiming));
+            }
+        }
+        cudaStream_t cs = ctx->copy_stream;
+        NAPG_CU(ctx, cudaEventRecord(ctx->ev_run[set], st));
+        NAPG_CU(ctx, cudaStreamWaitEvent(cs, ctx->ev_run[set], 0));
+        if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, cs));
+        if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, cs));
+        if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, cs));
+        if (!de1) NAPG_CU(ctx, cudaMemcpyAsync(he1, a.es1, sizeof(double) * cnt, cudaMemcpyDeviceToHost, cs));
+        if (!de2) NAPG_CU(ctx, cudaMemcpyAsync(he2, a.es2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, cs));
+        NAPG_CU(ctx, cudaEventRecord(ctx->ev_copy[set], cs));
+        ctx->copy_used[set] = true;
+        ctx->stage_set = 1 - set;
+        return NAPG_OK;
+    }
     if (!ds) NAPG_CU(ctx, cudaMemcpyAsync(hs, a.stat, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!dp) NAPG_CU(ctx, cudaMemcpyAsync(hp, a.pval, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!dn) NAPG_CU(ctx, cudaMemcpyAsync(hn, a.n, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
     if (!de1) NAPG_CU(ctx, cudaMemcpyAsync(he1, a.es1, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
     if (!de2) NAPG_CU(ctx, cudaMemcpyAsync(he2, a.es2, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
-    if (!ds || !dp || !dn || !de1 || !de2) {
+    if (host_out) {
         NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         NAPG_CU(ctx, cudaStreamSynchronize(st));
         if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
@@ -584,6 +633,7 @@ void napg_default_options(napg_options *o) {
     o->mwu_mode = 0;
     o->mwu_continuity = 1;
     o->debug_checks = 0;
+    o->async_host_outputs = 0;
 }
 
 const char *napg_version(void) { return "napg 0.1 (sm_103a)"; }
@@ -626,6 +676,14 @@ void napg_destroy(napg_ctx *ctx) {
     if (ctx->serve) napg_serve_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+        for (int k = 0; k < 2; ++k) {
+            cudaEventDestroy(ctx->ev_run[k]);
+            cudaEventDestroy(ctx->ev_copy[k]);
+        }
+    }
     free_batch(ctx);
     free_cohort(ctx->coh);
     free_ws(ctx->ws);
@@ -641,7 +699,11 @@ napg_status napg_sync(napg_ctx *ctx) {
     if (!ctx) return NAPG_E_ARG;
     NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
     NAPG_CU(ctx, cudaStreamSynchronize(ctx->stream));
-    if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    if (ctx->copy_stream) NAPG_CU(ctx, cudaStreamSynchronize(ctx->copy_stream));
+    if (*ctx->host_err & kErrTimeout) {
+        NAPG_CU(ctx, cudaMemset(ctx->dev_err, 0, sizeof(uint32_t)));
+        return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    }
     return NAPG_OK;
 }
 
@@ -819,6 +881,7 @@ napg_status napg_adjust(napg_ctx *ctx, int32_t method, const double *p, int64_t 
     cudaStream_t st = ctx->stream;
     const size_t bytes = sizeof(double) * (size_t)rows * (size_t)cols;
     if (bytes == 0) return NAPG_OK;
+    NAPG_ST(wait_pending_copies(ctx));
     napg_status st_ = NAPG_OK;
     const bool dp = is_device_ptr(p), dout = is_device_ptr(out);
     const double *pd = p;
@@ -851,10 +914,12 @@ napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
     a.test = test;
     if (opt) a.opt = *opt;
     else napg_default_options(&a.opt);
+    a.opt.async_host_outputs = 0;               // the batch call returns with its outputs written
     a.va = vars_a;
     a.na = n_a;
     a.vb = vars_b;
     a.nb = vars_b ? n_b : n_a;
+    NAPG_ST(wait_pending_copies(ctx));
     return run_batch(ctx, a, n_ctx, sample_masks, stat, pval, n);
 }
 
@@ -864,6 +929,7 @@ napg_status napg_debug_pvalues(napg_ctx *ctx, int32_t kind, const double *s, con
     if (count == 0) return NAPG_OK;
     if (!s || !p || (kind != 4 && !a) || ((kind == 2 || kind == 5) && !b)) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    NAPG_ST(wait_pending_copies(ctx));
     ctx->err.clear();
     NAPG_CU(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
@@ -891,6 +957,7 @@ napg_status napg_debug_integers(napg_ctx *ctx, int32_t test, const uint8_t *samp
                                 int64_t *out, int64_t cap, int64_t *written) {
     if (!ctx || !out || !written) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
+    NAPG_ST(wait_pending_copies(ctx));
     ctx->err.clear();
     NAPG_CU(ctx, cudaSetDevice(ctx->device));
     Cohort &c = ctx->coh;

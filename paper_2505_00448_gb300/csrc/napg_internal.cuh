@@ -59,7 +59,8 @@ struct Workspace {
         kLevPresent, kMomA, kMomB, kMomC, kMomD, kMomE, kMomF, kIntA, kIntB, kIntC, kFlagList,
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
         kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kPlShift, kPlVsq,
-        kPresortTmp, kBgrat, kUnionE1, kUnionE2, kOutE1, kOutE2, kAdjKeys, kAdjVals, kAdjTmp, kNumSlots
+        kPresortTmp, kBgrat, kUnionE1, kUnionE2, kOutE1, kOutE2, kAdjKeys, kAdjVals, kAdjTmp,
+        kOutStatB, kOutPB, kOutNB, kOutE1B, kOutE2B, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -144,6 +145,12 @@ struct napg_ctx {
     napg::Tracer trace;
     napg::Tuner tune;
     std::mutex mu;                     // guards cohort/workspace use from the serving threads
+    // asynchronous host outputs: two staging sets (kOut* and kOut*B), copied to
+    // the host on copy_stream; ev_copy[k] marks set k's last copy done
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_run[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
+    bool copy_used[2] = {false, false};
+    int stage_set = 0;
 };
 
 namespace napg {
@@ -179,6 +186,8 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
 void free_cohort(Cohort &c);
 uint64_t next_cohort_gen();
 napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunArgs a, bool symmetric_shape);
+// orders the context stream after every pending host-output copy (device-side wait)
+napg_status wait_pending_copies(napg_ctx *ctx);
 // runs run(choice) with the launch shape the autotuner picks for `key`
 napg_status tuned_launch(napg_ctx *ctx, const TuneKey &key, int ncand, const std::function<napg_status(int)> &run,
                          cudaStream_t st);

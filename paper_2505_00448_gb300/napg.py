@@ -37,7 +37,8 @@ ADJUST = {"bonferroni": 0, "bh": 1, "by": 2}
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("welch", C.c_int32), ("yates_2x2", C.c_int32),
-                ("mwu_mode", C.c_int32), ("mwu_continuity", C.c_int32), ("debug_checks", C.c_int32)]
+                ("mwu_mode", C.c_int32), ("mwu_continuity", C.c_int32), ("debug_checks", C.c_int32),
+                ("async_host_outputs", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -201,10 +202,12 @@ class Context:
         """One test over all pairs vars_a x vars_b (vars_a x vars_a when vars_b is None).
 
         out="cuda": torch tensors on the device (stream-ordered; synchronised unless
-        sync=False); out="numpy": host numpy arrays. `outputs` may supply the
-        dict(stat, p, n[, effect, effect2]) buffers to write. Returns dict(stat, p, n),
-        plus effect and effect2 (Table 2's effect sizes; Cramer's V for chi-squared)
-        with effects=True.
+        sync=False); out="numpy": host numpy arrays, written before the call returns,
+        or with sync=False once sync() returns (the copies then overlap the next
+        call's kernels; pinned arrays let them run asynchronously). `outputs` may
+        supply the dict(stat, p, n[, effect, effect2]) buffers to write. Returns
+        dict(stat, p, n), plus effect and effect2 (Table 2's effect sizes; Cramer's
+        V for chi-squared) with effects=True.
         """
         torch = self.torch
         t = TESTS[test] if isinstance(test, str) else int(test)
@@ -212,6 +215,8 @@ class Context:
         na = len(va)
         nb = na if vb is None else len(vb)
         o = options(**opt)
+        if not sync and (out == "numpy" or (outputs is not None and isinstance(outputs.get("stat", outputs.get("p")), np.ndarray))):
+            o.async_host_outputs = 1
         e1 = e2 = None
         if outputs is not None:
             stat, p, n = outputs.get("stat"), outputs.get("p"), outputs.get("n")

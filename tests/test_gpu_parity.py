@@ -330,6 +330,39 @@ def test_paper_simulation_all_tests(napg):
     c.close()
 
 
+def test_async_host_outputs(napg):
+    """Host outputs with sync=False: several calls in flight (the staging sets
+    alternate), outputs written once sync() returns, equal to synchronous runs;
+    a correction queued behind them sees their results."""
+    import torch
+    coh = synth.small_cohort(160, n_cont=50, n_cat=10, S=1200 + 5, miss=0.2, lev_lo=2, lev_hi=5, binary_cats=3)
+    c = ctx_for(napg, coh)
+    cont, cat = coh["cont"], coh["cat"]
+    jobs = [("pearson", cont, None), ("chi2", cat, None), ("kruskal", cat[3:], cont), ("pearson", cont[:20], None),
+            ("anova", cat, cont)]
+    ref = [c.run(t, a, b, out="numpy") for t, a, b in jobs]
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
+    bufs = []
+    for t, a, b in jobs:
+        nb = len(a) if b is None else len(b)
+        o = {"stat": pin((len(a), nb), torch.float64), "p": pin((len(a), nb), torch.float64),
+             "n": pin((len(a), nb), torch.int32)}
+        c.run(t, a, b, outputs=o, out="numpy", sync=False)
+        bufs.append(o)
+    c.sync()
+    for r, o in zip(ref, bufs):
+        for k in ("stat", "p", "n"):
+            assert np.array_equal(r[k], o[k], equal_nan=True)
+    # pageable outputs in flight, then a synchronous call and a correction
+    o = {"stat": np.empty((50, 50)), "p": np.empty((50, 50)), "n": np.empty((50, 50), np.int32)}
+    c.run("pearson", cont, outputs=o, out="numpy", sync=False)
+    adj = c.adjust(ref[0]["p"], "bh", symmetric=True)
+    c.sync()
+    assert np.array_equal(o["p"], ref[0]["p"], equal_nan=True)
+    assert np.array_equal(adj, O.adjust(ref[0]["p"], "bh", True), equal_nan=True)
+    c.close()
+
+
 def test_invalid_inputs_are_errors(napg):
     c = napg.Context(0)
     X = np.array([[0, 1, 3.0], [1.0, 2.0, 3.0]])
