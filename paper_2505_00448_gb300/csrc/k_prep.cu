@@ -12,11 +12,13 @@ __device__ __forceinline__ bool is_missing_val(T v, double m, bool m_is_nan) {
 
 // One warp per (variable, 32-sample word): observed bit via ballot; checks finite
 // values and integer labels in [0, c); writes labels of categorical variables.
+// With copy_to, X is the cohort in (device-mapped) host memory and each value is
+// also written to the device copy as it is checked.
 template <typename T>
 __global__ void k_validate_obs(const T *__restrict__ X, int64_t F, int64_t S, int64_t W, double missing,
                                const uint8_t *__restrict__ vtype, const int32_t *__restrict__ nlev,
                                const int32_t *__restrict__ catrow, uint32_t *__restrict__ obs,
-                               uint8_t *__restrict__ lab, uint32_t *err, int64_t v_base) {
+                               uint8_t *__restrict__ lab, uint32_t *err, int64_t v_base, T *__restrict__ copy_to) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int64_t v = (int64_t)blockIdx.y + v_base;
@@ -29,6 +31,7 @@ __global__ void k_validate_obs(const T *__restrict__ X, int64_t F, int64_t S, in
     uint8_t lb = kMissingLabel;
     if (s < S) {
         const T x = X[v * S + s];
+        if (copy_to) copy_to[v * S + s] = x;
         ob = !is_missing_val(x, missing, m_nan);
         if (ob) {
             const double xd = (double)x;
@@ -48,19 +51,19 @@ __global__ void k_validate_obs(const T *__restrict__ X, int64_t F, int64_t S, in
 
 void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int64_t W, double missing,
                          const uint8_t *vtype_dev, const int32_t *nlev_dev, const int32_t *catrow_dev,
-                         uint32_t *obs, uint8_t *lab, uint32_t *err, cudaStream_t st) {
+                         uint32_t *obs, uint8_t *lab, uint32_t *err, cudaStream_t st, void *copy_to) {
     if (F == 0 || W == 0) return;
     for (int64_t v0 = 0; v0 < F; v0 += 65535) {      // grid.y limit
         dim3 grid((unsigned)((W + 7) / 8), (unsigned)std::min<int64_t>(65535, F - v0));
         if (dtype == NAPG_F32) {
             count_launch();
             k_validate_obs<float><<<grid, 256, 0, st>>>((const float *)X, F, S, W, missing, vtype_dev, nlev_dev,
-                                                         catrow_dev, obs, lab, err, v0);
+                                                         catrow_dev, obs, lab, err, v0, (float *)copy_to);
         }
         else {
             count_launch();
             k_validate_obs<double><<<grid, 256, 0, st>>>((const double *)X, F, S, W, missing, vtype_dev, nlev_dev,
-                                                          catrow_dev, obs, lab, err, v0);
+                                                          catrow_dev, obs, lab, err, v0, (double *)copy_to);
         }
     }
 }

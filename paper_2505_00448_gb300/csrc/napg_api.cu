@@ -791,8 +791,21 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
         }
     }
     const bool on_dev = is_device_ptr(X);
+    // page-locked host memory mapped for the device: the validation kernel reads
+    // it over the host link and writes the device copy as it checks each value
+    // (one pass instead of a copy and a pass)
+    const void *mapped = nullptr;
+    if (!on_dev && !samples_major) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, X) == cudaSuccess) {
+            if (at.type == cudaMemoryTypeHost && at.devicePointer) mapped = at.devicePointer;
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
     if (!samples_major) {
-        NAPG_CU(ctx, cudaMemcpyAsync(c.X, X, xbytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        if (!mapped)
+            NAPG_CU(ctx, cudaMemcpyAsync(c.X, X, xbytes, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     } else {
         void *tmp = nullptr;
         NAPG_CU(ctx, cudaMalloc(&tmp, xbytes));
@@ -812,8 +825,8 @@ napg_status napg_load_cohort(napg_ctx *ctx, const void *X, int32_t dtype, int64_
     NAPG_CU(ctx, cudaMemcpyAsync(dtab, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice, st));
     NAPG_CU(ctx, cudaMemcpyAsync(dvt, var_type, (size_t)n_vars, cudaMemcpyHostToDevice, st));
     NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
-    launch_validate_obs(c.X, dtype, n_vars, n_samples, c.W, missing, dvt, dtab, dtab + n_vars, c.obs, c.lab,
-                        ctx->dev_err, st);
+    launch_validate_obs(mapped ? mapped : c.X, dtype, n_vars, n_samples, c.W, missing, dvt, dtab, dtab + n_vars,
+                        c.obs, c.lab, ctx->dev_err, st, mapped ? c.X : nullptr);
     NAPG_CU(ctx, cudaGetLastError());
     NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     NAPG_CU(ctx, cudaStreamSynchronize(st));

@@ -213,7 +213,7 @@ void launch_debug_pvalues(int32_t kind, const double *s, const double *a, const 
 // prep
 void launch_validate_obs(const void *X, int32_t dtype, int64_t F, int64_t S, int64_t W, double missing,
                          const uint8_t *vtype_dev, const int32_t *nlev_dev, const int32_t *catrow_dev,
-                         uint32_t *obs, uint8_t *lab, uint32_t *err, cudaStream_t st);
+                         uint32_t *obs, uint8_t *lab, uint32_t *err, cudaStream_t st, void *copy_to = nullptr);
 void launch_transpose(const void *in, void *out, int32_t dtype, int64_t rows, int64_t cols, cudaStream_t st);
 void launch_ctx_bits(const uint8_t *mask, int64_t S, int64_t W, uint32_t *ctxw, cudaStream_t st);
 void launch_gather_obs(const uint32_t *obs, const int32_t *vars_dev, int32_t nv, const uint32_t *ctxw,

@@ -363,6 +363,44 @@ def test_async_host_outputs(napg):
     c.close()
 
 
+def test_cohort_from_pinned_pageable_and_device_memory(napg):
+    """The same cohort loaded from pageable host memory (copied), page-locked host
+    memory (read by the validation kernel over the host link) and device memory
+    gives identical results; bad values are caught on every path."""
+    import torch
+    coh = synth.small_cohort(161, n_cont=30, n_cat=8, S=2000 + 11, miss=0.2, lev_lo=2, lev_hi=5,
+                             dtype=np.float32)
+    outs = []
+    for src in ("numpy", "pinned", "device"):
+        X = coh["X"]
+        if src == "pinned":
+            X = torch.from_numpy(coh["X"]).pin_memory()
+        elif src == "device":
+            X = torch.from_numpy(coh["X"]).cuda()
+        c = napg.Context(0)
+        c.load_cohort(X, coh["vtype"], coh["nlev"], coh["missing"])
+        outs.append([c.run(t, a, b, out="numpy") for t, a, b in (("pearson", coh["cont"], None),
+                                                                  ("chi2", coh["cat"], None),
+                                                                  ("kruskal", coh["cat"], coh["cont"]))])
+        c.close()
+    for o in outs[1:]:
+        for r0, r1 in zip(outs[0], o):
+            for k in ("stat", "p", "n"):
+                assert np.array_equal(r0[k], r1[k], equal_nan=True)
+    bad = coh["X"].copy()
+    bad[coh["cat"][0], 5] = 7.5                    # not a label
+    c = napg.Context(0)
+    with pytest.raises(napg.NapgError) as e:
+        c.load_cohort(torch.from_numpy(bad).pin_memory(), coh["vtype"], coh["nlev"], coh["missing"])
+    assert e.value.code == napg.E_LABEL
+    bad = coh["X"].copy()
+    bad[coh["cont"][3], 9] = np.inf
+    with pytest.raises(napg.NapgError) as e:
+        c.load_cohort(torch.from_numpy(bad).pin_memory(), coh["vtype"], coh["nlev"], coh["missing"])
+    assert e.value.code == napg.E_NONFINITE
+    c.close()
+
+
 def test_invalid_inputs_are_errors(napg):
     c = napg.Context(0)
     X = np.array([[0, 1, 3.0], [1.0, 2.0, 3.0]])
