@@ -120,6 +120,8 @@ struct BatchState {
     std::vector<size_t> doff;
     int32_t *host_counts = nullptr;      // pinned
     size_t sub_x_cap = 0, sub_obs_cap = 0, sub_lab_cap = 0;
+    void *stage = nullptr;               // device outputs of every context when the caller's are on the host
+    size_t stage_cap = 0;
 };
 
 void free_batch(napg_ctx *ctx) {
@@ -129,7 +131,7 @@ void free_batch(napg_ctx *ctx) {
     free_cohort(b->sub);
     for (int i = 0; i < Workspace::kNumSlots; ++i)
         if (b->ws.ptr[i]) cudaFree(b->ws.ptr[i]);
-    void *p[] = {b->masks, b->idx, b->counts, b->rows, b->dints};
+    void *p[] = {b->masks, b->idx, b->counts, b->rows, b->dints, b->stage};
     for (void *q : p)
         if (q) cudaFree(q);
     if (b->host_counts) cudaFreeHost(b->host_counts);
@@ -223,6 +225,50 @@ static napg_status batch_loop(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, c
     return NAPG_OK;
 }
 
+// Host outputs: the batch runs on the graph path into device buffers (one region
+// for every context's outputs), then each context's outputs are copied back.
+// If the region cannot be allocated, the contexts go through the loop instead.
+static napg_status batch_host_outputs(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uint8_t *const *masks,
+                                      double *const *stat, double *const *pval, int32_t *const *n, bool symmetric) {
+    if (!ctx->batch) ctx->batch = new BatchState();
+    BatchState &b = *ctx->batch;
+    const int64_t cnt = (int64_t)a0.na * (symmetric ? a0.na : a0.nb);
+    const size_t dbl = sizeof(double) * (size_t)cnt, i32 = sizeof(int32_t) * (size_t)cnt;
+    const size_t per = (stat ? dbl : 0) + (pval ? dbl : 0) + (n ? ((i32 + 255) / 256) * 256 : 0);
+    const size_t need = per * (size_t)n_ctx;
+    if (b.stage_cap < need) {
+        if (b.stage) cudaFree(b.stage);
+        b.stage = nullptr;
+        b.stage_cap = 0;
+        if (cudaMalloc(&b.stage, need) != cudaSuccess) {
+            (void)cudaGetLastError();
+            b.stage = nullptr;
+            return batch_loop(ctx, a0, n_ctx, masks, stat, pval, n);
+        }
+        b.stage_cap = need;
+    }
+    std::vector<double *> ds(n_ctx, nullptr), dp(n_ctx, nullptr);
+    std::vector<int32_t *> dn(n_ctx, nullptr);
+    unsigned char *cur = (unsigned char *)b.stage;
+    for (int32_t k = 0; k < n_ctx; ++k) {
+        if (stat) { ds[k] = (double *)cur; cur += dbl; }
+        if (pval) { dp[k] = (double *)cur; cur += dbl; }
+        if (n) { dn[k] = (int32_t *)cur; cur += ((i32 + 255) / 256) * 256; }
+    }
+    NAPG_ST(run_batch(ctx, a0, n_ctx, masks, stat ? ds.data() : nullptr, pval ? dp.data() : nullptr,
+                      n ? dn.data() : nullptr));
+    cudaStream_t st = ctx->stream;
+    for (int32_t k = 0; k < n_ctx; ++k) {
+        if (stat && stat[k]) NAPG_CU(ctx, cudaMemcpyAsync(stat[k], ds[k], dbl, cudaMemcpyDefault, st));
+        if (pval && pval[k]) NAPG_CU(ctx, cudaMemcpyAsync(pval[k], dp[k], dbl, cudaMemcpyDefault, st));
+        if (n && n[k]) NAPG_CU(ctx, cudaMemcpyAsync(n[k], dn[k], i32, cudaMemcpyDefault, st));
+    }
+    NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    NAPG_CU(ctx, cudaStreamSynchronize(st));
+    if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    return NAPG_OK;
+}
+
 napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uint8_t *const *masks,
                       double *const *stat, double *const *pval, int32_t *const *n) {
     Cohort &P = ctx->coh;
@@ -234,13 +280,15 @@ napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uin
     // (those run on the union of the lists and gather a block with a host sync).
     bool graphable = symmetric || !(a0.test == NAPG_PEARSON || a0.test == NAPG_CHI2);
     if (a0.test == NAPG_MWU && a0.pval && !a0.stat) graphable = false;   // exact U reads the statistic back
+    bool host_out = false;
     for (int32_t k = 0; k < n_ctx && graphable; ++k) {
         const void *o[3] = {stat ? stat[k] : nullptr, pval ? pval[k] : nullptr, n ? n[k] : nullptr};
         for (const void *q : o)
-            if (q && !is_device_ptr(q)) graphable = false;
+            if (q && !is_device_ptr(q)) host_out = true;
         if (a0.test == NAPG_MWU && pval && pval[k] && !(stat && stat[k])) graphable = false;
     }
     if (!graphable) return batch_loop(ctx, a0, n_ctx, masks, stat, pval, n);
+    if (host_out) return batch_host_outputs(ctx, a0, n_ctx, masks, stat, pval, n, symmetric);
 
     if (!ctx->batch) ctx->batch = new BatchState();
     BatchState &b = *ctx->batch;
