@@ -51,7 +51,7 @@ typedef enum {
     NAPG_E_LABEL = 4,        /* a categorical value is not an integer in [0, c) */
     NAPG_E_NONFINITE = 5,    /* a non-missing value is +-inf or NaN */
     NAPG_E_TIMEOUT = 6,      /* a bounded device wait gave up */
-    NAPG_E_UNSUPPORTED = 7,  /* valid request outside this build's limits */
+    NAPG_E_UNSUPPORTED = 7,  /* valid request outside the library's limits */
     NAPG_E_BUSY = 8          /* serving queue full / no free slot */
 } napg_status;
 
@@ -72,7 +72,7 @@ typedef enum { NAPG_FP64_PLAIN = 0, NAPG_MIXED = 1 } napg_precision;
 
 typedef enum { NAPG_F32 = 0, NAPG_F64 = 1 } napg_dtype;
 
-/* Maximum levels of a categorical variable in this build. */
+/* Maximum levels of a categorical variable the library accepts. */
 #define NAPG_MAX_LEVELS 64
 
 typedef struct {
