@@ -788,11 +788,13 @@ int orc_run(int test, const double *X, int64_t F, int64_t S, double miss,
     int64_t total = (int64_t)na * ncols;
     int err = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();   /* this call only */
 #else
+    const int nt = 1;
     (void)nthreads;
 #endif
-#pragma omp parallel
+    (void)nt;
+#pragma omp parallel num_threads(nt)
     {
         orc_scratch w;
         int ok = alloc_scratch(&w, S) == ORC_OK;
@@ -836,11 +838,13 @@ int orc_run_pairs(int test, const double *X, int64_t F, int64_t S, double miss,
     }
     int err = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();   /* this call only */
 #else
+    const int nt = 1;
     (void)nthreads;
 #endif
-#pragma omp parallel
+    (void)nt;
+#pragma omp parallel num_threads(nt)
     {
         orc_scratch w;
         int ok = alloc_scratch(&w, S) == ORC_OK;
@@ -1037,11 +1041,13 @@ int orc_effects(int test, const double *X, int64_t F, int64_t S, double miss,
     int64_t total = (int64_t)na * ncols;
     int err = 0;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();   /* this call only */
 #else
+    const int nt = 1;
     (void)nthreads;
 #endif
-#pragma omp parallel
+    (void)nt;
+#pragma omp parallel num_threads(nt)
     {
         orc_scratch w;
         int ok = alloc_scratch(&w, S) == ORC_OK;
