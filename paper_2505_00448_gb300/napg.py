@@ -291,9 +291,10 @@ class Context:
     def run_batch(self, test, masks, vars_a, vars_b=None, out="numpy", outputs=None, sync=True, **opt):
         """One test for several sample contexts (a list of uint8 masks, host or
         device; None = every sample). Returns a list of dict(stat, p, n): numpy
-        arrays (out="numpy"), or device tensors (out="cuda": the batch runs as one
-        captured CUDA graph, stream-ordered; synchronised unless sync=False).
-        `outputs` may supply the per-context dict buffers to write."""
+        arrays (out="numpy"), or device tensors (out="cuda", stream-ordered;
+        synchronised unless sync=False). Either way the batch runs as one captured
+        CUDA graph; host outputs are written to a device region first and copied
+        back. `outputs` may supply the per-context dict buffers to write."""
         torch = self.torch
         t = TESTS[test] if isinstance(test, str) else int(test)
         va, vb = _i32(vars_a), _i32(vars_b)
