@@ -247,37 +247,51 @@ void launch_presort(const void *X, int32_t dtype, int64_t S, int64_t W, const in
 
 // --------------------------------------------------------- rank machinery --
 
-// Per column side of a pair, all in shared memory (W words each, B and P with
-// one extra word so that position == nobs can be queried).
+// Per column side of a pair, all in shared memory (W + 1 words each, so that
+// position == nobs can be queried). The four values a rank needs from one word
+// sit in one 16-byte record, read with a single shared-memory load:
+//   R[w].x = B   co-observed bits of the word's 32 sorted positions
+//   R[w].y = P   exclusive prefix popcount of B at the word
+//   R[w].z = T   tie-group start bits
+//   R[w].w = GS  the bound (position, then co-observed prefix) of the group open
+//                across the word's start; GE[w] likewise at the word's end.
 struct Side {
-    uint32_t *B;     // co-observed bit per sorted position
-    int32_t *P;      // exclusive prefix popcount of B per word
-    uint32_t *T;     // tie-group start bits
-    int32_t *GS, *GE;
+    uint4 *R;
+    int32_t *GE;
     int32_t n;       // observed count of the column
 };
 
 __device__ __forceinline__ int32_t prefix_at(const Side &sd, int32_t x) {
     const int w = x >> 5, l = x & 31;
-    return sd.P[w] + __popc(sd.B[w] & ((1u << l) - 1u));
+    const uint4 r = sd.R[w];
+    return (int32_t)r.y + __popc(r.x & ((1u << l) - 1u));
 }
 
 // Doubled rank 2R = P(gs) + P(ge) + 1 of the position at bit l of word w, from
 // that word's tie-start bits Tw, co-observed bits Bw and prefix Pw; pgs / pge are
 // P at the bounds of the group open across the word's start / end (the side's
 // GS / GE after bounds_to_prefix). Below 2^31 for any S.
-__device__ __forceinline__ uint32_t rank2_word(uint32_t Tw, uint32_t Bw, int32_t Pw, int32_t pgs, int32_t pge,
-                                               int l) {
+// group_bounds gives P(gs) and P(ge) themselves: the co-observed tie-group size
+// is their difference.
+__device__ __forceinline__ void group_bounds(uint32_t Tw, uint32_t Bw, int32_t Pw, int32_t pgs, int32_t pge, int l,
+                                             int32_t &lo, int32_t &hi) {
     const uint32_t le = (l == 31) ? 0xffffffffu : ((2u << l) - 1u);
     const uint32_t m_le = Tw & le, m_gt = Tw & ~le;
-    const int32_t a = m_le ? Pw + __popc(Bw & ((1u << (31 - __clz(m_le))) - 1u)) : pgs;
-    const int32_t b = m_gt ? Pw + __popc(Bw & ((1u << (__ffs(m_gt) - 1)) - 1u)) : pge;
-    return (uint32_t)(a + b + 1);
+    lo = m_le ? Pw + __popc(Bw & ((1u << (31 - __clz(m_le))) - 1u)) : pgs;
+    hi = m_gt ? Pw + __popc(Bw & ((1u << (__ffs(m_gt) - 1)) - 1u)) : pge;
+}
+
+__device__ __forceinline__ uint32_t rank2_word(uint32_t Tw, uint32_t Bw, int32_t Pw, int32_t pgs, int32_t pge,
+                                               int l) {
+    int32_t lo, hi;
+    group_bounds(Tw, Bw, Pw, pgs, pge, l, lo, hi);
+    return (uint32_t)(lo + hi + 1);
 }
 
 __device__ __forceinline__ uint32_t rank2_at(const Side &sd, int32_t p) {
     const int w = p >> 5;
-    return rank2_word(sd.T[w], sd.B[w], sd.P[w], sd.GS[w], sd.GE[w], p & 31);
+    const uint4 r = sd.R[w];
+    return rank2_word(r.z, r.x, (int32_t)r.y, (int32_t)r.w, sd.GE[w], p & 31);
 }
 
 // Build B over the column's sorted positions from the co-observed sample bits,
@@ -288,16 +302,20 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int nw = (sd.n + 31) >> 5;
     for (int w = warp; w <= W; w += nwarps) {
+        if (w >= nw) {                          // past the column's observed positions (warp-uniform)
+            if (lane == 0) sd.R[w].x = 0u;
+            continue;
+        }
         const int p = w * 32 + lane;
         bool b = false;
-        if (w < nw && p < sd.n) {
+        if (p < sd.n) {
             const int s = perm[p];
             b = (co[s >> 5] >> (s & 31)) & 1u;
             // the label of a co-observed position, in sorted order (others are never read)
             if (lab_s && b) lab_s[p] = la[s];
         }
         const uint32_t bits = __ballot_sync(0xffffffffu, b);
-        if (lane == 0) sd.B[w] = bits;
+        if (lane == 0) sd.R[w].x = bits;
     }
     __syncthreads();
     // exclusive scan of popc(B[w]) over w = 0..W (W+1 entries), block-wide:
@@ -306,7 +324,7 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
     const int per = (W + 1 + blockDim.x - 1) / blockDim.x;
     const int w0 = threadIdx.x * per, w1 = min(W + 1, w0 + per);
     int c = 0;
-    for (int w = w0; w < w1; ++w) c += __popc(sd.B[w]);
+    for (int w = w0; w < w1; ++w) c += __popc(sd.R[w].x);
     int incl = c;
     for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
@@ -325,11 +343,11 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
     }
     __syncthreads();
     int run = scan_tmp[32 + warp] + incl - c;
-    for (int w = w0; w < w1; ++w) { sd.P[w] = run; run += __popc(sd.B[w]); }
+    for (int w = w0; w < w1; ++w) { sd.R[w].y = (uint32_t)run; run += __popc(sd.R[w].x); }
     __syncthreads();
     // group bounds (positions) -> co-observed prefix counts at them, in place
     for (int w = threadIdx.x; w <= W; w += blockDim.x) {
-        sd.GS[w] = prefix_at(sd, sd.GS[w]);
+        sd.R[w].w = (uint32_t)prefix_at(sd, (int32_t)sd.R[w].w);
         sd.GE[w] = prefix_at(sd, sd.GE[w]);
     }
     __syncthreads();
@@ -337,11 +355,11 @@ __device__ void build_side(Side &sd, const int32_t *__restrict__ perm, const uin
 
 __device__ void load_side_static(Side &sd, const RankData &rd, int crow, int W) {
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
-        sd.T[w] = rd.tie[(int64_t)crow * rd.W + w];
-        sd.GS[w] = rd.gsw[(int64_t)crow * rd.W + w];
+        sd.R[w].z = rd.tie[(int64_t)crow * rd.W + w];
+        sd.R[w].w = (uint32_t)rd.gsw[(int64_t)crow * rd.W + w];
         sd.GE[w] = rd.gew[(int64_t)crow * rd.W + w];
     }
-    if (threadIdx.x == 0) { sd.T[W] = 0u; sd.GS[W] = 0; sd.GE[W] = 0; }
+    if (threadIdx.x == 0) { sd.R[W].z = 0u; sd.R[W].w = 0u; sd.GE[W] = 0; }
     sd.n = rd.nobs[crow];
 }
 
@@ -356,16 +374,17 @@ __device__ __forceinline__ int64_t block_sum64(int64_t v, int64_t *red) {
     return tot;   // valid in thread 0
 }
 
-// smem layout per side: B[W+1] u32, P[W+1] i32, T[W+1] u32, GS[W+1] i32, GE[W+1] i32
-__device__ Side carve_side(unsigned char *&cur, int W) {
-    Side sd;
-    sd.B = (uint32_t *)cur; cur += (W + 1) * 4;
-    sd.P = (int32_t *)cur; cur += (W + 1) * 4;
-    sd.T = (uint32_t *)cur; cur += (W + 1) * 4;
-    sd.GS = (int32_t *)cur; cur += (W + 1) * 4;
-    sd.GE = (int32_t *)cur; cur += (W + 1) * 4;
+// smem per side: R[W+1] uint4 (carved where cur is 16-byte aligned: the kernels
+// carve every side's records first), GE[W+1] i32
+__device__ __forceinline__ void carve_records(Side &sd, unsigned char *&cur, int W) {
+    sd.R = (uint4 *)cur;
+    cur += (W + 1) * 16;
     sd.n = 0;
-    return sd;
+}
+
+__device__ __forceinline__ void carve_bounds(Side &sd, unsigned char *&cur, int W) {
+    sd.GE = (int32_t *)cur;
+    cur += (W + 1) * 4;
 }
 
 // ----------------------------------------------------------------- Spearman --
@@ -395,8 +414,12 @@ __global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t
         a = (int)(pid / nb); b = (int)(pid - (int64_t)a * nb);
     }
     unsigned char *cur = smem_raw;
+    Side si, sj;
+    carve_records(si, cur, W);
+    carve_records(sj, cur, W);
+    carve_bounds(si, cur, W);
+    carve_bounds(sj, cur, W);
     uint32_t *co = (uint32_t *)cur; cur += (W + 1) * 4;
-    Side si = carve_side(cur, W), sj = carve_side(cur, W);
     const uint32_t *oa = obs_a + (int64_t)a * W, *ob = obs_b + (int64_t)b * W;
     for (int w = threadIdx.x; w < W; w += blockDim.x) co[w] = oa[w] & ob[w];
     const int ci = crow_a[a], cj = crow_b[b];
@@ -408,14 +431,15 @@ __global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t
     build_side(si, perm_i, co, W, scan_tmp);
     build_side(sj, perm_j, co, W, scan_tmp);
     uint64_t sab = 0, saa = 0, sbb = 0;
-    int64_t cnt = 0;
+    int32_t cnt = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     // each warp takes one word of 32 sorted positions of column i at a time
     for (int w = warp; w < ((si.n + 31) >> 5); w += nwarps) {
-        const uint32_t Bw = si.B[w];
+        const uint4 r = si.R[w];
+        const uint32_t Bw = r.x;
         if (Bw == 0u) continue;
-        const uint32_t Tw = si.T[w];
-        const int32_t Pw = si.P[w], pgs = si.GS[w], pge = si.GE[w];
+        const uint32_t Tw = r.z;
+        const int32_t Pw = (int32_t)r.y, pgs = (int32_t)r.w, pge = si.GE[w];
         if ((Bw >> lane) & 1u) {
             const int s = perm_i[w * 32 + lane];
             const int q = pos_j[s];
@@ -486,6 +510,8 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
 // them from the cohort).
 constexpr int kPackShift = 40;
 
+static_assert(kMaxLevels * 12 % 16 == 0, "the level tables keep the records after them 16-byte aligned");
+
 template <int CMAX>
 __host__ __device__ constexpr size_t rank_group_table_bytes(int nwarp) {
     return CMAX ? (size_t)nwarp * CMAX * 32 * 8 : (size_t)nwarp * kMaxLevels * 12;
@@ -509,9 +535,11 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
     unsigned long long *acc = (unsigned long long *)cur;
     unsigned long long *lsum = acc;
     int *lcnt = (int *)(cur + (size_t)nwarp * kMaxLevels * 8);
-    cur += rank_group_table_bytes<CMAX>(nwarp);
+    cur += rank_group_table_bytes<CMAX>(nwarp);      // a multiple of 16 bytes
+    Side sj;
+    carve_records(sj, cur, W);
+    carve_bounds(sj, cur, W);
     uint32_t *co = (uint32_t *)cur; cur += (W + 1) * 4;
-    Side sj = carve_side(cur, W);
     uint8_t *lab_s = SLAB ? (uint8_t *)cur : nullptr;   // (W + 1) * 32 bytes
     const uint32_t *oa = obs_a + (int64_t)a * W, *ob = obs_b + (int64_t)j * W;
     for (int w = threadIdx.x; w < W; w += blockDim.x) co[w] = oa[w] & ob[w];
@@ -536,23 +564,22 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
     for (int w0 = 0; w0 < nwj; w0 += nwarp) {
         const int w = w0 + warp;               // warps past the end still join the warp-wide steps
         const bool inw = w < nwj;
-        const uint32_t Bw = inw ? sj.B[w] : 0u, Tw = inw ? sj.T[w] : 0u;
-        const int32_t Pw = inw ? sj.P[w] : 0, pgs = inw ? sj.GS[w] : 0, pge = inw ? sj.GE[w] : 0;
+        const uint4 r = inw ? sj.R[w] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t Bw = r.x, Tw = r.z;
+        const int32_t Pw = (int32_t)r.y, pgs = (int32_t)r.w, pge = inw ? sj.GE[w] : 0;
         const int p = w * 32 + lane;
-        if (inw && p < sj.n && ((Tw >> lane) & 1u)) {
-            // group starting at p: co-observed size t = P(ge) - P(p)
-            const uint32_t le = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
-            const uint32_t m_gt = Tw & ~le;
-            const int32_t pge_here = m_gt ? Pw + __popc(Bw & ((1u << (__ffs(m_gt) - 1)) - 1u)) : pge;
-            const int64_t t = (int64_t)pge_here - (Pw + __popc(Bw & ((1u << lane) - 1u)));
-            tsum += t * t * t - t;
-        }
         const bool on = inw && ((Bw >> lane) & 1u);
         int g = kMaxLevels;                    // no level
         uint32_t r2 = 0;
         if (on) {
             g = SLAB ? lab_s[p] : la[perm_j[p]];
-            r2 = rank2_word(Tw, Bw, Pw, pgs, pge, lane);
+            int32_t lo, hi;
+            group_bounds(Tw, Bw, Pw, pgs, pge, lane, lo, hi);
+            r2 = (uint32_t)(lo + hi + 1);
+            // sum of (t^3 - t) over co-observed tie groups = sum of (t^2 - 1) over
+            // their co-observed members, t = P(ge) - P(gs)
+            const int64_t t = hi - lo;
+            tsum += t * t - 1;
         }
         if (CMAX) {
             if (on) acc[(warp * CMAX + g) * 32 + lane] += (1ull << kPackShift) + r2;
