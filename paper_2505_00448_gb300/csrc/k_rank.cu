@@ -12,6 +12,8 @@
 //   L = P(gs) values strictly below it and t = P(ge) - P(gs) tied with it,
 // so its doubled rank is 2R = 2L + t + 1 = P(gs) + P(ge) + 1, an integer.
 // Rank sums are accumulated in int64 and are exact.
+#include <type_traits>
+
 #include "napg_internal.cuh"
 
 namespace napg {
@@ -507,17 +509,26 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
 // levels) lanes of one level are grouped by match_any and their leader adds
 // into the warp's table. SLAB: the labels are gathered into shared memory in
 // sorted order while the co-observed bits are built (otherwise the walk reads
-// them from the cohort).
-constexpr int kPackShift = 40;
+// them from the cohort). P32: the slots are 32-bit words, (1 << 24) + 2R, when a
+// lane's totals provably fit (rank_groups_pack32: at most 255 words per warp and
+// 255 (2S + 1) < 2^24), which halves the tables.
+constexpr int kPackShift = 40, kPackShift32 = 24;
 
 static_assert(kMaxLevels * 12 % 16 == 0, "the level tables keep the records after them 16-byte aligned");
 
-template <int CMAX>
+template <int CMAX, bool P32 = false>
 __host__ __device__ constexpr size_t rank_group_table_bytes(int nwarp) {
-    return CMAX ? (size_t)nwarp * CMAX * 32 * 8 : (size_t)nwarp * kMaxLevels * 12;
+    return CMAX ? (size_t)nwarp * CMAX * 32 * (P32 ? 4 : 8) : (size_t)nwarp * kMaxLevels * 12;
 }
 
-template <int CMAX, bool SLAB>
+// whether every lane's per-level count and doubled-rank sum fit the 32-bit slot:
+// a lane sees at most ceil(W / nwarp) positions, each 2R <= 2S + 1
+static bool rank_groups_pack32(int64_t S, int64_t W, int nwarp) {
+    const int64_t per_lane = (W + nwarp - 1) / nwarp;
+    return per_lane < (1 << (32 - kPackShift32)) && per_lane * (2 * S + 1) < ((int64_t)1 << kPackShift32);
+}
+
+template <int CMAX, bool SLAB, bool P32>
 __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd, const uint8_t *__restrict__ lab,
                                                      const int32_t *__restrict__ catrow_a, const int32_t *__restrict__ nlev_a,
                                                      const int32_t *__restrict__ levoff_a, int32_t na,
@@ -532,10 +543,12 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     unsigned char *cur = smem_raw;
     // CMAX > 0: acc[(warp * CMAX + g) * 32 + lane]; CMAX = 0: lsum / lcnt[warp * kMaxLevels + g]
-    unsigned long long *acc = (unsigned long long *)cur;
-    unsigned long long *lsum = acc;
+    using Acc = typename std::conditional<P32, uint32_t, unsigned long long>::type;
+    constexpr int kShift = P32 ? kPackShift32 : kPackShift;
+    Acc *acc = (Acc *)cur;
+    unsigned long long *lsum = (unsigned long long *)cur;
     int *lcnt = (int *)(cur + (size_t)nwarp * kMaxLevels * 8);
-    cur += rank_group_table_bytes<CMAX>(nwarp);      // a multiple of 16 bytes
+    cur += rank_group_table_bytes<CMAX, P32>(nwarp);      // a multiple of 16 bytes
     Side sj;
     carve_records(sj, cur, W);
     carve_bounds(sj, cur, W);
@@ -547,7 +560,7 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
     load_side_static(sj, rd, cj, W);
     const int c = nlev_a[a];
     if (CMAX) {
-        for (int i = threadIdx.x; i < nwarp * CMAX * 32; i += blockDim.x) acc[i] = 0ull;
+        for (int i = threadIdx.x; i < nwarp * CMAX * 32; i += blockDim.x) acc[i] = 0;
     } else {
         for (int i = threadIdx.x; i < nwarp * kMaxLevels; i += blockDim.x) {
             lsum[i] = 0ull;
@@ -582,7 +595,7 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
             tsum += t * t - 1;
         }
         if (CMAX) {
-            if (on) acc[(warp * CMAX + g) * 32 + lane] += (1ull << kPackShift) + r2;
+            if (on) acc[(warp * CMAX + g) * 32 + lane] += ((Acc)1 << kShift) + r2;
         } else {
             // lanes with the same level add their doubled ranks (a warp's sum fits 32 bits)
             const unsigned same = __match_any_sync(0xffffffffu, g);
@@ -600,7 +613,11 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
         // warp g sums level g over warps (per lane), then over lanes
         if (warp < c) {
             unsigned long long v = 0;
-            for (int k = 0; k < nwarp; ++k) v += acc[(k * CMAX + warp) * 32 + lane];
+            for (int k = 0; k < nwarp; ++k) {
+                const Acc e = acc[(k * CMAX + warp) * 32 + lane];
+                v += P32 ? (((unsigned long long)(e >> kShift) << kPackShift) + (e & (((Acc)1 << kShift) - 1)))
+                         : (unsigned long long)e;
+            }
             for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
             if (lane == 0) {
                 rsum[(int64_t)(off + warp) * nb + j] = (int64_t)(v & ((1ull << kPackShift) - 1ull));
@@ -619,12 +636,12 @@ __global__ void __launch_bounds__(1024, SLAB ? 2 : 1) k_rank_groups(RankData rd,
     if (threadIdx.x == 0) tie_term[(int64_t)a * nb + j] = T;
 }
 
-template <int CMAX, bool SLAB>
+template <int CMAX, bool SLAB, bool P32>
 static void launch_rank_groups_t(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a,
                                  const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
                                  const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int64_t *rsum,
                                  int32_t *rcnt, int64_t *tie_term, int threads, size_t smem, cudaStream_t st) {
-    auto kern = k_rank_groups<CMAX, SLAB>;
+    auto kern = k_rank_groups<CMAX, SLAB, P32>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     kern<<<(unsigned)((int64_t)na * nb), threads, smem, st>>>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a,
@@ -641,24 +658,28 @@ void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *c
     const int threads = threads_req > 0 ? threads_req : rank_threads(side);
     const int cmax = max_levels <= 2 ? 2 : max_levels <= 4 ? 4 : max_levels <= 8 ? 8 : 0;
     const int nwarp = threads / 32;
-    const size_t tables = cmax == 2 ? rank_group_table_bytes<2>(nwarp)
-                        : cmax == 4 ? rank_group_table_bytes<4>(nwarp)
-                        : cmax == 8 ? rank_group_table_bytes<8>(nwarp) : rank_group_table_bytes<0>(nwarp);
     const size_t labs = (size_t)(rd.W + 1) * 32;
+    // per-lane slots (cmax > 0): 32-bit when the totals fit and the labels can be staged
+    const size_t tables64 = cmax ? (size_t)nwarp * cmax * 32 * 8 : rank_group_table_bytes<0>(nwarp);
+    const bool p32 = cmax > 0 && rank_groups_pack32(rd.S, rd.W, nwarp) && side + tables64 / 2 + labs <= kRankSmemCap;
+    const size_t tables = p32 ? tables64 / 2 : tables64;
     const bool slab = side + tables + labs <= kRankSmemCap;
     const size_t smem = side + tables + (slab ? labs : 0);
+#define NAPG_RG_ARGS rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b, nb, rsum, rcnt, tie_term, threads, smem, st
 #define NAPG_RG(C)                                                                                                  \
-    (slab ? launch_rank_groups_t<C, true>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b, nb, rsum,   \
-                                          rcnt, tie_term, threads, smem, st)                                        \
-          : launch_rank_groups_t<C, false>(rd, lab, catrow_a, nlev_a, levoff_a, na, crow_b, obs_a, obs_b, nb, rsum,  \
-                                           rcnt, tie_term, threads, smem, st))
+    (p32 ? launch_rank_groups_t<C, true, true>(NAPG_RG_ARGS)                                                        \
+         : slab ? launch_rank_groups_t<C, true, false>(NAPG_RG_ARGS) : launch_rank_groups_t<C, false, false>(NAPG_RG_ARGS))
     switch (cmax) {
         case 2: NAPG_RG(2); break;
         case 4: NAPG_RG(4); break;
         case 8: NAPG_RG(8); break;
-        default: NAPG_RG(0); break;
+        default:
+            if (slab) launch_rank_groups_t<0, true, false>(NAPG_RG_ARGS);
+            else launch_rank_groups_t<0, false, false>(NAPG_RG_ARGS);
+            break;
     }
 #undef NAPG_RG
+#undef NAPG_RG_ARGS
 }
 
 // ------------------------------------------------------ exact Mann-Whitney --

@@ -261,6 +261,24 @@ def test_kruskal_level_classes(napg, levels):
     c.close()
 
 
+def test_rank_groups_wide_level_slots(napg):
+    """60,007 samples: a lane's level totals may pass the 32-bit slot (more than
+    2^24 / (2S + 1) words per warp at 256 threads), so the kernel keeps 64-bit
+    slots; rank sums, counts and tie terms bit-exact for 2, 4 and 8 levels."""
+    for levels in ((2, 2), (3, 4), (5, 8)):
+        coh = synth.small_cohort(150 + levels[1], n_cont=3, n_cat=3, S=60_000 + 7, miss=0.2, ties=True,
+                                 lev_lo=levels[0], lev_hi=levels[1])
+        c = ctx_for(napg, coh)
+        cats, conts = coh["cat"], coh["cont"]
+        compare("kruskal", c.run("kruskal", cats, conts, out="numpy"), oracle_run("kruskal", coh, cats, conts))
+        Xd = coh["X"].astype(np.float64)
+        for a, j in ((cats[0], conts[0]), (cats[2], conts[1])):
+            got = c.debug_integers("kruskal", int(a), int(j))
+            ref = O.pair_ints("kruskal", Xd, NAN, coh["vtype"], coh["nlev"], int(a), int(j))
+            assert np.array_equal(got, ref), (levels, got, ref)
+        c.close()
+
+
 def test_rank_groups_labels_from_cohort(napg):
     """150,000 samples: the sorted labels no longer fit beside the per-pair rank
     arrays in shared memory, so the walk reads them from the cohort."""
