@@ -199,7 +199,12 @@ napg_status napg_adjust(napg_ctx *ctx, int32_t method, const double *p, int64_t 
  * (Sec. 1: per-context association networks). sample_masks[k] is a context mask
  * as in napg_run (host or device); stat[k], pval[k], n[k] are n_a x n_b outputs
  * (each may be NULL). The contexts are processed from one captured CUDA graph
- * per batch shape; results equal n_ctx separate napg_run calls.
+ * per batch shape; results equal n_ctx separate napg_run calls. With host
+ * outputs the graph writes every context's outputs to one device region
+ * (n_ctx x the outputs' bytes, kept by the context for reuse until
+ * napg_destroy), which is then copied back; if that region cannot be allocated
+ * the contexts run one napg_run at a time instead. The A x B form of Pearson and
+ * chi-squared also runs one context at a time. Synchronous with host outputs.
  * Errors: as napg_run. */
 napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
                            int32_t n_ctx, const uint8_t *const *sample_masks,
