@@ -770,7 +770,7 @@ def main():
         coh, tests, desc = make_workload(args.workload, args.scale)
         samples = []
         for k in range(args.warmup + args.steps):
-            r = oracle_sample(coh, tests, budget_s=max(1.5, 60.0 / (args.warmup + args.steps)), seed=k,
+            r = oracle_sample(coh, tests, budget_s=max(0.5, 60.0 / (args.warmup + args.steps)), seed=k,
                              one_thread=False)
             if k >= args.warmup:
                 samples.append(r)
