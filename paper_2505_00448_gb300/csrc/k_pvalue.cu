@@ -42,15 +42,15 @@ __global__ void k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t cap
 }
 
 __global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capacity, double *pval,
-                          const double *bgrat) {
+                          const double *bgrat, sf::LargeATab lat) {
     const int32_t n = min(*count, capacity);
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const PJob j = sorted[t];
         double p;
         switch (j.kind & 0xff) {
-            case kPjCorr: p = sf::corr_p(j.s, j.a, bgrat); break;
-            case kPjT: p = sf::t_two_sided(j.s, j.a, bgrat); break;
-            case kPjF: p = sf::f_sf(j.s, j.a, j.b, bgrat); break;
+            case kPjCorr: p = sf::corr_p(j.s, j.a, bgrat, lat); break;
+            case kPjT: p = sf::t_two_sided(j.s, j.a, bgrat, lat); break;
+            case kPjF: p = sf::f_sf(j.s, j.a, j.b, bgrat, lat); break;
             default: p = sf::chi2_sf(j.s, j.a); break;
         }
         pval[j.idx] = p;
@@ -67,7 +67,26 @@ void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t 
     count_launch(3);
     k_pj_scan<<<1, 32, 0, st>>>(q.hist, offs, cursor);
     k_pj_scatter<<<152 * 8, 256, 0, st>>>(q.jobs, q.count, q.capacity, offs, cursor, sorted);
-    k_pj_eval<<<152 * 16, 128, 0, st>>>(sorted, q.count, q.capacity, pval, q.bgrat);
+    k_pj_eval<<<152 * 16, 128, 0, st>>>(sorted, q.count, q.capacity, pval, q.bgrat, q.lat);
+}
+
+// the (log M, 1/T^2) table of sf::LargeATab, one thread per entry
+__global__ void k_large_a_table(double2 *v, int32_t n2a, int32_t rows) {
+    const int64_t cols = (int64_t)n2a + 1, total = (int64_t)rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols, a2 = t - r * cols;
+        const double a = 0.5 * (double)a2, b = 0.5 * (double)(r + 1);
+        double logM = __longlong_as_double(0x7ff8000000000000LL), invT2 = logM;
+        if (a >= 20.0) sf::large_a_consts(a, b, logM, invT2);
+        v[t] = make_double2(logM, invT2);
+    }
+}
+
+void launch_large_a_table(double2 *v, int32_t n2a, int32_t rows, cudaStream_t st) {
+    const int64_t total = (int64_t)rows * ((int64_t)n2a + 1);
+    if (total <= 0) return;
+    count_launch();
+    k_large_a_table<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, st>>>(v, n2a, rows);
 }
 
 // the table of expansion coefficients c_k(b), 2b = 1..64 (one thread per row)

@@ -31,6 +31,7 @@ void *ws_get(napg_ctx *ctx, Workspace &ws, int slot, size_t bytes, napg_status *
     if (ws.cap[slot] >= bytes) return ws.ptr[slot];
     if (Workspace::plane_slot(slot)) ws.plane_key.valid = false;
     if (slot == Workspace::kBgrat) ws.bgrat_ready = false;
+    if (slot == Workspace::kLargeA) ws.lat_ready = false;
     if (ws.ptr[slot]) {
         cudaFree(ws.ptr[slot]);
         ws.ptr[slot] = nullptr;
@@ -201,6 +202,8 @@ struct PJobBufs {
     int32_t *offs = nullptr, *cursor = nullptr;
 };
 
+constexpr size_t kLargeATabMaxBytes = (size_t)128 << 20;
+
 static napg_status pjobs_setup(napg_ctx *ctx, Workspace &ws, cudaStream_t st, int64_t capacity, bool want,
                                PJobBufs &b) {
     b = PJobBufs();
@@ -226,6 +229,32 @@ static napg_status pjobs_setup(napg_ctx *ctx, Workspace &ws, cudaStream_t st, in
         ws.bgrat_ready = true;
     }
     b.q.bgrat = tab;
+    // (log M, 1/T^2) of the large-a expansion for every degrees-of-freedom value
+    // the cohort's tests can produce (2a <= S, 2b <= levels - 1), once per
+    // workspace. Not while a graph is captured: a replay must not hold a pointer
+    // that a later, larger table frees (the jobs then form the values themselves).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NAPG_CU(ctx, cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+        int32_t maxlev = 0;
+        for (size_t v = 0; v < ctx->coh.nlev.size(); ++v)
+            if (ctx->coh.vtype[v] == 1) maxlev = std::max(maxlev, ctx->coh.nlev[v]);
+        const int32_t rows = std::min(64, std::max(1, maxlev - 1));
+        const int64_t n2a = ctx->coh.S;
+        const size_t bytes = sizeof(double2) * (size_t)rows * (size_t)(n2a + 1);
+        if (n2a > 0 && bytes <= kLargeATabMaxBytes) {
+            double2 *lt = (double2 *)ws_get(ctx, ws, Workspace::kLargeA, bytes, &st_);
+            if (st_) return st_;
+            if (!ws.lat_ready || ws.lat_n2a < n2a || ws.lat_rows < rows) {
+                launch_large_a_table(lt, (int32_t)n2a, rows, st);
+                NAPG_CU(ctx, cudaGetLastError());
+                ws.lat_ready = true;
+                ws.lat_n2a = (int32_t)n2a;
+                ws.lat_rows = rows;
+            }
+            b.q.lat = sf::LargeATab{lt, ws.lat_n2a, ws.lat_rows};
+        }
+    }
     return NAPG_OK;
 }
 

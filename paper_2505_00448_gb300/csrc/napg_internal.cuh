@@ -60,7 +60,7 @@ struct Workspace {
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
         kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kPlShift, kPlVsq,
         kPresortTmp, kBgrat, kUnionE1, kUnionE2, kOutE1, kOutE2, kAdjKeys, kAdjVals, kAdjTmp,
-        kOutStatB, kOutPB, kOutNB, kOutE1B, kOutE2B, kNumSlots
+        kOutStatB, kOutPB, kOutNB, kOutE1B, kOutE2B, kLargeA, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -73,6 +73,9 @@ struct Workspace {
         std::vector<int32_t> vars;
     } plane_key;
     bool bgrat_ready = false;   // kBgrat holds the p-value expansion coefficients
+    // kLargeA holds the sf::LargeATab entries for 2a <= lat_n2a, 2b <= lat_rows
+    bool lat_ready = false;
+    int32_t lat_n2a = 0, lat_rows = 0;
     static bool plane_slot(int s) { return (s >= kTmpA && s <= kTmpE) || s == kExp || s == kPlShift || s == kPlVsq; }
     size_t total() const {
         size_t t = 0;
@@ -208,6 +211,7 @@ namespace napg {
 void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
                        cudaStream_t st);
 void launch_bgrat_table(double *tab, cudaStream_t st);
+void launch_large_a_table(double2 *v, int32_t n2a, int32_t rows, cudaStream_t st);
 void launch_debug_pvalues(int32_t kind, const double *s, const double *a, const double *b, int64_t count, double *p,
                           const double *bgrat, cudaStream_t st);
 // prep

@@ -29,6 +29,7 @@ struct PJobQueue {
     int32_t *hist;      // [kPjBins] jobs per key
     int32_t capacity;
     const double *bgrat;   // sf::bgrat_coefs rows for 2b = 1..64 (NULL: formed per job)
+    sf::LargeATab lat;     // (log M, 1/T^2) on the half-integer grid (lat.v NULL: formed per job)
 };
 
 // bucket of log2(v + 1) clipped to [0, 31]

@@ -291,14 +291,10 @@ __device__ __forceinline__ double log_m_half(double invT2) {
     return s * invT2;
 }
 
-// coef: the table row c_k(b) (see bgrat_coefs), or NULL to form it here
-static __device__ double ibeta_large_a(double a, double b, double x, double y, const double *coef) {
+// log M and 1/T^2 of the expansion below for one (a, b), T = a + (b - 1)/2
+__device__ __forceinline__ void large_a_consts(double a, double b, double &logM, double &invT2) {
     const double T = a + 0.5 * (b - 1.0);
-    const double u = -T * ((x <= 0.5) ? log(x) : log1p(-y));
-    // the result is below the smallest subnormal: p <= 2 e^-u u^(b+41)
-    if (u > 700.0 && u - (b + 41.0) * log(u) > 760.0) return 0.0;
-    const double invT2 = 1.0 / (T * T);
-    double logM;
+    invT2 = 1.0 / (T * T);
     if (b == 0.5) {
         logM = log_m_half(invT2);
     } else {
@@ -306,6 +302,34 @@ static __device__ double ibeta_large_a(double a, double b, double x, double y, c
         const double inv_a = 1.0 / a;
         logM = (a + b - 0.5) * log1p(b * inv_a) - b * log1p((b - 1.0) * 0.5 * inv_a) - b
                + stirling_series(1.0 / (a + b)) - stirling_series(inv_a);
+    }
+}
+
+// large_a_consts on the half-integer grid the test p-values use (a = df/2,
+// b = d1/2): v[(2b - 1) (n2a + 1) + 2a] = {log M, 1/T^2} for 2a = 0..n2a,
+// 2b = 1..rows (entries with a < 20 unused). Formed once by the same function,
+// so a lookup gives the values the job would compute.
+struct LargeATab {
+    const double2 *v;
+    int32_t n2a, rows;
+};
+
+// coef: the table row c_k(b) (see bgrat_coefs), or NULL to form it here;
+// lat: the (log M, 1/T^2) table (lat.v NULL: formed here)
+static __device__ double ibeta_large_a(double a, double b, double x, double y, const double *coef,
+                                       LargeATab lat) {
+    const double T = a + 0.5 * (b - 1.0);
+    const double u = -T * ((x <= 0.5) ? log(x) : log1p(-y));
+    // the result is below the smallest subnormal: p <= 2 e^-u u^(b+41)
+    if (u > 700.0 && u - (b + 41.0) * log(u) > 760.0) return 0.0;
+    double logM, invT2;
+    const double a2 = 2.0 * a, b2 = 2.0 * b;    // b2 is an integer here
+    if (lat.v && a2 <= (double)lat.n2a && b2 <= (double)lat.rows && a2 == floor(a2)) {
+        const double2 e = lat.v[((int64_t)b2 - 1) * ((int64_t)lat.n2a + 1) + (int64_t)a2];
+        logM = e.x;
+        invT2 = e.y;
+    } else {
+        large_a_consts(a, b, logM, invT2);
     }
     int m;             // 2 s
     double Q, th;      // Q = e^u Q(s,u), th = u^s / Gamma(s+1)
@@ -349,14 +373,15 @@ static __device__ double ibeta_large_a(double a, double b, double x, double y, c
 }
 
 // regularized I_x(a,b) with x + y = 1 supplied; bgrat: table of c_k(b) rows
-// for 2b = 1..kBgratRows (or NULL)
-static __device__ double ibeta(double a, double b, double x, double y, const double *bgrat = nullptr) {
+// for 2b = 1..kBgratRows (or NULL); lat: see LargeATab (or empty)
+static __device__ double ibeta(double a, double b, double x, double y, const double *bgrat = nullptr,
+                               LargeATab lat = LargeATab{nullptr, 0, 0}) {
     if (!(a > 0.0) || !(b > 0.0) || isnan(x) || isnan(y)) return nan("");
     if (x <= 0.0) return 0.0;
     if (y <= 0.0) return 1.0;
     if (ibeta_underflows(a, b, y)) return 0.0;
     if (ibeta_large_a_applies(a, b, x))
-        return ibeta_large_a(a, b, x, y, bgrat ? bgrat + ((int)(2.0 * b) - 1) * kBgratTerms : nullptr);
+        return ibeta_large_a(a, b, x, y, bgrat ? bgrat + ((int)(2.0 * b) - 1) * kBgratTerms : nullptr, lat);
     if (x > (a + 1.0) / (a + b + 2.0)) return 1.0 - ibeta_lower(b, a, y, x);
     return ibeta_lower(a, b, x, y);
 }
@@ -400,27 +425,30 @@ static __device__ double gamma_q(double a, double x) {
 }
 
 // two-sided p of Student t with df degrees of freedom
-__device__ __forceinline__ double t_two_sided(double t, double df, const double *bgrat = nullptr) {
+__device__ __forceinline__ double t_two_sided(double t, double df, const double *bgrat = nullptr,
+                                              LargeATab lat = LargeATab{nullptr, 0, 0}) {
     if (isnan(t) || !(df > 0.0)) return nan("");
     if (isinf(t)) return 0.0;
     const double t2 = t * t;
-    return ibeta(0.5 * df, 0.5, df / (df + t2), t2 / (df + t2), bgrat);
+    return ibeta(0.5 * df, 0.5, df / (df + t2), t2 / (df + t2), bgrat, lat);
 }
 
 // p of a correlation coefficient with n observations: I_{1-r^2}((n-2)/2, 1/2)
-__device__ __forceinline__ double corr_p(double r, double n, const double *bgrat = nullptr) {
+__device__ __forceinline__ double corr_p(double r, double n, const double *bgrat = nullptr,
+                                         LargeATab lat = LargeATab{nullptr, 0, 0}) {
     if (isnan(r) || n <= 2.0) return nan("");
     if (fabs(r) >= 1.0) return 0.0;
-    return ibeta(0.5 * (n - 2.0), 0.5, (1.0 - r) * (1.0 + r), r * r, bgrat);
+    return ibeta(0.5 * (n - 2.0), 0.5, (1.0 - r) * (1.0 + r), r * r, bgrat, lat);
 }
 
 // survival function of F(d1, d2)
-__device__ __forceinline__ double f_sf(double F, double d1, double d2, const double *bgrat = nullptr) {
+__device__ __forceinline__ double f_sf(double F, double d1, double d2, const double *bgrat = nullptr,
+                                       LargeATab lat = LargeATab{nullptr, 0, 0}) {
     if (isnan(F) || !(d1 > 0.0) || !(d2 > 0.0)) return nan("");
     if (isinf(F)) return 0.0;
     if (F <= 0.0) return 1.0;
     const double den = d2 + d1 * F;
-    return ibeta(0.5 * d2, 0.5 * d1, d2 / den, d1 * F / den, bgrat);
+    return ibeta(0.5 * d2, 0.5 * d1, d2 / den, d1 * F / den, bgrat, lat);
 }
 
 __device__ __forceinline__ double chi2_sf(double x, double df) {
