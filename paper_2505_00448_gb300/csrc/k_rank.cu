@@ -510,8 +510,8 @@ void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int3
 // into the warp's table. SLAB: the labels are gathered into shared memory in
 // sorted order while the co-observed bits are built (otherwise the walk reads
 // them from the cohort). P32: the slots are 32-bit words, (1 << 24) + 2R, when a
-// lane's totals provably fit (rank_groups_pack32: at most 255 words per warp and
-// 255 (2S + 1) < 2^24), which halves the tables.
+// lane's totals provably fit (rank_groups_pack32: a lane sees at most m < 256
+// positions, and m (2S + 1) < 2^24), which halves the tables.
 constexpr int kPackShift = 40, kPackShift32 = 24;
 
 static_assert(kMaxLevels * 12 % 16 == 0, "the level tables keep the records after them 16-byte aligned");
