@@ -24,8 +24,19 @@ a 20,000-sample cohort (1,600 continuous FP32 + 400 categorical, 25% MCAR):
 per context all-pairs Pearson and chi-squared, each test's 256 contexts as one
 napg_run_batch call (one captured CUDA graph).
 
+--workload small-pearson times single calls on the 200 x 1,000 plain-FP64
+Pearson cohort (p50/p99 latency); --workload paper-sim runs all seven tests on
+the paper's simulated data (uniform values, 4 levels, 10% missing; F, S in
+250..1,000).
+
+--impl reference times the FP64 CPU oracle (the reference of this method) on
+bounded samples of the same workload.
+
+Defaults: 100 timed steps after 10 warm-ups (the p99 over 100 steps).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--precision mixed|fp64] [--workload mixed|ranks]
+                       [--precision mixed|fp64]
+                       [--workload mixed|ranks|batch|serve|small-pearson|paper-sim]
 """
 from __future__ import annotations
 
