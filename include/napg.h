@@ -163,7 +163,10 @@ napg_status napg_run(napg_ctx *ctx, int32_t test, const napg_options *opt,
  *            (z tie-corrected, no continuity correction); ANOVA partial eta^2 =
  *            SSB / (SSB + SSW); KRUSKAL eta^2 = (H - k + 1) / (n - k).
  *   effect2  CHI2 Cramer's V = sqrt(chi2 / (n (min(k_a, k_b) - 1))) over the levels
- *            present in the context; NaN for the other tests.
+ *            present in the context; TTEST the degrees of freedom of the t
+ *            distribution its p-value is taken from (Welch-Satterthwaite nu for
+ *            Welch, n - 2 for Student; NaN where t is NaN or infinite); NaN for the
+ *            other tests.
  * Each is NaN where the statistic is NaN, and where the paper makes it
  * undefined (Sec. 3.5.4, 3.5.5, 3.5.8): V with a single level, Welch's d when
  * both groups are constant, Kruskal-Wallis eta^2 when n <= k.
@@ -329,9 +332,11 @@ uint64_t napg_kernel_launches(void);
  * Limits: 1 <= n_vars <= 256 and 1 <= n_samples <= 8192; larger requests return
  * NAPG_E_UNSUPPORTED without touching the GPU.
  * The first call on each device looks up the array's device address; make that
- * first call before capturing any stream. All calls share the array: calls whose
- * work overlaps on the GPU (other streams, other host threads) race and give
- * wrong results; serialize them. The call returns after its results are written
+ * first call before capturing any stream. Do not use this entry point after
+ * resetting the device (cudaDeviceReset) in the same process: the address
+ * looked up before the reset may no longer be the array's. All calls share the
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and give wrong results; serialize them. The call returns after its results are written
  * (it reads a status word back), with NAPG_E_NONFINITE if a non-missing value is
  * +-inf or NaN, NAPG_E_ARG for bad arguments and NAPG_E_CUDA on a CUDA error. */
 napg_status napg_pearson_fp64_noalloc(const double *X, int32_t n_vars, int32_t n_samples, double missing,

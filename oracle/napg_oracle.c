@@ -931,7 +931,9 @@ int64_t orc_pair_ints(int test, const double *X, int64_t F, int64_t S, double mi
  *     sqrt(chi2 / (n (min(k_a, k_b) - 1))) over the present levels, NaN when a
  *     variable has a single level (Sec. 3.5.4).
  *   t-test: e1 = Cohen's d = (mean_0 - mean_1) / s, s the pooled SD (Student)
- *     or sqrt((v_0 + v_1) / 2) (Welch); NaN when s = 0 (Sec. 3.5.5).
+ *     or sqrt((v_0 + v_1) / 2) (Welch); NaN when s = 0 (Sec. 3.5.5); e2 = the
+ *     degrees of freedom of the t distribution (Welch-Satterthwaite, or
+ *     n0 + n1 - 2), NaN when t is infinite.
  *   Mann-Whitney: e1 = Pearson's r = |z| / sqrt(n), z = (U_0 - n_0 n_1 / 2) / sigma
  *     with the tie-corrected sigma and no continuity correction; NaN when sigma = 0.
  *   ANOVA: e1 = partial eta^2 = SSB / (SSB + SSW) (one-way: the same as eta^2);
@@ -978,6 +980,17 @@ static void effect_pair(const orc_cohort *c, int test, int64_t a, int64_t b, orc
         const double v0 = q0 / (double)(n0 - 1), v1 = q1 / (double)(n1 - 1);
         const double s2 = c->welch ? 0.5 * (v0 + v1) : (q0 + q1) / (double)(n0 + n1 - 2);
         if (s2 > 0.0) *e1 = (m0 - m1) / sqrt(s2);
+        /* second output: the degrees of freedom of the t distribution the
+         * p-value comes from (Sec. 3.5.5): Welch-Satterthwaite for Welch,
+         * n0 + n1 - 2 for Student; none when t is infinite */
+        if (!isinf(st)) {
+            if (c->welch) {
+                const double a0 = v0 / (double)n0, a1 = v1 / (double)n1;
+                *e2 = (a0 + a1) * (a0 + a1) / (a0 * a0 / (double)(n0 - 1) + a1 * a1 / (double)(n1 - 1));
+            } else {
+                *e2 = (double)(n0 + n1 - 2);
+            }
+        }
         return;
     }
     case ORC_MWU: {

@@ -8,8 +8,9 @@
 // ANOVA partial eta^2 = F d1 / (F d1 + d2) (= SSB / (SSB + SSW); 1 when F is
 // infinite); Mann-Whitney r = |U_0 - n_0 n_1 / 2| / sigma / sqrt(n) with the
 // tie-corrected sigma, no continuity correction; Kruskal-Wallis eta^2 =
-// (H - k + 1) / (n - k), NaN when n <= k. The t-test's Cohen's d is formed by
-// the group finalize and the rescue, which hold the group variances.
+// (H - k + 1) / (n - k), NaN when n <= k. The t-test's Cohen's d and its
+// degrees of freedom are formed by the group finalize and the rescue, which
+// hold the group variances.
 //
 // Correction: the tests are the entries with a p-value (the upper triangle
 // i < j of a symmetric matrix, whose diagonal is no test and becomes NaN). The
@@ -79,8 +80,10 @@ __global__ void k_effects(EffectArgs e) {
                 default: break;
             }
         }
+        // the t-test's two outputs (Cohen's d, degrees of freedom) come from the
+        // group finalize and the rescue
         if (e.es1 && e.test != NAPG_TTEST) e.es1[t] = x1;
-        if (e.es2) e.es2[t] = x2;
+        if (e.es2 && e.test != NAPG_TTEST) e.es2[t] = x2;
     }
 }
 

@@ -119,7 +119,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 if (ng == 0) empty = true;
             }
         }
-        double s = dnan(), p = dnan(), es = dnan();
+        double s = dnan(), p = dnan(), es = dnan(), dof = dnan();
         if (f.test == NAPG_ANOVA) {
             if (!empty && k >= 2 && n - k >= 1) {
                 double s1 = 0.0, raw = 0.0;
@@ -170,17 +170,20 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, nu, 0.0, t, kPjT, 0});
                     // Cohen's d over the mean of the two variances
                     es = (m0 - m1) / sqrt(0.5 * (q0 / (double)(n0 - 1) + q1 / (double)(n1 - 1)));
+                    dof = nu;
                 } else {
                     const double df = (double)(n - 2);
                     const double sp2 = (q0 + q1) / df;
                     s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
                     if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, df, 0.0, t, kPjT, 0});
                     es = (m0 - m1) / sqrt(sp2);      // Cohen's d over the pooled SD
+                    dof = df;
                 }
             }
         }
         put(stat, pval, nout, t, s, p, (int32_t)n);
         if (f.es) f.es[t] = es;
+        if (f.es2) f.es2[t] = dof;
     }
 }
 
@@ -572,7 +575,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
         const int ia = (int)(t / ncols), ib = (int)(t - (int64_t)ia * ncols);
         const int va = r.va[ia], vb = symmetric ? r.va[ib] : r.vb[ib];
         const uint32_t *oa = r.obs + (int64_t)va * r.W, *ob = r.obs + (int64_t)vb * r.W;
-        double s = dnan(), p = dnan(), es = dnan();
+        double s = dnan(), p = dnan(), es = dnan(), dof = dnan();
         if (r.test == NAPG_PEARSON) {
             double n = 0, sx = 0, sy = 0, mnx = inf, mxx = -inf, mny = inf, mxy = -inf;
             for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
@@ -681,6 +684,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                         s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
                         p = sf::t_two_sided(s, df);
                         es = (m0 - m1) / sqrt(sp2);
+                        dof = df;
                     }
                 } else if (cst[0] && cst[1]) {
                     // Cohen's d undefined: the two variances sum to zero
@@ -692,10 +696,12 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                     const double nu = se2 * se2 / (e0 * e0 / (n0 - 1.0) + e1 * e1 / (n1 - 1.0));
                     p = sf::t_two_sided(s, nu);
                     es = (m0 - m1) / sqrt(0.5 * (ss[0] / (n0 - 1.0) + ss[1] / (n1 - 1.0)));
+                    dof = nu;
                 }
             }
             put(stat, pval, nout, t, s, p, (int32_t)n);
             if (r.es && r.test == NAPG_TTEST) r.es[t] = es;
+            if (r.es2 && r.test == NAPG_TTEST) r.es2[t] = dof;
         }
         __syncthreads();
     }

@@ -296,14 +296,6 @@ void var_lists(const Cohort &c, const RunArgs &a, bool symmetric, std::vector<in
     off = di.off;
 }
 
-// A pair whose centred sum falls to rel_tol x its raw sum (about the column's
-// in-context mean) is recomputed exactly by the two-pass rescue: for the FP64
-// form only true degeneracy (a constant column/group) reaches 1e-9; for the
-// mixed form the sums carry ~1e-7 relative error, so the statistic keeps
-// |dr| <= 1e-6 only while raw/centred stays small.
-constexpr double kPlainRelTol = 1e-9;
-constexpr double kMixedRelTol = 0.25;
-
 napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a) {
     Cohort &c = a.coh ? *a.coh : ctx->coh;
     if (!c.loaded) return fail(ctx, NAPG_E_ARG, "no cohort loaded");
@@ -424,7 +416,8 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
     prep_stage.end();
 
     RescueArgs rsc{c.X, c.dtype, S, W, ctxw, c.obs, c.lab, d_cat, d_va, symmetric ? nullptr : d_vb, na, nb, t,
-                   a.opt.welch, d_nl, levcnt, d_lo, t == NAPG_TTEST ? a.es1 : nullptr};
+                   a.opt.welch, d_nl, levcnt, d_lo, t == NAPG_TTEST ? a.es1 : nullptr,
+                   t == NAPG_TTEST ? a.es2 : nullptr};
     // Mann-Whitney's per-level counts and tie terms, for its effect size
     const int32_t *eff_rcnt = nullptr;
     const int64_t *eff_tie = nullptr;
@@ -474,7 +467,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
         GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? kMixedRelTol : kPlainRelTol,
-                   vsq, pj.q, g2tot, t == NAPG_TTEST ? a.es1 : nullptr};
+                   vsq, pj.q, g2tot, t == NAPG_TTEST ? a.es1 : nullptr, t == NAPG_TTEST ? a.es2 : nullptr};
         { Stage s_(ctx->trace, st, "finalize_groups"); launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, maxlev, st); }

@@ -23,6 +23,15 @@ constexpr int64_t kMaxRankSamples = 163840;  // per-pair rank state fits shared 
 // Error flags raised by device-side checks (bitwise OR into a device word).
 enum : uint32_t { kErrLabel = 1u, kErrNonfinite = 2u, kErrTimeout = 4u, kErrIndex = 8u };
 
+// A pair whose centred sum falls to rel_tol x its raw sum (about the column's
+// in-context mean) is recomputed exactly by the two-pass rescue: for the FP64
+// form only true degeneracy (a constant column/group) reaches 1e-9; for the
+// mixed form the sums carry ~1e-7 relative error, so the statistic keeps
+// |dr| <= 1e-6 only while raw/centred stays small. Every entry point that
+// finalizes moments uses these two values, so all of them rescue the same pairs.
+constexpr double kPlainRelTol = 1e-9;
+constexpr double kMixedRelTol = 0.25;
+
 // Device-resident cohort (Sec. 3.2): one row per variable.
 struct Cohort {
     int64_t F = 0, S = 0, W = 0;         // variables, samples, 32-bit words per bit row
@@ -256,6 +265,7 @@ struct GroupFin {
     const double *g2tot; // ANOVA, mixed form: [na][nb] sum (x~^2 - v) over all co-observed samples
                          // (then g2 is not read); NULL: per-level g2
     double *es;          // t-test: Cohen's d per pair (NULL: not asked)
+    double *es2;         // t-test: degrees of freedom of the t distribution per pair (NULL: not asked)
 };
 void launch_finalize_groups(const GroupFin &f, double *stat, double *pval, int32_t *nout,
                             int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -272,6 +282,7 @@ struct RescueArgs {
     const uint8_t *lab; const int32_t *catrow; const int32_t *va, *vb; int32_t na, nb; int32_t test;
     int32_t welch; const int32_t *nlev_a; const int32_t *present; const int32_t *levoff;
     double *es;          // t-test: Cohen's d of the rescued pairs (NULL: not asked)
+    double *es2;         // t-test: degrees of freedom of the rescued pairs (NULL: not asked)
 };
 void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
                    double *stat, double *pval, int32_t *nout, int32_t symmetric, int32_t max_levels,

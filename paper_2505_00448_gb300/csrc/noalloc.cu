@@ -12,10 +12,18 @@
 // The array is a file-scope __device__ variable, so every GPU that loads the
 // library holds it until the process exits. Host code cannot use the variable's
 // name as an address; the first call on each device looks the address up with
-// cudaGetSymbolAddress while that device is current, and later calls reuse it.
+// cudaGetSymbolAddress while that device is current, and later calls reuse it
+// as long as the thread's current CUDA context is the one it was looked up in
+// (a call made in another context looks it up again). A device reset
+// (cudaDeviceReset) loads the library's device code again and may keep the
+// context handle, so the entry point must not be used after resetting the
+// device in the same process.
 // Every call shares the one array and leaves its contents behind: the counters
 // that must start at zero are cleared on the stream at the start of each call,
 // and two calls whose work overlaps on the GPU race on the array.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "napg_internal.cuh"
@@ -30,6 +38,24 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[64] = {};                  // per device, filled on first use
+static void *g_noalloc_owner[64] = {};                // the CUDA context each address belongs to
+
+// the calling thread's current driver context (NULL if it cannot be read), to
+// tell a reset device's new context from the one an address was looked up in
+static void *current_context() {
+    static PFN_cuCtxGetCurrent_v4000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuCtxGetCurrent_v4000)p;
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return (void *)c;
+}
 
 // observed bits of every row (missing: == sentinel, or isnan when it is NaN);
 // a non-missing +-inf/NaN raises bit kErrNonfinite in *err
@@ -100,14 +126,18 @@ extern "C" napg_status napg_pearson_fp64_noalloc(const double *X, int32_t n_vars
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return NAPG_E_CUDA;
     void *base = nullptr;
     {
+        // set-up, once per device (and again after a device reset): the array's
+        // device address, looked up with this device current
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        void *owner = current_context();    // NULL before the runtime has bound one to this thread
+        if (!g_noalloc_ptr[dev] || !owner || owner != g_noalloc_owner[dev]) {
             void *ptr = nullptr;
             if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
                 (void)cudaGetLastError();
                 return NAPG_E_CUDA;
             }
             g_noalloc_ptr[dev] = ptr;
+            g_noalloc_owner[dev] = current_context();
         }
         base = g_noalloc_ptr[dev];
     }
@@ -133,7 +163,7 @@ extern "C" napg_status napg_pearson_fp64_noalloc(const double *X, int32_t n_vars
         q.hist = pl.pj_meta + 1;
         q.capacity = (int32_t)pl.pairs;
     }
-    PearsonFin f{pl.Sxy, pl.Sx, pl.Sxx, pl.nn, pl.shift, n_vars, 1e-9, nullptr, q, nullptr};
+    PearsonFin f{pl.Sxy, pl.Sx, pl.Sxx, pl.nn, pl.shift, n_vars, kPlainRelTol, nullptr, q, nullptr};
     launch_finalize_pearson(f, r, p, n, pl.flags, pl.counter, st);
     RescueArgs rsc{X, NAPG_F64, S, pl.W, pl.ctxw, pl.obs, nullptr, nullptr, pl.vars, nullptr, n_vars, n_vars,
                    NAPG_PEARSON, 1, nullptr, nullptr, nullptr};

@@ -207,7 +207,8 @@ class Context:
         call's kernels; pinned arrays let them run asynchronously). `outputs` may
         supply the dict(stat, p, n[, effect, effect2]) buffers to write. Returns
         dict(stat, p, n), plus effect and effect2 (Table 2's effect sizes; Cramer's
-        V for chi-squared) with effects=True.
+        V for chi-squared, the t distribution's degrees of freedom for the t-test)
+        with effects=True.
         """
         torch = self.torch
         t = TESTS[test] if isinstance(test, str) else int(test)

@@ -7,7 +7,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2505_00448_gb300 import synth
-from tests._parity import compare
+from tests._parity import compare, oracle_run, oracle_run_pairs
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -44,7 +44,7 @@ def sampled(test, coh, g, va, vb, rng, k, mask=None, bar=None, **kw):
     ib = np.concatenate([ib, sb.ravel()])
     pa = np.asarray(va)[ia]
     pb = (np.asarray(va) if vb is None else np.asarray(vb))[ib]
-    ref = O.run_pairs(test, coh["X64"], coh["missing"], coh["vtype"], coh["nlev"], pa, pb, ctx=mask, validate=False, **kw)
+    ref = oracle_run_pairs(test, coh, pa, pb, mask=mask, **kw)
     got = {k2: (v.cpu().numpy() if hasattr(v, "cpu") else np.asarray(v))[ia, ib] for k2, v in g.items()}
     compare(test, got, ref, stat_tol=bar)
 
@@ -55,7 +55,7 @@ def test_small_pearson_full(napg):
     c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
     va = coh["cont"]
     g = c.run("pearson", va, out="numpy")
-    compare("pearson", g, O.run("pearson", coh["X"], coh["missing"], coh["vtype"], coh["nlev"], va))
+    compare("pearson", g, oracle_run("pearson", coh, va))
     c.close()
 
 

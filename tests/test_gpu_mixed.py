@@ -14,7 +14,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2505_00448_gb300 import synth
-from tests._parity import compare
+from tests._parity import compare, oracle_run, p_function_agrees as _p_agrees, pair_dof
 
 pytestmark = pytest.mark.gpu
 NAN = float("nan")
@@ -26,20 +26,11 @@ def napg():
     return N
 
 
-def oracle_run(test, coh, va, vb=None, mask=None, **kw):
-    return O.run(test, coh["X"].astype(np.float64), coh["missing"], coh["vtype"], coh["nlev"], va, vb, ctx=mask, **kw)
 
 
-def p_function_agrees(test, g, extra=None):
-    """c14 (i): p_gpu == oracle p-function(stat_gpu) to 1e-12 relative."""
-    s, p, n = np.asarray(g["stat"]), np.asarray(g["p"]), np.asarray(g["n"])
-    ok = np.isfinite(s) & np.isfinite(p) & (p > 1e-300)
-    if test == "pearson":
-        ref = O.corr_p(s[ok], n[ok].astype(float))
-    else:
-        raise NotImplementedError
-    rel = np.abs(p[ok] - ref) / ref
-    assert rel.max(initial=0) < 1e-12, rel.max()
+def p_function_agrees(test, g):
+    """c14 (i) for the correlation tests: p_gpu == oracle p-function(stat_gpu, n)."""
+    return _p_agrees(test, g, {"n": np.asarray(g["n"], dtype=np.float64)})
 
 
 @pytest.mark.parametrize("offset,lognormal", [(0.0, False), (1e4, False), (0.0, True)])
@@ -99,6 +90,41 @@ def test_mixed_anova_ttest(napg, welch):
     bins = cats[:12]
     compare("ttest", c.run("ttest", bins, conts, out="numpy", precision="mixed", welch=welch),
             oracle_run("ttest", coh, bins, conts, welch=int(welch)), stat_tol=("effect", 1e-6))
+    c.close()
+
+
+@pytest.mark.parametrize("welch", [True, False])
+def test_mixed_p_function_on_device_statistics(napg, welch):
+    """c14 part (i) for F, t and chi-squared: each device p-value equals the
+    oracle's p-function at the device's own statistic and degrees of freedom
+    (F: k - 1 and n - k from the present levels and the exact n; Welch t: the
+    device's Welch-Satterthwaite nu, returned as the t-test's second effect
+    output; Student t: n - 2; chi-squared: (k_a - 1)(k_b - 1)), to 1e-12
+    relative. Part (ii) is the end-to-end comparison against the oracle with the
+    p-value's slope over the statistic's difference."""
+    coh = synth.small_cohort(212, n_cont=120, n_cat=30, S=4000 + 13, miss=0.25, lev_lo=2, lev_hi=8, binary_cats=10,
+                             dtype=np.float32, offset=30.0)
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    cats, conts = coh["cat"], coh["cont"]
+    bins = cats[:10]
+    ga = c.run("anova", cats, conts, out="numpy", precision="mixed")
+    assert _p_agrees("anova", ga, pair_dof("anova", coh, cats, conts, ga["n"])) > 1000
+    gt = c.run("ttest", bins, conts, out="numpy", precision="mixed", welch=welch, effects=True)
+    dof = {"df": gt["effect2"]} if welch else {"df": gt["n"].astype(np.float64) - 2}
+    fin = np.isfinite(gt["stat"])
+    assert np.array_equal(np.isfinite(gt["effect2"]), fin)
+    if not welch:
+        assert np.array_equal(gt["effect2"][fin], gt["n"][fin] - 2.0)
+    assert _p_agrees("ttest", gt, dof) > 1000
+    ref_t = oracle_run("ttest", coh, bins, conts, welch=int(welch))
+    compare("ttest", gt, ref_t, stat_tol=("effect", 1e-6))
+    # the device's degrees of freedom against the oracle's (Welch nu moves with
+    # the group variances: 1e-6 relative in the mixed form)
+    okd = np.isfinite(ref_t.dof["df"]) & fin
+    assert np.allclose(gt["effect2"][okd], ref_t.dof["df"][okd], rtol=1e-6, atol=0)
+    gc = c.run("chi2", cats, out="numpy", precision="mixed")
+    assert _p_agrees("chi2", gc, pair_dof("chi2", coh, cats, None, gc["n"])) > 300
     c.close()
 
 

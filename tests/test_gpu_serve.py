@@ -6,7 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2505_00448_gb300 import synth
-from tests._parity import compare
+from tests._parity import compare, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -17,8 +17,6 @@ def napg():
     return N
 
 
-def oracle_run(test, coh, va, vb=None, mask=None, **kw):
-    return O.run(test, coh["X"].astype(np.float64), coh["missing"], coh["vtype"], coh["nlev"], va, vb, ctx=mask, **kw)
 
 
 def make_requests(coh, rng, count):

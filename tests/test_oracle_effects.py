@@ -86,6 +86,25 @@ def test_cohens_d(coh):
                 assert d[ia, ib] == pytest.approx(ref, rel=1e-10)
 
 
+def test_ttest_degrees_of_freedom_match_scipy(coh):
+    """The t-test's second output is the degrees of freedom of its t
+    distribution: SciPy's Welch-Satterthwaite df (Welch) and n0 + n1 - 2
+    (Student) on the arrays left after deletion; and p is the two-sided t tail
+    at that df."""
+    X = coh["X"]
+    bins = coh["cat"][:2]
+    for welch in (0, 1):
+        _, df = O.effects("ttest", X, NAN, coh["vtype"], coh["nlev"], bins, coh["cont"], welch=welch)
+        t, p, _ = O.run("ttest", X, NAN, coh["vtype"], coh["nlev"], bins, coh["cont"], welch=welch)
+        for ia, a in enumerate(bins):
+            for ib, j in enumerate(coh["cont"]):
+                lab, x = deleted(X[a], X[j])
+                g0, g1 = x[lab == 0], x[lab == 1]
+                ref = st.ttest_ind(g0, g1, equal_var=not welch)
+                assert df[ia, ib] == pytest.approx(float(ref.df), rel=1e-12)
+                assert p[ia, ib] == pytest.approx(2 * st.t.sf(abs(t[ia, ib]), float(ref.df)), rel=1e-10)
+
+
 def test_welch_d_equals_student_d_for_equal_groups():
     rng = np.random.default_rng(5)
     lab = np.array([0] * 30 + [1] * 30, float)

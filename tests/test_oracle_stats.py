@@ -349,6 +349,64 @@ def test_kruskal_vs_scipy_and_mwu_identity():
     assert np.allclose(H, z * z, rtol=1e-8)
 
 
+def _exact_kruskal(lab, y, k):
+    """Kruskal-Wallis H (Sec. 3.5.8) in exact rational arithmetic: tie-averaged
+    ranks as halves of integers, H0 = 12/(n(n+1)) sum R_g^2/n_g - 3(n+1), divided
+    by 1 - sum(t^3 - t)/(n^3 - n)."""
+    from fractions import Fraction as Fr
+    n = len(y)
+    order = np.argsort(y, kind="stable")
+    ys = y[order]
+    twice_rank = np.empty(n, dtype=np.int64)      # 2R = (first + last) positions, 1-based
+    tie = 0
+    i = 0
+    while i < n:
+        j = i
+        while j + 1 < n and ys[j + 1] == ys[i]:
+            j += 1
+        twice_rank[order[i:j + 1]] = (i + 1) + (j + 1)
+        t = j - i + 1
+        tie += t ** 3 - t
+        i = j + 1
+    h0 = Fr(0)
+    for g in range(k):
+        sel = lab == g
+        R2 = int(twice_rank[sel].sum())           # 2 R_g, an exact integer
+        h0 += Fr(R2 * R2, 4 * int(sel.sum()))
+    h0 = Fr(12, n * (n + 1)) * h0 - 3 * (n + 1)
+    return h0 / (1 - Fr(tie, n ** 3 - n))
+
+
+def test_kruskal_large_n_small_h_against_exact_rationals():
+    """At n = 50,000 with groups from one distribution (H of order 1, the sums
+    R_g^2 / n_g agreeing to ~1e-10 relative before the 3(n+1) subtraction), with
+    heavy ties: the oracle's H equals the exact rational H to 1e-12 relative; for
+    two groups the same holds for the Mann-Whitney z^2 without continuity
+    correction, which equals H."""
+    rng = np.random.default_rng(27)
+    n = 50_000
+    y = np.round(rng.normal(size=n), 1)          # about 70 distinct values: ties everywhere
+    for k in (4, 2):
+        lab = rng.integers(0, k, n).astype(float)
+        X = np.array([lab, y])
+        vt = np.array([1, 0], np.uint8)
+        nl = np.array([k, 0], np.int32)
+        H, _, nn = O.run("kruskal", X, NAN, vt, nl, [0], [1])
+        assert nn[0, 0] == n
+        Hx = _exact_kruskal(lab, y, k)
+        assert 0.0 < float(Hx) < 20.0
+        assert abs(H[0, 0] - float(Hx)) <= 1e-12 * float(Hx), (k, H[0, 0], float(Hx))
+        if k == 2:
+            U, pu, _ = O.run("mwu", X, NAN, vt, nl, [0], [1], mwu_mode=2, mwu_cc=0)
+            from fractions import Fraction as Fr
+            n0 = int((lab == 0).sum())
+            n1 = n - n0
+            # z^2 = (U0 - n0 n1 / 2)^2 / sigma^2 with the tie-corrected variance,
+            # exactly equal to H
+            assert abs(st.norm.isf(pu[0, 0] / 2) ** 2 - float(Hx)) <= 1e-8 * float(Hx)
+            assert Fr(U[0, 0]) * 2 == int(round(2 * U[0, 0]))
+
+
 def test_kruskal_mwu_edge_rules():
     lab = np.array([0, 0, 0, 1, 1, 1], float)
     tied = np.array([2, 2, 2, 2, 2, 2], float)
