@@ -323,22 +323,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 
 // --------------------------------------------------- stacked contraction --
 //
-// A 0/1 plane (observed mask or one-hot levels) against the five planes M, Xh,
-// Xl, Dh, Dl of kSV B variables stacked into one operand of N = 5 kSV rows:
-// one MMA per 16 samples reads the A tile once for all five sums (five separate
-// N = kSV products would read it five times, more shared-memory traffic than
-// the tensor core's operand path carries). All five blocks of the accumulator
-// restart every chunk and are drained: counts as exact integers, the hi sums by
-// TwoSum into float-float running sums, the lo sums into the low parts.
+// A 0/1 plane (observed mask or one-hot levels) against the planes M, Xh, Xl,
+// Dh, Dl of SV B variables stacked into one operand of N = NPL SV rows: one MMA
+// per 16 samples reads the A tile once for all the sums. The MMA spans a pair
+// of CTAs on two SMs (cta_group::2, M = 256): each CTA loads 128 rows of A and
+// half of the stacked B rows (the first half in the even CTA; with an odd
+// number of planes the middle plane is split between the two), so each SM
+// streams half of B per sample and the tensor core is fed at its full rate. The
+// even CTA's full barrier counts the bytes of both CTAs (the odd CTA's copies
+// signal it across the pair); MMA commits arrive in both CTAs; each CTA's
+// epilogue warps drain its own 128 accumulator rows and report to the even
+// CTA's drain barrier. All blocks of the accumulator restart every chunk and
+// are drained: counts as exact integers, the hi sums by TwoSum into float-float
+// running sums, the lo sums into the low parts. The sums drained here are
+// centred (x - c, (x - c)^2 - v) or exact counts, so a partial sum random-walks
+// instead of growing with the chunk, and chunks of 16 K-blocks keep the FP32
+// accumulation error far below the statistics' bars.
 // SV = B variables per tile (a multiple of 16: the epilogue's two halves read
-// 8-column groups); the autotuner picks 32 or 48 per shape.
-constexpr int kSGroup = 16;        // A tiles per rasterisation group
+// 8-column groups); the autotuner picks the width per shape.
+constexpr int kSGroup = 8;         // A tile pairs per rasterisation group
 
 struct StackParams {
     CUtensorMap mapA;              // 0/1 plane, box 64 x 128
-    CUtensorMap mapB[5];           // M, Xh, Xl, Dh[, Dl] of the B variables, box 64 x SV
+    CUtensorMap mapB[5];           // the B planes in role order, box 64 x SV
+    CUtensorMap mapSplit;          // the plane split between the pair (odd plane counts), box 64 x SV/2
     int rowsA, rowsB;              // valid rows of A and B
-    int tilesA, tilesB;
+    int tilesA, tilesB;            // 128-row A tiles (a pair takes two), SV-row B tiles
     int nkb, chunk;                // K-blocks, K-blocks per drain
     int32_t *out_n;                // counts      [rowsA][ld] (or transposed)
     double *out_s1, *out_s2;       // sum x~, sum (x~^2 - v)
@@ -347,6 +357,28 @@ struct StackParams {
     const int8_t *exp1, *exp2;     // per-B-row scale exponents of X~ and D
     uint32_t *err;
 };
+
+// B rows of the stack held by CTA `rank` of the pair: the even CTA holds stacked
+// rows [0, N/2), the odd one [N/2, N). Loads the CTA's half for K-block x of B
+// tile J into `bh`, counting the bytes on the barrier at cluster address `bar`.
+template <int NPL, int SV>
+__device__ __forceinline__ void load_b_half(const StackParams &P, uint32_t rank, uint8_t *bh, uint32_t bar, int x,
+                                            int J) {
+    constexpr int N = NPL * SV, HALF = N / 2;
+    constexpr int PS = HALF / SV;              // plane holding stacked row HALF
+    constexpr int OS = HALF % SV;              // its rows in the even CTA (0: a plane boundary)
+    const int y = J * SV;
+    if (rank == 0) {
+#pragma unroll
+        for (int p = 0; p < PS; ++p) tma_load_2d_pair(bh + p * SV * 128, &P.mapB[p], bar, x, y);
+        if (OS) tma_load_2d_pair(bh + PS * SV * 128, &P.mapSplit, bar, x, y);
+    } else {
+        if (OS) tma_load_2d_pair(bh, &P.mapSplit, bar, x, y + OS);
+#pragma unroll
+        for (int p = (OS ? PS + 1 : PS); p < NPL; ++p)
+            tma_load_2d_pair(bh + (p * SV - HALF) * 128, &P.mapB[p], bar, x, y);
+    }
+}
 
 // NPL planes stacked, playing the roles ROLE0, ROLE0 + 1, ... of the list (M,
 // Xh, Xl, Dh, Dl): all five (counts and both sums), the first three (counts and
@@ -360,16 +392,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
     constexpr bool kHasN = ROLE0 == 0;
     constexpr bool kHasS1 = ROLE0 <= 1 && ROLE0 + NPL > 1;
     constexpr bool kHasS2 = ROLE0 + NPL > 3;
-    constexpr int kSV = SV;
     constexpr int kSPerThread = SV / 2;
     static_assert(SV % 16 == 0, "SV");
+    constexpr int kSN = NPL * SV;                 // MMA N
+    constexpr int HALF = kSN / 2;                 // B rows per CTA
     constexpr int A_BYTES = kTM * kKB * 2;
-    constexpr int BP_BYTES = kSV * kKB * 2;
-    constexpr int STAGE_BYTES = A_BYTES + NPL * BP_BYTES;
-    constexpr int kSN = NPL * kSV;    // MMA N
-    static_assert(BP_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0, "8-row swizzle atoms stay 1024-B aligned");
+    constexpr int BH_BYTES = HALF * kKB * 2;
+    constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
+    static_assert(BH_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0 && (SV / 2 * 128) % 1024 == 0,
+                  "8-row swizzle atoms stay 1024-B aligned");
     static_assert(kSN % 16 == 0 && kSN <= 256, "N");
-    constexpr uint32_t IDESC = idesc_f16_f32(kTM, kSN);
+    constexpr uint32_t IDESC = idesc_f16_f32(2 * kTM, kSN);
     constexpr int BUF = 256;       // tensor-memory columns per accumulator buffer (kSN used)
 
     extern __shared__ uint8_t smem_raw[];
@@ -382,89 +415,101 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
     uint32_t *tslot = (uint32_t *)(mdone + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // grouped rasterisation: within a group of kSGroup A tiles, consecutive CTAs
-    // step through the A tiles of the group, then the B tiles, so a wave of
-    // resident CTAs covers a block of both operands and streams each from HBM
-    // about once
-    int I, J;
+    const uint32_t rank = cluster_rank();
+    // grouped rasterisation over tile pairs: within a group of kSGroup A tile
+    // pairs, consecutive pairs step through the group's A tiles, then the B
+    // tiles, so a wave of resident pairs covers a block of both operands and
+    // streams each from HBM about once
+    int I2, J;
     {
+        const int tilesA2 = (P.tilesA + 1) / 2;
+        const int cl = blockIdx.x >> 1;
         const int per_group = kSGroup * P.tilesB;
-        const int g = blockIdx.x / per_group, r = blockIdx.x - g * per_group;
-        const int gsz = min(kSGroup, P.tilesA - g * kSGroup);
+        const int g = cl / per_group, r = cl - g * per_group;
+        const int gsz = min(kSGroup, tilesA2 - g * kSGroup);
         J = r / gsz;
-        I = g * kSGroup + (r - J * gsz);
+        I2 = g * kSGroup + (r - J * gsz);
     }
     const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 16); }
         mbar_init(mdone, 1);
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, 512);
+    if (warp == 1) tmem_alloc_pair(tslot, 512);
     fence_before_sync();
     __syncthreads();
+    cluster_sync();                // both CTAs' barriers set up and tensor memory allocated
     fence_after_sync();
     const uint32_t tbase = *tslot;
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
-        const uint32_t leader = lane == 0;
-        if (leader) {
+        if (lane == 0) {
             prefetch_tmap(&P.mapA);
             for (int p = 0; p < NPL; ++p) prefetch_tmap(&P.mapB[p]);
+            if (NPL & 1) prefetch_tmap(&P.mapSplit);
+            const uint32_t full0 = cluster_addr(&full[0], 0);
+            int issued = 0;
+            for (int kb = 0; kb < P.nkb; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
+                const uint32_t bar = full0 + (uint32_t)(s * 8);
+                if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);   // both CTAs' bytes
+                uint8_t *st = smem + s * STAGE_BYTES;
+                tma_load_2d_pair(st, &P.mapA, bar, kb * kKB, (2 * I2 + (int)rank) * kTM);
+                load_b_half<NPL, SV>(P, rank, st + A_BYTES, bar, kb * kKB, J);
+                issued = kb + 1;
+            }
+            // the copies of both CTAs are counted on the even CTA's barriers: it
+            // waits for the last ones before the pair leaves (the MMA warp has
+            // waited for all the others)
+            if (rank == 0)
+                for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+                    mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
         }
-        int issued = 0;
-        for (int kb = 0; kb < P.nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
-            mbar_arrive_expect_tx_by(&full[s], STAGE_BYTES, leader);
-            uint8_t *st = smem + s * STAGE_BYTES;
-            tma_load_2d_by(st, &P.mapA, &full[s], kb * kKB, I * kTM, leader);
-#pragma unroll
-            for (int p = 0; p < NPL; ++p)
-                tma_load_2d_by(st + A_BYTES + p * BP_BYTES, &P.mapB[p], &full[s], kb * kKB, J * kSV, leader);
-            issued = kb + 1;
-        }
-        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-            mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
+        __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        const uint32_t leader = lane == 0;
-        const uint64_t dbase = sdesc_sw128(smem_u32(smem));
-        int kb = 0;
-        bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            const int b = c & 1;
-            if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
-            fence_after_sync();
-            const int kb_end = min(P.nkb, (c + 1) * P.chunk);
-            const int kb_chunk0 = kb;
-            const uint32_t dcol = tbase + (uint32_t)(b * BUF);
-            for (; kb < kb_end; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+        if (rank == 0 && lane == 0) {
+            const uint64_t dbase = sdesc_sw128(smem_u32(smem));
+            int kb = 0;
+            bool ok = true;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                const int b = c & 1;
+                if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
                 fence_after_sync();
-                const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
+                const int kb_end = min(P.nkb, (c + 1) * P.chunk);
+                const int kb_chunk0 = kb;
+                const uint32_t dcol = tbase + (uint32_t)(b * BUF);
+                for (; kb < kb_end; ++kb) {
+                    const int s = kb % STAGES;
+                    if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+                    fence_after_sync();
+                    const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
 #pragma unroll
-                for (int k = 0; k < kKB / 16; ++k)
-                    mma_f16_by(dcol, ds + (uint64_t)(2 * k), ds + (uint64_t)((A_BYTES >> 4) + 2 * k), IDESC,
-                               (kb == kb_chunk0 && k == 0) ? 0u : 1u, leader);
-                mma_commit_by(&empty[s], leader);
+                    for (int k = 0; k < kKB / 16; ++k)
+                        mma_f16_pair(dcol, ds + (uint64_t)(2 * k), ds + (uint64_t)((A_BYTES >> 4) + 2 * k), IDESC,
+                                     (kb == kb_chunk0 && k == 0) ? 0u : 1u);
+                    mma_commit_pair(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit_pair(&tfull[b]);
             }
-            if (!ok) break;
-            mma_commit_by(&tfull[b], leader);
+            mma_commit_pair(mdone);
         }
-        mma_commit_by(mdone, leader);
+        __syncwarp();
         mbar_wait(mdone, 0, P.err);
     } else {
         // ---------------------------------------------------------- epilogue
         const int ew = warp - 2;               // 0..7
         const int q = warp & 3;                // TMEM lane quadrant this warp may access
-        const int h = ew >> 2;                 // which half of the kSV variables
+        const int h = ew >> 2;                 // which half of the SV variables
         const int row = q * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        const uint32_t tempty0 = cluster_addr(&tempty[0], 0);
         constexpr int K2 = kSPerThread / 2;
         int32_t cnt[kSPerThread];
         uint64_t s1h[K2], s1l[K2], s2h[K2], s2l[K2];    // packed float-float sums
@@ -484,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
 #pragma unroll
                 for (int g = 0; g < kSPerThread / 8; ++g) {
                     uint32_t t8[8];
-                    tmem_ld8(col0 + (uint32_t)(p * kSV + g * 8), t8);
+                    tmem_ld8(col0 + (uint32_t)(p * SV + g * 8), t8);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) r[g * 8 + k] = t8[k];
                 }
@@ -506,10 +551,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             }
             fence_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
+            if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)(b * 8));
         }
         if (ok) {
-            const int gi = I * kTM + row;
+            const int gi = (2 * I2 + (int)rank) * kTM + row;
             if (gi < P.rowsA) {
 #pragma unroll
                 for (int k = 0; k < K2; ++k) {
@@ -520,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
                     unpk2(s2l[k], d0, d1);
 #pragma unroll
                     for (int e2 = 0; e2 < 2; ++e2) {
-                        const int col = J * kSV + h * kSPerThread + 2 * k + e2;
+                        const int col = J * SV + h * kSPerThread + 2 * k + e2;
                         if (col < P.rowsB) {
                             const int64_t o = P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col;
                             if (kHasN) P.out_n[o] = cnt[2 * k + e2];
@@ -536,8 +581,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
     }
     fence_before_sync();
     __syncthreads();
+    cluster_sync();                // neither CTA leaves while the pair still reads its shared memory
     fence_after_sync();
-    if (warp == 1) tmem_dealloc(tbase, 512);
+    if (warp == 1) tmem_dealloc_pair(tbase, 512);
 }
 
 // ------------------------------------------------------------ plane prep --
@@ -799,16 +845,28 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
 
 template <int NPL, int SV, int ROLE0>
 static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
-    constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * SV * kKB * 2;
-    constexpr int STAGES = (220 * 1024) / STAGE_BYTES > 6 ? 6 : (220 * 1024) / STAGE_BYTES;
+    constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * SV / 2 * kKB * 2;
+    constexpr int STAGES = (220 * 1024) / STAGE_BYTES > 8 ? 8 : (220 * 1024) / STAGE_BYTES;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
     auto kern = k_umma_stacked<NPL, SV, STAGES, ROLE0>;
     NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int tiles = P.tilesA * P.tilesB;
-    if (tiles == 0) return NAPG_OK;
+    const int pairs = ((P.tilesA + 1) / 2) * P.tilesB;
+    if (pairs == 0) return NAPG_OK;
+    // pairs of CTAs on two SMs (one cluster per tile pair)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     count_launch();
-    kern<<<tiles, kThreads, smem, st>>>(P);
-    NAPG_CU(ctx, cudaGetLastError());
+    NAPG_CU(ctx, cudaLaunchKernelEx(&cfg, kern, P));
     return NAPG_OK;
 }
 
@@ -826,9 +884,13 @@ static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *cons
                                   int64_t S_pad, int kind, cudaStream_t st) {
     auto run = [&](int choice) -> napg_status {
         const int sv = kStackWidths[set][choice];
-        for (int k = 0; k < kStackPlaneCount[set]; ++k)
+        const int npl = kStackPlaneCount[set];
+        for (int k = 0; k < npl; ++k)
             if (!make_map(&P.mapB[k], pb[k], rows_b_pad, S_pad, sv))
                 return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        // an odd number of planes: the middle one is split between the pair
+        if ((npl & 1) && !make_map(&P.mapSplit, pb[npl / 2], rows_b_pad, S_pad, sv / 2))
+            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         P.tilesB = (P.rowsB + sv - 1) / sv;
         if (set == kStackAll) return sv == 48 ? launch_stacked_sv<5, 48, 0>(ctx, P, st) : launch_stacked_sv<5, 32, 0>(ctx, P, st);
         if (set == kStackNS1) return sv == 64 ? launch_stacked_sv<3, 64, 0>(ctx, P, st) : launch_stacked_sv<3, 48, 0>(ctx, P, st);
@@ -916,14 +978,14 @@ static napg_status prep_onehot(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStre
     return NAPG_OK;
 }
 
-// chunk lengths (K-blocks of 64 samples between drains)
-// K-blocks between drains: Sxy of correlated pairs has same-sign terms and the
-// accumulator's per-instruction rounding adds up within a chunk, so its hi*hi
-// sum is drained every K-block; the other sums (n-weighted shifts, centred
-// squares, group sums) are far from the bar and drain every 4 (the epilogue's
-// float-float work then stays below the MMA time).
+// K-blocks (of 64 samples) between drains: Sxy of correlated pairs has
+// same-sign terms and the accumulator's per-instruction rounding adds up within
+// a chunk, so its hi*hi sum is drained every K-block; the stacked sums (counts,
+// centred x~ and centred squares, per variable or per level) random-walk, are
+// far from the bar, and drain every 16 (a drain of the stacked accumulator
+// takes longer than 4 K-blocks of MMAs, so shorter chunks would stall the pair).
 constexpr int kChunkSxy = 1;
-constexpr int kChunkOther = 4;
+constexpr int kChunkStacked = 16;
 
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
@@ -968,7 +1030,7 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
         P.rowsA = nv; P.rowsB = nv; P.tilesA = T;
-        P.nkb = nkb; P.chunk = kChunkOther;
+        P.nkb = nkb; P.chunk = kChunkStacked;
         P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
@@ -989,7 +1051,7 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     StackParams P{};
     if (!make_map(&P.mapA, H, hrows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
     P.rowsA = R; P.rowsB = nb; P.tilesA = (int)(hrows / kTM);
-    P.nkb = (int)(S_pad / kKB); P.chunk = kChunkOther;
+    P.nkb = (int)(S_pad / kKB); P.chunk = kChunkStacked;
     P.out_n = gn; P.out_s1 = g1; P.out_s2 = g2; P.ld = nb; P.out_transpose = 0;
     P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
     if (!g2tot) {
@@ -1013,7 +1075,7 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     StackParams Q{};
     if (!make_map(&Q.mapA, O, orows, S_pad, kTM)) return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
     Q.rowsA = na; Q.rowsB = nb; Q.tilesA = (int)(orows / kTM);
-    Q.nkb = (int)(S_pad / kKB); Q.chunk = kChunkOther;
+    Q.nkb = (int)(S_pad / kKB); Q.chunk = kChunkStacked;
     Q.out_n = nullptr; Q.out_s1 = nullptr; Q.out_s2 = g2tot; Q.ld = nb; Q.out_transpose = 0;
     Q.exp1 = cp.sexp; Q.exp2 = cp.texp; Q.err = ctx->dev_err;
     const void *qb[2] = {cp.Dh, cp.Dl};
