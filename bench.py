@@ -514,7 +514,8 @@ def serve_main(args, world, rank, local_rank):
 # ------------------------------------------------------------ batch workload --
 
 def batch_main(args, world, rank, local_rank):
-    """256 sample contexts per test in one napg_run_batch call each (replicas per GPU)."""
+    """256 sample contexts per test in one napg_run_batch call each; under torchrun
+    the contexts are dealt to the ranks block-cyclically (each rank runs its share)."""
     import torch
     dist = None
     if world > 1:
@@ -538,13 +539,14 @@ def batch_main(args, world, rank, local_rank):
     ctx.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
     dev = torch.device("cuda", device)
     dmask = torch.from_numpy(masks).to(dev)
-    mlist = [dmask[k] for k in range(K)]
+    mine = D.shard_blocks(K, world, rank)          # this rank's contexts (all of them at N = 1)
+    mlist = [dmask[k] for k in mine]
     outs = {}
     for test, va in tests:
         n = len(va)
         outs[test] = [{"stat": torch.empty((n, n), dtype=torch.float64, device=dev),
                        "p": torch.empty((n, n), dtype=torch.float64, device=dev),
-                       "n": torch.empty((n, n), dtype=torch.int32, device=dev)} for _ in range(K)]
+                       "n": torch.empty((n, n), dtype=torch.int32, device=dev)} for _ in mine]
 
     def step():
         ctx.release_cache()
@@ -586,8 +588,8 @@ def batch_main(args, world, rank, local_rank):
     ms_step = D.max_over_ranks(ms_step, dist)      # the slowest rank sets the time
     step_ms = sorted(a.elapsed_time(b) for a, b in per_step)
     pairs_ctx = {t: len(va) * (len(va) - 1) // 2 for t, va in tests}
-    pairs_step = K * sum(pairs_ctx.values())
-    value = D.weak_scaling_value(pairs_step, ms_step / 1000.0, world)
+    pairs_step = K * sum(pairs_ctx.values())       # every context of the batch, over all ranks
+    value = D.split_value(pairs_step, ms_step / 1000.0)
 
     # accuracy of the timed outputs on a few contexts (random pairs) against the oracle
     accuracy = None
@@ -670,10 +672,12 @@ def batch_main(args, world, rank, local_rank):
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f16x2-split/f32-acc/f64" if prec == "mixed" else "f64",
                 "data": "synthetic",
                 "config": {"workload": desc, "precision": prec, "contexts": int(K), "pairs_per_step": pairs_step,
+                           "parallelism": (f"contexts dealt block-cyclically over {world} GPUs" if world > 1
+                                           else "1 GPU"),
                            "context_samples_total": int(masks.sum()),
                            "l2": "cohort (160 MB) and outputs (13.9 GB) larger than L2: no flush between steps",
                            "first_call_s": t_first, "autotuned": ctx.tune_read(), "step_ms_p50": statistics.median(step_ms),
@@ -856,7 +860,11 @@ def main():
         for test, va, vb in tests:
             if per_test_events is not None:
                 per_test_events[test][0].record(stream)
-            ctx.run(test, va, vb, outputs=outs[test], sync=False, precision=prec)
+            if world > 1:
+                # this rank's part of the split call (napg_run_part): its output rows' pairs
+                ctx.run_part(test, va, vb, part=rank, nparts=world, outputs=outs[test], precision=prec)
+            else:
+                ctx.run(test, va, vb, outputs=outs[test], sync=False, precision=prec)
             if per_test_events is not None:
                 per_test_events[test][1].record(stream)
 
@@ -896,8 +904,27 @@ def main():
     per_test_ms = {t: [pe[t][0].elapsed_time(pe[t][1]) for pe in step_events] for t, _, _ in tests}
     first, last = tests[0][0], tests[-1][0]
     step_ms = sorted(pe[first][0].elapsed_time(pe[last][1]) for pe in step_events)
-    pairs_step = sum(pair_count(t, va, vb) for t, va, vb in tests)
-    value = D.weak_scaling_value(pairs_step, ms_step / 1000.0, world)
+    pairs_step = sum(pair_count(t, va, vb) for t, va, vb in tests)   # the whole call, over all ranks
+    value = D.split_value(pairs_step, ms_step / 1000.0)
+    # the split's outputs, gathered once after the timed region: every entry of
+    # every test must have been written by exactly its owner
+    split_check = None
+    if dist:
+        for o in outs.values():
+            o["n"].fill_(-1)
+        step()
+        torch.cuda.synchronize()
+        complete = True
+        for test, va, vb in tests:
+            loc = outs[test]["n"]
+            allr = [torch.empty_like(loc) for _ in range(world)]
+            dist.all_gather(allr, loc)
+            if rank == 0:
+                parts = [a.cpu().numpy() for a in allr]
+                na, nb = loc.shape
+                got = D.stitch(parts, na, nb, vb is None)
+                complete &= bool((got >= 0).all())
+        split_check = {"gathered": True, "every_entry_written_by_its_owner": complete}
 
     # e2e through the public API with host buffers: upload + run + download per step
     e2e = None
@@ -990,10 +1017,13 @@ def main():
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f16x2-split/f32-acc/f64" if prec == "mixed" else "f64",
                 "data": "synthetic",
                 "config": {"workload": desc, "precision": prec, "pairs_per_step": pairs_step,
+                           "parallelism": (f"split over {world} GPUs: napg_run_part, output rows in blocks of "
+                                           f"{D.PART_ROWS} dealt back and forth" if world > 1 else "1 GPU"),
+                           "split_check": split_check,
                            "l2": "cohort (1.0 GB) larger than L2: no flush between steps",
                            "step_ms_p50": statistics.median(step_ms),
                            "step_ms_p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],

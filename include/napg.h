@@ -176,6 +176,27 @@ napg_status napg_run_ex(napg_ctx *ctx, int32_t test, const napg_options *opt,
                         const int32_t *vars_b, int32_t n_b, double *stat, double *pval,
                         int32_t *n, double *effect, double *effect2);
 
+/* One part of a call split over n_parts processes, one per GPU (Sec. 3.5.1: the
+ * pairs are independent, so the output splits without any exchange during the
+ * computation). Arguments as napg_run, plus:
+ *   part, n_parts  0 <= part < n_parts; n_parts == 1 is napg_run.
+ * The output rows (the rows of vars_a) go in blocks of NAPG_PART_ROWS
+ * consecutive rows, dealt to the parts back and forth: block b belongs to
+ * part b mod n_parts in even rounds r = b / n_parts and to part
+ * n_parts - 1 - (b mod n_parts) in odd rounds, so a triangle's long and short
+ * rows pair up. A symmetric call (vars_b == NULL) computes the pairs (i, j),
+ * i <= j, whose row i is owned, and writes both (i, j) and (j, i); an A x B
+ * call computes the owned rows of A. Every output entry is written by exactly
+ * one part (entry (i, j) of a symmetric call by the owner of min(i, j)), with
+ * the same value as the unsplit call; entries of other parts are left as they
+ * were, so the union of the parts' writes is the whole matrix. Synchronous.
+ * Errors: as napg_run; NAPG_E_ARG for part outside [0, n_parts). */
+#define NAPG_PART_ROWS 256
+napg_status napg_run_part(napg_ctx *ctx, int32_t test, const napg_options *opt,
+                          const uint8_t *sample_mask, const int32_t *vars_a, int32_t n_a,
+                          const int32_t *vars_b, int32_t n_b, int32_t part, int32_t n_parts,
+                          double *stat, double *pval, int32_t *n);
+
 /* Effect sizes are returned by napg_run_ex only; the batch and serving entry
  * points return stat, p and n. */
 

@@ -12,11 +12,12 @@ constexpr int kCT = 32;     // cells per tile edge
 constexpr int kCK = 32;     // words per stage
 
 __global__ void __launch_bounds__(256) k_contingency(const uint32_t *__restrict__ lb, int64_t W, int32_t R,
-                                                     int32_t *__restrict__ T) {
+                                                     int32_t *__restrict__ T, const uint8_t *__restrict__ own_lev) {
     const int nt = (R + kCT - 1) / kCT;
     int t = blockIdx.x, I = 0;
     while (t >= nt - I) { t -= nt - I; ++I; }
     const int J = I + t;
+    if (!rows_owned(own_lev, (int64_t)I * kCT, kCT, R)) return;   // no level of this part's variables
     __shared__ uint32_t sa[kCT][kCK + 1], sb[kCT][kCK + 1];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     int acc[2][2] = {};
@@ -50,11 +51,25 @@ __global__ void __launch_bounds__(256) k_contingency(const uint32_t *__restrict_
         }
 }
 
-void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, cudaStream_t st) {
+void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, const uint8_t *own_lev,
+                        cudaStream_t st) {
     if (R == 0) return;
     const int nt = (R + kCT - 1) / kCT;
     count_launch();
-    k_contingency<<<nt * (nt + 1) / 2, 256, 0, st>>>(levbits, W, R, T);
+    k_contingency<<<nt * (nt + 1) / 2, 256, 0, st>>>(levbits, W, R, T, own_lev);
+}
+
+__global__ void k_level_ownership(const uint8_t *own, const int32_t *levoff, const int32_t *nlev, int32_t na,
+                                  uint8_t *own_lev) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < na; a += gridDim.x * blockDim.x)
+        for (int g = 0; g < nlev[a]; ++g) own_lev[levoff[a] + g] = own[a];
+}
+
+void launch_level_ownership(const uint8_t *own, const int32_t *levoff, const int32_t *nlev, int32_t na,
+                            uint8_t *own_lev, cudaStream_t st) {
+    if (na == 0) return;
+    count_launch();
+    k_level_ownership<<<(na + 255) / 256, 256, 0, st>>>(own, levoff, nlev, na, own_lev);
 }
 
 }  // namespace napg

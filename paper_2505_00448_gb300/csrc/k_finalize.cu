@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(256) k_finalize_pearson(PearsonFin f, double *
     int t = blockIdx.x, I = 0;
     while (t >= T - I) { t -= T - I; ++I; }
     const int J = I + t;
+    if (!rows_owned(f.own, (int64_t)I * kFinT, kFinT, nv)) return;   // another part's rows
     __shared__ double m_sx[kFinT][kFinT + 1], m_sxx[kFinT][kFinT + 1];   // mirrored tile (rows j, columns i)
     __shared__ double o_r[kFinT][kFinT + 1], o_p[kFinT][kFinT + 1];      // outputs by (i, j) for the mirror
     __shared__ int32_t o_n[kFinT][kFinT + 1];
@@ -222,6 +223,7 @@ __global__ void NAME(Chi2Fin f, double *stat, double *pval, int32_t *nout) { \
             a = (int)(t / f.nb); \
             b = (int)(t - (int64_t)a * f.nb); \
         } \
+        if (f.symmetric && f.own && !f.own[a]) continue;   /* another part's row */ \
         const int64_t ab = (int64_t)a * f.nb + b; \
         const int ca = f.nlev_a[a], cb = f.nlev_b[b]; \
         const int oa = f.levoff_a[a], ob = f.levoff_b[b]; \
@@ -304,6 +306,7 @@ __global__ void k_finalize_spearman(SpearmanFin f, double *stat, double *pval, i
          t += (int64_t)gridDim.x * blockDim.x) {
         const int a = (int)(t / f.nb), b = (int)(t - (int64_t)a * f.nb);
         if (f.symmetric && b < a) continue;
+        if (f.symmetric && f.own && !f.own[a]) continue;   // another part's row
         const int64_t *q = f.q + 4 * t;
         const int64_t n = q[0];
         double r = dnan(), p = dnan();

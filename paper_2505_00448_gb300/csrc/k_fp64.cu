@@ -58,12 +58,13 @@ __global__ void __launch_bounds__(256) k_pearson_fp64(const double *__restrict__
                                                       const uint32_t *__restrict__ obsv, int64_t W, int32_t nv,
                                                       int split, double *__restrict__ Sxy,
                                                       double *__restrict__ Sx, double *__restrict__ Sxx,
-                                                      int32_t *__restrict__ nn) {
+                                                      int32_t *__restrict__ nn, const uint8_t *__restrict__ own) {
     const int T = (nv + kPT - 1) / kPT;
     int t = blockIdx.x / split, I = 0;
     const int rank = blockIdx.x - t * split;
     while (t >= T - I) { t -= T - I; ++I; }
     const int J = I + t;
+    if (!rows_owned(own, (int64_t)I * kPT, kPT, nv)) return;    // another part's rows (every CTA of the tile)
     __shared__ union {
         struct { double xa[kPT][kPK + 1], xb[kPT][kPK + 1], qa[kPT][kPK + 1], qb[kPT][kPK + 1]; } st;
         double part[20][256];
@@ -185,14 +186,14 @@ int pearson_fp64_split(int32_t nv, int64_t S_pad) {
 }
 
 void launch_pearson_fp64(const double *xs, int64_t S_pad, const uint32_t *obsv, int64_t W, int32_t nv,
-                         double *Sxy, double *Sx, double *Sxx, int32_t *nn, cudaStream_t st) {
+                         double *Sxy, double *Sx, double *Sxx, int32_t *nn, cudaStream_t st, const uint8_t *own) {
     if (nv == 0) return;
     const int T = (nv + kPT - 1) / kPT;
     const int tiles = T * (T + 1) / 2;
     const int split = pearson_fp64_split(nv, S_pad);
     count_launch();
     if (split == 1) {
-        k_pearson_fp64<<<tiles, 256, 0, st>>>(xs, S_pad, obsv, W, nv, 1, Sxy, Sx, Sxx, nn);
+        k_pearson_fp64<<<tiles, 256, 0, st>>>(xs, S_pad, obsv, W, nv, 1, Sxy, Sx, Sxx, nn, own);
         return;
     }
     cudaLaunchConfig_t cfg = {};
@@ -207,7 +208,7 @@ void launch_pearson_fp64(const double *xs, int64_t S_pad, const uint32_t *obsv, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_pearson_fp64, xs, S_pad, obsv, W, nv, split, Sxy, Sx, Sxx, nn);
+    cudaLaunchKernelEx(&cfg, k_pearson_fp64, xs, S_pad, obsv, W, nv, split, Sxy, Sx, Sxx, nn, own);
 }
 
 // One warp per (categorical a, continuous j): lane l takes samples l, l+32, ...

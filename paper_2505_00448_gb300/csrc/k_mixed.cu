@@ -61,6 +61,7 @@ struct UmmaParams {
     const int8_t *expA[2];     // drained output d: per-row scale exponents of A (NULL: 0)
     const int8_t *expB[2];     // ... and of B; the output is divided by 2^(eA + eB)
     uint32_t *err;
+    const uint8_t *own;        // triangle launches of a split call: A rows computed (NULL: all)
 };
 
 // Full grids: the operand with more planes should be the one the concurrently
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int I, J;
     tile_coords(blockIdx.x, P.tilesA, P.tilesB, P.triangle, P.a_fastest, I, J);
+    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rowsA)) return;   // another part's rows
     const int nchunks = NDRAIN ? (P.nkb + P.chunk - 1) / P.chunk : 1;
 
     if (threadIdx.x == 0) {
@@ -356,6 +358,8 @@ struct StackParams {
     int out_transpose;
     const int8_t *exp1, *exp2;     // per-B-row scale exponents of X~ and D
     uint32_t *err;
+    const uint8_t *own;            // split symmetric calls (A and B rows are the same
+                                   // variables): rows computed (NULL: all)
 };
 
 // B rows of the stack held by CTA `rank` of the pair: the even CTA holds stacked
@@ -429,6 +433,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
         const int gsz = min(kSGroup, tilesA2 - g * kSGroup);
         J = r / gsz;
         I2 = g * kSGroup + (r - J * gsz);
+    }
+    if (P.own) {
+        // a split call needs the sums of pairs (i, j), i <= j, i owned: tiles with
+        // owned A rows and a B column at or after them, or owned B rows and an A
+        // row at or after them (both CTAs of the pair decide alike)
+        const int64_t a0 = (int64_t)2 * I2 * kTM, c0 = (int64_t)J * SV;
+        const bool need = (rows_owned(P.own, a0, 2 * kTM, P.rowsA) && c0 + SV - 1 >= a0) ||
+                          (rows_owned(P.own, c0, SV, P.rowsB) && a0 + 2 * kTM - 1 >= c0);
+        if (!need) return;
     }
     const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;
 
@@ -989,7 +1002,7 @@ constexpr int kChunkStacked = 16;
 
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
-                          double *vsq, const std::vector<int32_t> *cache_vars) {
+                          double *vsq, const std::vector<int32_t> *cache_vars, const uint8_t *own) {
     ContPlanes cp;
     NAPG_ST(prep_cont_planes(ctx, c, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp, cache_vars));
     const int nkb = (int)(cp.S_pad / kKB);
@@ -1018,6 +1031,7 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         P.out_drain[0] = Sxy; P.out_drain[1] = nullptr; P.ld = nv;
         P.out_res = nullptr; P.res_sym = 0; P.res_into[0] = 0; P.err = ctx->dev_err;
         P.expA[0] = cp.sexp; P.expB[0] = cp.sexp;
+        P.own = own;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
         NAPG_ST((launch_umma<128, 2, 2, 4, 1, 1, true, 3>(ctx, P, T * (T + 1) / 2, st)));
     }
@@ -1033,6 +1047,7 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         P.nkb = nkb; P.chunk = kChunkStacked;
         P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
+        P.own = own;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
         NAPG_ST(launch_stacked(ctx, P, pb, kStackAll, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
     }
@@ -1084,7 +1099,7 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
 }
 
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
-                              int32_t *T) {
+                              int32_t *T, const uint8_t *own_lev) {
     __half *H = nullptr;
     int64_t hrows = 0, S_pad = 0;
     NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
@@ -1097,6 +1112,7 @@ napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStrea
     P.nkb = (int)(S_pad / kKB); P.chunk = P.nkb;
     P.out_drain[0] = nullptr; P.out_drain[1] = nullptr; P.ld = R;
     P.out_res = T; P.res_sym = 1; P.err = ctx->dev_err;
+    P.own = own_lev;
     Stage s_(ctx->trace, st, "contingency_tc");
     return launch_umma<128, 1, 1, 1, 0, 1, false, 4>(ctx, P, TT * (TT + 1) / 2, st);
 }

@@ -394,7 +394,8 @@ __device__ __forceinline__ void carve_bounds(Side &sd, unsigned char *&cur, int 
 __global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t *__restrict__ crow_a,
                                                   const int32_t *__restrict__ crow_b, const uint32_t *__restrict__ obs_a,
                                                   const uint32_t *__restrict__ obs_b, int32_t na, int32_t nb,
-                                                  int32_t symmetric, int64_t *__restrict__ out4) {
+                                                  int32_t symmetric, int64_t *__restrict__ out4,
+                                                  const uint8_t *__restrict__ own) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int32_t scan_tmp[64];
     __shared__ int64_t red4[32][4];
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(1024, 2) k_spearman(RankData rd, const int32_t
     } else {
         a = (int)(pid / nb); b = (int)(pid - (int64_t)a * nb);
     }
+    if (symmetric && own && !own[a]) return;    // another part's row (the whole CTA)
     unsigned char *cur = smem_raw;
     Side si, sj;
     carve_records(si, cur, W);
@@ -488,14 +490,14 @@ int rank_threads_default(int64_t W, bool groups) { return rank_threads(rank_smem
 
 void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b, const uint32_t *obs_a,
                            const uint32_t *obs_b, int32_t na, int32_t nb, int32_t symmetric, int64_t *out4,
-                           cudaStream_t st, int threads) {
+                           cudaStream_t st, int threads, const uint8_t *own) {
     const int64_t pairs = symmetric ? (int64_t)na * (na + 1) / 2 : (int64_t)na * nb;
     if (pairs == 0) return;
     const size_t smem = rank_smem_bytes(rd.W, 2, true);
     cudaFuncSetAttribute(k_spearman, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     count_launch();
     k_spearman<<<(unsigned)pairs, threads > 0 ? threads : rank_threads(smem), smem, st>>>(
-        rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric, out4);
+        rd, crow_a, crow_b, obs_a, obs_b, na, nb, symmetric, out4, own);
 }
 
 // ------------------------------------------------------------ MWU / Kruskal --

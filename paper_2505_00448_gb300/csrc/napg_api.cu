@@ -431,16 +431,16 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         double *vsq = mixed ? WS(kVsq, double, na) : nullptr;
         if (st_) return st_;
         if (mixed) {
-            NAPG_ST(mixed_pearson(ctx, c, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift, vsq, (a.mask || a.no_plane_cache) ? nullptr : &va));
+            NAPG_ST(mixed_pearson(ctx, c, ws, st, d_va, na, obsA, Sxy, Sx, Sxx, nn, shift, vsq, (a.mask || a.no_plane_cache) ? nullptr : &va, a.own));
         } else {
             double *xs = WS(kXsA, double, (int64_t)na * S_pad);
             if (st_) return st_;
             { Stage s_(ctx->trace, st, "shift_fp64"); launch_shift_values(c.X, c.dtype, S, S_pad, d_va, na, obsA, W, shift, xs, st); }
-            { Stage s_(ctx->trace, st, "pearson_moments_fp64"); launch_pearson_fp64(xs, S_pad, obsA, W, na, Sxy, Sx, Sxx, nn, st); }
+            { Stage s_(ctx->trace, st, "pearson_moments_fp64"); launch_pearson_fp64(xs, S_pad, obsA, W, na, Sxy, Sx, Sxx, nn, st, a.own); }
         }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
-        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq, pj.q, d_va};
+        PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq, pj.q, d_va, a.own};
         { Stage s_(ctx->trace, st, "finalize_pearson"); launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, 0, st); }
@@ -474,11 +474,18 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
     } else if (t == NAPG_CHI2) {
         int32_t *T = WS(kIntA, int32_t, (int64_t)R * R);
         if (st_) return st_;
-        if (mixed) NAPG_ST(mixed_contingency(ctx, c, ws, st, levbits, R, T));
-        else { Stage s_(ctx->trace, st, "contingency_popc"); launch_contingency(levbits, W, R, T, st); }
+        // a split call: the level rows of the part's variables
+        uint8_t *own_lev = nullptr;
+        if (a.own) {
+            own_lev = WS(kTmpE, uint8_t, R);
+            if (st_) return st_;
+            launch_level_ownership(a.own, d_lo, d_nl, na, own_lev, st);
+        }
+        if (mixed) NAPG_ST(mixed_contingency(ctx, c, ws, st, levbits, R, T, own_lev));
+        else { Stage s_(ctx->trace, st, "contingency_popc"); launch_contingency(levbits, W, R, T, own_lev, st); }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
-        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2, pj.q, maxlev};
+        Chi2Fin f{T, R, d_lo, d_nl, d_lo, d_nl, levcnt, na, na, 1, a.opt.yates_2x2, pj.q, maxlev, a.own};
         { Stage s_(ctx->trace, st, "finalize_chi2"); launch_finalize_chi2(f, a.stat, a.pval, a.n, st); }
         pjobs_run(ctx, pj, a.pval, st);
     } else if (t == NAPG_SPEARMAN) {
@@ -490,7 +497,8 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
             Stage s_(ctx->trace, st, "spearman_rank");
             const int t0 = rank_threads_default(W, false), cand[2] = {t0, t0 == 256 ? 1024 : 256};
             auto run = [&](int c) -> napg_status {
-                launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st, cand[c]);
+                launch_spearman_pairs(rd, d_ca, d_cb, obsA, obsB, na, nb, symmetric ? 1 : 0, q, st, cand[c],
+                                      symmetric ? a.own : nullptr);
                 NAPG_CU(ctx, cudaGetLastError());
                 return NAPG_OK;
             };
@@ -498,7 +506,7 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         }
         PJobBufs pj;
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * nb, a.pval != nullptr, pj));
-        SpearmanFin f{q, na, nb, symmetric ? 1 : 0, pj.q};
+        SpearmanFin f{q, na, nb, symmetric ? 1 : 0, pj.q, symmetric ? a.own : nullptr};
         { Stage s_(ctx->trace, st, "finalize_spearman"); launch_finalize_spearman(f, a.stat, a.pval, a.n, st); }
         pjobs_run(ctx, pj, a.pval, st);
     } else {  // MWU / KRUSKAL
@@ -904,6 +912,126 @@ napg_status napg_run_ex(napg_ctx *ctx, int32_t test, const napg_options *opt, co
     a.es1 = effect;
     a.es2 = effect2;
     return run_with_outputs(ctx, ctx->ws, ctx->stream, a, vars_b == nullptr);
+}
+
+// One part of a call split over n_parts (Sec. 3.5.1: the pairs are independent).
+// Output rows go in blocks of kPartRows dealt back and forth to the parts.
+// Symmetric calls compute the pairs (i, j), i <= j, of the owned rows i and
+// write (i, j) and (j, i); A x B calls compute the owned rows of A. Entries of
+// other parts are left as they were (host outputs are staged on the device
+// from the caller's arrays, so the copy back keeps them).
+napg_status napg_run_part(napg_ctx *ctx, int32_t test, const napg_options *opt, const uint8_t *sample_mask,
+                          const int32_t *vars_a, int32_t n_a, const int32_t *vars_b, int32_t n_b, int32_t part,
+                          int32_t n_parts, double *stat, double *pval, int32_t *n) {
+    if (!ctx) return NAPG_E_ARG;
+    if (n_parts < 1 || part < 0 || part >= n_parts) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        return fail(ctx, NAPG_E_ARG, "part must be in [0, n_parts) with n_parts >= 1");
+    }
+    if (n_parts == 1) return napg_run(ctx, test, opt, sample_mask, vars_a, n_a, vars_b, n_b, stat, pval, n);
+    if (n_a < 0 || (vars_b && n_b < 0) || (n_a > 0 && !vars_a)) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        return fail(ctx, NAPG_E_ARG, "bad variable lists");
+    }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->err.clear();
+    NAPG_CU(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    NAPG_ST(wait_pending_copies(ctx));
+    RunArgs a{};
+    a.test = test;
+    if (opt) a.opt = *opt;
+    else napg_default_options(&a.opt);
+    a.opt.async_host_outputs = 0;
+    a.mask = sample_mask;
+    a.mask_on_device = is_device_ptr(sample_mask);
+    const bool symmetric = vars_b == nullptr;
+    const int32_t nb = symmetric ? n_a : n_b;
+    std::vector<int32_t> rows;
+    for (int32_t i = 0; i < n_a; ++i)
+        if (part_of_row(i, n_parts) == part) rows.push_back(i);
+    napg_status st_ = NAPG_OK;
+    double *outs_d[2] = {stat, pval};
+    const int sl_d[2] = {Workspace::kPartS, Workspace::kPartP};
+    if (symmetric) {
+        const int64_t cnt = (int64_t)n_a * n_a;
+        std::vector<uint8_t> own(std::max<int32_t>(n_a, 1), 0);
+        for (int32_t i : rows) own[i] = 1;
+        uint8_t *own_d = (uint8_t *)ws_get(ctx, ctx->ws, Workspace::kPartOwn, own.size(), &st_);
+        if (st_) return st_;
+        NAPG_CU(ctx, cudaMemcpyAsync(own_d, own.data(), own.size(), cudaMemcpyHostToDevice, st));
+        // host outputs: staged on the device from the caller's arrays
+        double *dd[2] = {stat, pval};
+        int32_t *dn = n;
+        for (int k = 0; k < 2; ++k)
+            if (outs_d[k] && !is_device_ptr(outs_d[k])) {
+                dd[k] = (double *)ws_get(ctx, ctx->ws, sl_d[k], sizeof(double) * cnt, &st_);
+                if (st_) return st_;
+                NAPG_CU(ctx, cudaMemcpyAsync(dd[k], outs_d[k], sizeof(double) * cnt, cudaMemcpyHostToDevice, st));
+            }
+        if (n && !is_device_ptr(n)) {
+            dn = (int32_t *)ws_get(ctx, ctx->ws, Workspace::kPartN, sizeof(int32_t) * cnt, &st_);
+            if (st_) return st_;
+            NAPG_CU(ctx, cudaMemcpyAsync(dn, n, sizeof(int32_t) * cnt, cudaMemcpyHostToDevice, st));
+        }
+        a.va = vars_a;
+        a.na = n_a;
+        a.nb = n_a;
+        a.stat = dd[0];
+        a.pval = dd[1];
+        a.n = dn;
+        a.own = own_d;
+        NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
+        if (!rows.empty()) NAPG_ST(run_with_outputs(ctx, ctx->ws, st, a, true));
+        for (int k = 0; k < 2; ++k)
+            if (dd[k] != outs_d[k])
+                NAPG_CU(ctx, cudaMemcpyAsync(outs_d[k], dd[k], sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+        if (dn != n) NAPG_CU(ctx, cudaMemcpyAsync(n, dn, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, st));
+    } else {
+        // A x B: the owned rows of A into device buffers, then row blocks copied to the outputs
+        if (rows.empty()) return NAPG_OK;
+        const int32_t np = (int32_t)rows.size();
+        std::vector<int32_t> va(np);
+        for (int32_t r = 0; r < np; ++r) va[r] = vars_a[rows[r]];
+        const int64_t cnt = (int64_t)np * nb;
+        double *td[2] = {nullptr, nullptr};
+        for (int k = 0; k < 2; ++k)
+            if (outs_d[k]) {
+                td[k] = (double *)ws_get(ctx, ctx->ws, sl_d[k], sizeof(double) * cnt, &st_);
+                if (st_) return st_;
+            }
+        int32_t *tn = nullptr;
+        if (n) {
+            tn = (int32_t *)ws_get(ctx, ctx->ws, Workspace::kPartN, sizeof(int32_t) * cnt, &st_);
+            if (st_) return st_;
+        }
+        a.va = va.data();
+        a.na = np;
+        a.vb = vars_b;
+        a.nb = n_b;
+        a.stat = td[0];
+        a.pval = td[1];
+        a.n = tn;
+        NAPG_CU(ctx, cudaMemsetAsync(ctx->dev_err, 0, sizeof(uint32_t), st));
+        NAPG_ST(run_with_outputs(ctx, ctx->ws, st, a, false));
+        // runs of consecutive owned rows are one copy each
+        for (int32_t r0 = 0; r0 < np;) {
+            int32_t r1 = r0 + 1;
+            while (r1 < np && rows[r1] == rows[r1 - 1] + 1) ++r1;
+            const size_t len = (size_t)(r1 - r0) * (size_t)nb;
+            const int64_t src = (int64_t)r0 * nb, dst = (int64_t)rows[r0] * nb;
+            for (int k = 0; k < 2; ++k)
+                if (outs_d[k])
+                    NAPG_CU(ctx, cudaMemcpyAsync(outs_d[k] + dst, td[k] + src, sizeof(double) * len, cudaMemcpyDefault, st));
+            if (n) NAPG_CU(ctx, cudaMemcpyAsync(n + dst, tn + src, sizeof(int32_t) * len, cudaMemcpyDefault, st));
+            r0 = r1;
+        }
+    }
+    // synchronous: the row lists above live on the host
+    NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    NAPG_CU(ctx, cudaStreamSynchronize(st));
+    if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    return NAPG_OK;
 }
 
 napg_status napg_adjust(napg_ctx *ctx, int32_t method, const double *p, int64_t rows, int64_t cols,

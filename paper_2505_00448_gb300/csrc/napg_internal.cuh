@@ -69,7 +69,7 @@ struct Workspace {
         kCounter, kOutStat, kOutP, kOutN, kMask, kVarsDev, kTmpA, kTmpB, kTmpC, kTmpD, kTmpE,
         kTmpF, kTmpG, kVsq, kUnionS, kUnionP, kUnionN, kExp, kPjJobs, kPjSorted, kPjMeta, kPlShift, kPlVsq,
         kPresortTmp, kBgrat, kUnionE1, kUnionE2, kOutE1, kOutE2, kAdjKeys, kAdjVals, kAdjTmp,
-        kOutStatB, kOutPB, kOutNB, kOutE1B, kOutE2B, kLargeA, kNumSlots
+        kOutStatB, kOutPB, kOutNB, kOutE1B, kOutE2B, kLargeA, kPartS, kPartP, kPartN, kPartOwn, kNumSlots
     };
     void *ptr[kNumSlots] = {};
     size_t cap[kNumSlots] = {};
@@ -193,7 +193,27 @@ struct RunArgs {
     int32_t *n;
     double *es1, *es2;        // effect sizes (device, n_a x n_b) or NULL: Table 2's effect size, and
                               // Cramer's V for chi-squared (NaN for the other tests)
+    // symmetric calls split by napg_run_part (NULL: every row): own[i] != 0 for
+    // the output rows i this part computes (pairs i <= j of the upper triangle)
+    const uint8_t *own;
 };
+
+// Split of a call's output rows over parts (napg_run_part): rows go in blocks
+// of kPartRows, dealt to the parts back and forth (0, 1, ..., n-1, n-1, ..., 1,
+// 0, 0, 1, ...) so that the blocks of a triangle's long and short rows pair up.
+constexpr int kPartRows = NAPG_PART_ROWS;
+__host__ __device__ inline int part_of_row(int64_t row, int nparts) {
+    const int64_t b = row / kPartRows, r = b / nparts, k = b - r * nparts;
+    return (int)((r & 1) ? nparts - 1 - k : k);
+}
+// a tile of rows [r0, r0 + len) of a split call takes part in it when any row is owned
+__host__ __device__ inline bool rows_owned(const uint8_t *own, int64_t r0, int64_t len, int64_t rows) {
+    if (!own) return true;
+    const int64_t r1 = r0 + len < rows ? r0 + len : rows;
+    for (int64_t r = r0; r < r1; ++r)
+        if (own[r]) return true;
+    return false;
+}
 napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const RunArgs &a);
 void free_cohort(Cohort &c);
 uint64_t next_cohort_gen();
@@ -239,13 +259,18 @@ void launch_level_bits(const uint8_t *lab, int64_t S, int64_t W, const int32_t *
                        const uint32_t *obsv, uint32_t *levbits, int32_t *levcnt, cudaStream_t st);
 // plain FP64 moments
 void launch_pearson_fp64(const double *xs, int64_t S_pad, const uint32_t *obsv, int64_t W, int32_t nv,
-                         double *Sxy, double *Sx, double *Sxx, int32_t *nn, cudaStream_t st);
+                         double *Sxy, double *Sx, double *Sxx, int32_t *nn, cudaStream_t st,
+                         const uint8_t *own = nullptr);
 void launch_groupsum_fp64(const uint8_t *lab, int64_t S, const int32_t *catrow_dev, int32_t na,
                           const int32_t *levoff_dev, const int32_t *nlev_dev, const double *xs,
                           int64_t S_pad, const uint32_t *obsb, int64_t W, int32_t nb,
                           int32_t *gn, double *g1, double *g2, int32_t max_levels, cudaStream_t st);
 // contingency tables
-void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, cudaStream_t st);
+void launch_contingency(const uint32_t *levbits, int64_t W, int32_t R, int32_t *T, const uint8_t *own_lev,
+                        cudaStream_t st);
+// own_lev[levoff[a] + g] = own[a] for the levels g of every variable a
+void launch_level_ownership(const uint8_t *own, const int32_t *levoff, const int32_t *nlev, int32_t na,
+                            uint8_t *own_lev, cudaStream_t st);
 // finalize (p-values included)
 struct PearsonFin {
     const double *Sxy, *Sx, *Sxx; const int32_t *nn; const double *shift; int32_t nv;
@@ -253,6 +278,7 @@ struct PearsonFin {
     const double *vsq;   // mixed form: Sxx holds sum (x~^2 - v) m; add v n back (NULL: plain)
     PJobQueue q;         // p-value jobs (q.jobs NULL: no p-values wanted)
     const int32_t *vars; // variable ids of the rows (NULL: rows are distinct variables)
+    const uint8_t *own;  // split calls: rows computed (NULL: all)
 };
 void launch_finalize_pearson(const PearsonFin &f, double *stat, double *pval, int32_t *nout,
                              int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
@@ -274,6 +300,7 @@ struct Chi2Fin {
     const int32_t *present; int32_t na, nb; int32_t symmetric; int32_t yates;
     PJobQueue q;
     int32_t maxc;        // most levels of any variable in the call
+    const uint8_t *own;  // split symmetric calls: rows (variables of A) computed (NULL: all)
 };
 void launch_finalize_chi2(const Chi2Fin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
 // exact rescue of pairs whose moments are degenerate (constant columns/groups)
@@ -313,13 +340,17 @@ struct RankData {
 };
 void launch_spearman_pairs(const RankData &rd, const int32_t *crow_a, const int32_t *crow_b,
                            const uint32_t *obs_a, const uint32_t *obs_b, int32_t na, int32_t nb,
-                           int32_t symmetric, int64_t *out4, cudaStream_t st, int threads = 0);
+                           int32_t symmetric, int64_t *out4, cudaStream_t st, int threads = 0,
+                           const uint8_t *own = nullptr);
 int rank_threads_default(int64_t W, bool groups);
 void launch_rank_groups(const RankData &rd, const uint8_t *lab, const int32_t *catrow_a,
                         const int32_t *nlev_a, const int32_t *levoff_a, int32_t na, const int32_t *crow_b,
                         const uint32_t *obs_a, const uint32_t *obs_b, int32_t nb, int32_t max_levels,
                         int64_t *rsum, int32_t *rcnt, int64_t *tie_term, cudaStream_t st, int threads = 0);
-struct SpearmanFin { const int64_t *q; int32_t na, nb; int32_t symmetric; PJobQueue pq; };
+struct SpearmanFin {
+    const int64_t *q; int32_t na, nb; int32_t symmetric; PJobQueue pq;
+    const uint8_t *own;  // split symmetric calls: rows computed (NULL: all)
+};
 void launch_finalize_spearman(const SpearmanFin &f, double *stat, double *pval, int32_t *nout, cudaStream_t st);
 struct RankGroupFin {
     const int64_t *rsum; const int32_t *rcnt; const int64_t *tie_term; int32_t total_rows;
@@ -340,14 +371,15 @@ struct MixedPlan;
 // (the planes may then be reused by the next run on the same list), else NULL
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn,
-                          double *shift_out, double *vsq_out, const std::vector<int32_t> *cache_vars);
+                          double *shift_out, double *vsq_out, const std::vector<int32_t> *cache_vars,
+                          const uint8_t *own = nullptr);
 napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                            const int32_t *vars_b_dev, int32_t nb, const uint32_t *obsb, int32_t *gn,
                            double *g1, double *g2, double *shift_out, double *vsq_out,
                            const std::vector<int32_t> *cache_vars,
                            const uint32_t *obsa = nullptr, int32_t na = 0, double *g2tot = nullptr);
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits,
-                              int32_t R, int32_t *T);
+                              int32_t R, int32_t *T, const uint8_t *own_lev = nullptr);
 
 }  // namespace napg
 

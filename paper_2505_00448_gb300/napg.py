@@ -70,6 +70,8 @@ def _load():
     L.napg_run.restype = C.c_int
     L.napg_run_ex.argtypes = [p, i32, p, p, p, i32, p, i32, p, p, p, p, p]
     L.napg_run_ex.restype = C.c_int
+    L.napg_run_part.argtypes = [p, i32, p, p, p, i32, p, i32, i32, i32, p, p, p]
+    L.napg_run_part.restype = C.c_int
     L.napg_adjust.argtypes = [p, i32, p, i64, i64, i32, p]
     L.napg_adjust.restype = C.c_int
     L.napg_run_batch.argtypes = [p, i32, p, i32, p, p, i32, p, i32, p, p, p]
@@ -247,6 +249,36 @@ class Context:
         if e1 is not None or e2 is not None:
             res["effect"], res["effect2"] = e1, e2
         return res
+
+    def run_part(self, test, vars_a, vars_b=None, part=0, nparts=1, mask=None, outputs=None, out="numpy", **opt):
+        """One part of a call split over `nparts` (napg_run_part): the pairs of the
+        output rows this part owns (rows in blocks of PART_ROWS dealt back and
+        forth to the parts). `outputs` may supply dict(stat, p, n) buffers (entries
+        of other parts are left as they are); otherwise new arrays are made,
+        filled with NaN (stat, p) and -1 (n) where this part writes nothing."""
+        torch = self.torch
+        t = TESTS[test] if isinstance(test, str) else int(test)
+        va, vb = _i32(vars_a), _i32(vars_b)
+        na = len(va)
+        nb = na if vb is None else len(vb)
+        o = options(**opt)
+        if outputs is not None:
+            stat, p, n = outputs.get("stat"), outputs.get("p"), outputs.get("n")
+        elif out == "numpy":
+            stat = np.full((na, nb), np.nan)
+            p = np.full((na, nb), np.nan)
+            n = np.full((na, nb), -1, np.int32)
+        else:
+            dev = torch.device("cuda", self.device)
+            stat = torch.full((na, nb), float("nan"), dtype=torch.float64, device=dev)
+            p = torch.full((na, nb), float("nan"), dtype=torch.float64, device=dev)
+            n = torch.full((na, nb), -1, dtype=torch.int32, device=dev)
+        m = None
+        if mask is not None:
+            m = np.ascontiguousarray(mask, dtype=np.uint8) if isinstance(mask, np.ndarray) else mask
+        self._check(lib.napg_run_part(self.h, t, C.byref(o), _ptr(m), _ptr(va), na, _ptr(vb),
+                                      0 if vb is None else nb, int(part), int(nparts), _ptr(stat), _ptr(p), _ptr(n)))
+        return {"stat": stat, "p": p, "n": n}
 
     def adjust(self, p, method="bh", symmetric=False, out=None):
         """Multiple-testing correction (Sec. 3.4) of a p-value matrix (numpy or
