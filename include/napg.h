@@ -79,7 +79,13 @@ typedef struct {
     int32_t precision;       /* napg_precision; default NAPG_FP64_PLAIN */
     int32_t welch;           /* 1: Welch t (default), 0: Student t (Sec. 3.5.5) */
     int32_t yates_2x2;       /* 1: Yates continuity correction on 2x2 tables; default 0 */
-    int32_t mwu_mode;        /* 0 auto (default), 1 exact, 2 asymptotic (Sec. 3.5.6) */
+    int32_t mwu_mode;        /* 0 auto (default), 1 exact, 2 asymptotic (Sec. 3.5.6). Auto takes
+                                the exact null distribution when there are no ties and
+                                min(n0, n1) < 8. Forced exact (1) counts arrangements in exact
+                                128-bit integers: a pair with min(n0, n1) > 64, C(n, n0) >= 2^126
+                                or min(U0, U1) above max(3.5 n_samples, 65,534) gets p = NaN, and the call
+                                returns NAPG_E_UNSUPPORTED once all its outputs are written
+                                (napg_sync for asynchronous calls; a serving request's status) */
     int32_t mwu_continuity;  /* 1: 0.5 continuity correction in asymptotic mode (default) */
     int32_t debug_checks;    /* 1: extra device-side argument checks */
     int32_t async_host_outputs; /* 1: napg_run / napg_run_ex return once the work and the

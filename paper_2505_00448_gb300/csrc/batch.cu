@@ -5,8 +5,12 @@
 // selected variables' values, observed bits and labels for the context's
 // samples into a dense sub-cohort, and the ordinary pipeline runs on it with
 // no mask. Tensor and rank work then scale with N_k instead of the cohort's S.
-// The whole batch (compaction of every mask, then gather + pipeline per context)
-// is captured once into a CUDA graph and replayed by a single graph launch; the
+// The contexts are dealt to kBatchBranches branches (largest first, onto the
+// least-loaded branch), each with its own sub-cohort, workspace and stream, so
+// that the kernels of small contexts run side by side. The whole batch
+// (compaction of every mask, then the branches forked from it, gather +
+// pipeline per context, joined at the end) is captured once into a CUDA graph
+// and replayed by a single graph launch; the
 // executable graph is kept for the next call with the same shape (test,
 // options, variable lists, context sizes, output buffers). Only the mask
 // contents change between such calls: they are copied into a staging buffer
@@ -92,6 +96,20 @@ __global__ void k_ctx_gather(const T *__restrict__ X, const uint32_t *__restrict
 
 // ------------------------------------------------------------- batch state --
 
+// Contexts run on this many concurrent branches of the captured graph, each with
+// its own dense sub-cohort, workspace and stream: a small context leaves most
+// SMs idle, and the other branches' contexts fill them.
+constexpr int kBatchBranches = 4;
+
+struct BatchBranch {
+    Cohort sub;                          // dense sub-cohort, arrays sized for the branch's largest context
+    Workspace ws;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    size_t sub_x_cap = 0, sub_obs_cap = 0, sub_lab_cap = 0;
+    std::vector<int32_t> ctxs;           // contexts of this branch, in launch order
+};
+
 struct BatchState {
     // shape of the captured graph
     bool valid = false;
@@ -107,8 +125,7 @@ struct BatchState {
     cudaStream_t stream = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     // buffers
-    Cohort sub;                          // dense sub-cohort, arrays sized for the largest context
-    Workspace ws;
+    BatchBranch br[kBatchBranches];
     uint8_t *masks = nullptr;            // [n_ctx][S] staged masks
     size_t masks_cap = 0;
     int32_t *idx = nullptr;              // [n_ctx][idx_stride] selected sample ids
@@ -119,7 +136,6 @@ struct BatchState {
     int32_t *dints = nullptr;            // staged variable lists of the sub-cohort run
     std::vector<size_t> doff;
     int32_t *host_counts = nullptr;      // pinned
-    size_t sub_x_cap = 0, sub_obs_cap = 0, sub_lab_cap = 0;
     void *stage = nullptr;               // device outputs of every context when the caller's are on the host
     size_t stage_cap = 0;
 };
@@ -128,9 +144,13 @@ void free_batch(napg_ctx *ctx) {
     BatchState *b = ctx->batch;
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
-    free_cohort(b->sub);
-    for (int i = 0; i < Workspace::kNumSlots; ++i)
-        if (b->ws.ptr[i]) cudaFree(b->ws.ptr[i]);
+    for (BatchBranch &r : b->br) {
+        free_cohort(r.sub);
+        for (int i = 0; i < Workspace::kNumSlots; ++i)
+            if (r.ws.ptr[i]) cudaFree(r.ws.ptr[i]);
+        if (r.done) cudaEventDestroy(r.done);
+        if (r.stream) cudaStreamDestroy(r.stream);
+    }
     void *p[] = {b->masks, b->idx, b->counts, b->rows, b->dints, b->stage};
     for (void *q : p)
         if (q) cudaFree(q);
@@ -158,11 +178,12 @@ static bool same_opt(const napg_options &a, const napg_options &b) {
 }
 
 // gather + pipeline of context k (stream-ordered, capture-safe once sized)
-static napg_status run_context(napg_ctx *ctx, BatchState &b, cudaStream_t st, int k, int64_t idx_stride,
+static napg_status run_context(napg_ctx *ctx, BatchState &b, BatchBranch &br, cudaStream_t st, int k,
+                               int64_t idx_stride,
                                const int32_t *sub_va, const int32_t *sub_vb, int32_t na, int32_t nb,
                                double *stat, double *pval, int32_t *n) {
     const Cohort &P = ctx->coh;
-    Cohort &c = b.sub;
+    Cohort &c = br.sub;
     const int64_t Nk = b.nk[k];
     c.S = Nk;
     c.W = (Nk + 31) / 32;
@@ -205,7 +226,7 @@ static napg_status run_context(napg_ctx *ctx, BatchState &b, cudaStream_t st, in
         if (n) NAPG_CU(ctx, cudaMemsetAsync(n, 0, sizeof(int32_t) * cnt, st));
         return NAPG_OK;
     }
-    return run_on_stream(ctx, b.ws, st, a);
+    return run_on_stream(ctx, br.ws, st, a);
 }
 
 // loop over the contexts through napg_run's path (host outputs, or shapes the
@@ -265,7 +286,7 @@ static napg_status batch_host_outputs(napg_ctx *ctx, const RunArgs &a0, int32_t 
     }
     NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     NAPG_CU(ctx, cudaStreamSynchronize(st));
-    if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    if (*ctx->host_err) return device_error_status(ctx, *ctx->host_err);
     return NAPG_OK;
 }
 
@@ -351,7 +372,7 @@ napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uin
         std::vector<int32_t> parent = va;
         if (!symmetric) parent.insert(parent.end(), vb.begin(), vb.end());
         const int F = (int)parent.size();
-        Cohort &c = b.sub;
+        Cohort &c = b.br[0].sub;
         c.F = F;
         c.dtype = P.dtype;
         c.missing = P.missing;
@@ -388,18 +409,47 @@ napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uin
         b.rows = nullptr;
         NAPG_CU(ctx, cudaMalloc(&b.rows, sizeof(int32_t) * rows_dev.size()));
         NAPG_CU(ctx, cudaMemcpy(b.rows, rows_dev.data(), sizeof(int32_t) * rows_dev.size(), cudaMemcpyHostToDevice));
-        if (c.cont_vars_dev) cudaFree(c.cont_vars_dev);
-        c.cont_vars_dev = nullptr;
-        if (!cont_ids.empty()) {
-            NAPG_CU(ctx, cudaMalloc(&c.cont_vars_dev, sizeof(int32_t) * cont_ids.size()));
-            NAPG_CU(ctx, cudaMemcpy(c.cont_vars_dev, cont_ids.data(), sizeof(int32_t) * cont_ids.size(),
-                                    cudaMemcpyHostToDevice));
+        // contexts to branches, largest first onto the least-loaded branch
+        std::vector<int32_t> order(n_ctx);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return nk[x] > nk[y]; });
+        int64_t load[kBatchBranches] = {};
+        for (BatchBranch &r : b.br) r.ctxs.clear();
+        for (int32_t k : order) {
+            int jb = 0;
+            for (int j = 1; j < kBatchBranches; ++j)
+                if (load[j] < load[jb]) jb = j;
+            load[jb] += std::max<int64_t>(nk[k], 1);
+            b.br[jb].ctxs.push_back(k);
         }
         const size_t esz = P.dtype == NAPG_F32 ? 4 : 8;
-        const int64_t wmax = (nmax + 31) / 32;
-        NAPG_ST(grow(ctx, &c.X, &b.sub_x_cap, esz * (size_t)F * (size_t)std::max<int64_t>(nmax, 1)));
-        NAPG_ST(grow(ctx, (void **)&c.obs, &b.sub_obs_cap, sizeof(uint32_t) * (size_t)F * (size_t)std::max<int64_t>(wmax, 1)));
-        NAPG_ST(grow(ctx, (void **)&c.lab, &b.sub_lab_cap, (size_t)std::max<int64_t>(c.n_cat, 1) * (size_t)std::max<int64_t>(nmax, 1)));
+        for (int j = 0; j < kBatchBranches; ++j) {
+            BatchBranch &r = b.br[j];
+            std::sort(r.ctxs.begin(), r.ctxs.end());
+            Cohort &cj = r.sub;
+            if (j > 0) {
+                cj.F = c.F; cj.dtype = c.dtype; cj.missing = c.missing; cj.loaded = true;
+                cj.vtype = c.vtype; cj.nlev = c.nlev; cj.cat_index = c.cat_index; cj.cont_index = c.cont_index;
+                cj.n_cat = c.n_cat; cj.n_cont = c.n_cont;
+            }
+            if (!r.stream) {
+                NAPG_CU(ctx, cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking));
+                NAPG_CU(ctx, cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming));
+            }
+            if (cj.cont_vars_dev) cudaFree(cj.cont_vars_dev);
+            cj.cont_vars_dev = nullptr;
+            if (!cont_ids.empty()) {
+                NAPG_CU(ctx, cudaMalloc(&cj.cont_vars_dev, sizeof(int32_t) * cont_ids.size()));
+                NAPG_CU(ctx, cudaMemcpy(cj.cont_vars_dev, cont_ids.data(), sizeof(int32_t) * cont_ids.size(),
+                                        cudaMemcpyHostToDevice));
+            }
+            int64_t nj = 1;
+            for (int32_t k : r.ctxs) nj = std::max<int64_t>(nj, nk[k]);
+            const int64_t wj = (nj + 31) / 32;
+            NAPG_ST(grow(ctx, &cj.X, &r.sub_x_cap, esz * (size_t)F * (size_t)nj));
+            NAPG_ST(grow(ctx, (void **)&cj.obs, &r.sub_obs_cap, sizeof(uint32_t) * (size_t)F * (size_t)wj));
+            NAPG_ST(grow(ctx, (void **)&cj.lab, &r.sub_lab_cap, (size_t)std::max<int64_t>(c.n_cat, 1) * (size_t)nj));
+        }
         NAPG_ST(grow(ctx, (void **)&b.idx, &b.idx_cap, sizeof(int32_t) * (size_t)n_ctx * (size_t)idx_stride));
         // variable lists of the sub-cohort run, staged once
         std::vector<int32_t> sva(na), svb(symmetric ? 0 : nb);
@@ -419,7 +469,7 @@ napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uin
         NAPG_CU(ctx, cudaMalloc(&b.dints, sizeof(int32_t) * (all.size() + 1)));
         NAPG_CU(ctx, cudaMemcpy(b.dints, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice));
 
-        // size everything with the largest context, uncaptured
+        // size every branch with its largest context, uncaptured
         const bool trace_on = ctx->trace.on;
         ctx->trace.on = false;
         NAPG_CU(ctx, cudaEventRecord(b.fork, st));
@@ -427,24 +477,46 @@ napg_status run_batch(napg_ctx *ctx, const RunArgs &a0, int32_t n_ctx, const uin
         count_launch();
         k_ctx_compact<<<n_ctx, 1024, 0, b.stream>>>(b.masks, S, b.idx, idx_stride);
         NAPG_CU(ctx, cudaGetLastError());
-        const int kmax = (int)(std::max_element(nk.begin(), nk.end()) - nk.begin());
-        napg_status r0 = run_context(ctx, b, b.stream, kmax, idx_stride, sva.data(), svb.data(), na, nb,
-                                     stat ? stat[kmax] : nullptr, pval ? pval[kmax] : nullptr, n ? n[kmax] : nullptr);
-        cudaError_t e0 = cudaStreamSynchronize(b.stream);
+        NAPG_CU(ctx, cudaEventRecord(b.join, b.stream));
+        napg_status r0 = NAPG_OK;
+        for (BatchBranch &r : b.br) {
+            if (r.ctxs.empty() || r0 != NAPG_OK) continue;
+            int32_t kmax = r.ctxs[0];
+            for (int32_t k : r.ctxs)
+                if (nk[k] > nk[kmax]) kmax = k;
+            NAPG_CU(ctx, cudaStreamWaitEvent(r.stream, b.join, 0));
+            r0 = run_context(ctx, b, r, r.stream, kmax, idx_stride, sva.data(), svb.data(), na, nb,
+                             stat ? stat[kmax] : nullptr, pval ? pval[kmax] : nullptr, n ? n[kmax] : nullptr);
+        }
+        cudaError_t e0 = cudaSuccess;
+        for (BatchBranch &r : b.br) {
+            const cudaError_t e = cudaStreamSynchronize(r.stream);
+            if (e0 == cudaSuccess) e0 = e;
+        }
         if (r0 != NAPG_OK) { ctx->trace.on = trace_on; return r0; }
         if (e0 != cudaSuccess) { ctx->trace.on = trace_on; return cuda_fail(ctx, e0, "batch sizing run"); }
 
-        // capture the whole batch
+        // capture the whole batch: compaction, then the branches forked from it and joined at the end
         cudaGraph_t g = nullptr;
         NAPG_CU(ctx, cudaStreamBeginCapture(b.stream, cudaStreamCaptureModeRelaxed));
         const uint64_t l0 = launches_so_far();
         k_ctx_compact<<<n_ctx, 1024, 0, b.stream>>>(b.masks, S, b.idx, idx_stride);
         napg_status rc = NAPG_OK;
-        for (int32_t k = 0; k < n_ctx && rc == NAPG_OK; ++k)
-            rc = run_context(ctx, b, b.stream, k, idx_stride, sva.data(), svb.data(), na, nb,
-                             stat ? stat[k] : nullptr, pval ? pval[k] : nullptr, n ? n[k] : nullptr);
+        cudaError_t ef = cudaEventRecord(b.fork, b.stream);
+        for (BatchBranch &r : b.br) {
+            if (r.ctxs.empty() || rc != NAPG_OK || ef != cudaSuccess) continue;
+            ef = cudaStreamWaitEvent(r.stream, b.fork, 0);
+            for (size_t q = 0; q < r.ctxs.size() && rc == NAPG_OK && ef == cudaSuccess; ++q) {
+                const int32_t k = r.ctxs[q];
+                rc = run_context(ctx, b, r, r.stream, k, idx_stride, sva.data(), svb.data(), na, nb,
+                                 stat ? stat[k] : nullptr, pval ? pval[k] : nullptr, n ? n[k] : nullptr);
+            }
+            if (ef == cudaSuccess) ef = cudaEventRecord(r.done, r.stream);
+            if (ef == cudaSuccess) ef = cudaStreamWaitEvent(b.stream, r.done, 0);
+        }
         const cudaError_t ec = cudaStreamEndCapture(b.stream, &g);
         ctx->trace.on = trace_on;
+        if (rc == NAPG_OK && ef != cudaSuccess) rc = cuda_fail(ctx, ef, "batch graph branches");
         if (rc != NAPG_OK) {
             if (g) cudaGraphDestroy(g);
             return rc;

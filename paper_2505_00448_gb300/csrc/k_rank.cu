@@ -14,6 +14,8 @@
 // Rank sums are accumulated in int64 and are exact.
 #include <type_traits>
 
+#include <algorithm>
+
 #include "napg_internal.cuh"
 
 namespace napg {
@@ -695,7 +697,7 @@ typedef unsigned __int128 u128;
 __global__ void k_mwu_exact(const double *__restrict__ stat, const int32_t *__restrict__ rcnt,
                             const int32_t *__restrict__ levoff, int32_t nb, const int32_t *__restrict__ flags,
                             const int32_t *__restrict__ nflag, int32_t max_flags, double *__restrict__ pval,
-                            u128 *__restrict__ scratch, int64_t cap) {
+                            u128 *__restrict__ scratch, int64_t cap, uint32_t *__restrict__ err) {
     const int32_t cnt = min(*nflag, max_flags);
     u128 *G = scratch + (int64_t)blockIdx.x * 2 * cap;
     u128 *H = G + cap;
@@ -738,25 +740,30 @@ __global__ void k_mwu_exact(const double *__restrict__ stat, const int32_t *__re
             }
         }
         __syncthreads();
+        // beyond the exact range the p-value stays NaN and the call reports it
+        if (threadIdx.x == 0 && isnan(s_p)) atomicOr(err, kErrExactLimit);
         if (threadIdx.x == 0) pval[t] = s_p;
         __syncthreads();
     }
 }
 
-size_t mwu_exact_scratch_bytes(int64_t S) {
-    // blocks x 2 arrays x (7 S / 2 + 2) entries covers auto mode (min group < 8)
-    const int64_t cap = 7 * S / 2 + 2;
+size_t mwu_exact_scratch_bytes(int64_t S, bool forced) {
+    // blocks x 2 arrays x (7 S / 2 + 2) entries covers auto mode (min group < 8);
+    // forced exact mode: the whole range min(U0, U1) <= S^2 / 8 where that stays
+    // within 65,536 entries per array (64 MiB in all), else 7 S / 2 + 2
+    int64_t cap = 7 * S / 2 + 2;
+    if (forced) cap = std::min<int64_t>(S * S / 8 + 2, std::max<int64_t>(cap, (int64_t)1 << 16));
     return (size_t)32 * 2 * (size_t)cap * sizeof(u128);
 }
 
 void launch_mwu_exact(const double *stat, const int32_t *rcnt, const int32_t *levoff, int32_t total_rows, int32_t nb,
                       const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags, double *pval,
-                      void *scratch, size_t scratch_bytes, cudaStream_t st) {
+                      void *scratch, size_t scratch_bytes, uint32_t *err, cudaStream_t st) {
     (void)total_rows;
     const int64_t cap = (int64_t)(scratch_bytes / (32 * 2 * sizeof(u128)));
     count_launch();
     k_mwu_exact<<<32, 128, 0, st>>>(stat, rcnt, levoff, nb, flag_list, flag_count, max_flags, pval, (u128 *)scratch,
-                                    cap);
+                                    cap, err);
 }
 
 }  // namespace napg

@@ -537,13 +537,13 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         { Stage s_(ctx->trace, st, "finalize_rankgroups"); launch_finalize_rankgroups(f, a.stat, a.pval, a.n, flags, counter, st); }
         pjobs_run(ctx, pj, a.pval, st);
         if (t == NAPG_MWU && a.pval) {
-            const size_t sb = mwu_exact_scratch_bytes(S);
+            const size_t sb = mwu_exact_scratch_bytes(S, a.opt.mwu_mode == 1);
             void *scratch = ws_get(ctx, ws, Workspace::kTmpG, sb, &st_);
             if (st_) return st_;
             if (!a.stat) return fail(ctx, NAPG_E_ARG, "exact Mann-Whitney p needs the stat buffer");
             Stage s_(ctx->trace, st, "mwu_exact");
             launch_mwu_exact(a.stat, rcnt, d_lo, R, nb, flags, counter, (int32_t)((int64_t)na * nb + 1), a.pval,
-                             scratch, sb, st);
+                             scratch, sb, ctx->dev_err, st);
         }
     }
     if (a.es1 || a.es2) {
@@ -552,6 +552,15 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         launch_effects(e, st);
     }
     NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
+napg_status device_error_status(napg_ctx *ctx, uint32_t bits) {
+    if (bits & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    if (bits & kErrExactLimit)
+        return fail(ctx, NAPG_E_UNSUPPORTED,
+                    "forced exact Mann-Whitney p beyond the exact range (min(n0, n1) > 64, C(n, n0) >= 2^126, or "
+                    "min(U0, U1) above max(3.5 x samples, 65,534)): those p-values are NaN");
     return NAPG_OK;
 }
 
@@ -642,7 +651,7 @@ napg_status run_with_outputs(napg_ctx *ctx, Workspace &ws, cudaStream_t st, RunA
     if (host_out) {
         NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         NAPG_CU(ctx, cudaStreamSynchronize(st));
-        if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+        if (*ctx->host_err) return device_error_status(ctx, *ctx->host_err);
     }
     return NAPG_OK;
 }
@@ -730,9 +739,10 @@ napg_status napg_sync(napg_ctx *ctx) {
     NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
     NAPG_CU(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->copy_stream) NAPG_CU(ctx, cudaStreamSynchronize(ctx->copy_stream));
-    if (*ctx->host_err & kErrTimeout) {
+    if (*ctx->host_err & (kErrTimeout | kErrExactLimit)) {
+        const uint32_t bits = *ctx->host_err;
         NAPG_CU(ctx, cudaMemset(ctx->dev_err, 0, sizeof(uint32_t)));
-        return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+        return device_error_status(ctx, bits);
     }
     return NAPG_OK;
 }
@@ -1030,7 +1040,7 @@ napg_status napg_run_part(napg_ctx *ctx, int32_t test, const napg_options *opt, 
     // synchronous: the row lists above live on the host
     NAPG_CU(ctx, cudaMemcpyAsync(ctx->host_err, ctx->dev_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     NAPG_CU(ctx, cudaStreamSynchronize(st));
-    if (*ctx->host_err & kErrTimeout) return fail(ctx, NAPG_E_TIMEOUT, "a device wait timed out");
+    if (*ctx->host_err) return device_error_status(ctx, *ctx->host_err);
     return NAPG_OK;
 }
 

@@ -21,7 +21,7 @@ constexpr int64_t kMaxSamples = (int64_t)1 << 24;      // counts stay exact in F
 constexpr int64_t kMaxRankSamples = 163840;  // per-pair rank state fits shared memory
 
 // Error flags raised by device-side checks (bitwise OR into a device word).
-enum : uint32_t { kErrLabel = 1u, kErrNonfinite = 2u, kErrTimeout = 4u, kErrIndex = 8u };
+enum : uint32_t { kErrLabel = 1u, kErrNonfinite = 2u, kErrTimeout = 4u, kErrIndex = 8u, kErrExactLimit = 16u };
 
 // A pair whose centred sum falls to rel_tol x its raw sum (about the column's
 // in-context mean) is recomputed exactly by the two-pass rescue: for the FP64
@@ -361,8 +361,11 @@ void launch_finalize_rankgroups(const RankGroupFin &f, double *stat, double *pva
                                 int32_t *flag_list, int32_t *flag_count, cudaStream_t st);
 void launch_mwu_exact(const double *stat, const int32_t *rcnt, const int32_t *levoff, int32_t total_rows,
                       int32_t nb, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
-                      double *pval, void *scratch, size_t scratch_bytes, cudaStream_t st);
-size_t mwu_exact_scratch_bytes(int64_t S);
+                      double *pval, void *scratch, size_t scratch_bytes, uint32_t *err, cudaStream_t st);
+// the status a finished call reports for the device error word `bits` (timeouts
+// first, then forced exact Mann-Whitney p-values beyond the exact range)
+napg_status device_error_status(napg_ctx *ctx, uint32_t bits);
+size_t mwu_exact_scratch_bytes(int64_t S, bool forced);
 void launch_fill_nan(double *p, int64_t count, cudaStream_t st);
 
 // mixed precision (tcgen05) path

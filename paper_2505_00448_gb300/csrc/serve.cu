@@ -234,6 +234,7 @@ static void scheduler(napg_ctx *ctx) {
                 if (r.pval) std::copy(s.h_p, s.h_p + r.cnt, r.pval);
                 if (r.n) std::copy(s.h_n, s.h_n + r.cnt, r.n);
                 if (*(volatile uint32_t *)s.h_err & kErrTimeout) status = NAPG_E_TIMEOUT;
+                else if (*(volatile uint32_t *)s.h_err & kErrExactLimit) status = NAPG_E_UNSUPPORTED;
             }
             {
                 std::lock_guard<std::mutex> lk(S.mu);

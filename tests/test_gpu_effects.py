@@ -85,7 +85,15 @@ def test_effect_sizes_plain(napg, cohort, test, a, b, opt):
     va, vb = sets[a], (sets[b] if b else None)
     if test == "kruskal":
         va = cohort["cat"][6:]
-    g = c.run(test, va, vb, out="numpy", effects=True, **opt)
+    nb = len(va) if vb is None else len(vb)
+    g = {k: np.empty((len(va), nb), np.int32 if k == "n" else np.float64)
+         for k in ("stat", "p", "n", "effect", "effect2")}
+    try:
+        c.run(test, va, vb, outputs=g, effects=True, **opt)
+    except napg.NapgError as e:
+        # forced exact Mann-Whitney beyond its exact range: p NaN for those pairs
+        # and the call says so; the effect size does not depend on the p-value mode
+        assert test == "mwu" and opt.get("mwu_mode") == "exact" and e.code == napg.E_UNSUPPORTED
     kw = {}
     if "welch" in opt:
         kw["welch"] = int(opt["welch"])

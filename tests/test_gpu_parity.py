@@ -314,6 +314,43 @@ def test_mwu_exact_mode(napg):
     c.close()
 
 
+def test_mwu_forced_exact_within_and_beyond_its_range(napg):
+    """Forced exact Mann-Whitney (Sec. 3.5.6): groups of 10-25 of 100 samples
+    without ties give the oracle's exact p; groups of 70 and more (beyond the
+    exact 128-bit range) give U exactly, p = NaN, and the call reports
+    NAPG_E_UNSUPPORTED after writing its outputs."""
+    rng = np.random.default_rng(18)
+
+    def cohort(S, g_lo, g_hi, k):
+        rows, vt, nl = [], [], []
+        for _ in range(k):
+            lab = np.ones(S)
+            lab[rng.choice(S, size=int(rng.integers(g_lo, g_hi + 1)), replace=False)] = 0.0
+            rows.append(lab); vt.append(1); nl.append(2)
+        for _ in range(4):
+            rows.append(rng.permutation(S).astype(float) + 0.5); vt.append(0); nl.append(0)
+        return {"X": np.array(rows), "vtype": np.array(vt, np.uint8), "nlev": np.array(nl, np.int32), "missing": NAN}
+
+    coh = cohort(100, 10, 25, 4)
+    c = ctx_for(napg, coh)
+    A, B = list(range(4)), list(range(4, 8))
+    compare("mwu", c.run("mwu", A, B, mwu_mode="exact", out="numpy"), oracle_run("mwu", coh, A, B, mwu_mode=1))
+    c.close()
+    coh = cohort(300, 70, 120, 3)
+    c = ctx_for(napg, coh)
+    A, B = list(range(3)), list(range(3, 7))
+    out = {"stat": np.full((3, 4), -1.0), "p": np.full((3, 4), -1.0), "n": np.full((3, 4), -1, np.int32)}
+    with pytest.raises(napg.NapgError) as e:
+        c.run("mwu", A, B, mwu_mode="exact", outputs=out)
+    assert e.value.code == napg.E_UNSUPPORTED
+    ref = oracle_run("mwu", coh, A, B, mwu_mode=1)
+    assert np.array_equal(out["stat"], ref[0]) and np.array_equal(out["n"], ref[2])
+    assert np.isnan(out["p"]).all()
+    # the context stays usable: the asymptotic mode on the same pairs
+    compare("mwu", c.run("mwu", A, B, mwu_mode="asymptotic", out="numpy"), oracle_run("mwu", coh, A, B, mwu_mode=2))
+    c.close()
+
+
 # -------------------------------------------------------------- errors --
 
 def test_reloading_cohorts_reuses_buffers(napg):
