@@ -626,9 +626,9 @@ def batch_main(args, world, rank, local_rank):
         # pinned host outputs (allocated once, outside the timed region)
         pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()
         host_outs = {t: [{"stat": pin((len(va), len(va)), torch.float64), "p": pin((len(va), len(va)), torch.float64),
-                          "n": pin((len(va), len(va)), torch.int32)} for _ in range(K)] for t, va in tests}
-        hmasks = [masks[k] for k in range(K)]
-        h2d = coh["X"].nbytes + masks.nbytes
+                          "n": pin((len(va), len(va)), torch.int32)} for _ in mine] for t, va in tests}
+        hmasks = [masks[k] for k in mine]           # this rank's contexts, as in the timed step
+        h2d = coh["X"].nbytes + sum(m.nbytes for m in hmasks)
         d2h = sum(sum(a.nbytes for a in o.values()) for v in host_outs.values() for o in v)
         ctx2 = napg.Context(device)
         times = []
@@ -640,9 +640,10 @@ def batch_main(args, world, rank, local_rank):
                 ctx2.run_batch(test, hmasks, va, out="numpy", outputs=host_outs[test], precision=prec)
             times.append(time.perf_counter() - t0)
         ctx2.close()
-        e2e = {"value": world * pairs_step / statistics.mean(times[1:] or times), "unit": UNIT,
+        t_e2e = D.max_over_ranks(statistics.mean(times[1:] or times), dist)    # the slowest rank
+        e2e = {"value": pairs_step / t_e2e, "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": 1000 * statistics.mean(times[1:] or times),
+               "ms_per_step": 1000 * t_e2e,
                "path": "host outputs: the captured graph writes device buffers, then every context's outputs "
                        "are copied to pinned host arrays"}
 
@@ -697,13 +698,21 @@ def paper_sim_main(args, world, rank, local_rank):
     categorical and dichotomous features with 10% missing per feature, on the two
     lines of its runtime figures (S = 1,000 with F in 250..1,000; F = 1,000 with S
     in 250..1,000). Every test in the plain FP64 form; device time per call
-    (median of the timed calls after the warm-up ones)."""
+    (median of the timed calls after the warm-up ones). Over N GPUs the grid's
+    calls are dealt round robin; value = every rank's pairs over the slowest
+    rank's summed device time."""
     import torch
     from paper_2505_00448_gb300 import napg
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
     device = local_rank if world > 1 else 0
     torch.cuda.set_device(device)
     grid = sorted({(F, 1000) for F in (250, 500, 750, 1000)} | {(1000, S) for S in (250, 500, 750, 1000)})
     rows = []
+    skipped = []
     total_pairs = 0
     total_ms = 0.0
     launches0 = napg.kernel_launches()
@@ -716,6 +725,10 @@ def paper_sim_main(args, world, rank, local_rank):
                  ("ttest", coh["bins"], coh["cont"]), ("mwu", coh["bins"], coh["cont"]),
                  ("anova", coh["cat"], coh["cont"]), ("kruskal", coh["cat"], coh["cont"])]
         for test, va, vb in tests:
+            call = len(rows) + len(skipped)
+            if call % world != rank:
+                skipped.append(call)
+                continue
             nb = len(va) if vb is None else len(vb)
             dev = torch.device("cuda", device)
             out = {"stat": torch.empty((len(va), nb), dtype=torch.float64, device=dev),
@@ -739,9 +752,12 @@ def paper_sim_main(args, world, rank, local_rank):
             total_ms += med
         ctx.close()
     launches = napg.kernel_launches() - launches0
+    total_pairs = D.sum_over_ranks(total_pairs, dist)
+    total_ms = D.max_over_ranks(total_ms, dist)
+    launches = int(D.sum_over_ranks(launches, dist))
     value = total_pairs / (total_ms / 1000.0)
     cpu = None
-    if not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         coh = synth.paper_simulation(1000, 1000)
         tests = [("pearson", coh["cont"], None), ("spearman", coh["cont"], None), ("chi2", coh["cat"], None),
                  ("ttest", coh["bins"], coh["cont"]), ("mwu", coh["bins"], coh["cont"]),
@@ -749,9 +765,11 @@ def paper_sim_main(args, world, rank, local_rank):
         cpu = oracle_sample(coh, tests, budget_s=min(args.cpu_budget, 14.0))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "the paper's simulated benchmark: uniform [0,1] continuous, c = 4 categorical "
+                "config": {"parallelism": (f"the grid's calls dealt round robin over {world} GPUs" if world > 1
+                                           else "1 GPU"),
+                           "workload": "the paper's simulated benchmark: uniform [0,1] continuous, c = 4 categorical "
                            "and dichotomous features, 10% missing per feature; S = 1,000 with F = 250..1,000 and "
                            "F = 1,000 with S = 250..1,000; all seven tests, plain FP64 form; one step = every "
                            "(test, F, S) call once; value = pairs over the summed device times",
@@ -944,15 +962,21 @@ def main():
             t0 = time.perf_counter()
             ctx2.load_cohort(Xh, coh["vtype"], coh["nlev"], coh["missing"])
             for test, va, vb in tests:
-                ctx2.run(test, va, vb, outputs=host_out[test], out="numpy", sync=False, precision=prec)
+                if world > 1:       # this rank's part (synchronous), as in the timed step
+                    ctx2.run_part(test, va, vb, part=rank, nparts=world, outputs=host_out[test], precision=prec)
+                else:
+                    ctx2.run(test, va, vb, outputs=host_out[test], out="numpy", sync=False, precision=prec)
             ctx2.sync()
             dt = time.perf_counter() - t0
             if k > 0:
                 times.append(dt)
         ctx2.close()
-        # the median step: a host-timed loop sees the host's own jitter
-        e2e = {"value": world * pairs_step / statistics.median(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * statistics.median(times),
+        if world > 1:
+            h2d += d2h      # a part's host outputs are staged on the device first (other parts' entries kept)
+        # the median step (a host-timed loop sees the host's own jitter), slowest rank
+        t_e2e = D.max_over_ranks(statistics.median(times), dist)
+        e2e = {"value": pairs_step / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000 * t_e2e,
                "ms_steps": [round(1000 * t, 2) for t in times]}
 
     # error of the timed (last step's) outputs against the FP64 oracle on sampled pairs

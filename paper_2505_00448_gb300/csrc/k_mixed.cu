@@ -323,6 +323,200 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
     if (warp == 1) tmem_dealloc(tbase, TCOLS);
 }
 
+// ------------------------------------------------------ Sxy (Sec. 3.5.2) --
+//
+// Sum over the co-observed samples of x~_i x~_j for the pairs of a triangle
+// tile (I <= J) of 128 x 128 variables, from the FP16 planes Xh, Xl of the
+// centred, scaled values (zero where a value is missing, so every product off
+// the co-observed set vanishes). Per K-block of 64 samples the MMA thread
+// issues the three small cross products (Xh Xl, Xl Xh, Xl Xl: 2^-11 and 2^-22
+// of Xh Xh, random sign) first and Xh Xh last, all into one accumulator that
+// starts the K-block at zero: the Xh Xh sum is rounded over its own 4
+// instructions, as when drained alone every K-block (correlated pairs add
+// same-sign terms, and the accumulator's per-instruction rounding error grows
+// with the instructions between restarts). Four such accumulators fill the 512
+// columns of tensor memory: a chunk is two K-blocks, each in its own
+// accumulator, and two chunks are in flight. The epilogue adds a chunk's two
+// K-block sums in FP32 (round to nearest, so the added error has no bias) and
+// folds the result into float-float running sums by TwoSum: one TwoSum per two
+// K-blocks of MMAs.
+constexpr int kSxyStages = 3;
+
+struct SxyParams {
+    CUtensorMap mapH, mapL;        // Xh, Xl planes [rows_pad][S_pad], box 64 x 128
+    int rows, tiles, nkb;          // variables, 128-row tiles, K-blocks
+    double *out;                   // Sxy[i][j] for i in tile I, j in tile J (I <= J), row-major, ld
+    int64_t ld;
+    const int8_t *sexp;            // per-row scale exponents: the output is divided by 2^(e_i + e_j)
+    uint32_t *err;
+    const uint8_t *own;            // rows computed (a split call's part; NULL: all)
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_sxy(const __grid_constant__ SxyParams P) {
+    constexpr int T_BYTES = kTM * kKB * 2;             // one 128 x 64 FP16 tile
+    constexpr int STAGE_BYTES = 4 * T_BYTES;           // Ah, Al, Bh, Bl
+    constexpr int N = kTM;
+    constexpr int HC = N / 2;                          // columns per epilogue thread
+    constexpr int H2 = HC / 2;
+    constexpr uint32_t IDESC = idesc_f16_f32(kTM, N);
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + kSxyStages * STAGE_BYTES);
+    uint64_t *empty = full + kSxyStages;
+    uint64_t *tfull = empty + kSxyStages;   // [2] chunk accumulators ready
+    uint64_t *tempty = tfull + 2;           // [2] chunk accumulators drained
+    uint64_t *mdone = tempty + 2;
+    uint32_t *tslot = (uint32_t *)(mdone + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int I, J;
+    tile_coords(blockIdx.x, P.tiles, P.tiles, 1, 0, I, J);
+    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;   // another part's rows
+    const bool diag = I == J;                  // B is A: loaded once
+    const int nchunks = (P.nkb + 1) / 2;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSxyStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
+        mbar_init(mdone, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tmem_alloc(tslot, 512);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            prefetch_tmap(&P.mapH);
+            prefetch_tmap(&P.mapL);
+            const uint32_t bytes = diag ? 2 * T_BYTES : STAGE_BYTES;
+            int issued = 0;
+            for (int kb = 0; kb < P.nkb; ++kb) {
+                const int s = kb % kSxyStages;
+                if (kb >= kSxyStages && !mbar_wait(&empty[s], ((kb / kSxyStages) - 1) & 1, P.err)) break;
+                mbar_arrive_expect_tx(&full[s], bytes);
+                uint8_t *st = smem + s * STAGE_BYTES;
+                tma_load_2d(st, &P.mapH, &full[s], kb * kKB, I * kTM);
+                tma_load_2d(st + T_BYTES, &P.mapL, &full[s], kb * kKB, I * kTM);
+                if (!diag) {
+                    tma_load_2d(st + 2 * T_BYTES, &P.mapH, &full[s], kb * kKB, J * kTM);
+                    tma_load_2d(st + 3 * T_BYTES, &P.mapL, &full[s], kb * kKB, J * kTM);
+                }
+                issued = kb + 1;
+            }
+            // our own copies must have landed before the CTA tears down
+            for (int kb = issued - kSxyStages < 0 ? 0 : issued - kSxyStages; kb < issued; ++kb)
+                mbar_wait(&full[kb % kSxyStages], (kb / kSxyStages) & 1, P.err);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint64_t dbase = sdesc_sw128(smem_u32(smem));
+            // descriptor offsets (16-byte units) of Ah, Al, Bh, Bl within a stage
+            constexpr uint32_t oAh = 0, oAl = T_BYTES >> 4;
+            const uint32_t oBh = diag ? 0u : (uint32_t)(2 * T_BYTES) >> 4;
+            const uint32_t oBl = diag ? (uint32_t)T_BYTES >> 4 : (uint32_t)(3 * T_BYTES) >> 4;
+            int kb = 0;
+            bool ok = true;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                const int b = c & 1;
+                if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
+                fence_after_sync();
+                const int kb_end = min(P.nkb, 2 * c + 2);
+                for (; kb < kb_end; ++kb) {
+                    const int s = kb % kSxyStages;
+                    if (!mbar_wait(&full[s], (kb / kSxyStages) & 1, P.err)) { ok = false; break; }
+                    fence_after_sync();
+                    const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
+                    const uint32_t d = tbase + (uint32_t)((2 * b + (kb & 1)) * N);
+#pragma unroll
+                    for (int k = 0; k < kKB / 16; ++k)      // Xh Xl (restarts the accumulator)
+                        mma_f16(d, ds + oAh + 2 * k, ds + oBl + 2 * k, IDESC, k ? 1u : 0u);
+#pragma unroll
+                    for (int k = 0; k < kKB / 16; ++k)      // Xl Xh
+                        mma_f16(d, ds + oAl + 2 * k, ds + oBh + 2 * k, IDESC, 1u);
+#pragma unroll
+                    for (int k = 0; k < kKB / 16; ++k)      // Xl Xl
+                        mma_f16(d, ds + oAl + 2 * k, ds + oBl + 2 * k, IDESC, 1u);
+#pragma unroll
+                    for (int k = 0; k < kKB / 16; ++k)      // Xh Xh, last
+                        mma_f16(d, ds + oAh + 2 * k, ds + oBh + 2 * k, IDESC, 1u);
+                    mma_commit(&empty[s]);                   // frees the stage once these MMAs are done
+                }
+                if (!ok) break;
+                mma_commit(&tfull[b]);
+            }
+            mma_commit(mdone);
+        }
+        __syncwarp();
+        mbar_wait(mdone, 0, P.err);
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int ew = warp - 2;               // 0..7
+        const int q = warp & 3;                // TMEM lane quadrant this warp may access
+        const int half = ew >> 2;              // which half of the columns
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        uint64_t hi[H2], lo[H2];               // float-float running sums, two columns per register pair
+#pragma unroll
+        for (int k = 0; k < H2; ++k) hi[k] = lo[k] = 0ull;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            if (!mbar_wait(&tfull[b], (c >> 1) & 1, P.err)) { ok = false; break; }
+            fence_after_sync();
+            const bool two = 2 * c + 1 < P.nkb;
+            const uint32_t a0 = tbase + lane_addr + (uint32_t)(2 * b * N + half * HC);
+#pragma unroll
+            for (int g = 0; g < HC / 8; ++g) {
+                uint32_t r0[8], r1[8];
+                tmem_ld8(a0 + g * 8, r0);
+                if (two) tmem_ld8(a0 + N + g * 8, r1);
+                tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    uint64_t v = pk2(__uint_as_float(r0[2 * k]), __uint_as_float(r0[2 * k + 1]));
+                    if (two) v = add2(v, pk2(__uint_as_float(r1[2 * k]), __uint_as_float(r1[2 * k + 1])));
+                    two_sum2(hi[g * 4 + k], lo[g * 4 + k], v);
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        if (ok) {
+            const int gi = I * kTM + row;
+            if (gi < P.rows) {
+                const int ei = P.sexp ? (int)P.sexp[gi] : 0;
+#pragma unroll
+                for (int k = 0; k < H2; ++k) {
+                    float h0, h1, l0, l1;
+                    unpk2(hi[k], h0, h1);
+                    unpk2(lo[k], l0, l1);
+#pragma unroll
+                    for (int e2 = 0; e2 < 2; ++e2) {
+                        const int col = J * N + half * HC + 2 * k + e2;
+                        if (col < P.rows) {
+                            const double v = (double)(e2 ? h1 : h0) + (double)(e2 ? l1 : l0);
+                            const int e = ei + (P.sexp ? (int)P.sexp[col] : 0);
+                            P.out[(int64_t)gi * P.ld + col] = ldexp(v, -e);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 1) tmem_dealloc(tbase, 512);
+}
+
 // --------------------------------------------------- stacked contraction --
 //
 // A 0/1 plane (observed mask or one-hot levels) against the planes M, Xh, Xl,
@@ -856,6 +1050,16 @@ static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int til
     return NAPG_OK;
 }
 
+static napg_status launch_sxy(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st) {
+    const size_t smem = (size_t)kSxyStages * 4 * kTM * kKB * 2 + 1024 + 256;
+    NAPG_CU(ctx, cudaFuncSetAttribute(k_sxy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (tiles == 0) return NAPG_OK;
+    count_launch();
+    k_sxy<<<tiles, kThreads, smem, st>>>(P);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
 template <int NPL, int SV, int ROLE0>
 static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
     constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * SV / 2 * kKB * 2;
@@ -991,13 +1195,12 @@ static napg_status prep_onehot(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStre
     return NAPG_OK;
 }
 
-// K-blocks (of 64 samples) between drains: Sxy of correlated pairs has
-// same-sign terms and the accumulator's per-instruction rounding adds up within
-// a chunk, so its hi*hi sum is drained every K-block; the stacked sums (counts,
-// centred x~ and centred squares, per variable or per level) random-walk, are
-// far from the bar, and drain every 16 (a drain of the stacked accumulator
-// takes longer than 4 K-blocks of MMAs, so shorter chunks would stall the pair).
-constexpr int kChunkSxy = 1;
+// K-blocks (of 64 samples) between drains of the stacked sums: they are
+// counts, centred x~ and centred squares (per variable or per level), whose
+// partial sums random-walk instead of growing with the chunk, so their FP32
+// accumulation error stays far from the bar; a drain of the stacked
+// accumulator takes longer than 4 K-blocks of MMAs, so shorter chunks would
+// stall the pair.
 constexpr int kChunkStacked = 16;
 
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
@@ -1007,33 +1210,15 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
     NAPG_ST(prep_cont_planes(ctx, c, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp, cache_vars));
     const int nkb = (int)(cp.S_pad / kKB);
     const int T = (int)(cp.rows_pad / kTM);
-    // P1: triangle tiles, N = 128, Sxy only. The hi*hi product alone is
-    // accumulated in short chunks drained into float-float sums (the tensor core
-    // rounds its FP32 accumulator about once per instruction, so the error grows
-    // with the instructions per chunk, and correlated pairs have same-sign terms);
-    // the three small cross products (hi*lo, lo*hi, lo*lo: random sign, 2^-11
-    // smaller) stay resident for the whole K loop. Dropping lo*lo would bias
-    // Sxy low on correlated pairs (it is a square on the diagonal).
+    // P1: Sxy on the triangle tiles (k_sxy).
     {
-        UmmaParams<2, 2, 4> P{};
-        const void *pl[2] = {cp.Xh, cp.Xl};
-        for (int k = 0; k < 2; ++k) {
-            if (!make_map(&P.mapA[k], pl[k], cp.rows_pad, cp.S_pad, kTM) ||
-                !make_map(&P.mapB[k], pl[k], cp.rows_pad, cp.S_pad, 128))
-                return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        }
-        P.prod[0] = {0, 0, 0, 0};    // Xh Xh -> Sxy hi (drained 0)
-        P.prod[1] = {0, 1, -1, 0};   // Xh Xl -> Sxy cross (resident 0, float)
-        P.prod[2] = {1, 0, -1, 0};   // Xl Xh
-        P.prod[3] = {1, 1, -1, 0};   // Xl Xl
-        P.rowsA = nv; P.rowsB = nv; P.tilesA = T; P.tilesB = T; P.triangle = 1;
-        P.nkb = nkb; P.chunk = kChunkSxy;
-        P.out_drain[0] = Sxy; P.out_drain[1] = nullptr; P.ld = nv;
-        P.out_res = nullptr; P.res_sym = 0; P.res_into[0] = 0; P.err = ctx->dev_err;
-        P.expA[0] = cp.sexp; P.expB[0] = cp.sexp;
-        P.own = own;
+        SxyParams P{};
+        if (!make_map(&P.mapH, cp.Xh, cp.rows_pad, cp.S_pad, kTM) || !make_map(&P.mapL, cp.Xl, cp.rows_pad, cp.S_pad, kTM))
+            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        P.rows = nv; P.tiles = T; P.nkb = nkb;
+        P.out = Sxy; P.ld = nv; P.sexp = cp.sexp; P.err = ctx->dev_err; P.own = own;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST((launch_umma<128, 2, 2, 4, 1, 1, true, 3>(ctx, P, T * (T + 1) / 2, st)));
+        NAPG_ST(launch_sxy(ctx, P, T * (T + 1) / 2, st));
     }
     // P2: all ordered (A tile, B tile) pairs, the mask as A against the stacked
     // planes of kSV B variables: n = M M^T, sum_s m_i x~_j = Sx[j][i] and
