@@ -330,14 +330,21 @@ napg_status napg_trace_read(napg_ctx *ctx, char *buf, size_t cap);
 
 /* Autotuner (on by default): the first run of a problem shape times each
  * launch-shape candidate of its tunable kernels once (the B-tile width of the
- * stacked tensor contractions, threads per pair of the rank kernels) and keeps
- * the fastest for the context; candidates give identical results. Runs being
- * captured into a CUDA graph use the choice recorded for the nearest shape.
+ * stacked tensor contractions, the samples per pipeline stage of the Sxy
+ * contraction, threads per pair of the rank kernels) and keeps the fastest for
+ * the context; candidates give identical results. Runs being captured into a
+ * CUDA graph use the choice recorded for the nearest shape.
  * napg_tune_read writes the records as JSON
  *   [{"kind": K, "rows_a": A, "rows_b": B, "k": L, "choice": C, "ms": [...]}, ...]
- * Errors: NAPG_E_ARG (NULL context, buffer too small). */
+ * napg_tune_pin fixes the candidate (0 or 1) of one kind for every later run
+ * of the context, without timing; choice -1 unpins. Kinds: "stacked_mask",
+ * "stacked_onehot", "stacked_onehot_counts_sums", "stacked_observed_squares",
+ * "sxy_stage_samples", "spearman_threads", "rank_groups_threads".
+ * Errors: NAPG_E_ARG (NULL context, buffer too small, unknown kind, choice
+ * outside [-1, 1]). */
 napg_status napg_tune_enable(napg_ctx *ctx, int32_t on);
 napg_status napg_tune_read(napg_ctx *ctx, char *buf, size_t cap);
+napg_status napg_tune_pin(napg_ctx *ctx, const char *kind, int32_t choice);
 
 /* Number of kernels this process has launched through the library so far. */
 uint64_t napg_kernel_launches(void);

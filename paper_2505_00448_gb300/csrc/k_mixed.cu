@@ -17,11 +17,11 @@
 //                                     n = M M^T, Sx^T = M X~^T, Sxx^T = M D^T + v n
 // Group sums (Sec. 3.5.5, 3.5.7):     n_g = H M^T, S1 = H X~^T, S2 = H D^T + v n_g
 // Contingency tables (Sec. 3.5.4):    T = H H^T
-// 0/1 operands give integer sums that FP32 holds exactly (S < 2^24), so n, n_g
-// and T stay in tensor memory for the whole K loop. The other sums are
-// accumulated in short K-chunks in tensor memory and drained by the epilogue
-// warps into running sums (float-float where the terms may all be positive),
-// which bounds the FP32 accumulation error independently of S.
+// 0/1 operands give integer sums that FP32 holds exactly (S < 2^24): T stays in
+// tensor memory for the whole K loop, and n, n_g are drained as integers. The
+// other sums are accumulated in short K-chunks in tensor memory and drained by
+// the epilogue warps into float-float running sums, which bounds the FP32
+// accumulation error independently of S.
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
@@ -35,51 +35,10 @@ using namespace umma;
 constexpr int kKB = 64;    // samples per K-block: one 128-byte swizzle row of 16-bit values
 constexpr int kTM = 128;   // rows of an A tile (M of the MMA)
 
-struct Prod {
-    // plane of A, plane of B, accumulator (d >= 0: drained d; -1 - r: resident r),
-    // first writer of that accumulator
-    int8_t a, b, acc, first;
-};
-
-template <int NA, int NB, int NP>
-struct UmmaParams {
-    CUtensorMap mapA[NA];
-    CUtensorMap mapB[NB];
-    Prod prod[NP];
-    int rowsA, rowsB;          // valid rows of A and B
-    int tilesA, tilesB;        // tile counts along A rows and B rows
-    int triangle;              // 1: only tiles with I <= J
-    int a_fastest;             // full grids: 1 = consecutive CTAs step through A tiles (share the B tile)
-    int nkb;                   // K-blocks
-    int chunk;                 // K-blocks per drain chunk
-    double *out_drain[2];      // drained sums, row-major [rowsA][ld]
-    int64_t ld;
-    int32_t *out_res;          // resident accumulator 0: integer sums, row-major [rowsA][ld]
-    int res_sym;               // also write out_res transposed
-    int out_transpose;         // write every output at [col][row] instead of [row][col]
-    int res_into[3];           // float resident r: added into drained output res_into[r]
-    const int8_t *expA[2];     // drained output d: per-row scale exponents of A (NULL: 0)
-    const int8_t *expB[2];     // ... and of B; the output is divided by 2^(eA + eB)
-    uint32_t *err;
-    const uint8_t *own;        // triangle launches of a split call: A rows computed (NULL: all)
-};
-
-// Full grids: the operand with more planes should be the one the concurrently
-// resident CTAs share, so that each wave streams it from HBM about once.
-__device__ __forceinline__ void tile_coords(int t, int tilesA, int tilesB, int triangle, int a_fastest, int &I,
-                                            int &J) {
-    if (!triangle) {
-        if (a_fastest) {
-            J = t / tilesA;
-            I = t - J * tilesA;
-        } else {
-            I = t / tilesB;
-            J = t - I * tilesB;
-        }
-        return;
-    }
+// Triangle tiles (I <= J) of a T x T tile grid in row order: t -> (I, J)
+__device__ __forceinline__ void tri_coords(int t, int T, int &I, int &J) {
     int i = 0;
-    while (t >= tilesB - i) { t -= tilesB - i; ++i; }
+    while (t >= T - i) { t -= T - i; ++i; }
     I = i;
     J = i + t;
 }
@@ -88,45 +47,56 @@ __device__ __forceinline__ void tile_coords(int t, int tilesA, int tilesB, int t
 // epilogue (two warps per TMEM lane quadrant, each half the columns).
 constexpr int kThreads = 320;
 
-// Resident accumulator 0 (if NRES > 0) holds exact integer sums unless there is
-// no integer output; the other residents hold small FP32 sums added to a
-// drained output at the end.
-template <int N, int NA, int NB, int NP, int NDRAIN, int NRES, bool FF, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ UmmaParams<NA, NB, NP> P) {
-    constexpr int A_BYTES = kTM * kKB * 2;
-    constexpr int B_BYTES = N * kKB * 2;
-    constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
-    constexpr int RESC = NRES * N;             // first column of the chunk buffers
-    constexpr int USED = RESC + 2 * NDRAIN * N;
-    constexpr int TCOLS = USED <= 32 ? 32 : USED <= 64 ? 64 : USED <= 128 ? 128 : USED <= 256 ? 256 : 512;
-    static_assert(USED <= 512, "tensor memory has 512 columns");
-    static_assert(N % 32 == 0 && N >= 32 && N <= 256, "N");
+// ----------------------------------------- contingency counts (Sec. 3.5.4) --
+//
+// T[r][c] = sum_s H[r][s] H[c][s] over the one-hot level rows r, c: the number
+// of samples in level r of one categorical and level c of another (0 where
+// either is missing). Integer sums below 2^24 are exact in FP32, so the counts
+// stay in tensor memory for the whole K loop. Tiles are 128 level rows (A) by
+// 256 (B, one MMA of N = 256) over the upper triangle: tile (I, J) for
+// J * 256 + 255 >= I * 128; each pair (r, c), r <= c, is written once, at
+// (r, c) and (c, r), by the tile that holds it with r in A. Four 48 KB stages.
+constexpr int kCountN = 256, kCountStages = 4;
+
+struct CountParams {
+    CUtensorMap mapA;              // one-hot plane [rows_pad][S_pad], box 64 x 128
+    CUtensorMap mapB;              // the same plane, box 64 x 256
+    int rows, tilesA, tilesB, nkb; // level rows, 128-row tiles, 256-row tiles, K-blocks
+    int32_t *out;                  // T [rows][ld], both triangles
+    int64_t ld;
+    uint32_t *err;
+    const uint8_t *own;            // level rows computed (a split call's part; NULL: all)
+};
+
+__global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ CountParams P) {
+    constexpr int N = kCountN;
+    constexpr int A_BYTES = kTM * kKB * 2, B_BYTES = N * kKB * 2, STAGE_BYTES = A_BYTES + B_BYTES;
     constexpr int HC = N / 2;                  // columns per epilogue thread
-    constexpr int ND = NDRAIN > 0 ? NDRAIN : 1;
     constexpr uint32_t IDESC = idesc_f16_f32(kTM, N);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *tfull = empty + STAGES;     // [2] chunk accumulators ready
-    uint64_t *tempty = tfull + 2;         // [2] chunk accumulators drained
-    uint64_t *mdone = tempty + 2;         // all MMAs of this CTA retired
-    uint32_t *tslot = (uint32_t *)(mdone + 1);
+    uint64_t *full = (uint64_t *)(smem + kCountStages * STAGE_BYTES);
+    uint64_t *empty = full + kCountStages;
+    uint64_t *tfull = empty + kCountStages;
+    uint32_t *tslot = (uint32_t *)(tfull + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int I, J;
-    tile_coords(blockIdx.x, P.tilesA, P.tilesB, P.triangle, P.a_fastest, I, J);
-    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rowsA)) return;   // another part's rows
-    const int nchunks = NDRAIN ? (P.nkb + P.chunk - 1) / P.chunk : 1;
+    // tile t -> (I, J): row tile I takes the column tiles J >= I / 2
+    int I = 0, J = 0;
+    {
+        int t = blockIdx.x;
+        while (t >= P.tilesB - I / 2) { t -= P.tilesB - I / 2; ++I; }
+        J = I / 2 + t;
+    }
+    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;   // another part's rows
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
-        mbar_init(mdone, 1);
+        for (int s = 0; s < kCountStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(tfull, 1);
         fence_mbar_init();
     }
-    if (warp == 1) tmem_alloc(tslot, TCOLS);
+    if (warp == 1) tmem_alloc(tslot, N);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -134,183 +104,64 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
-        // The whole warp runs the loop (uniform control flow); lane 0 issues.
-        const uint32_t leader = lane == 0;
-        if (leader) {
-            for (int p = 0; p < NA; ++p) prefetch_tmap(&P.mapA[p]);
-            for (int p = 0; p < NB; ++p) prefetch_tmap(&P.mapB[p]);
+        if (lane == 0) {
+            prefetch_tmap(&P.mapA);
+            prefetch_tmap(&P.mapB);
+            int issued = 0;
+            for (int kb = 0; kb < P.nkb; ++kb) {
+                const int s = kb % kCountStages;
+                if (kb >= kCountStages && !mbar_wait(&empty[s], ((kb / kCountStages) - 1) & 1, P.err)) break;
+                mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                uint8_t *st = smem + s * STAGE_BYTES;
+                tma_load_2d(st, &P.mapA, &full[s], kb * kKB, I * kTM);
+                tma_load_2d(st + A_BYTES, &P.mapB, &full[s], kb * kKB, J * N);
+                issued = kb + 1;
+            }
+            // our own copies must have landed before the CTA tears down
+            for (int kb = issued - kCountStages < 0 ? 0 : issued - kCountStages; kb < issued; ++kb)
+                mbar_wait(&full[kb % kCountStages], (kb / kCountStages) & 1, P.err);
         }
-        int issued = 0;
-        for (int kb = 0; kb < P.nkb; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
-            mbar_arrive_expect_tx_by(&full[s], STAGE_BYTES, leader);
-            uint8_t *st = smem + s * STAGE_BYTES;
-#pragma unroll
-            for (int p = 0; p < NA; ++p)
-                tma_load_2d_by(st + p * A_BYTES, &P.mapA[p], &full[s], kb * kKB, I * kTM, leader);
-#pragma unroll
-            for (int p = 0; p < NB; ++p)
-                tma_load_2d_by(st + NA * A_BYTES + p * B_BYTES, &P.mapB[p], &full[s], kb * kKB, J * N, leader);
-            issued = kb + 1;
-        }
-        // our own copies must have landed before the CTA tears down
-        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-            mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
+        __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        // Whole warp in the loop, lane 0 issues. Descriptors are the stage's base
-        // descriptor plus precomputed offsets (start address in 16-byte units in
-        // the low bits; shared addresses stay below 2^18 so no carry leaves them).
-        const uint32_t leader = lane == 0;
-        uint32_t aoff[NP], boff[NP], tcol[NP], drained[NP], first[NP];
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            const Prod pr = P.prod[q];
-            aoff[q] = (uint32_t)(pr.a * A_BYTES) >> 4;
-            boff[q] = (uint32_t)(NA * A_BYTES + pr.b * B_BYTES) >> 4;
-            drained[q] = pr.acc >= 0;
-            tcol[q] = pr.acc < 0 ? (uint32_t)(-1 - pr.acc) * N : (uint32_t)(RESC + pr.acc * N);
-            first[q] = pr.first;
-        }
-        const uint64_t dbase = sdesc_sw128(smem_u32(smem));
-        int kb = 0;
-        bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            const int b = c & 1;
-            if (NDRAIN && c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
-            fence_after_sync();
-            const int kb_end = NDRAIN ? min(P.nkb, (c + 1) * P.chunk) : P.nkb;
-            const int kb_chunk0 = kb;
-            const uint32_t cbuf = (uint32_t)(b * ND * N);
-            for (; kb < kb_end; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+        if (lane == 0) {
+            const uint64_t dbase = sdesc_sw128(smem_u32(smem));
+            bool ok = true;
+            for (int kb = 0; kb < P.nkb; ++kb) {
+                const int s = kb % kCountStages;
+                if (!mbar_wait(&full[s], (kb / kCountStages) & 1, P.err)) { ok = false; break; }
                 fence_after_sync();
                 const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
 #pragma unroll
-                for (int k = 0; k < kKB / 16; ++k) {
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        const uint64_t ad = ds + (uint64_t)(aoff[q] + 2 * k);
-                        const uint64_t bd = ds + (uint64_t)(boff[q] + 2 * k);
-                        const uint32_t col = drained[q] ? tcol[q] + cbuf : tcol[q];
-                        const bool restart = first[q] && k == 0 && (drained[q] ? kb == kb_chunk0 : kb == 0);
-                        mma_f16_by(tbase + col, ad, bd, IDESC, restart ? 0u : 1u, leader);
-                    }
-                }
-                mma_commit_by(&empty[s], leader);      // frees the stage once these MMAs are done
+                for (int k = 0; k < kKB / 16; ++k)
+                    mma_f16(tbase, ds + 2 * k, ds + (A_BYTES >> 4) + 2 * k, IDESC, (kb | k) ? 1u : 0u);
+                mma_commit(&empty[s]);             // frees the stage once these MMAs are done
             }
-            if (!ok) break;
-            mma_commit_by(&tfull[b], leader);          // chunk (and, last, the resident sums) ready
+            if (ok) mma_commit(tfull);
         }
-        mma_commit_by(mdone, leader);
-        mbar_wait(mdone, 0, P.err);
+        __syncwarp();
     } else {
         // ---------------------------------------------------------- epilogue
         const int ew = warp - 2;               // 0..7
         const int q = warp & 3;                // TMEM lane quadrant this warp may access
         const int half = ew >> 2;              // which half of the columns
-        const int row = q * 32 + lane;
-        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-        // running sums: FF = float-float pairs packed two columns per register pair
-        constexpr int H2 = HC / 2;
-        uint64_t hi[ND][H2];
-        uint64_t lo[ND][FF ? H2 : 1];
-#pragma unroll
-        for (int d = 0; d < ND; ++d)
-#pragma unroll
-            for (int k = 0; k < H2; ++k) {
-                hi[d][k] = 0ull;
-                if (FF) lo[d][FF ? k : 0] = 0ull;
-            }
-        bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            if (!mbar_wait(&tfull[b], (c >> 1) & 1, P.err)) { ok = false; break; }
+        const int gi = I * kTM + q * 32 + lane;
+        if (mbar_wait(tfull, 0, P.err)) {
             fence_after_sync();
-            if (NDRAIN) {
-#pragma unroll
-                for (int d = 0; d < ND; ++d) {
-#pragma unroll
-                    for (int g = 0; g < HC / 16; ++g) {
-                        uint32_t r[16];
-                        tmem_ld16(tbase + lane_addr + RESC + (b * ND + d) * N + half * HC + g * 16, r);
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
-                            if (FF) two_sum2(hi[d][g * 8 + k], lo[d][FF ? g * 8 + k : 0], v);
-                            else hi[d][g * 8 + k] = add2(hi[d][g * 8 + k], v);
-                        }
-                    }
-                }
-                fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[b]);
-            }
-        }
-        if (ok) {
-            const int gi = I * kTM + row;
-            const bool row_ok = gi < P.rowsA;
-            // small resident sums join their drained outputs (resident 0 does too
-            // when there is no integer output)
-#pragma unroll
-            for (int rr = 0; rr < NRES; ++rr) {
-                if (rr == 0 && P.out_res != nullptr) continue;
-                const int d = P.res_into[rr];
-#pragma unroll
-                for (int g = 0; g < HC / 16; ++g) {
-                    uint32_t r[16];
-                    tmem_ld16(tbase + lane_addr + rr * N + half * HC + g * 16, r);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
-#pragma unroll
-                        for (int dd = 0; dd < ND; ++dd)
-                            if (dd == d) {
-                                if (FF) lo[dd][FF ? g * 8 + k : 0] = add2(lo[dd][FF ? g * 8 + k : 0], v);
-                                else hi[dd][g * 8 + k] = add2(hi[dd][g * 8 + k], v);
-                            }
-                    }
-                }
-            }
-            if (NRES > 0 && P.out_res != nullptr) {
-#pragma unroll
-                for (int g = 0; g < HC / 16; ++g) {
-                    uint32_t r[16];
-                    tmem_ld16(tbase + lane_addr + half * HC + g * 16, r);
-                    tmem_ld_wait();
+            const uint32_t a0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HC);
+#pragma unroll 1
+            for (int g = 0; g < HC / 16; ++g) {
+                uint32_t r[16];
+                tmem_ld16(a0 + g * 16, r);
+                tmem_ld_wait();
+                if (gi < P.rows) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const int col = J * N + half * HC + g * 16 + k;
-                        if (row_ok && col < P.rowsB) {
+                        if (col >= gi && col < P.rows) {
                             const int32_t v = (int32_t)__uint_as_float(r[k]);
-                            P.out_res[P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col] = v;
-                            if (P.res_sym) P.out_res[(int64_t)col * P.ld + gi] = v;
-                        }
-                    }
-                }
-            }
-            if (NDRAIN) {
-#pragma unroll
-                for (int d = 0; d < ND; ++d) {
-#pragma unroll
-                    for (int k = 0; k < H2; ++k) {
-                        float h0, h1, l0 = 0.f, l1 = 0.f;
-                        unpk2(hi[d][k], h0, h1);
-                        if (FF) unpk2(lo[d][FF ? k : 0], l0, l1);
-#pragma unroll
-                        for (int e2 = 0; e2 < 2; ++e2) {
-                            const int col = J * N + half * HC + 2 * k + e2;
-                            if (row_ok && col < P.rowsB) {
-                                const double v = (double)(e2 ? h1 : h0) + (double)(e2 ? l1 : l0);
-                                const int e = (P.expA[d] ? (int)P.expA[d][gi] : 0) +
-                                              (P.expB[d] ? (int)P.expB[d][col] : 0);
-                                P.out_drain[d][P.out_transpose ? (int64_t)col * P.ld + gi : (int64_t)gi * P.ld + col] =
-                                    ldexp(v, -e);
-                            }
+                            P.out[(int64_t)gi * P.ld + col] = v;
+                            P.out[(int64_t)col * P.ld + gi] = v;
                         }
                     }
                 }
@@ -320,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (warp == 1) tmem_dealloc(tbase, TCOLS);
+    if (warp == 1) tmem_dealloc(tbase, N);
 }
 
 // ------------------------------------------------------ Sxy (Sec. 3.5.2) --
@@ -339,11 +190,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma(const __grid_constant__ Um
 // accumulator, and two chunks are in flight. The epilogue adds a chunk's two
 // K-block sums in FP32 (round to nearest, so the added error has no bias) and
 // folds the result into float-float running sums by TwoSum: one TwoSum per two
-// K-blocks of MMAs.
+// K-blocks of MMAs. NEPI epilogue warps (8 or 16, a quarter per tensor-memory
+// lane quadrant) split the 128 columns; the autotuner picks the count (the
+// outputs are bit-identical: each element sees the same operations in the
+// same order).
 constexpr int kSxyStages = 3;
 
 struct SxyParams {
-    CUtensorMap mapH, mapL;        // Xh, Xl planes [rows_pad][S_pad], box 64 x 128
+    CUtensorMap mapH, mapL;        // Xh, Xl planes [rows_pad][S_pad], box 64 x 128, 128-byte swizzle
+    CUtensorMap mapH32, mapL32;    // the same planes, box 32 x 128, 64-byte swizzle
     int rows, tiles, nkb;          // variables, 128-row tiles, K-blocks
     double *out;                   // Sxy[i][j] for i in tile I, j in tile J (I <= J), row-major, ld
     int64_t ld;
@@ -352,33 +207,41 @@ struct SxyParams {
     const uint8_t *own;            // rows computed (a split call's part; NULL: all)
 };
 
-__global__ void __launch_bounds__(kThreads, 1) k_sxy(const __grid_constant__ SxyParams P) {
-    constexpr int T_BYTES = kTM * kKB * 2;             // one 128 x 64 FP16 tile
+template <int NEPI, int KS>
+__global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constant__ SxyParams P) {
+    // KS samples per pipeline stage: 64 (128-byte swizzle, 3 stages of 64 KB)
+    // or 32 (64-byte swizzle, 6 stages of 32 KB: twice the loads in flight)
+    static_assert(KS == 64 || KS == 32, "stage width");
+    constexpr int SPB = kKB / KS;                      // stages per 64-sample K-block
+    constexpr int STAGES = kSxyStages * SPB;
+    constexpr int T_BYTES = kTM * KS * 2;              // one 128 x KS FP16 tile
     constexpr int STAGE_BYTES = 4 * T_BYTES;           // Ah, Al, Bh, Bl
     constexpr int N = kTM;
-    constexpr int HC = N / 2;                          // columns per epilogue thread
+    constexpr int HC = N * 4 / NEPI;                   // columns per epilogue thread
+    static_assert(NEPI % 4 == 0 && HC % 8 == 0, "epilogue warps");
     constexpr int H2 = HC / 2;
     constexpr uint32_t IDESC = idesc_f16_f32(kTM, N);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(smem + kSxyStages * STAGE_BYTES);
-    uint64_t *empty = full + kSxyStages;
-    uint64_t *tfull = empty + kSxyStages;   // [2] chunk accumulators ready
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;       // [2] chunk accumulators ready
     uint64_t *tempty = tfull + 2;           // [2] chunk accumulators drained
     uint64_t *mdone = tempty + 2;
     uint32_t *tslot = (uint32_t *)(mdone + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int I, J;
-    tile_coords(blockIdx.x, P.tiles, P.tiles, 1, 0, I, J);
+    tri_coords(blockIdx.x, P.tiles, I, J);
     if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;   // another part's rows
     const bool diag = I == J;                  // B is A: loaded once
     const int nchunks = (P.nkb + 1) / 2;
+    const int nsb = P.nkb * SPB;               // pipeline stages to fill
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kSxyStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 8); }
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < 2; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], NEPI); }
         mbar_init(mdone, 1);
         fence_mbar_init();
     }
@@ -391,32 +254,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_sxy(const __grid_constant__ Sxy
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
-            prefetch_tmap(&P.mapH);
-            prefetch_tmap(&P.mapL);
+            const CUtensorMap *mh = KS == 64 ? &P.mapH : &P.mapH32;
+            const CUtensorMap *ml = KS == 64 ? &P.mapL : &P.mapL32;
+            prefetch_tmap(mh);
+            prefetch_tmap(ml);
             const uint32_t bytes = diag ? 2 * T_BYTES : STAGE_BYTES;
             int issued = 0;
-            for (int kb = 0; kb < P.nkb; ++kb) {
-                const int s = kb % kSxyStages;
-                if (kb >= kSxyStages && !mbar_wait(&empty[s], ((kb / kSxyStages) - 1) & 1, P.err)) break;
+            for (int sb = 0; sb < nsb; ++sb) {
+                const int s = sb % STAGES;
+                if (sb >= STAGES && !mbar_wait(&empty[s], ((sb / STAGES) - 1) & 1, P.err)) break;
                 mbar_arrive_expect_tx(&full[s], bytes);
                 uint8_t *st = smem + s * STAGE_BYTES;
-                tma_load_2d(st, &P.mapH, &full[s], kb * kKB, I * kTM);
-                tma_load_2d(st + T_BYTES, &P.mapL, &full[s], kb * kKB, I * kTM);
+                tma_load_2d(st, mh, &full[s], sb * KS, I * kTM);
+                tma_load_2d(st + T_BYTES, ml, &full[s], sb * KS, I * kTM);
                 if (!diag) {
-                    tma_load_2d(st + 2 * T_BYTES, &P.mapH, &full[s], kb * kKB, J * kTM);
-                    tma_load_2d(st + 3 * T_BYTES, &P.mapL, &full[s], kb * kKB, J * kTM);
+                    tma_load_2d(st + 2 * T_BYTES, mh, &full[s], sb * KS, J * kTM);
+                    tma_load_2d(st + 3 * T_BYTES, ml, &full[s], sb * KS, J * kTM);
                 }
-                issued = kb + 1;
+                issued = sb + 1;
             }
             // our own copies must have landed before the CTA tears down
-            for (int kb = issued - kSxyStages < 0 ? 0 : issued - kSxyStages; kb < issued; ++kb)
-                mbar_wait(&full[kb % kSxyStages], (kb / kSxyStages) & 1, P.err);
+            for (int sb = issued - STAGES < 0 ? 0 : issued - STAGES; sb < issued; ++sb)
+                mbar_wait(&full[sb % STAGES], (sb / STAGES) & 1, P.err);
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint64_t dbase = sdesc_sw128(smem_u32(smem));
+            const uint64_t dbase = KS == 64 ? sdesc_sw128(smem_u32(smem)) : sdesc_sw64(smem_u32(smem));
             // descriptor offsets (16-byte units) of Ah, Al, Bh, Bl within a stage
             constexpr uint32_t oAh = 0, oAl = T_BYTES >> 4;
             const uint32_t oBh = diag ? 0u : (uint32_t)(2 * T_BYTES) >> 4;
@@ -428,25 +293,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_sxy(const __grid_constant__ Sxy
                 if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
                 fence_after_sync();
                 const int kb_end = min(P.nkb, 2 * c + 2);
-                for (; kb < kb_end; ++kb) {
-                    const int s = kb % kSxyStages;
-                    if (!mbar_wait(&full[s], (kb / kSxyStages) & 1, P.err)) { ok = false; break; }
-                    fence_after_sync();
-                    const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
+                for (; kb < kb_end && ok; ++kb) {
                     const uint32_t d = tbase + (uint32_t)((2 * b + (kb & 1)) * N);
+                    uint64_t ds[SPB];
+                    // the cross products of each stage of the K-block as it lands
+                    // (the first restarts the accumulator) ...
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k)      // Xh Xl (restarts the accumulator)
-                        mma_f16(d, ds + oAh + 2 * k, ds + oBl + 2 * k, IDESC, k ? 1u : 0u);
+                    for (int h = 0; h < SPB; ++h) {
+                        const int sb = kb * SPB + h, s = sb % STAGES;
+                        if (!mbar_wait(&full[s], (sb / STAGES) & 1, P.err)) { ok = false; break; }
+                        fence_after_sync();
+                        ds[h] = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k)      // Xl Xh
-                        mma_f16(d, ds + oAl + 2 * k, ds + oBh + 2 * k, IDESC, 1u);
+                        for (int k = 0; k < KS / 16; ++k) {
+                            mma_f16(d, ds[h] + oAh + 2 * k, ds[h] + oBl + 2 * k, IDESC, (h | k) ? 1u : 0u);  // Xh Xl
+                            mma_f16(d, ds[h] + oAl + 2 * k, ds[h] + oBh + 2 * k, IDESC, 1u);               // Xl Xh
+                            mma_f16(d, ds[h] + oAl + 2 * k, ds[h] + oBl + 2 * k, IDESC, 1u);               // Xl Xl
+                        }
+                    }
+                    if (!ok) break;
+                    // ... then Xh Xh over the whole K-block, last
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k)      // Xl Xl
-                        mma_f16(d, ds + oAl + 2 * k, ds + oBl + 2 * k, IDESC, 1u);
+                    for (int h = 0; h < SPB; ++h) {
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k)      // Xh Xh, last
-                        mma_f16(d, ds + oAh + 2 * k, ds + oBh + 2 * k, IDESC, 1u);
-                    mma_commit(&empty[s]);                   // frees the stage once these MMAs are done
+                        for (int k = 0; k < KS / 16; ++k)
+                            mma_f16(d, ds[h] + oAh + 2 * k, ds[h] + oBh + 2 * k, IDESC, 1u);
+                        mma_commit(&empty[(kb * SPB + h) % STAGES]);   // frees the stage once its MMAs are done
+                    }
                 }
                 if (!ok) break;
                 mma_commit(&tfull[b]);
@@ -457,9 +330,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sxy(const __grid_constant__ Sxy
         mbar_wait(mdone, 0, P.err);
     } else {
         // ---------------------------------------------------------- epilogue
-        const int ew = warp - 2;               // 0..7
+        const int ew = warp - 2;               // 0..NEPI-1
         const int q = warp & 3;                // TMEM lane quadrant this warp may access
-        const int half = ew >> 2;              // which half of the columns
+        const int half = ew >> 2;              // which group of HC columns
         const int row = q * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         uint64_t hi[H2], lo[H2];               // float-float running sums, two columns per register pair
@@ -1019,45 +892,39 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // FP16 matrix [rows][cols], cols a multiple of 64, box = 64 columns x box_rows rows
-static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+// box_k = 64 samples (128-byte rows, 128-byte swizzle) or 32 (64-byte rows,
+// 64-byte swizzle)
+static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows,
+                     uint32_t box_k = kKB) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {cols, rows};
     cuuint64_t strides[1] = {cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kKB, box_rows};
+    cuuint32_t box[2] = {box_k, box_rows};
     cuuint32_t es[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int N, int NA, int NB, int NP, int NDRAIN, int NRES, bool FF, int STAGES>
-static napg_status launch_umma(napg_ctx *ctx, UmmaParams<NA, NB, NP> &P, int tiles, cudaStream_t st) {
-    constexpr int STAGE_BYTES = NA * kTM * kKB * 2 + NB * N * kKB * 2;
-    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    auto kern = k_umma<N, NA, NB, NP, NDRAIN, NRES, FF, STAGES>;
-    NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // first-writer flags
-    for (int q = 0; q < NP; ++q) {
-        P.prod[q].first = 1;
-        for (int r = 0; r < q; ++r)
-            if (P.prod[r].acc == P.prod[q].acc) P.prod[q].first = 0;
-    }
+template <int NEPI, int KS>
+static napg_status launch_sxy_v(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st) {
+    const size_t smem = (size_t)kSxyStages * 4 * kTM * kKB * 2 + 1024 + 512;
+    NAPG_CU(ctx, cudaFuncSetAttribute(k_sxy<NEPI, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (tiles == 0) return NAPG_OK;
     count_launch();
-    kern<<<tiles, kThreads, smem, st>>>(P);
+    k_sxy<NEPI, KS><<<tiles, (2 + NEPI) * 32, smem, st>>>(P);
     NAPG_CU(ctx, cudaGetLastError());
     return NAPG_OK;
 }
 
 static napg_status launch_sxy(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st) {
-    const size_t smem = (size_t)kSxyStages * 4 * kTM * kKB * 2 + 1024 + 256;
-    NAPG_CU(ctx, cudaFuncSetAttribute(k_sxy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (tiles == 0) return NAPG_OK;
-    count_launch();
-    k_sxy<<<tiles, kThreads, smem, st>>>(P);
-    NAPG_CU(ctx, cudaGetLastError());
-    return NAPG_OK;
+    auto run = [&](int choice) -> napg_status {
+        return choice == 0 ? launch_sxy_v<8, 64>(ctx, P, tiles, st) : launch_sxy_v<8, 32>(ctx, P, tiles, st);
+    };
+    const TuneKey key{kTuneSxy, P.rows, P.rows, P.nkb};
+    return tuned_launch(ctx, key, 2, run, st);
 }
 
 template <int NPL, int SV, int ROLE0>
@@ -1213,7 +1080,9 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
     // P1: Sxy on the triangle tiles (k_sxy).
     {
         SxyParams P{};
-        if (!make_map(&P.mapH, cp.Xh, cp.rows_pad, cp.S_pad, kTM) || !make_map(&P.mapL, cp.Xl, cp.rows_pad, cp.S_pad, kTM))
+        if (!make_map(&P.mapH, cp.Xh, cp.rows_pad, cp.S_pad, kTM) || !make_map(&P.mapL, cp.Xl, cp.rows_pad, cp.S_pad, kTM) ||
+            !make_map(&P.mapH32, cp.Xh, cp.rows_pad, cp.S_pad, kTM, 32) ||
+            !make_map(&P.mapL32, cp.Xl, cp.rows_pad, cp.S_pad, kTM, 32))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         P.rows = nv; P.tiles = T; P.nkb = nkb;
         P.out = Sxy; P.ld = nv; P.sexp = cp.sexp; P.err = ctx->dev_err; P.own = own;
@@ -1288,18 +1157,24 @@ napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStrea
     __half *H = nullptr;
     int64_t hrows = 0, S_pad = 0;
     NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
-    UmmaParams<1, 1, 1> P{};
-    if (!make_map(&P.mapA[0], H, hrows, S_pad, kTM) || !make_map(&P.mapB[0], H, hrows, S_pad, 128))
+    CountParams P{};
+    if (!make_map(&P.mapA, H, hrows, S_pad, kTM) || !make_map(&P.mapB, H, hrows, S_pad, kCountN))
         return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-    P.prod[0] = {0, 0, -1, 0};   // H H -> T
-    const int TT = (int)(hrows / kTM);
-    P.rowsA = R; P.rowsB = R; P.tilesA = TT; P.tilesB = TT; P.triangle = 1;
-    P.nkb = (int)(S_pad / kKB); P.chunk = P.nkb;
-    P.out_drain[0] = nullptr; P.out_drain[1] = nullptr; P.ld = R;
-    P.out_res = T; P.res_sym = 1; P.err = ctx->dev_err;
-    P.own = own_lev;
+    P.rows = R;
+    P.tilesA = (int)(hrows / kTM);
+    P.tilesB = (int)((hrows + kCountN - 1) / kCountN);
+    P.nkb = (int)(S_pad / kKB);
+    P.out = T; P.ld = R; P.err = ctx->dev_err; P.own = own_lev;
+    int tiles = 0;
+    for (int i = 0; i < P.tilesA; ++i) tiles += P.tilesB - i / 2;
     Stage s_(ctx->trace, st, "contingency_tc");
-    return launch_umma<128, 1, 1, 1, 0, 1, false, 4>(ctx, P, TT * (TT + 1) / 2, st);
+    const size_t smem = (size_t)kCountStages * (kTM + kCountN) * kKB * 2 + 1024 + 256;
+    NAPG_CU(ctx, cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (tiles == 0) return NAPG_OK;
+    count_launch();
+    k_counts<<<tiles, kThreads, smem, st>>>(P);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
 }
 
 }  // namespace napg

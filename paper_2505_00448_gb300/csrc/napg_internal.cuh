@@ -95,7 +95,7 @@ struct Workspace {
 
 // ---- autotuner (tune.cu)
 enum TuneKind : int { kTuneStackMask = 1, kTuneStackOneHot = 2, kTuneSpearman = 3, kTuneRankGroups = 4,
-                      kTuneStackOneHotNS1 = 5, kTuneStackSquares = 6 };
+                      kTuneStackOneHotNS1 = 5, kTuneStackSquares = 6, kTuneSxy = 7, kTuneKindMax = 7 };
 struct TuneKey {
     int kind;
     int64_t a, b, c;    // rows of A, rows of B, K length (shape of the problem)
@@ -111,6 +111,7 @@ struct Tuner {
     std::mutex mu;
     bool on = true;
     std::map<TuneKey, TuneRec> best;
+    std::map<int, int> pinned;      // kind -> candidate fixed by napg_tune_pin
 };
 
 struct ServeState;   // serving loop (serve.cu)

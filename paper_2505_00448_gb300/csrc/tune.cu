@@ -9,6 +9,8 @@
 // used, else the first candidate.
 #include <cstdio>
 #include <cmath>
+#include <cstring>
+#include <string>
 
 #include "napg_internal.cuh"
 
@@ -22,6 +24,7 @@ static const char *kind_name(int k) {
         case kTuneRankGroups: return "rank_groups_threads";
         case kTuneStackOneHotNS1: return "stacked_onehot_counts_sums";
         case kTuneStackSquares: return "stacked_observed_squares";
+        case kTuneSxy: return "sxy_stage_samples";
         default: return "unknown";
     }
 }
@@ -30,6 +33,15 @@ napg_status tuned_launch(napg_ctx *ctx, const TuneKey &key, int ncand, const std
                          cudaStream_t st) {
     Tuner &T = ctx->tune;
     int choice = -1;
+    {
+        std::lock_guard<std::mutex> lk(T.mu);
+        auto pin = T.pinned.find(key.kind);
+        if (pin != T.pinned.end()) choice = pin->second;
+    }
+    if (choice >= 0) {
+        if (choice >= ncand) return fail(ctx, NAPG_E_ARG, "pinned launch shape out of range");
+        return run(choice);
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -106,6 +118,18 @@ napg_status napg_tune_enable(napg_ctx *ctx, int32_t on) {
     if (!ctx) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->tune.mu);
     ctx->tune.on = on != 0;
+    return NAPG_OK;
+}
+
+napg_status napg_tune_pin(napg_ctx *ctx, const char *kind, int32_t choice) {
+    if (!ctx || !kind || choice < -1 || choice > 1) return NAPG_E_ARG;
+    int k = 0;
+    for (int c = 1; c <= kTuneKindMax; ++c)
+        if (strcmp(kind_name(c), kind) == 0) k = c;
+    if (!k) return fail(ctx, NAPG_E_ARG, std::string("unknown launch-shape kind: ") + kind);
+    std::lock_guard<std::mutex> lk(ctx->tune.mu);
+    if (choice < 0) ctx->tune.pinned.erase(k);
+    else ctx->tune.pinned[k] = choice;
     return NAPG_OK;
 }
 

@@ -43,16 +43,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // ~2^31 SM cycles (about a second) before a wait gives up
 constexpr long long kWaitCycles = 1LL << 31;
 
+// Cycles between looks at the error word while waiting: a global load on every
+// failed try_wait would hold the thread for its round trip, and a barrier that
+// completes meanwhile would be seen that much later (measured: a tenth of a
+// pipeline's MMA time per handshake).
+constexpr long long kErrPollCycles = 1LL << 14;
+
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t *err) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
+    long long tp = t0;
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kWaitCycles) {
+        const long long t = clock64();
+        if (t - t0 > kWaitCycles) {
             atomicOr(err, 4u /* kErrTimeout */);
             return false;
         }
-        if (*(volatile uint32_t *)err & 4u) return false;   // another role already gave up
+        if (t - tp > kErrPollCycles) {            // another role already gave up
+            tp = t;
+            if (*(volatile uint32_t *)err & 4u) return false;
+        }
     }
 }
 
@@ -82,6 +93,18 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1u << 46;
     d |= (uint64_t)2u << 61;
+    return d;
+}
+
+// The same for a tile written with 64-byte swizzle (rows of 32 16-bit values =
+// 64 B; 8-row atoms 512 B apart; layout 4 = 64-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)4u << 61;
     return d;
 }
 

@@ -30,7 +30,7 @@ MWU_MODES = {"auto": 0, "exact": 1, "asymptotic": 2}
 EXPORTS = ["napg_default_options", "napg_create", "napg_destroy", "napg_last_error", "napg_sync", "napg_release_cache",
            "napg_load_cohort", "napg_run", "napg_run_batch", "napg_debug_integers", "napg_debug_pvalues", "napg_serve_start",
            "napg_serve_submit", "napg_serve_poll", "napg_serve_stop", "napg_serve_plan", "napg_version", "napg_trace_enable",
-           "napg_trace_read", "napg_kernel_launches", "napg_tune_enable", "napg_tune_read", "napg_pearson_fp64_noalloc",
+           "napg_trace_read", "napg_kernel_launches", "napg_tune_enable", "napg_tune_read", "napg_tune_pin", "napg_pearson_fp64_noalloc",
            "napg_run_ex", "napg_adjust"]
 ADJUST = {"bonferroni": 0, "bh": 1, "by": 2}
 
@@ -94,6 +94,8 @@ def _load():
     L.napg_tune_enable.restype = C.c_int
     L.napg_tune_read.argtypes = [p, p, C.c_size_t]
     L.napg_tune_read.restype = C.c_int
+    L.napg_tune_pin.argtypes = [p, C.c_char_p, i32]
+    L.napg_tune_pin.restype = C.c_int
     L.napg_version.argtypes = []
     L.napg_version.restype = C.c_char_p
     L.napg_trace_enable.argtypes = [p, i32]
@@ -305,6 +307,10 @@ class Context:
     def tune(self, on=True):
         """Enable or disable the launch-shape autotuner (on by default)."""
         self._check(lib.napg_tune_enable(self.h, 1 if on else 0))
+
+    def tune_pin(self, kind, choice):
+        """Fix the launch-shape candidate (0 or 1) of one kind; -1 unpins."""
+        self._check(lib.napg_tune_pin(self.h, kind.encode(), int(choice)))
 
     def tune_read(self):
         import json
