@@ -336,12 +336,15 @@ napg_status napg_trace_read(napg_ctx *ctx, char *buf, size_t cap);
  * CUDA graph use the choice recorded for the nearest shape.
  * napg_tune_read writes the records as JSON
  *   [{"kind": K, "rows_a": A, "rows_b": B, "k": L, "choice": C, "ms": [...]}, ...]
- * napg_tune_pin fixes the candidate (0 or 1) of one kind for every later run
- * of the context, without timing; choice -1 unpins. Kinds: "stacked_mask",
- * "stacked_onehot", "stacked_onehot_counts_sums", "stacked_observed_squares",
- * "sxy_stage_samples", "spearman_threads", "rank_groups_threads".
+ * napg_tune_pin fixes the candidate of one kind for every later run of the
+ * context, without timing; choice -1 unpins. Kinds and their candidates:
+ * "stacked_mask", "stacked_onehot", "stacked_onehot_counts_sums",
+ * "stacked_observed_squares" (0-3: B-tile width, then 1 or 2 K-blocks per
+ * pipeline stage), "sxy_stage_samples", "spearman_threads",
+ * "rank_groups_threads" (0-1).
  * Errors: NAPG_E_ARG (NULL context, buffer too small, unknown kind, choice
- * outside [-1, 1]). */
+ * outside [-1, 3]; a choice past the kind's candidates fails at the next run
+ * that launches it). */
 napg_status napg_tune_enable(napg_ctx *ctx, int32_t on);
 napg_status napg_tune_read(napg_ctx *ctx, char *buf, size_t cap);
 napg_status napg_tune_pin(napg_ctx *ctx, const char *kind, int32_t choice);

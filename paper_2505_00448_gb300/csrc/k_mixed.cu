@@ -458,7 +458,9 @@ __device__ __forceinline__ void load_b_half(const StackParams &P, uint32_t rank,
 // ~2^-12 / sqrt(n) relative error on the within-group sum, which at n of a few
 // hundred and F well above 1 moves the F statistic's effect-scale value by more
 // than 1e-6.
-template <int NPL, int SV, int STAGES, int ROLE0>
+// KPS K-blocks per pipeline stage (1 or 2): two put twice the MMAs between
+// barrier round trips, which pays when N is small.
+template <int NPL, int SV, int STAGES, int ROLE0, int KPS>
 __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_constant__ StackParams P) {
     constexpr bool kHasN = ROLE0 == 0;
     constexpr bool kHasS1 = ROLE0 <= 1 && ROLE0 + NPL > 1;
@@ -469,7 +471,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
     constexpr int HALF = kSN / 2;                 // B rows per CTA
     constexpr int A_BYTES = kTM * kKB * 2;
     constexpr int BH_BYTES = HALF * kKB * 2;
-    constexpr int STAGE_BYTES = A_BYTES + BH_BYTES;
+    constexpr int KB_BYTES = A_BYTES + BH_BYTES;  // one K-block: A tile, then this CTA's half of B
+    constexpr int STAGE_BYTES = KPS * KB_BYTES;
+    static_assert(KPS == 1 || KPS == 2, "K-blocks per stage");
     static_assert(BH_BYTES % 1024 == 0 && STAGE_BYTES % 1024 == 0 && (SV / 2 * 128) % 1024 == 0,
                   "8-row swizzle atoms stay 1024-B aligned");
     static_assert(kSN % 16 == 0 && kSN <= 256, "N");
@@ -510,7 +514,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
                           (rows_owned(P.own, c0, SV, P.rowsB) && a0 + 2 * kTM - 1 >= c0);
         if (!need) return;
     }
-    const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;
+    const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;   // P.chunk is a multiple of KPS
+    const int nsb = (P.nkb + KPS - 1) / KPS;                  // pipeline stages to fill
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -533,46 +538,58 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             if (NPL & 1) prefetch_tmap(&P.mapSplit);
             const uint32_t full0 = cluster_addr(&full[0], 0);
             int issued = 0;
-            for (int kb = 0; kb < P.nkb; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, P.err)) break;
+            for (int sb = 0; sb < nsb; ++sb) {
+                const int s = sb % STAGES;
+                if (sb >= STAGES && !mbar_wait(&empty[s], ((sb / STAGES) - 1) & 1, P.err)) break;
                 const uint32_t bar = full0 + (uint32_t)(s * 8);
-                if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);   // both CTAs' bytes
+                const int nk = min(KPS, P.nkb - sb * KPS);       // K-blocks in this stage
+                if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * nk * KB_BYTES);   // both CTAs' bytes
                 uint8_t *st = smem + s * STAGE_BYTES;
-                tma_load_2d_pair(st, &P.mapA, bar, kb * kKB, (2 * I2 + (int)rank) * kTM);
-                load_b_half<NPL, SV>(P, rank, st + A_BYTES, bar, kb * kKB, J);
-                issued = kb + 1;
+                for (int h = 0; h < nk; ++h) {
+                    const int x = (sb * KPS + h) * kKB;
+                    tma_load_2d_pair(st + h * KB_BYTES, &P.mapA, bar, x, (2 * I2 + (int)rank) * kTM);
+                    load_b_half<NPL, SV>(P, rank, st + h * KB_BYTES + A_BYTES, bar, x, J);
+                }
+                issued = sb + 1;
             }
             // the copies of both CTAs are counted on the even CTA's barriers: it
             // waits for the last ones before the pair leaves (the MMA warp has
             // waited for all the others)
             if (rank == 0)
-                for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
-                    mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, P.err);
+                for (int sb = issued - STAGES < 0 ? 0 : issued - STAGES; sb < issued; ++sb)
+                    mbar_wait(&full[sb % STAGES], (sb / STAGES) & 1, P.err);
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (rank == 0 && lane == 0) {
             const uint64_t dbase = sdesc_sw128(smem_u32(smem));
-            int kb = 0;
+            const int spc = P.chunk / KPS;                      // stages per chunk
+            int sb = 0;
             bool ok = true;
             for (int c = 0; c < nchunks && ok; ++c) {
                 const int b = c & 1;
                 if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
                 fence_after_sync();
-                const int kb_end = min(P.nkb, (c + 1) * P.chunk);
-                const int kb_chunk0 = kb;
+                const int sb_end = min(nsb, (c + 1) * spc);
+                const int sb_chunk0 = sb;
                 const uint32_t dcol = tbase + (uint32_t)(b * BUF);
-                for (; kb < kb_end; ++kb) {
-                    const int s = kb % STAGES;
-                    if (!mbar_wait(&full[s], (kb / STAGES) & 1, P.err)) { ok = false; break; }
+                for (; sb < sb_end; ++sb) {
+                    const int s = sb % STAGES;
+                    if (!mbar_wait(&full[s], (sb / STAGES) & 1, P.err)) { ok = false; break; }
                     fence_after_sync();
                     const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
+                    const int nk = min(KPS, P.nkb - sb * KPS);
 #pragma unroll
-                    for (int k = 0; k < kKB / 16; ++k)
-                        mma_f16_pair(dcol, ds + (uint64_t)(2 * k), ds + (uint64_t)((A_BYTES >> 4) + 2 * k), IDESC,
-                                     (kb == kb_chunk0 && k == 0) ? 0u : 1u);
+                    for (int h = 0; h < KPS; ++h) {
+                        if (h < nk) {
+                            const uint64_t dh = ds + (uint64_t)((uint32_t)(h * KB_BYTES) >> 4);
+#pragma unroll
+                            for (int k = 0; k < kKB / 16; ++k)
+                                mma_f16_pair(dcol, dh + (uint64_t)(2 * k), dh + (uint64_t)((A_BYTES >> 4) + 2 * k),
+                                             IDESC, (sb == sb_chunk0 && h == 0 && k == 0) ? 0u : 1u);
+                        }
+                    }
                     mma_commit_pair(&empty[s]);
                 }
                 if (!ok) break;
@@ -927,12 +944,12 @@ static napg_status launch_sxy(napg_ctx *ctx, const SxyParams &P, int tiles, cuda
     return tuned_launch(ctx, key, 2, run, st);
 }
 
-template <int NPL, int SV, int ROLE0>
+template <int NPL, int SV, int ROLE0, int KPS>
 static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaStream_t st) {
-    constexpr int STAGE_BYTES = kTM * kKB * 2 + NPL * SV / 2 * kKB * 2;
+    constexpr int STAGE_BYTES = KPS * (kTM * kKB * 2 + NPL * SV / 2 * kKB * 2);
     constexpr int STAGES = (220 * 1024) / STAGE_BYTES > 8 ? 8 : (220 * 1024) / STAGE_BYTES;
     const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    auto kern = k_umma_stacked<NPL, SV, STAGES, ROLE0>;
+    auto kern = k_umma_stacked<NPL, SV, STAGES, ROLE0, KPS>;
     NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int pairs = ((P.tilesA + 1) / 2) * P.tilesB;
     if (pairs == 0) return NAPG_OK;
@@ -954,9 +971,11 @@ static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaSt
     return NAPG_OK;
 }
 
-// B-tile widths the autotuner chooses from, per plane set (every width gives the
-// same sums: each output accumulates the same products in the same order and
-// drains); MMA N = planes x width stays a multiple of 16 and at most 256
+// Launch shapes the autotuner chooses from, per plane set: the B-tile width
+// (two per set) times 1 or 2 K-blocks per pipeline stage, candidate
+// 2 * kps_index + width_index. Every shape gives the same sums: each output
+// accumulates the same products in the same order and drains. MMA N = planes x
+// width stays a multiple of 16 and at most 256.
 enum StackPlanes { kStackAll = 0, kStackNS1 = 1, kStackS2 = 2 };
 constexpr int kStackWidths[3][2] = {{48, 32}, {64, 48}, {64, 48}};
 constexpr int kStackPlaneCount[3] = {5, 3, 2};
@@ -967,7 +986,8 @@ constexpr int kStackPlaneCount[3] = {5, 3, 2};
 static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *const *pb, int set, int64_t rows_b_pad,
                                   int64_t S_pad, int kind, cudaStream_t st) {
     auto run = [&](int choice) -> napg_status {
-        const int sv = kStackWidths[set][choice];
+        const int sv = kStackWidths[set][choice & 1];
+        const bool two = choice >= 2;
         const int npl = kStackPlaneCount[set];
         for (int k = 0; k < npl; ++k)
             if (!make_map(&P.mapB[k], pb[k], rows_b_pad, S_pad, sv))
@@ -976,12 +996,17 @@ static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *cons
         if ((npl & 1) && !make_map(&P.mapSplit, pb[npl / 2], rows_b_pad, S_pad, sv / 2))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
         P.tilesB = (P.rowsB + sv - 1) / sv;
-        if (set == kStackAll) return sv == 48 ? launch_stacked_sv<5, 48, 0>(ctx, P, st) : launch_stacked_sv<5, 32, 0>(ctx, P, st);
-        if (set == kStackNS1) return sv == 64 ? launch_stacked_sv<3, 64, 0>(ctx, P, st) : launch_stacked_sv<3, 48, 0>(ctx, P, st);
-        return sv == 64 ? launch_stacked_sv<2, 64, 3>(ctx, P, st) : launch_stacked_sv<2, 48, 3>(ctx, P, st);
+        if (set == kStackAll)
+            return sv == 48 ? (two ? launch_stacked_sv<5, 48, 0, 2>(ctx, P, st) : launch_stacked_sv<5, 48, 0, 1>(ctx, P, st))
+                            : (two ? launch_stacked_sv<5, 32, 0, 2>(ctx, P, st) : launch_stacked_sv<5, 32, 0, 1>(ctx, P, st));
+        if (set == kStackNS1)
+            return sv == 64 ? (two ? launch_stacked_sv<3, 64, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 64, 0, 1>(ctx, P, st))
+                            : (two ? launch_stacked_sv<3, 48, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 48, 0, 1>(ctx, P, st));
+        return sv == 64 ? (two ? launch_stacked_sv<2, 64, 3, 2>(ctx, P, st) : launch_stacked_sv<2, 64, 3, 1>(ctx, P, st))
+                        : (two ? launch_stacked_sv<2, 48, 3, 2>(ctx, P, st) : launch_stacked_sv<2, 48, 3, 1>(ctx, P, st));
     };
     const TuneKey key{kind, P.rowsA, P.rowsB, P.nkb};
-    return tuned_launch(ctx, key, 2, run, st);
+    return tuned_launch(ctx, key, 4, run, st);
 }
 
 // Rows up to this many bytes (values plus observed bits) are staged in shared

@@ -122,7 +122,7 @@ napg_status napg_tune_enable(napg_ctx *ctx, int32_t on) {
 }
 
 napg_status napg_tune_pin(napg_ctx *ctx, const char *kind, int32_t choice) {
-    if (!ctx || !kind || choice < -1 || choice > 1) return NAPG_E_ARG;
+    if (!ctx || !kind || choice < -1 || choice > 3) return NAPG_E_ARG;
     int k = 0;
     for (int c = 1; c <= kTuneKindMax; ++c)
         if (strcmp(kind_name(c), kind) == 0) k = c;

@@ -309,7 +309,8 @@ class Context:
         self._check(lib.napg_tune_enable(self.h, 1 if on else 0))
 
     def tune_pin(self, kind, choice):
-        """Fix the launch-shape candidate (0 or 1) of one kind; -1 unpins."""
+        """Fix the launch-shape candidate of one kind (0-3 for the stacked
+        contractions, 0-1 for the others); -1 unpins."""
         self._check(lib.napg_tune_pin(self.h, kind.encode(), int(choice)))
 
     def tune_read(self):
