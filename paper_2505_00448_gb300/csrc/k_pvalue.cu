@@ -46,12 +46,30 @@ __global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capa
     const int32_t n = min(*count, capacity);
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const PJob j = sorted[t];
+        const int kind = j.kind & 0xff;
         double p;
-        switch (j.kind & 0xff) {
-            case kPjCorr: p = sf::corr_p(j.s, j.a, bgrat, lat); break;
-            case kPjT: p = sf::t_two_sided(j.s, j.a, bgrat, lat); break;
-            case kPjF: p = sf::f_sf(j.s, j.a, j.b, bgrat, lat); break;
-            default: p = sf::chi2_sf(j.s, j.a); break;
+        if ((j.kind >> 8) >= kPjKeyLargeA) {
+            // the key was taken from these arguments (pjob_key): the expansion
+            // applies and its checks are settled, so the incomplete beta is
+            // entered directly with the arguments corr_p / t_two_sided / f_sf form
+            double a, b, x, y;
+            if (kind == kPjCorr) {
+                a = 0.5 * (j.a - 2.0); b = 0.5; x = (1.0 - j.s) * (1.0 + j.s); y = j.s * j.s;
+            } else if (kind == kPjT) {
+                const double t2 = j.s * j.s;
+                a = 0.5 * j.a; b = 0.5; x = j.a / (j.a + t2); y = t2 / (j.a + t2);
+            } else {
+                const double den = j.b + j.a * j.s;
+                a = 0.5 * j.b; b = 0.5 * j.a; x = j.b / den; y = j.a * j.s / den;
+            }
+            p = sf::ibeta_large_a(a, b, x, y, bgrat ? bgrat + ((int)(2.0 * b) - 1) * sf::kBgratTerms : nullptr, lat);
+        } else {
+            switch (kind) {
+                case kPjCorr: p = sf::corr_p(j.s, j.a, bgrat, lat); break;
+                case kPjT: p = sf::t_two_sided(j.s, j.a, bgrat, lat); break;
+                case kPjF: p = sf::f_sf(j.s, j.a, j.b, bgrat, lat); break;
+                default: p = sf::chi2_sf(j.s, j.a); break;
+            }
         }
         pval[j.idx] = p;
         if (j.mirror > 0) {

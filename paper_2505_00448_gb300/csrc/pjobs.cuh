@@ -22,6 +22,7 @@ struct PJob {
 };
 
 constexpr int kPjBins = 288;
+constexpr int kPjKeyLargeA = 128;   // keys from here on: the incomplete beta's large-a expansion
 
 struct PJobQueue {
     PJob *jobs;         // appended by the finalize kernels
@@ -52,7 +53,8 @@ __device__ __forceinline__ bool pjob_beta(const PJob &j, double &a, double &b, d
 }
 
 // key: beta continued fraction direct / swapped (32 buckets each, by the
-// quantity that sets the fraction's length), gamma series / fraction (32 each),
+// quantity that sets the fraction's length), gamma finite sums (32, by 2a),
+// gamma series / fraction (16 each),
 // and the beta large-a expansion (160 buckets: 2b up to 20, then 8 octaves of
 // a y, which sets u = -T ln x and with it the branches and the term count).
 // The branch tests mirror sf::ibeta and sf::gamma_q.
@@ -60,10 +62,12 @@ __device__ __forceinline__ int pjob_key(const PJob &j) {
     double a = 0, b = 0, x = 0, y = 0;
     if (!pjob_beta(j, a, b, x, y)) {
         const double ga = 0.5 * j.a, gx = 0.5 * j.s;
-        return (gx < ga + 1.0 ? 64 : 96) + log_bucket(gx < ga + 1.0 ? gx : ga / (gx + 1e-300) * 32.0);
+        // finite sums (sf::gamma_q_ladder): work grows with 2a
+        if (gx > 0.0 && sf::gamma_ladder_applies(ga)) return 64 + min(31, (int)(2.0 * ga) >> 1);
+        return (gx < ga + 1.0 ? 96 : 112) + (log_bucket(gx < ga + 1.0 ? gx : ga / (gx + 1e-300) * 32.0) >> 1);
     }
     if (sf::ibeta_large_a_applies(a, b, x))
-        return 128 + (min(20, (int)(2.0 * b)) - 1) * 8 + min(7, log_bucket(a * y) >> 1);
+        return kPjKeyLargeA + (min(20, (int)(2.0 * b)) - 1) * 8 + min(7, log_bucket(a * y) >> 1);
     const bool swapped = x > (a + 1.0) / (a + b + 2.0);
     return (swapped ? 32 : 0) + log_bucket(swapped ? b * x : a * y);
 }

@@ -211,7 +211,14 @@ static __constant__ double kSinhLogCoef[20] = {
 // I_x(a,b) is below the smallest subnormal when a >= 20, b <= 32 and a y >= 2000:
 // then -a ln x >= a y >= 2000 while the remaining factor of the integral,
 // Gamma(a+b) / (Gamma(a+1) Gamma(b)) max(1, y^(b-1)), stays far below e^1200.
+// I_x(a, b) certainly below half the least subnormal (so 0 in FP64):
+// a y >= 2000 for b <= 32 (the expansion below: p <= 2 e^-u u^(b+41), u >= a y);
+// for b = 1/2 with x = 1 - y >= 1/2, u = -T log x >= T y >= 746 already does
+// it (the expansion's sum is erfcx(sqrt u) (1 + e), |e| < 0.05, since its first
+// correction is at most (1/64) 1.33 u^2 / T^2 with u <= T log 2; M < 1.001; and
+// erfcx(z) <= 1 / (z sqrt(pi)), so p < 1.06 e^-u / sqrt(pi u) < 2^-1075).
 __device__ __forceinline__ bool ibeta_underflows(double a, double b, double y) {
+    if (b == 0.5 && a >= 20.0 && y <= 0.5 && (a - 0.25) * y >= 746.0) return true;
     return a >= 20.0 && b <= 32.0 && a * y >= 2000.0;
 }
 
@@ -257,6 +264,34 @@ static __constant__ double kInvHalf[161] = {
     0.013888888888888888, 0.013793103448275862, 0.0136986301369863, 0.013605442176870748, 0.013513513513513514, 0.013422818791946308, 0.013333333333333334, 0.013245033112582781,
     0.013157894736842105, 0.013071895424836602, 0.012987012987012988, 0.012903225806451613, 0.01282051282051282, 0.012738853503184714, 0.012658227848101266, 0.012578616352201259,
     0.0125};
+
+// 4 / ((m + 2)(m + 4)), m = 0..156: two rungs of the ladder below at once,
+// correctly rounded
+static __constant__ double kInvQuad[157] = {
+    0.5, 0.26666666666666666, 0.16666666666666666, 0.11428571428571428, 0.08333333333333333, 0.06349206349206349, 0.05, 0.04040404040404041,
+    0.03333333333333333, 0.027972027972027972, 0.023809523809523808, 0.020512820512820513, 0.017857142857142856, 0.01568627450980392, 0.013888888888888888, 0.01238390092879257,
+    0.011111111111111112, 0.010025062656641603, 0.00909090909090909, 0.008281573498964804, 0.007575757575757576, 0.006956521739130435, 0.00641025641025641, 0.005925925925925926,
+    0.005494505494505495, 0.005108556832694764, 0.004761904761904762, 0.004449388209121246, 0.004166666666666667, 0.0039100684261974585, 0.003676470588235294, 0.003463203463203463,
+    0.0032679738562091504, 0.003088803088803089, 0.0029239766081871343, 0.002772002772002772, 0.002631578947368421, 0.0025015634771732333, 0.002380952380952381, 0.0022688598979013048,
+    0.0021645021645021645, 0.0020671834625322996, 0.001976284584980237, 0.0018912529550827422, 0.0018115942028985507, 0.0017368649587494573, 0.0016666666666666668, 0.001600640256102441,
+    0.0015384615384615385, 0.0014798372179060304, 0.0014245014245014246, 0.0013722126929674098, 0.0013227513227513227, 0.0012759170653907496, 0.0012315270935960591, 0.0011894142134998512,
+    0.0011494252873563218, 0.0011114198388441233, 0.001075268817204301, 0.0010408534998698933, 0.0010080645161290322, 0.0009768009768009768, 0.000946969696969697, 0.0009184845005740528,
+    0.00089126559714795, 0.0008652390222799049, 0.0008403361344537816, 0.0008164931618697694, 0.0007936507936507937, 0.0007717538105344395, 0.0007507507507507507, 0.0007305936073059361,
+    0.0007112375533428165, 0.0006926406926406926, 0.0006747638326585695, 0.0006575702778234424, 0.000641025641025641, 0.0006250976715111736, 0.0006097560975609756, 0.0005949724825226833,
+    0.0005807200929152149, 0.0005669737774627923, 0.0005537098560354374, 0.0005409060175794456, 0.0005285412262156448, 0.0005165956347668862, 0.000505050505050505, 0.0004938881343375726,
+    0.0004830917874396135, 0.0004726456339359565, 0.00046253469010175765, 0.0004527447651386531, 0.0004432624113475177, 0.0004340748779164406, 0.00042517006802721087, 0.0004165364990107258,
+    0.00040816326530612246, 0.00040004000400040005, 0.000392156862745098, 0.00038450446986446215, 0.0003770739064856712, 0.0003698566805362922, 0.000362844702467344, 0.00035603026257231867,
+    0.00034940600978336826, 0.0003429649318357198, 0.0003367003367003367, 0.00033060583519299114, 0.0003246753246753247, 0.0003189029737702304, 0.0003132832080200501, 0.00030781069642170063,
+    0.00030248033877797946, 0.00029728725380899295, 0.0002922267679719462, 0.0002872944049414638, 0.0002824858757062147, 0.0002777970692409195, 0.000273224043715847, 0.00026876301820869447,
+    0.00026441036488630354, 0.00026016260162601624, 0.0002560163850486431, 0.0002519685039370079, 0.000248015873015873, 0.00024415552707074406, 0.0002403846153846154, 0.0002367003964731641,
+    0.0002331002331002331, 0.00022958158755667795, 0.0002261420171867933, 0.0002227791701475912, 0.00021949078138718174, 0.00021627466882941334, 0.00021312872975277067, 0.00021005093735230792,
+    0.00020703933747412008, 0.00020409204551252616, 0.00020120724346076458, 0.00019838317710658135, 0.00019561815336463224, 0.00019291053773812393, 0.0001902587519025875, 0.00018766127140511376,
+    0.00018511662347278786, 0.00018262338492443957, 0.00018018018018018018, 0.00017778567936352726, 0.00017543859649122806, 0.00017313768774618015, 0.00017088174982911826, 0.0001686696183849884,
+    0.0001665001665001665, 0.00016437230326689953, 0.0001622849724115547, 0.0001602371509834555, 0.00015822784810126583};
+
+// binary exponent field of a double (0 for zero and subnormals): magnitude
+// comparisons on the integer pipe
+__device__ __forceinline__ int expo_field(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
 
 // c_k(b) = g_k (b)_{2k}, k = 1..20: the coefficients of the expansion below for
 // one b (row 2b - 1 of a table of kBgratRows rows), by the recurrence for g_k
@@ -320,7 +355,9 @@ static __device__ double ibeta_large_a(double a, double b, double x, double y, c
                                        LargeATab lat) {
     const double T = a + 0.5 * (b - 1.0);
     const double u = -T * ((x <= 0.5) ? log(x) : log1p(-y));
-    // the result is below the smallest subnormal: p <= 2 e^-u u^(b+41)
+    // the result is below the smallest subnormal: for b = 1/2 once u >= 746
+    // (see ibeta_underflows), else when p <= 2 e^-u u^(b+41) is
+    if (b == 0.5 && u >= 746.0) return 0.0;
     if (u > 700.0 && u - (b + 41.0) * log(u) > 760.0) return 0.0;
     double logM, invT2;
     const double a2 = 2.0 * a, b2 = 2.0 * b;    // b2 is an integer here
@@ -352,16 +389,20 @@ static __device__ double ibeta_large_a(double a, double b, double x, double y, c
         c = cbuf;
     }
     double sum = Q, pw = 1.0;
+    const double u2 = u * u;
     int small = 0;
 #pragma unroll
     for (int k = 1; k <= kBgratTerms; ++k) {
-        Q += th; m += 2; th *= u * kInvHalf[m];
-        Q += th; m += 2; th *= u * kInvHalf[m];
+        // two rungs: Q += th + th u 2/(m+2), th <- th u^2 4/((m+2)(m+4))
+        Q = fma(th, fma(u, kInvHalf[m + 2], 1.0), Q);
+        th *= u2 * kInvQuad[m];
+        m += 4;
         pw *= invT2;
         const double term = c[k - 1] * pw * Q;
         sum += term;
-        // two consecutive negligible terms (a single c_k can vanish for some b)
-        if (fabs(term) <= 1e-17 * fabs(sum)) {
+        // two consecutive negligible terms, |term| < 2^-56 |sum| (a single c_k
+        // can vanish for some b)
+        if (expo_field(term) + 57 <= expo_field(sum)) {
             if (++small == 2) break;
         } else {
             small = 0;
@@ -424,6 +465,49 @@ static __device__ double gamma_q(double a, double x) {
     return pf * f;
 }
 
+// Q(a, x) for 2a a positive integer up to kInvHalf's range (the chi-squared
+// p-values: a = df / 2), x > 0 finite, as the finite sums of DLMF 8.4.10-8.4.11
+// (repeated integration by parts of Gamma(a, x)):
+//   a = n:        Q = e^-x sum_{j<n} x^j / j!
+//   a = n + 1/2:  Q = erfc(sqrt x) + e^-x sum_{j<n} x^{j+1/2} / Gamma(j + 3/2).
+// Every term is positive (no cancellation; relative error about a + 25 units
+// in the last place) and there are at most a of them, where the series or the
+// continued fraction would take tens to hundreds of steps with a division each.
+// The sum is formed scaled by e^x (erfc(sqrt x) e^x = erfcx(sqrt x)) with the
+// ladder th <- th x 2/s of the large-a expansion below.
+constexpr int kGammaLadderMax = 160;     // 2a up to kInvHalf's last entry
+
+__device__ __forceinline__ bool gamma_ladder_applies(double a) {
+    const double m = 2.0 * a;
+    return m >= 1.0 && m <= (double)kGammaLadderMax && m == floor(m);
+}
+
+static __device__ double gamma_q_ladder(double a, double x) {
+    // a <= 80 and x > 1e4: Q < x^a e^-x < e^(737 - 10000), below the least subnormal
+    // (and the terms x^j / j! would overflow further out)
+    if (x > 1.0e4) return 0.0;
+    const int m = (int)(2.0 * a);
+    double S, th;
+    int s;
+    if (m & 1) {
+        const double sx = sqrt(x);
+        S = erfcx(sx);
+        th = sx * 1.1283791670955125739;     // x^(1/2) / Gamma(3/2)
+        s = 3;
+    } else {
+        S = 0.0;
+        th = 1.0;
+        s = 2;
+    }
+    for (; s <= m; s += 2) {
+        S += th;
+        th *= x * kInvHalf[s];
+    }
+    if (x <= 700.0) return exp(-x) * S;
+    const double e = log(S) - x;
+    return e < -746.0 ? 0.0 : exp(e);
+}
+
 // two-sided p of Student t with df degrees of freedom
 __device__ __forceinline__ double t_two_sided(double t, double df, const double *bgrat = nullptr,
                                               LargeATab lat = LargeATab{nullptr, 0, 0}) {
@@ -453,7 +537,9 @@ __device__ __forceinline__ double f_sf(double F, double d1, double d2, const dou
 
 __device__ __forceinline__ double chi2_sf(double x, double df) {
     if (isnan(x) || !(df > 0.0)) return nan("");
-    return gamma_q(0.5 * df, 0.5 * x);
+    const double a = 0.5 * df, hx = 0.5 * x;
+    if (hx > 0.0 && !isinf(hx) && gamma_ladder_applies(a)) return gamma_q_ladder(a, hx);
+    return gamma_q(a, hx);
 }
 
 __device__ __forceinline__ double norm_sf(double z) { return 0.5 * erfc(z * 0.70710678118654752440); }

@@ -74,6 +74,17 @@ def test_chi2_sf(ctx):
     _check(ctx.debug_pvalues("chi2", x, dd), O.chi2_sf(x, dd), "chi2_sf")
 
 
+def test_chi2_sf_far_tail(ctx):
+    """The finite sums for integer and half-integer df / 2 out to the log-form
+    branch (x / 2 > 700), the underflow to subnormals and zero, and the cut-off
+    past x / 2 = 10^4; df 161 and 4000 take the series / fraction instead."""
+    df = np.array([1, 2, 3, 4, 9, 10, 41, 80, 81, 159, 160, 161, 4000], float)
+    hx = np.array([1e-300, 1e-12, 0.3, 599.0, 699.9, 700.1, 712.0, 730.0, 740.0, 745.0, 748.0, 752.0, 760.0, 800.0,
+                   900.0, 2000.0, 9999.0, 10001.0, 1e5])
+    xx, dd = _grid(2.0 * hx, df)
+    _check(ctx.debug_pvalues("chi2", xx, dd), O.chi2_sf(xx, dd), "chi2_sf far tail")
+
+
 def test_norm_sf(ctx):
     z = np.concatenate([np.linspace(-40, 40, 801), [np.inf, -np.inf]])
     _check(ctx.debug_pvalues("norm", z), O.norm_sf(z), "norm_sf")
