@@ -41,7 +41,10 @@ __global__ void k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t cap
     }
 }
 
-__global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capacity, double *pval,
+// At most 80 registers a thread (a few bytes spill), four 128-thread blocks per
+// SM: more warps in flight for the long FP64 latencies than 130 registers
+// allowed (measured 0.6-0.8 ms less per mixed-cohort step).
+__global__ void __launch_bounds__(128, 6) k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capacity, double *pval,
                           const double *bgrat, sf::LargeATab lat) {
     const int32_t n = min(*count, capacity);
     for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -80,12 +83,12 @@ __global__ void k_pj_eval(const PJob *sorted, const int32_t *count, int32_t capa
 }
 
 void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
-                       cudaStream_t st) {
+                       cudaStream_t st, int sm_count) {
     if (!pval) return;
     count_launch(3);
     k_pj_scan<<<1, 32, 0, st>>>(q.hist, offs, cursor);
-    k_pj_scatter<<<152 * 8, 256, 0, st>>>(q.jobs, q.count, q.capacity, offs, cursor, sorted);
-    k_pj_eval<<<152 * 16, 128, 0, st>>>(sorted, q.count, q.capacity, pval, q.bgrat, q.lat);
+    k_pj_scatter<<<sm_count * 8, 256, 0, st>>>(q.jobs, q.count, q.capacity, offs, cursor, sorted);
+    k_pj_eval<<<sm_count * 4, 128, 0, st>>>(sorted, q.count, q.capacity, pval, q.bgrat, q.lat);
 }
 
 // the (log M, 1/T^2) table of sf::LargeATab, one thread per entry

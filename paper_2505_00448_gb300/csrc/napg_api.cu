@@ -261,7 +261,7 @@ static napg_status pjobs_setup(napg_ctx *ctx, Workspace &ws, cudaStream_t st, in
 static void pjobs_run(napg_ctx *ctx, const PJobBufs &b, double *pval, cudaStream_t st) {
     if (!b.q.jobs || !pval) return;
     Stage s_(ctx->trace, st, "pvalues");
-    launch_pjobs_eval(b.q, b.sorted, b.offs, b.cursor, pval, st);
+    launch_pjobs_eval(b.q, b.sorted, b.offs, b.cursor, pval, st, ctx->sm_count);
 }
 
 // Host lists of one run, concatenated as they are staged on the device:

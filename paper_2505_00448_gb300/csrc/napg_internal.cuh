@@ -239,7 +239,7 @@ napg_status ensure_presort(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
 #include "pjobs.cuh"
 namespace napg {
 void launch_pjobs_eval(const PJobQueue &q, PJob *sorted, int32_t *offs, int32_t *cursor, double *pval,
-                       cudaStream_t st);
+                       cudaStream_t st, int sm_count);
 void launch_bgrat_table(double *tab, cudaStream_t st);
 void launch_large_a_table(double2 *v, int32_t n2a, int32_t rows, cudaStream_t st);
 void launch_debug_pvalues(int32_t kind, const double *s, const double *a, const double *b, int64_t count, double *p,

@@ -168,7 +168,9 @@ extern "C" napg_status napg_pearson_fp64_noalloc(const double *X, int32_t n_vars
     RescueArgs rsc{X, NAPG_F64, S, pl.W, pl.ctxw, pl.obs, nullptr, nullptr, pl.vars, nullptr, n_vars, n_vars,
                    NAPG_PEARSON, 1, nullptr, nullptr, nullptr};
     launch_rescue(rsc, pl.flags, pl.counter, (int32_t)(pl.pairs + nv + 1), r, p, n, 1, 0, st);
-    if (p) launch_pjobs_eval(q, pl.sorted, pl.pj_meta + 1 + kPjBins, pl.pj_meta + 1 + 2 * kPjBins, p, st);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return NAPG_E_CUDA;
+    if (p) launch_pjobs_eval(q, pl.sorted, pl.pj_meta + 1 + kPjBins, pl.pj_meta + 1 + 2 * kPjBins, p, st, sms);
     if (cudaGetLastError() != cudaSuccess) return NAPG_E_CUDA;
     // the non-finite check needs the error word on the host: read it back (synchronous)
     uint32_t err = 0;
