@@ -149,7 +149,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                     flags[atomicAdd(nflag, 1)] = (int32_t)t;
                 } else {
                     const double d1 = (double)(k - 1), d2 = (double)(n - k);
-                    s = (ssb / d1) / (ssw / d2);
+                    s = (ssb * d2) / (ssw * d1);          // (ssb / d1) / (ssw / d2), one division
                     if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, d1, d2, t, kPjF, 0});
                 }
             }

@@ -42,12 +42,15 @@ __device__ __forceinline__ int log_bucket(double v) {
 }
 
 // the incomplete-beta parameters (a, b) and argument (x, y = 1 - x) of a job's
-// p-value; false for the chi-squared (incomplete gamma) kind
-__device__ __forceinline__ bool pjob_beta(const PJob &j, double &a, double &b, double &x, double &y) {
+// p-value (false for the chi-squared kind, an incomplete gamma), with one
+// reciprocal instead of two divisions: for the job's key and the
+// certain-underflow test only, which are decided with margins far above
+// rounding (the evaluation forms x and y as corr_p / t_two_sided / f_sf do)
+__device__ __forceinline__ bool pjob_beta_key(const PJob &j, double &a, double &b, double &x, double &y) {
     switch (j.kind & 0xff) {
         case kPjCorr: a = 0.5 * (j.a - 2.0); b = 0.5; y = j.s * j.s; x = 1.0 - y; return true;
-        case kPjT: { const double t2 = j.s * j.s; a = 0.5 * j.a; b = 0.5; x = j.a / (j.a + t2); y = t2 / (j.a + t2); } return true;
-        case kPjF: { const double den = j.b + j.a * j.s; a = 0.5 * j.b; b = 0.5 * j.a; x = j.b / den; y = j.a * j.s / den; } return true;
+        case kPjT: { const double t2 = j.s * j.s, inv = 1.0 / (j.a + t2); a = 0.5 * j.a; b = 0.5; x = j.a * inv; y = t2 * inv; } return true;
+        case kPjF: { const double inv = 1.0 / (j.b + j.a * j.s); a = 0.5 * j.b; b = 0.5 * j.a; x = j.b * inv; y = j.a * j.s * inv; } return true;
         default: return false;
     }
 }
@@ -58,9 +61,8 @@ __device__ __forceinline__ bool pjob_beta(const PJob &j, double &a, double &b, d
 // and the beta large-a expansion (160 buckets: 2b up to 20, then 8 octaves of
 // a y, which sets u = -T ln x and with it the branches and the term count).
 // The branch tests mirror sf::ibeta and sf::gamma_q.
-__device__ __forceinline__ int pjob_key(const PJob &j) {
-    double a = 0, b = 0, x = 0, y = 0;
-    if (!pjob_beta(j, a, b, x, y)) {
+__device__ __forceinline__ int pjob_key(const PJob &j, bool beta, double a, double b, double x, double y) {
+    if (!beta) {
         const double ga = 0.5 * j.a, gx = 0.5 * j.s;
         // finite sums (sf::gamma_q_ladder): work grows with 2a
         if (gx > 0.0 && sf::gamma_ladder_applies(ga)) return 64 + min(31, (int)(2.0 * ga) >> 1);
@@ -76,8 +78,7 @@ __device__ __forceinline__ int pjob_key(const PJob &j) {
 // atomic, and lanes with equal keys add to the histogram with one atomic (many
 // jobs share a key). The key is kept in the job's kind word (bits 8 and up) for
 // the scatter.
-__device__ __forceinline__ void pjob_push(const PJobQueue &q, PJob j) {
-    const int k = pjob_key(j);
+__device__ __forceinline__ void pjob_push(const PJobQueue &q, PJob j, int k) {
     j.kind |= k << 8;
     const unsigned act = __activemask();
     const int lane = threadIdx.x & 31;
@@ -91,12 +92,19 @@ __device__ __forceinline__ void pjob_push(const PJobQueue &q, PJob j) {
     if (lane == __ffs(same) - 1) atomicAdd(&q.hist[k], __popc(same));
 }
 
+__device__ __forceinline__ void pjob_push(const PJobQueue &q, const PJob &j) {
+    double a = 0, b = 0, x = 0, y = 0;
+    const bool beta = pjob_beta_key(j, a, b, x, y);
+    pjob_push(q, j, pjob_key(j, beta, a, b, x, y));
+}
+
 // Queues the job and returns NaN (its p-value is written by the evaluation), or
 // returns the p-value 0 at once when it certainly underflows (sf::ibeta_underflows).
 __device__ __forceinline__ double pjob_push_p(const PJobQueue &q, const PJob &j) {
-    double a, b, x, y;
-    if (pjob_beta(j, a, b, x, y) && isfinite(j.s) && sf::ibeta_underflows(a, b, y)) return 0.0;
-    pjob_push(q, j);
+    double a = 0, b = 0, x = 0, y = 0;
+    const bool beta = pjob_beta_key(j, a, b, x, y);
+    if (beta && isfinite(j.s) && sf::ibeta_underflows(a, b, y)) return 0.0;
+    pjob_push(q, j, pjob_key(j, beta, a, b, x, y));
     return __longlong_as_double(0x7ff8000000000000LL);
 }
 
