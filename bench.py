@@ -315,6 +315,18 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
             if issued:
                 e["issued_tflops"] = issued / secs / 1e12
                 e["issued_frac"] = e["issued_tflops"] / tens_peak
+        elif bound == "hbm" and name in ("spearman_rank", "rank_groups"):
+            # the rank kernels' byte model (16.25 S or 9.125 S bytes a pair) as an
+            # effective rate against the HBM copy rate: their working set stays in
+            # L2 and shared memory (DRAM carries under 0.5% of the model), so they
+            # are bound by instruction issue, not by HBM
+            e.update(bound="alu", achieved=alg / secs / 1e9, peak=hbm_peak, unit="GB/s of the byte model",
+                     peak_source=(("measured HBM copy (MEASURED_PEAKS)" if hbm_meas else
+                                   "fallback 6,800 GB/s (no measured peak)") +
+                                  " as the byte model's reference rate; the kernel is bound by instruction issue "
+                                  "(ncu: 65-80% of issue slots, profiles/rank_kernels_rank_cohort.md)"))
+            tr = load_traffic(name)
+            e["dram_share_of_model"] = tr / alg if tr else None      # both per step
         elif bound == "hbm":
             e.update(achieved=alg / secs / 1e9, peak=hbm_peak, unit="GB/s",
                      peak_source="measured HBM copy (MEASURED_PEAKS)" if hbm_meas else "fallback 6,800 GB/s (no measured peak)")
