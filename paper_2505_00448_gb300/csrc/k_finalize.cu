@@ -16,6 +16,19 @@ __device__ __forceinline__ double dnan() { return __longlong_as_double(0x7ff8000
 constexpr int32_t kMixedMinN = 64;
 __device__ __forceinline__ double dinf() { return __longlong_as_double(0x7ff0000000000000LL); }
 
+// 1/n for a count n >= 1: the FP32 reciprocal of the FP32 count (relative error
+// below 2^-22, also where the count rounds), refined by two Newton steps
+// r <- r (2 - n r) in FP64 (each squares the relative error: below 2^-88), so
+// within a unit or two in the last place: five FP64 instructions where a
+// division takes about a dozen (the finalize kernels are bound by the FP64 pipe)
+__device__ __forceinline__ double rcp_count(int32_t n) {
+    const double nd = (double)n;
+    double r = (double)__frcp_rn(__int2float_rn(n));
+    r *= fma(-nd, r, 2.0);
+    r *= fma(-nd, r, 2.0);
+    return r;
+}
+
 __device__ __forceinline__ void put(double *stat, double *pval, int32_t *nout, int64_t idx, double s, double p,
                                     int32_t n) {
     if (stat) stat[idx] = s;
@@ -59,7 +72,7 @@ __global__ void __launch_bounds__(256) k_finalize_pearson(PearsonFin f, double *
             const int64_t ij = (int64_t)i * nv + j;
             n = f.nn[ij];
             if (n > 1) {
-                const double nd = (double)n, inv_n = 1.0 / nd;
+                const double nd = (double)n, inv_n = rcp_count(n);
                 const double sx = f.Sx[ij], sy = m_sx[lx][ry], sxy = f.Sxy[ij];
                 const double sxx = f.vsq ? f.Sxx[ij] + f.vsq[i] * nd : f.Sxx[ij];
                 const double syy = f.vsq ? m_sxx[lx][ry] + f.vsq[j] * nd : m_sxx[lx][ry];
@@ -71,7 +84,7 @@ __global__ void __launch_bounds__(256) k_finalize_pearson(PearsonFin f, double *
                     // a variable against itself: r = 1 exactly, as the two-pass
                     // definition gives (its centred cross sum is its sum of squares)
                     const bool same = f.vars ? f.vars[i] == f.vars[j] : i == j;
-                    r = same ? 1.0 : cxy / sqrt(cxx * cyy);
+                    r = same ? 1.0 : cxy * rsqrt(cxx * cyy);
                     r = fmin(1.0, fmax(-1.0, r));
                     if (n <= 2) p = dnan();
                     else if (fabs(r) >= 1.0) p = 0.0;
@@ -131,12 +144,13 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 }
                 // sum of squares over all co-observed samples: per level, or one total
                 if (f.g2tot) raw = f.g2tot[t] + (f.vsq ? f.vsq[j] * (double)n : 0.0);
-                const double gm = s1 / (double)n;
+                const double gm = s1 * rcp_count((int32_t)n);
                 double ssb = 0.0, ssw = f.g2tot ? raw : 0.0;
                 for (int g = 0; g < c; ++g) {
                     if (!f.present[off + g]) continue;
                     const int64_t idx = (int64_t)(off + g) * f.nb + j;
-                    const double ng = (double)f.gn[idx], mg = f.g1[idx] / ng;
+                    const int32_t ngi = f.gn[idx];
+                    const double ng = (double)ngi, mg = f.g1[idx] * rcp_count(ngi);
                     ssb += ng * (mg - gm) * (mg - gm);
                     if (f.g2tot) {
                         ssw -= f.g1[idx] * mg;
@@ -157,7 +171,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
             const int64_t i0 = (int64_t)off * f.nb + j, i1 = (int64_t)(off + 1) * f.nb + j;
             const int32_t n0 = f.gn[i0], n1 = f.gn[i1];
             if (n0 >= 2 && n1 >= 2 && n >= 3) {
-                const double m0 = f.g1[i0] / n0, m1 = f.g1[i1] / n1;
+                const double m0 = f.g1[i0] * rcp_count(n0), m1 = f.g1[i1] * rcp_count(n1);
                 const double r0 = f.g2[i0] + (f.vsq ? f.vsq[j] * (double)n0 : 0.0);
                 const double r1 = f.g2[i1] + (f.vsq ? f.vsq[j] * (double)n1 : 0.0);
                 const double q0 = r0 - f.g1[i0] * m0, q1 = r1 - f.g1[i1] * m1;
