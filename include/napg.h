@@ -245,7 +245,7 @@ napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
 /* The library's device p-value functions applied to caller-supplied values,
  * for checking them on their own (Sec. 3.5: Beta CDF for r and t, F, chi-squared
  * and normal survival functions). s, a, b, p: count doubles each, host or device
- * (b read only for kinds 2 and 5, a not read for kind 4):
+ * (b read only for kinds 2 and 5, a not read for kinds 4, 7 and 8):
  *   0: p of a correlation s with n = a observations, I_{1-s^2}((a-2)/2, 1/2)
  *   1: two-sided p of Student t = s with a degrees of freedom
  *   2: F survival function at s with (a, b) degrees of freedom
@@ -253,6 +253,9 @@ napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
  *   4: standard normal survival function at s
  *   5: regularized incomplete beta I_s(a, b)
  *   6: regularized upper incomplete gamma Q(a, s)
+ *   7: erfcx(sqrt s) = exp(s) erfc(sqrt s), s >= 0, by the library's own
+ *      approximation (the one the p-value expansions use)
+ *   8: the same through CUDA's erfcx, for comparison
  * Synchronous. Errors: NAPG_E_ARG (unknown kind, NULL array), NAPG_E_OOM, NAPG_E_CUDA. */
 napg_status napg_debug_pvalues(napg_ctx *ctx, int32_t kind, const double *s, const double *a,
                                const double *b, int64_t count, double *p);

@@ -269,16 +269,16 @@ UNROLL \
         double s = dnan(), p = dnan(); \
         if (!empty) { \
             const bool yates = f.yates && ka == 2 && kb == 2; \
-            const double nd = (double)n, inv_n = 1.0 / nd; \
+            const double nd = (double)n, inv_n = rcp_count((int32_t)n); \
             double icol[MAXC]; \
 UNROLL \
-            for (int h = 0; h < MAXC; ++h) icol[h] = (h < cb && col[h] > 0) ? 1.0 / (double)col[h] : 0.0; \
+            for (int h = 0; h < MAXC; ++h) icol[h] = (h < cb && col[h] > 0) ? rcp_count(col[h]) : 0.0; \
             double chi = 0.0; \
 UNROLL \
             for (int g = 0; g < MAXC; ++g) { \
                 if (g >= ca) break; \
                 if (!f.present[oa + g]) continue; \
-                const double irow = 1.0 / (double)row[g]; \
+                const double irow = rcp_count(row[g]); \
                 double acc = 0.0; \
 UNROLL \
                 for (int h = 0; h < MAXC; ++h) { \

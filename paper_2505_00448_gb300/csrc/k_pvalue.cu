@@ -133,7 +133,9 @@ __global__ void k_debug_pvalues(int32_t kind, const double *s, const double *a, 
             case 3: v = sf::chi2_sf(s[t], a[t]); break;
             case 4: v = sf::norm_sf(s[t]); break;
             case 5: v = sf::ibeta(a[t], b[t], s[t], 1.0 - s[t], bgrat); break;
-            default: v = sf::gamma_q(a[t], s[t]); break;
+            case 6: v = sf::gamma_q(a[t], s[t]); break;
+            case 7: { double su; v = sf::erfcx_of_sqrt(s[t], su); } break;
+            default: v = erfcx(sqrt(s[t])); break;
         }
         p[t] = v;
     }

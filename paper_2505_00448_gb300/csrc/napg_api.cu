@@ -1098,9 +1098,9 @@ napg_status napg_run_batch(napg_ctx *ctx, int32_t test, const napg_options *opt,
 
 napg_status napg_debug_pvalues(napg_ctx *ctx, int32_t kind, const double *s, const double *a, const double *b,
                                int64_t count, double *p) {
-    if (!ctx || count < 0 || kind < 0 || kind > 6) return NAPG_E_ARG;
+    if (!ctx || count < 0 || kind < 0 || kind > 8) return NAPG_E_ARG;
     if (count == 0) return NAPG_OK;
-    if (!s || !p || (kind != 4 && !a) || ((kind == 2 || kind == 5) && !b)) return NAPG_E_ARG;
+    if (!s || !p || (kind != 4 && kind < 7 && !a) || ((kind == 2 || kind == 5) && !b)) return NAPG_E_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);
     NAPG_ST(wait_pending_copies(ctx));
     ctx->err.clear();

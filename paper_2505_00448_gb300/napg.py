@@ -419,7 +419,8 @@ class Context:
         self._check(lib.napg_debug_integers(self.h, t, _ptr(m), int(a), int(b), _ptr(out), len(out), C.byref(w)))
         return out[:w.value].copy()
 
-    PVALUE_KINDS = {"corr": 0, "t": 1, "f": 2, "chi2": 3, "norm": 4, "ibeta": 5, "gamma_q": 6}
+    PVALUE_KINDS = {"corr": 0, "t": 1, "f": 2, "chi2": 3, "norm": 4, "ibeta": 5, "gamma_q": 6,
+                    "erfcx_sqrt": 7, "erfcx_sqrt_cuda": 8}
 
     def debug_pvalues(self, kind, s, a=None, b=None):
         """The device p-value functions on given values (host float64 arrays)."""

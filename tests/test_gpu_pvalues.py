@@ -85,6 +85,25 @@ def test_chi2_sf_far_tail(ctx):
     _check(ctx.debug_pvalues("chi2", xx, dd), O.chi2_sf(xx, dd), "chi2_sf far tail")
 
 
+def test_erfcx_of_sqrt_against_cuda(ctx):
+    """The library's own erfcx (fitted polynomials, used by the p-value
+    expansions for half-integer b and the chi-squared finite sums) against CUDA's
+    erfcx on the same arguments: across every piece of 0 <= z < 4 and its
+    boundaries, both large-argument polynomials (1/64 <= 1/z^2 <= 1/16 and below)
+    and far out. The fit is within 3.2e-16 of the function; CUDA's own error adds
+    a few units in the last place."""
+    edges = np.arange(0.0, 8.01, 0.5)
+    z = np.concatenate([np.linspace(0.0, 4.0, 4001), np.linspace(4.0, 30.0, 5201), np.geomspace(30.0, 1e4, 2001),
+                        (edges[:, None] + np.array([-1e-9, 0.0, 1e-9])).ravel()])
+    z = z[z >= 0.0]
+    u = z * z
+    mine = ctx.debug_pvalues("erfcx_sqrt", u)
+    cuda = ctx.debug_pvalues("erfcx_sqrt_cuda", u)
+    rel = np.abs(mine - cuda) / cuda
+    k = int(np.argmax(rel))
+    assert rel[k] <= 1.5e-15, f"erfcx(sqrt u): rel diff {rel[k]:.3e} at u = {u[k]!r}"
+
+
 def test_norm_sf(ctx):
     z = np.concatenate([np.linspace(-40, 40, 801), [np.inf, -np.inf]])
     _check(ctx.debug_pvalues("norm", z), O.norm_sf(z), "norm_sf")
