@@ -977,7 +977,7 @@ static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaSt
 // accumulates the same products in the same order and drains. MMA N = planes x
 // width stays a multiple of 16 and at most 256.
 enum StackPlanes { kStackAll = 0, kStackNS1 = 1, kStackS2 = 2 };
-constexpr int kStackWidths[3][2] = {{48, 32}, {64, 48}, {64, 48}};
+constexpr int kStackWidths[3][2] = {{48, 32}, {80, 64}, {112, 64}};
 constexpr int kStackPlaneCount[3] = {5, 3, 2};
 
 // A x stacked B planes with the B-tile width chosen by the autotuner for this
@@ -1000,10 +1000,10 @@ static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *cons
             return sv == 48 ? (two ? launch_stacked_sv<5, 48, 0, 2>(ctx, P, st) : launch_stacked_sv<5, 48, 0, 1>(ctx, P, st))
                             : (two ? launch_stacked_sv<5, 32, 0, 2>(ctx, P, st) : launch_stacked_sv<5, 32, 0, 1>(ctx, P, st));
         if (set == kStackNS1)
-            return sv == 64 ? (two ? launch_stacked_sv<3, 64, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 64, 0, 1>(ctx, P, st))
-                            : (two ? launch_stacked_sv<3, 48, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 48, 0, 1>(ctx, P, st));
-        return sv == 64 ? (two ? launch_stacked_sv<2, 64, 3, 2>(ctx, P, st) : launch_stacked_sv<2, 64, 3, 1>(ctx, P, st))
-                        : (two ? launch_stacked_sv<2, 48, 3, 2>(ctx, P, st) : launch_stacked_sv<2, 48, 3, 1>(ctx, P, st));
+            return sv == 80 ? (two ? launch_stacked_sv<3, 80, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 80, 0, 1>(ctx, P, st))
+                            : (two ? launch_stacked_sv<3, 64, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 64, 0, 1>(ctx, P, st));
+        return sv == 112 ? (two ? launch_stacked_sv<2, 112, 3, 2>(ctx, P, st) : launch_stacked_sv<2, 112, 3, 1>(ctx, P, st))
+                         : (two ? launch_stacked_sv<2, 64, 3, 2>(ctx, P, st) : launch_stacked_sv<2, 64, 3, 1>(ctx, P, st));
     };
     const TuneKey key{kind, P.rowsA, P.rowsB, P.nkb};
     return tuned_launch(ctx, key, 4, run, st);
