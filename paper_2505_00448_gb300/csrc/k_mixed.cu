@@ -200,12 +200,28 @@ struct SxyParams {
     CUtensorMap mapH, mapL;        // Xh, Xl planes [rows_pad][S_pad], box 64 x 128, 128-byte swizzle
     CUtensorMap mapH32, mapL32;    // the same planes, box 32 x 128, 64-byte swizzle
     int rows, tiles, nkb;          // variables, 128-row tiles, K-blocks
+    // triangle tiles from nfull on run as two CTAs, K-blocks [0, kbmid) and
+    // [kbmid, nkb), each adding its part into the zeroed output (see launch_sxy)
+    int nfull, kbmid;
     double *out;                   // Sxy[i][j] for i in tile I, j in tile J (I <= J), row-major, ld
     int64_t ld;
     const int8_t *sexp;            // per-row scale exponents: the output is divided by 2^(e_i + e_j)
     uint32_t *err;
     const uint8_t *own;            // rows computed (a split call's part; NULL: all)
 };
+
+// this CTA's triangle tile and its K-blocks [kb0, kb0 + nk): the tiles from
+// nfull on run as two CTAs each, over [0, kbmid) and [kbmid, nkb)
+__device__ __forceinline__ int sxy_tile(const SxyParams &P, int &kb0, int &nk) {
+    const int t = blockIdx.x;
+    kb0 = 0;
+    nk = P.nkb;
+    if (t < P.nfull) return t;
+    const int q = t - P.nfull;
+    if (q & 1) { kb0 = P.kbmid; nk = P.nkb - P.kbmid; }
+    else nk = P.kbmid;
+    return P.nfull + (q >> 1);
+}
 
 template <int NEPI, int KS>
 __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constant__ SxyParams P) {
@@ -233,11 +249,12 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int I, J;
-    tri_coords(blockIdx.x, P.tiles, I, J);
+    {
+        int kb0, nk;
+        tri_coords(sxy_tile(P, kb0, nk), P.tiles, I, J);
+    }
     if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;   // another part's rows
     const bool diag = I == J;                  // B is A: loaded once
-    const int nchunks = (P.nkb + 1) / 2;
-    const int nsb = P.nkb * SPB;               // pipeline stages to fill
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -259,17 +276,20 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
             prefetch_tmap(mh);
             prefetch_tmap(ml);
             const uint32_t bytes = diag ? 2 * T_BYTES : STAGE_BYTES;
+            int kb0, nk;
+            sxy_tile(P, kb0, nk);
+            const int nsb = nk * SPB, x0 = kb0 * kKB;    // stages to fill, first sample
             int issued = 0;
             for (int sb = 0; sb < nsb; ++sb) {
                 const int s = sb % STAGES;
                 if (sb >= STAGES && !mbar_wait(&empty[s], ((sb / STAGES) - 1) & 1, P.err)) break;
                 mbar_arrive_expect_tx(&full[s], bytes);
                 uint8_t *st = smem + s * STAGE_BYTES;
-                tma_load_2d(st, mh, &full[s], sb * KS, I * kTM);
-                tma_load_2d(st + T_BYTES, ml, &full[s], sb * KS, I * kTM);
+                tma_load_2d(st, mh, &full[s], x0 + sb * KS, I * kTM);
+                tma_load_2d(st + T_BYTES, ml, &full[s], x0 + sb * KS, I * kTM);
                 if (!diag) {
-                    tma_load_2d(st + 2 * T_BYTES, mh, &full[s], sb * KS, J * kTM);
-                    tma_load_2d(st + 3 * T_BYTES, ml, &full[s], sb * KS, J * kTM);
+                    tma_load_2d(st + 2 * T_BYTES, mh, &full[s], x0 + sb * KS, J * kTM);
+                    tma_load_2d(st + 3 * T_BYTES, ml, &full[s], x0 + sb * KS, J * kTM);
                 }
                 issued = sb + 1;
             }
@@ -286,13 +306,16 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
             constexpr uint32_t oAh = 0, oAl = T_BYTES >> 4;
             const uint32_t oBh = diag ? 0u : (uint32_t)(2 * T_BYTES) >> 4;
             const uint32_t oBl = diag ? (uint32_t)T_BYTES >> 4 : (uint32_t)(3 * T_BYTES) >> 4;
+            int kb0, nk;
+            sxy_tile(P, kb0, nk);
+            const int nchunks = (nk + 1) / 2;
             int kb = 0;
             bool ok = true;
             for (int c = 0; c < nchunks && ok; ++c) {
                 const int b = c & 1;
                 if (c >= 2 && !mbar_wait(&tempty[b], ((c >> 1) - 1) & 1, P.err)) { ok = false; break; }
                 fence_after_sync();
-                const int kb_end = min(P.nkb, 2 * c + 2);
+                const int kb_end = min(nk, 2 * c + 2);       // K-blocks counted from kb0
                 for (; kb < kb_end && ok; ++kb) {
                     const uint32_t d = tbase + (uint32_t)((2 * b + (kb & 1)) * N);
                     uint64_t ds[SPB];
@@ -338,24 +361,28 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
         uint64_t hi[H2], lo[H2];               // float-float running sums, two columns per register pair
 #pragma unroll
         for (int k = 0; k < H2; ++k) hi[k] = lo[k] = 0ull;
+        int kb0, nk;
+        sxy_tile(P, kb0, nk);
+        const bool part = (int)blockIdx.x >= P.nfull;     // one of a split tile's two CTAs
+        const int nchunks = (nk + 1) / 2;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             const int b = c & 1;
             if (!mbar_wait(&tfull[b], (c >> 1) & 1, P.err)) { ok = false; break; }
             fence_after_sync();
-            const bool two = 2 * c + 1 < P.nkb;
+            const bool two = 2 * c + 1 < nk;
             const uint32_t a0 = tbase + lane_addr + (uint32_t)(2 * b * N + half * HC);
 #pragma unroll
-            for (int g = 0; g < HC / 8; ++g) {
-                uint32_t r0[8], r1[8];
-                tmem_ld8(a0 + g * 8, r0);
-                if (two) tmem_ld8(a0 + N + g * 8, r1);
+            for (int g = 0; g < HC / 4; ++g) {
+                uint32_t r0[4], r1[4];
+                tmem_ld4(a0 + g * 4, r0);
+                if (two) tmem_ld4(a0 + N + g * 4, r1);
                 tmem_ld_wait();
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < 2; ++k) {
                     uint64_t v = pk2(__uint_as_float(r0[2 * k]), __uint_as_float(r0[2 * k + 1]));
                     if (two) v = add2(v, pk2(__uint_as_float(r1[2 * k]), __uint_as_float(r1[2 * k + 1])));
-                    two_sum2(hi[g * 4 + k], lo[g * 4 + k], v);
+                    two_sum2(hi[g * 2 + k], lo[g * 2 + k], v);
                 }
             }
             fence_before_sync();
@@ -377,7 +404,8 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
                         if (col < P.rows) {
                             const double v = (double)(e2 ? h1 : h0) + (double)(e2 ? l1 : l0);
                             const int e = ei + (P.sexp ? (int)P.sexp[col] : 0);
-                            P.out[(int64_t)gi * P.ld + col] = ldexp(v, -e);
+                            if (part) atomicAdd(&P.out[(int64_t)gi * P.ld + col], ldexp(v, -e));   // two parts onto 0: order-free
+                            else P.out[(int64_t)gi * P.ld + col] = ldexp(v, -e);
                         }
                     }
                 }
@@ -925,20 +953,48 @@ static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t c
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// zeroes the outputs of the split triangle tiles (from nfull on) that this part
+// owns, before both halves add into them
+__global__ void k_sxy_zero(SxyParams P) {
+    int I, J;
+    tri_coords(P.nfull + (int)blockIdx.x, P.tiles, I, J);
+    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;
+    for (int idx = threadIdx.x; idx < kTM * kTM; idx += blockDim.x) {
+        const int gi = I * kTM + idx / kTM, col = J * kTM + idx % kTM;
+        if (gi < P.rows && col < P.rows) P.out[(int64_t)gi * P.ld + col] = 0.0;
+    }
+}
+
 template <int NEPI, int KS>
 static napg_status launch_sxy_v(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st) {
     const size_t smem = (size_t)kSxyStages * 4 * kTM * kKB * 2 + 1024 + 512;
     NAPG_CU(ctx, cudaFuncSetAttribute(k_sxy<NEPI, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (tiles == 0) return NAPG_OK;
+    const int nsplit = tiles - P.nfull;
+    if (nsplit > 0) {
+        count_launch();
+        k_sxy_zero<<<nsplit, 256, 0, st>>>(P);
+        NAPG_CU(ctx, cudaGetLastError());
+    }
     count_launch();
-    k_sxy<NEPI, KS><<<tiles, (2 + NEPI) * 32, smem, st>>>(P);
+    k_sxy<NEPI, KS><<<P.nfull + 2 * nsplit, (2 + NEPI) * 32, smem, st>>>(P);
     NAPG_CU(ctx, cudaGetLastError());
     return NAPG_OK;
 }
 
-static napg_status launch_sxy(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st) {
+// One CTA per SM: a last wave of R < SMs / 2 tiles would leave most SMs idle
+// for a whole tile's time, so those R tiles run as 2R CTAs over half the
+// K-blocks each (half a tile's time). The split depends only on the whole
+// triangle's tile count and the SM count, so every part of a split call and
+// every run of the shape computes each tile the same way.
+static napg_status launch_sxy(napg_ctx *ctx, SxyParams P, int tiles, cudaStream_t st) {
+    const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
+    const int rem = tiles % sms;
+    P.nfull = tiles;
+    P.kbmid = (P.nkb / 4) * 2;                 // an even K-block: the halves' chunks pair K-blocks alike
+    if (tiles > sms && rem > 0 && 2 * rem <= sms && P.kbmid >= 2) P.nfull = tiles - rem;
     auto run = [&](int choice) -> napg_status {
-        return choice == 0 ? launch_sxy_v<8, 64>(ctx, P, tiles, st) : launch_sxy_v<8, 32>(ctx, P, tiles, st);
+        return choice == 0 ? launch_sxy_v<16, 64>(ctx, P, tiles, st) : launch_sxy_v<16, 32>(ctx, P, tiles, st);
     };
     const TuneKey key{kTuneSxy, P.rows, P.rows, P.nkb};
     return tuned_launch(ctx, key, 2, run, st);
