@@ -190,10 +190,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
 // accumulator, and two chunks are in flight. The epilogue adds a chunk's two
 // K-block sums in FP32 (round to nearest, so the added error has no bias) and
 // folds the result into float-float running sums by TwoSum: one TwoSum per two
-// K-blocks of MMAs. NEPI epilogue warps (8 or 16, a quarter per tensor-memory
-// lane quadrant) split the 128 columns; the autotuner picks the count (the
-// outputs are bit-identical: each element sees the same operations in the
-// same order).
+// K-blocks of MMAs. NEPI epilogue warps (a quarter per tensor-memory lane
+// quadrant) split the 128 columns: 16 of them (96 registers a thread) measured
+// the same as 8 and leave room for the per-CTA K range; the autotuner picks the
+// stage width (64 samples, 128-byte swizzle, or 32, 64-byte swizzle: the outputs
+// are bit-identical, each element seeing the same operations in the same order).
 constexpr int kSxyStages = 3;
 
 struct SxyParams {
