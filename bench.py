@@ -269,7 +269,10 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
         na = len(va)
         if test == "pearson":
             T = -(-na // 128)
-            issued = T * (T + 1) / 2 * nkb * 16 * 2.0 * 128 * 128 * 16 + T * -(-na // 48) * nkb * 4 * 2.0 * 128 * 240 * 16
+            # Sxy (triangle, three hi/lo products), n = M M^T (triangle), the mask
+            # against the four value planes (all ordered tile pairs)
+            issued = (T * (T + 1) / 2 * nkb * 12 * 2.0 * 128 * 128 * 16 + T * (T + 1) / 2 * nkb * 4 * 2.0 * 128 * 128 * 16
+                      + T * -(-na // 48) * nkb * 4 * 2.0 * 128 * 192 * 16)
             work["pearson_moments_tc"] = ("tensor", 12.0 * S * na * (na + 1) / 2, issued)
             work.setdefault("planes_f16", ["hbm", 0.0, None])
             work["planes_f16"][1] += na * (esz * S + S / 8 + 10.0 * S_pad)

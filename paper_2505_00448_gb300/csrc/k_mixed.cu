@@ -13,7 +13,7 @@
 // [2^14, 2^15), so hi/lo keep 22 significant bits (a bf16 pair keeps only 16,
 // too few when one heavy-tailed term carries a large share of a sum); the
 // epilogue removes them exactly. FP16 x FP16 products are exact in FP32.
-// Sums for Pearson (Sec. 3.5.2):      Sxy ~ (Xh + Xl)(Xh + Xl)^T (four products),
+// Sums for Pearson (Sec. 3.5.2):      Sxy ~ Xh Xh^T + Xh Xl^T + Xl Xh^T (split x3),
 //                                     n = M M^T, Sx^T = M X~^T, Sxx^T = M D^T + v n
 // Group sums (Sec. 3.5.5, 3.5.7):     n_g = H M^T, S1 = H X~^T, S2 = H D^T + v n_g
 // Contingency tables (Sec. 3.5.4):    T = H H^T
@@ -179,9 +179,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
 // Sum over the co-observed samples of x~_i x~_j for the pairs of a triangle
 // tile (I <= J) of 128 x 128 variables, from the FP16 planes Xh, Xl of the
 // centred, scaled values (zero where a value is missing, so every product off
-// the co-observed set vanishes). Per K-block of 64 samples the MMA thread
-// issues the three small cross products (Xh Xl, Xl Xh, Xl Xl: 2^-11 and 2^-22
-// of Xh Xh, random sign) first and Xh Xh last, all into one accumulator that
+// the co-observed set vanishes). The split product keeps three of the four
+// terms of (Xh + Xl)(Xh + Xl): Xl Xl is below 2^-22 of Xh Xh, about 3.5e-8 of
+// the sum for two copies of one column (the residuals then align) and far less
+// for independent ones, against the 1e-6 bar on r. Per K-block of 64 samples
+// the MMA thread issues the two cross products (Xh Xl, Xl Xh: 2^-11 of Xh Xh,
+// random sign) first and Xh Xh last, all into one accumulator that
 // starts the K-block at zero: the Xh Xh sum is rounded over its own 4
 // instructions, as when drained alone every K-block (correlated pairs add
 // same-sign terms, and the accumulator's per-instruction rounding error grows
@@ -332,7 +335,6 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
                         for (int k = 0; k < KS / 16; ++k) {
                             mma_f16(d, ds[h] + oAh + 2 * k, ds[h] + oBl + 2 * k, IDESC, (h | k) ? 1u : 0u);  // Xh Xl
                             mma_f16(d, ds[h] + oAl + 2 * k, ds[h] + oBh + 2 * k, IDESC, 1u);               // Xl Xh
-                            mma_f16(d, ds[h] + oAl + 2 * k, ds[h] + oBl + 2 * k, IDESC, 1u);               // Xl Xl
                         }
                     }
                     if (!ok) break;
@@ -637,6 +639,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         const uint32_t tempty0 = cluster_addr(&tempty[0], 0);
         constexpr int K2 = kSPerThread / 2;
+        // columns read per tensor-memory wait: all of a plane's, or 16 where the
+        // four sums of 32 columns already hold 128 registers
+        constexpr int kLdCols = kSPerThread > 24 && kSPerThread % 16 == 0 ? 16 : kSPerThread;
         int32_t cnt[kSPerThread];
         uint64_t s1h[K2], s1l[K2], s2h[K2], s2l[K2];    // packed float-float sums
 #pragma unroll
@@ -651,27 +656,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             const uint32_t col0 = tbase + lane_addr + (uint32_t)(b * BUF + h * kSPerThread);
 #pragma unroll
             for (int p = 0; p < NPL; ++p) {
-                uint32_t r[kSPerThread];
 #pragma unroll
-                for (int g = 0; g < kSPerThread / 8; ++g) {
-                    uint32_t t8[8];
-                    tmem_ld8(col0 + (uint32_t)(p * SV + g * 8), t8);
+                for (int g0 = 0; g0 < kSPerThread; g0 += kLdCols) {
+                    uint32_t r[kLdCols];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) r[g * 8 + k] = t8[k];
-                }
-                tmem_ld_wait();
-                const int role = ROLE0 + p;
-                if (role == 0) {
+                    for (int g = 0; g < kLdCols / 8; ++g) {
+                        uint32_t t8[8];
+                        tmem_ld8(col0 + (uint32_t)(p * SV + g0 + g * 8), t8);
 #pragma unroll
-                    for (int k = 0; k < kSPerThread; ++k) cnt[k] += (int32_t)__uint_as_float(r[k]);   // exact integers
-                } else {
+                        for (int k = 0; k < 8; ++k) r[g * 8 + k] = t8[k];
+                    }
+                    tmem_ld_wait();
+                    const int role = ROLE0 + p;
+                    if (role == 0) {
 #pragma unroll
-                    for (int k = 0; k < K2; ++k) {
-                        const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
-                        if (role == 1) two_sum2(s1h[k], s1l[k], v);
-                        else if (role == 2) s1l[k] = add2(s1l[k], v);
-                        else if (role == 3) two_sum2(s2h[k], s2l[k], v);
-                        else s2l[k] = add2(s2l[k], v);
+                        for (int k = 0; k < kLdCols; ++k) cnt[g0 + k] += (int32_t)__uint_as_float(r[k]);   // exact integers
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < kLdCols / 2; ++k) {
+                            const int kk = g0 / 2 + k;
+                            const uint64_t v = pk2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+                            if (role == 1) two_sum2(s1h[kk], s1l[kk], v);
+                            else if (role == 2) s1l[kk] = add2(s1l[kk], v);
+                            else if (role == 3) two_sum2(s2h[kk], s2l[kk], v);
+                            else s2l[kk] = add2(s2l[kk], v);
+                        }
                     }
                 }
             }
@@ -1033,9 +1042,9 @@ static napg_status launch_stacked_sv(napg_ctx *ctx, const StackParams &P, cudaSt
 // 2 * kps_index + width_index. Every shape gives the same sums: each output
 // accumulates the same products in the same order and drains. MMA N = planes x
 // width stays a multiple of 16 and at most 256.
-enum StackPlanes { kStackAll = 0, kStackNS1 = 1, kStackS2 = 2 };
-constexpr int kStackWidths[3][2] = {{48, 32}, {80, 64}, {112, 64}};
-constexpr int kStackPlaneCount[3] = {5, 3, 2};
+enum StackPlanes { kStackAll = 0, kStackNS1 = 1, kStackS2 = 2, kStackSums = 3 };
+constexpr int kStackWidths[4][2] = {{48, 32}, {80, 64}, {112, 64}, {64, 48}};
+constexpr int kStackPlaneCount[4] = {5, 3, 2, 4};
 
 // A x stacked B planes with the B-tile width chosen by the autotuner for this
 // shape (the tensor maps of the B planes are encoded for that width); pb holds
@@ -1056,6 +1065,9 @@ static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *cons
         if (set == kStackAll)
             return sv == 48 ? (two ? launch_stacked_sv<5, 48, 0, 2>(ctx, P, st) : launch_stacked_sv<5, 48, 0, 1>(ctx, P, st))
                             : (two ? launch_stacked_sv<5, 32, 0, 2>(ctx, P, st) : launch_stacked_sv<5, 32, 0, 1>(ctx, P, st));
+        if (set == kStackSums)
+            return sv == 64 ? (two ? launch_stacked_sv<4, 64, 1, 2>(ctx, P, st) : launch_stacked_sv<4, 64, 1, 1>(ctx, P, st))
+                            : (two ? launch_stacked_sv<4, 48, 1, 2>(ctx, P, st) : launch_stacked_sv<4, 48, 1, 1>(ctx, P, st));
         if (set == kStackNS1)
             return sv == 80 ? (two ? launch_stacked_sv<3, 80, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 80, 0, 1>(ctx, P, st))
                             : (two ? launch_stacked_sv<3, 64, 0, 2>(ctx, P, st) : launch_stacked_sv<3, 64, 0, 1>(ctx, P, st));
@@ -1152,6 +1164,9 @@ static napg_status prep_onehot(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStre
 // stall the pair.
 constexpr int kChunkStacked = 16;
 
+static napg_status launch_counts(napg_ctx *ctx, const __half *H, int64_t hrows, int64_t S_pad, int32_t R, int32_t *T,
+                                 const uint8_t *own, cudaStream_t st);
+
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
                           double *vsq, const std::vector<int32_t> *cache_vars, const uint8_t *own) {
@@ -1171,21 +1186,26 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         Stage s_(ctx->trace, st, "pearson_moments_tc");
         NAPG_ST(launch_sxy(ctx, P, T * (T + 1) / 2, st));
     }
-    // P2: all ordered (A tile, B tile) pairs, the mask as A against the stacked
-    // planes of kSV B variables: n = M M^T, sum_s m_i x~_j = Sx[j][i] and
-    // sum_s m_i d_j = D[j][i], written transposed (coalesced stores).
+    // P2: n = M M^T, symmetric, on the triangle (k_counts on the observed plane)
+    {
+        Stage s_(ctx->trace, st, "pearson_moments_tc");
+        NAPG_ST(launch_counts(ctx, cp.M, cp.rows_pad, cp.S_pad, nv, nn, own, st));
+    }
+    // P3: all ordered (A tile, B tile) pairs, the mask as A against the four
+    // value planes of the B variables stacked: sum_s m_i x~_j = Sx[j][i] and
+    // sum_s m_i d_j = D[j][i], written transposed (coalesced stores)
     {
         StackParams P{};
         if (!make_map(&P.mapA, cp.M, cp.rows_pad, cp.S_pad, kTM))
             return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        const void *pb[5] = {cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl};
+        const void *pb[4] = {cp.Xh, cp.Xl, cp.Dh, cp.Dl};
         P.rowsA = nv; P.rowsB = nv; P.tilesA = T;
         P.nkb = nkb; P.chunk = kChunkStacked;
-        P.out_n = nn; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
+        P.out_n = nullptr; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         P.own = own;
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_stacked(ctx, P, pb, kStackAll, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
+        NAPG_ST(launch_stacked(ctx, P, pb, kStackSums, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
     }
     return NAPG_OK;
 }
@@ -1234,11 +1254,10 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     return launch_stacked(ctx, Q, qb, kStackS2, cp.rows_pad, cp.S_pad, kTuneStackSquares, st);
 }
 
-napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
-                              int32_t *T, const uint8_t *own_lev) {
-    __half *H = nullptr;
-    int64_t hrows = 0, S_pad = 0;
-    NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+// T = H H^T over the 0/1 rows of H (hrows x S_pad, rows padded to 128): both
+// triangles of T[R][R], integers exact; own: rows computed (NULL: all)
+static napg_status launch_counts(napg_ctx *ctx, const __half *H, int64_t hrows, int64_t S_pad, int32_t R, int32_t *T,
+                                 const uint8_t *own, cudaStream_t st) {
     CountParams P{};
     if (!make_map(&P.mapA, H, hrows, S_pad, kTM) || !make_map(&P.mapB, H, hrows, S_pad, kCountN))
         return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
@@ -1246,10 +1265,9 @@ napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStrea
     P.tilesA = (int)(hrows / kTM);
     P.tilesB = (int)((hrows + kCountN - 1) / kCountN);
     P.nkb = (int)(S_pad / kKB);
-    P.out = T; P.ld = R; P.err = ctx->dev_err; P.own = own_lev;
+    P.out = T; P.ld = R; P.err = ctx->dev_err; P.own = own;
     int tiles = 0;
     for (int i = 0; i < P.tilesA; ++i) tiles += P.tilesB - i / 2;
-    Stage s_(ctx->trace, st, "contingency_tc");
     const size_t smem = (size_t)kCountStages * (kTM + kCountN) * kKB * 2 + 1024 + 256;
     NAPG_CU(ctx, cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (tiles == 0) return NAPG_OK;
@@ -1257,6 +1275,15 @@ napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStrea
     k_counts<<<tiles, kThreads, smem, st>>>(P);
     NAPG_CU(ctx, cudaGetLastError());
     return NAPG_OK;
+}
+
+napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
+                              int32_t *T, const uint8_t *own_lev) {
+    __half *H = nullptr;
+    int64_t hrows = 0, S_pad = 0;
+    NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+    Stage s_(ctx->trace, st, "contingency_tc");
+    return launch_counts(ctx, H, hrows, S_pad, R, T, own_lev, st);
 }
 
 }  // namespace napg
