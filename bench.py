@@ -249,6 +249,10 @@ def sampled_accuracy(coh, tests, outs, k, seed=123):
 
 # ---------------------------------------------------------------- roofline --
 
+# stages whose MMAs are all E4M3 (the exact 0/1 count contractions)
+FP8_STAGES = ("contingency_tc",)
+
+
 def stage_rooflines(stage_ms, steps, coh, tests, peaks):
     """Roofline entry per traced stage: algorithmic work of the stage per step
     (the per-unit figures of the hot-path table: 12 S flops per Pearson pair,
@@ -258,6 +262,13 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
     S = coh["X"].shape[1]
     S_pad = -(-S // 64) * 64
     nkb = S_pad // 64
+    nkb8 = -(-S // 128)
+
+    def count_flops(tiles_a, kb8):
+        # the E4M3 counts kernel: 128-row A tiles against 256-row B tiles on the
+        # triangle, four MMAs of 128 x 256 x 32 per 128-sample K-block
+        tiles_b = -(-tiles_a // 2)
+        return sum(tiles_b - i // 2 for i in range(tiles_a)) * kb8 * 4 * 2.0 * 128 * 256 * 32
     # measured denominators, else the fallback figures (one earlier GB300 measurement)
     tens_meas, hbm_meas = peaks.get("bf16_tflops_sustained"), peaks.get("hbm_gbs")
     tens_peak = tens_meas or 1700.0
@@ -269,10 +280,11 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
         na = len(va)
         if test == "pearson":
             T = -(-na // 128)
-            # Sxy (triangle, three hi/lo products), n = M M^T (triangle), the mask
-            # against the four value planes (all ordered tile pairs)
-            issued = (T * (T + 1) / 2 * nkb * 12 * 2.0 * 128 * 128 * 16 + T * (T + 1) / 2 * nkb * 4 * 2.0 * 128 * 128 * 16
-                      + T * -(-na // 48) * nkb * 4 * 2.0 * 128 * 192 * 16)
+            # Sxy (triangle, three hi/lo products), the mask against the four value
+            # planes (all ordered tile pairs), and n = M M^T on the triangle in E4M3
+            # (counted at half its flops: the FP8 MMA runs at twice the f16 rate)
+            issued = (T * (T + 1) / 2 * nkb * 12 * 2.0 * 128 * 128 * 16 + T * -(-na // 48) * nkb * 4 * 2.0 * 128 * 192 * 16
+                      + count_flops(T, nkb8) / 2)
             work["pearson_moments_tc"] = ("tensor", 12.0 * S * na * (na + 1) / 2, issued)
             work.setdefault("planes_f16", ["hbm", 0.0, None])
             work["planes_f16"][1] += na * (esz * S + S / 8 + 10.0 * S_pad)
@@ -288,8 +300,7 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
             work["groupsum_tc"] = ("tensor", w[1] + 6.0 * S * na * len(vb), w[2] + issued)
         if test == "chi2":
             R = int(coh["nlev"][va].sum())
-            Tt = -(-R // 128)
-            work["contingency_tc"] = ("tensor", 1.0 * S * na * (na + 1) / 2, Tt * (Tt + 1) / 2 * nkb * 4 * 2.0 * 128 * 128 * 16)
+            work["contingency_tc"] = ("tensor", 1.0 * S * na * (na + 1) / 2, count_flops(-(-R // 128), nkb8))
         if test == "pearson":
             work["pearson_moments_fp64"] = ("fp64", 12.0 * S * na * (na + 1) / 2, None)
         if test in ("anova", "ttest") and vb is not None:
@@ -312,12 +323,17 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
         e = {"kernel": name, "bound": bound, "ms_per_step": v["ms"] / steps,
              "launches_per_step": max(1, v["launches"] // max(1, steps))}
         if bound == "tensor":
-            e.update(achieved=alg / secs / 1e12, peak=tens_peak, unit="TFLOP/s",
-                     peak_source=("measured bf16 dense, sustained (MEASURED_PEAKS; f16 runs at the bf16 rate)"
-                                  if tens_meas else "fallback 1,700 TFLOP/s bf16 sustained (no measured peak)"))
+            src = ("measured bf16 dense, sustained (MEASURED_PEAKS; f16 runs at the bf16 rate)"
+                   if tens_meas else "fallback 1,700 TFLOP/s bf16 sustained (no measured peak)")
+            peak = tens_peak
+            if name in FP8_STAGES:
+                # E4M3 MMAs (kind::f8f6f4): the bf16 figure times the nominal 2x FP8 ratio
+                peak = 2.0 * tens_peak
+                src += " x 2, the nominal FP8 (E4M3) to bf16 ratio"
+            e.update(achieved=alg / secs / 1e12, peak=peak, unit="TFLOP/s", peak_source=src)
             if issued:
                 e["issued_tflops"] = issued / secs / 1e12
-                e["issued_frac"] = e["issued_tflops"] / tens_peak
+                e["issued_frac"] = e["issued_tflops"] / peak
         elif bound == "hbm" and name in ("spearman_rank", "rank_groups"):
             # the rank kernels' byte model (16.25 S or 9.125 S bytes a pair) as an
             # effective rate against the HBM copy rate: their working set stays in

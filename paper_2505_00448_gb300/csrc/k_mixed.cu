@@ -16,12 +16,14 @@
 // Sums for Pearson (Sec. 3.5.2):      Sxy ~ Xh Xh^T + Xh Xl^T + Xl Xh^T (split x3),
 //                                     n = M M^T, Sx^T = M X~^T, Sxx^T = M D^T + v n
 // Group sums (Sec. 3.5.5, 3.5.7):     n_g = H M^T, S1 = H X~^T, S2 = H D^T + v n_g
-// Contingency tables (Sec. 3.5.4):    T = H H^T
+// Contingency tables (Sec. 3.5.4):    T = H H^T (E4M3 planes, kind::f8f6f4)
 // 0/1 operands give integer sums that FP32 holds exactly (S < 2^24): T stays in
-// tensor memory for the whole K loop, and n, n_g are drained as integers. The
-// other sums are accumulated in short K-chunks in tensor memory and drained by
-// the epilogue warps into float-float running sums, which bounds the FP32
-// accumulation error independently of S.
+// tensor memory for the whole K loop; the pair counts n = M M^T and T take
+// their 0/1 planes in FP8 E4M3 (1.0 is exact), at twice the FP16 MMA rate and
+// half the operand bytes. In the stacked contractions n_g is drained as
+// integers. The other sums are accumulated in short K-chunks in tensor memory
+// and drained by the epilogue warps into float-float running sums, which bounds
+// the FP32 accumulation error independently of S.
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
@@ -33,6 +35,7 @@ namespace napg {
 using namespace umma;
 
 constexpr int kKB = 64;    // samples per K-block: one 128-byte swizzle row of 16-bit values
+constexpr int kKB8 = 128;  // samples per K-block of the E4M3 planes: one 128-byte row
 constexpr int kTM = 128;   // rows of an A tile (M of the MMA)
 
 // Triangle tiles (I <= J) of a T x T tile grid in row order: t -> (I, J)
@@ -49,19 +52,21 @@ constexpr int kThreads = 320;
 
 // ----------------------------------------- contingency counts (Sec. 3.5.4) --
 //
-// T[r][c] = sum_s H[r][s] H[c][s] over the one-hot level rows r, c: the number
-// of samples in level r of one categorical and level c of another (0 where
-// either is missing). Integer sums below 2^24 are exact in FP32, so the counts
-// stay in tensor memory for the whole K loop. Tiles are 128 level rows (A) by
-// 256 (B, one MMA of N = 256) over the upper triangle: tile (I, J) for
+// T[r][c] = sum_s H[r][s] H[c][s] over 0/1 rows r, c: for one-hot level rows,
+// the number of samples in level r of one categorical and level c of another
+// (0 where either is missing); for observed-mask rows, the pair counts n. The
+// rows are E4M3 bytes (0x38 = 1.0, 0 = 0), 128 samples per K-block, four
+// kind::f8f6f4 MMAs of K = 32 each. Integer sums below 2^24 are exact in FP32,
+// so the counts stay in tensor memory for the whole K loop. Tiles are 128 rows
+// (A) by 256 (B, one MMA of N = 256) over the upper triangle: tile (I, J) for
 // J * 256 + 255 >= I * 128; each pair (r, c), r <= c, is written once, at
 // (r, c) and (c, r), by the tile that holds it with r in A. Four 48 KB stages.
 constexpr int kCountN = 256, kCountStages = 4;
 
 struct CountParams {
-    CUtensorMap mapA;              // one-hot plane [rows_pad][S_pad], box 64 x 128
-    CUtensorMap mapB;              // the same plane, box 64 x 256
-    int rows, tilesA, tilesB, nkb; // level rows, 128-row tiles, 256-row tiles, K-blocks
+    CUtensorMap mapA;              // E4M3 0/1 plane [rows_pad][S_pad8], box 128 x 128
+    CUtensorMap mapB;              // the same plane, box 128 x 256
+    int rows, tilesA, tilesB, nkb; // rows, 128-row tiles, 256-row tiles, 128-sample K-blocks
     int32_t *out;                  // T [rows][ld], both triangles
     int64_t ld;
     uint32_t *err;
@@ -70,9 +75,9 @@ struct CountParams {
 
 __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ CountParams P) {
     constexpr int N = kCountN;
-    constexpr int A_BYTES = kTM * kKB * 2, B_BYTES = N * kKB * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr int A_BYTES = kTM * kKB8, B_BYTES = N * kKB8, STAGE_BYTES = A_BYTES + B_BYTES;
     constexpr int HC = N / 2;                  // columns per epilogue thread
-    constexpr uint32_t IDESC = idesc_f16_f32(kTM, N);
+    constexpr uint32_t IDESC = idesc_e4m3_f32(kTM, N);
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -113,8 +118,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
                 if (kb >= kCountStages && !mbar_wait(&empty[s], ((kb / kCountStages) - 1) & 1, P.err)) break;
                 mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                 uint8_t *st = smem + s * STAGE_BYTES;
-                tma_load_2d(st, &P.mapA, &full[s], kb * kKB, I * kTM);
-                tma_load_2d(st + A_BYTES, &P.mapB, &full[s], kb * kKB, J * N);
+                tma_load_2d(st, &P.mapA, &full[s], kb * kKB8, I * kTM);
+                tma_load_2d(st + A_BYTES, &P.mapB, &full[s], kb * kKB8, J * N);
                 issued = kb + 1;
             }
             // our own copies must have landed before the CTA tears down
@@ -133,8 +138,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
                 fence_after_sync();
                 const uint64_t ds = dbase + (uint64_t)((uint32_t)(s * STAGE_BYTES) >> 4);
 #pragma unroll
-                for (int k = 0; k < kKB / 16; ++k)
-                    mma_f16(tbase, ds + 2 * k, ds + (A_BYTES >> 4) + 2 * k, IDESC, (kb | k) ? 1u : 0u);
+                for (int k = 0; k < kKB8 / 32; ++k)
+                    mma_e4m3(tbase, ds + 2 * k, ds + (A_BYTES >> 4) + 2 * k, IDESC, (kb | k) ? 1u : 0u);
                 mma_commit(&empty[s]);             // frees the stage once these MMAs are done
             }
             if (ok) mma_commit(tfull);
@@ -931,6 +936,28 @@ __global__ void k_planes_onehot(const uint32_t *__restrict__ levbits, int64_t W,
     }
 }
 
+// The same rows as E4M3 bytes (1.0 = 0x38) over S_pad8 samples (a multiple of
+// 128), sixteen samples (one 16-byte store) per thread and step.
+__global__ void k_planes_onehot8(const uint32_t *__restrict__ bits, int64_t W, int32_t R, int64_t S_pad8,
+                                 uint8_t *H8) {
+    const int r = blockIdx.x;
+    uint4 *h16 = reinterpret_cast<uint4 *>(H8 + (int64_t)r * S_pad8);
+    const int64_t n16 = S_pad8 / 16;
+    for (int64_t q = threadIdx.x; q < n16; q += blockDim.x) {
+        const int64_t s0 = 16 * q, w = s0 >> 5;
+        const uint32_t b = (r < R && w < W) ? (bits[(int64_t)r * W + w] >> (s0 & 31)) & 0xffffu : 0u;
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x |= ((b >> (4 * k + j)) & 1u) * (0x38u << (8 * j));
+            v[k] = x;
+        }
+        h16[q] = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 // ---------------------------------------------------------------- host --
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -960,6 +987,19 @@ static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t c
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, box_k == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// a K-major E4M3 plane [rows][cols], box 128 x box_rows (one 128-byte swizzle row)
+static bool make_map8(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols};
+    cuuint32_t box[2] = {(cuuint32_t)kKB8, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1156,6 +1196,22 @@ static napg_status prep_onehot(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStre
     return NAPG_OK;
 }
 
+// 0/1 rows from bitmask rows (bits[r * W + w]) as an E4M3 plane, rows padded to
+// 128 and samples to 128
+static napg_status prep_onehot8(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *bits,
+                                int32_t R, int slot, uint8_t **H8, int64_t &rows_pad, int64_t &S_pad8) {
+    S_pad8 = ((c.S + kKB8 - 1) / kKB8) * kKB8;
+    rows_pad = ((R + kTM - 1) / kTM) * kTM;
+    napg_status st_ = NAPG_OK;
+    *H8 = (uint8_t *)ws_get(ctx, ws, slot, (size_t)rows_pad * (size_t)S_pad8, &st_);
+    if (st_) return st_;
+    Stage s_(ctx->trace, st, "planes_onehot");
+    count_launch();
+    k_planes_onehot8<<<(unsigned)rows_pad, 256, 0, st>>>(bits, c.W, R, S_pad8, *H8);
+    NAPG_CU(ctx, cudaGetLastError());
+    return NAPG_OK;
+}
+
 // K-blocks (of 64 samples) between drains of the stacked sums: they are
 // counts, centred x~ and centred squares (per variable or per level), whose
 // partial sums random-walk instead of growing with the chunk, so their FP32
@@ -1164,7 +1220,7 @@ static napg_status prep_onehot(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStre
 // stall the pair.
 constexpr int kChunkStacked = 16;
 
-static napg_status launch_counts(napg_ctx *ctx, const __half *H, int64_t hrows, int64_t S_pad, int32_t R, int32_t *T,
+static napg_status launch_counts(napg_ctx *ctx, const uint8_t *H8, int64_t hrows, int64_t S_pad8, int32_t R, int32_t *T,
                                  const uint8_t *own, cudaStream_t st);
 
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
@@ -1186,10 +1242,14 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         Stage s_(ctx->trace, st, "pearson_moments_tc");
         NAPG_ST(launch_sxy(ctx, P, T * (T + 1) / 2, st));
     }
-    // P2: n = M M^T, symmetric, on the triangle (k_counts on the observed plane)
+    // P2: n = M M^T, symmetric, on the triangle (k_counts on the observed rows as
+    // an E4M3 plane)
     {
+        uint8_t *M8 = nullptr;
+        int64_t mrows = 0, S_pad8 = 0;
+        NAPG_ST(prep_onehot8(ctx, c, ws, st, obsv, nv, Workspace::kTmpF, &M8, mrows, S_pad8));
         Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_counts(ctx, cp.M, cp.rows_pad, cp.S_pad, nv, nn, own, st));
+        NAPG_ST(launch_counts(ctx, M8, mrows, S_pad8, nv, nn, own, st));
     }
     // P3: all ordered (A tile, B tile) pairs, the mask as A against the four
     // value planes of the B variables stacked: sum_s m_i x~_j = Sx[j][i] and
@@ -1254,21 +1314,21 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
     return launch_stacked(ctx, Q, qb, kStackS2, cp.rows_pad, cp.S_pad, kTuneStackSquares, st);
 }
 
-// T = H H^T over the 0/1 rows of H (hrows x S_pad, rows padded to 128): both
-// triangles of T[R][R], integers exact; own: rows computed (NULL: all)
-static napg_status launch_counts(napg_ctx *ctx, const __half *H, int64_t hrows, int64_t S_pad, int32_t R, int32_t *T,
+// T = H H^T over the 0/1 E4M3 rows of H8 (hrows x S_pad8, rows padded to 128):
+// both triangles of T[R][R], integers exact; own: rows computed (NULL: all)
+static napg_status launch_counts(napg_ctx *ctx, const uint8_t *H8, int64_t hrows, int64_t S_pad8, int32_t R, int32_t *T,
                                  const uint8_t *own, cudaStream_t st) {
     CountParams P{};
-    if (!make_map(&P.mapA, H, hrows, S_pad, kTM) || !make_map(&P.mapB, H, hrows, S_pad, kCountN))
+    if (!make_map8(&P.mapA, H8, hrows, S_pad8, kTM) || !make_map8(&P.mapB, H8, hrows, S_pad8, kCountN))
         return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
     P.rows = R;
     P.tilesA = (int)(hrows / kTM);
     P.tilesB = (int)((hrows + kCountN - 1) / kCountN);
-    P.nkb = (int)(S_pad / kKB);
+    P.nkb = (int)(S_pad8 / kKB8);
     P.out = T; P.ld = R; P.err = ctx->dev_err; P.own = own;
     int tiles = 0;
     for (int i = 0; i < P.tilesA; ++i) tiles += P.tilesB - i / 2;
-    const size_t smem = (size_t)kCountStages * (kTM + kCountN) * kKB * 2 + 1024 + 256;
+    const size_t smem = (size_t)kCountStages * (kTM + kCountN) * kKB8 + 1024 + 256;
     NAPG_CU(ctx, cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (tiles == 0) return NAPG_OK;
     count_launch();
@@ -1279,11 +1339,11 @@ static napg_status launch_counts(napg_ctx *ctx, const __half *H, int64_t hrows, 
 
 napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const uint32_t *levbits, int32_t R,
                               int32_t *T, const uint8_t *own_lev) {
-    __half *H = nullptr;
-    int64_t hrows = 0, S_pad = 0;
-    NAPG_ST(prep_onehot(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H, hrows, S_pad));
+    uint8_t *H8 = nullptr;
+    int64_t hrows = 0, S_pad8 = 0;
+    NAPG_ST(prep_onehot8(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H8, hrows, S_pad8));
     Stage s_(ctx->trace, st, "contingency_tc");
-    return launch_counts(ctx, H, hrows, S_pad, R, T, own_lev, st);
+    return launch_counts(ctx, H8, hrows, S_pad8, R, T, own_lev, st);
 }
 
 }  // namespace napg

@@ -38,7 +38,9 @@ def test_every_modelled_stage_and_the_dominant_one():
     S = coh["X"].shape[1]
     for name in ("pearson_moments_tc", "groupsum_tc", "contingency_tc"):
         e = ents[name]
-        assert e["bound"] == "tensor" and e["unit"] == "TFLOP/s" and e["peak"] == 1752.0
+        # the contingency tables run as E4M3 MMAs: twice the bf16 figure
+        assert e["bound"] == "tensor" and e["unit"] == "TFLOP/s"
+        assert e["peak"] == (2 * 1752.0 if name == "contingency_tc" else 1752.0)
         assert e["issued_tflops"] >= e["achieved"] > 0          # the split issues more than the algorithm needs
         assert abs(e["frac"] - e["achieved"] / e["peak"]) < 1e-12
     for name in ("spearman_rank", "rank_groups"):

@@ -221,7 +221,7 @@ def test_autotuner_keeps_results_identical(napg):
             # planes; the t-test: level rows x all five planes
             assert {"stacked_mask", "stacked_onehot", "stacked_onehot_counts_sums", "stacked_observed_squares",
                     "sxy_stage_samples", "spearman_threads", "rank_groups_threads"} <= kinds, recs
-            assert all(len(x["ms"]) == (4 if x["kind"].startswith("stacked") else 2) and min(x["ms"]) > 0
+            assert all(len(x["ms"]) == TUNE_CANDIDATES.get(x["kind"], 2) and min(x["ms"]) > 0
                        for x in recs), recs
         else:
             assert c.tune_read() == []
@@ -235,6 +235,8 @@ def test_autotuner_keeps_results_identical(napg):
 
 TUNE_KINDS = ("stacked_mask", "stacked_onehot", "stacked_onehot_counts_sums", "stacked_observed_squares",
               "sxy_stage_samples", "spearman_threads", "rank_groups_threads")
+TUNE_CANDIDATES = {"stacked_mask": 4, "stacked_onehot": 4, "stacked_onehot_counts_sums": 4,
+                   "stacked_observed_squares": 4}      # the other kinds: 2
 
 
 def test_autotuner_every_candidate_bit_identical(napg):
@@ -251,7 +253,7 @@ def test_autotuner_every_candidate_bit_identical(napg):
     for pin in (0, 1, 2, 3):
         c = napg.Context(0)
         for k in TUNE_KINDS:
-            c.tune_pin(k, pin if k.startswith("stacked") else pin % 2)
+            c.tune_pin(k, pin % TUNE_CANDIDATES.get(k, 2))
         c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
         r = {"pearson": c.run("pearson", coh["cont"], out="numpy", precision="mixed"),
              "anova": c.run("anova", coh["cat"], coh["cont"], out="numpy", precision="mixed"),
