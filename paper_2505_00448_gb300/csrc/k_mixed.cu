@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
         while (t >= P.tilesB - I / 2) { t -= P.tilesB - I / 2; ++I; }
         J = I / 2 + t;
     }
-    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;   // another part's rows
+    pdl_trigger();
+    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) { pdl_wait(); return; }   // another part's rows
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kCountStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
         const int gi = I * kTM + q * 32 + lane;
         if (mbar_wait(tfull, 0, P.err)) {
             fence_after_sync();
+            pdl_wait();
             const uint32_t a0 = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(half * HC);
 #pragma unroll 1
             for (int g = 0; g < HC / 16; ++g) {
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_counts(const __grid_constant__ 
             }
         }
     }
+    pdl_wait();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -262,7 +265,8 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
         int kb0, nk;
         tri_coords(sxy_tile(P, kb0, nk), P.tiles, I, J);
     }
-    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;   // another part's rows
+    pdl_trigger();
+    if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) { pdl_wait(); return; }   // another part's rows
     const bool diag = I == J;                  // B is A: loaded once
 
     if (threadIdx.x == 0) {
@@ -397,6 +401,7 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
         }
+        pdl_wait();
         if (ok) {
             const int gi = I * kTM + row;
             if (gi < P.rows) {
@@ -420,6 +425,7 @@ __global__ void __launch_bounds__((2 + NEPI) * 32, 1) k_sxy(const __grid_constan
             }
         }
     }
+    pdl_wait();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -541,6 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
         J = r / gsz;
         I2 = g * kSGroup + (r - J * gsz);
     }
+    pdl_trigger();
     if (P.own) {
         // a split call needs the sums of pairs (i, j), i <= j, i owned: tiles with
         // owned A rows and a B column at or after them, or owned B rows and an A
@@ -548,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
         const int64_t a0 = (int64_t)2 * I2 * kTM, c0 = (int64_t)J * SV;
         const bool need = (rows_owned(P.own, a0, 2 * kTM, P.rowsA) && c0 + SV - 1 >= a0) ||
                           (rows_owned(P.own, c0, SV, P.rowsB) && a0 + 2 * kTM - 1 >= c0);
-        if (!need) return;
+        if (!need) { pdl_wait(); return; }
     }
     const int nchunks = (P.nkb + P.chunk - 1) / P.chunk;   // P.chunk is a multiple of KPS
     const int nsb = (P.nkb + KPS - 1) / KPS;                  // pipeline stages to fill
@@ -693,6 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(tempty0 + (uint32_t)(b * 8));
         }
+        pdl_wait();
         if (ok) {
             const int gi = (2 * I2 + (int)rank) * kTM + row;
             if (gi < P.rowsA) {
@@ -719,6 +727,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_umma_stacked(const __grid_const
             }
         }
     }
+    pdl_wait();
     fence_before_sync();
     __syncthreads();
     cluster_sync();                // neither CTA leaves while the pair still reads its shared memory
@@ -1006,6 +1015,8 @@ static bool make_map8(CUtensorMap *m, const void *base, uint64_t rows, uint64_t 
 // zeroes the outputs of the split triangle tiles (from nfull on) that this part
 // owns, before both halves add into them
 __global__ void k_sxy_zero(SxyParams P) {
+    pdl_trigger();
+    pdl_wait();
     int I, J;
     tri_coords(P.nfull + (int)blockIdx.x, P.tiles, I, J);
     if (!rows_owned(P.own, (int64_t)I * kTM, kTM, P.rows)) return;
@@ -1015,20 +1026,38 @@ __global__ void k_sxy_zero(SxyParams P) {
     }
 }
 
+// kern<<<grid, block, smem, st>>>(P); with pdl, as a programmatic dependent of
+// the stream's previous kernel (the kernel's blocks may start in that kernel's
+// tail; the kernel orders its stores and its completion after it by pdl_wait)
+template <typename Par>
+static cudaError_t launch_chain(void (*kern)(Par), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                                bool pdl, const Par &P) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, P);
+}
+
 template <int NEPI, int KS>
-static napg_status launch_sxy_v(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st) {
+static napg_status launch_sxy_v(napg_ctx *ctx, const SxyParams &P, int tiles, cudaStream_t st, bool pdl) {
     const size_t smem = (size_t)kSxyStages * 4 * kTM * kKB * 2 + 1024 + 512;
     NAPG_CU(ctx, cudaFuncSetAttribute(k_sxy<NEPI, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (tiles == 0) return NAPG_OK;
     const int nsplit = tiles - P.nfull;
     if (nsplit > 0) {
         count_launch();
-        k_sxy_zero<<<nsplit, 256, 0, st>>>(P);
-        NAPG_CU(ctx, cudaGetLastError());
+        NAPG_CU(ctx, launch_chain(k_sxy_zero, (unsigned)nsplit, 256, 0, st, pdl, P));
+        pdl = true;              // k_sxy's split tiles add into what k_sxy_zero cleared
     }
     count_launch();
-    k_sxy<NEPI, KS><<<P.nfull + 2 * nsplit, (2 + NEPI) * 32, smem, st>>>(P);
-    NAPG_CU(ctx, cudaGetLastError());
+    NAPG_CU(ctx, launch_chain(k_sxy<NEPI, KS>, (unsigned)(P.nfull + 2 * nsplit), (2 + NEPI) * 32, smem, st, pdl, P));
     return NAPG_OK;
 }
 
@@ -1037,14 +1066,14 @@ static napg_status launch_sxy_v(napg_ctx *ctx, const SxyParams &P, int tiles, cu
 // K-blocks each (half a tile's time). The split depends only on the whole
 // triangle's tile count and the SM count, so every part of a split call and
 // every run of the shape computes each tile the same way.
-static napg_status launch_sxy(napg_ctx *ctx, SxyParams P, int tiles, cudaStream_t st) {
+static napg_status launch_sxy(napg_ctx *ctx, SxyParams P, int tiles, cudaStream_t st, bool pdl) {
     const int sms = ctx->sm_count > 0 ? ctx->sm_count : 152;
     const int rem = tiles % sms;
     P.nfull = tiles;
     P.kbmid = (P.nkb / 4) * 2;                 // an even K-block: the halves' chunks pair K-blocks alike
     if (tiles > sms && rem > 0 && 2 * rem <= sms && P.kbmid >= 2) P.nfull = tiles - rem;
     auto run = [&](int choice) -> napg_status {
-        return choice == 0 ? launch_sxy_v<16, 64>(ctx, P, tiles, st) : launch_sxy_v<16, 32>(ctx, P, tiles, st);
+        return choice == 0 ? launch_sxy_v<16, 64>(ctx, P, tiles, st, pdl) : launch_sxy_v<16, 32>(ctx, P, tiles, st, pdl);
     };
     const TuneKey key{kTuneSxy, P.rows, P.rows, P.nkb};
     return tuned_launch(ctx, key, 2, run, st);
@@ -1221,7 +1250,7 @@ static napg_status prep_onehot8(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStr
 constexpr int kChunkStacked = 16;
 
 static napg_status launch_counts(napg_ctx *ctx, const uint8_t *H8, int64_t hrows, int64_t S_pad8, int32_t R, int32_t *T,
-                                 const uint8_t *own, cudaStream_t st);
+                                 const uint8_t *own, cudaStream_t st, bool pdl);
 
 napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t st, const int32_t *vars_dev, int32_t nv,
                           const uint32_t *obsv, double *Sxy, double *Sx, double *Sxx, int32_t *nn, double *shift,
@@ -1230,28 +1259,15 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
     NAPG_ST(prep_cont_planes(ctx, c, ws, st, vars_dev, nv, obsv, Workspace::kTmpA, shift, vsq, cp, cache_vars));
     const int nkb = (int)(cp.S_pad / kKB);
     const int T = (int)(cp.rows_pad / kTM);
-    // P1: Sxy on the triangle tiles (k_sxy).
-    {
-        SxyParams P{};
-        if (!make_map(&P.mapH, cp.Xh, cp.rows_pad, cp.S_pad, kTM) || !make_map(&P.mapL, cp.Xl, cp.rows_pad, cp.S_pad, kTM) ||
-            !make_map(&P.mapH32, cp.Xh, cp.rows_pad, cp.S_pad, kTM, 32) ||
-            !make_map(&P.mapL32, cp.Xl, cp.rows_pad, cp.S_pad, kTM, 32))
-            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
-        P.rows = nv; P.tiles = T; P.nkb = nkb;
-        P.out = Sxy; P.ld = nv; P.sexp = cp.sexp; P.err = ctx->dev_err; P.own = own;
-        Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_sxy(ctx, P, T * (T + 1) / 2, st));
-    }
-    // P2: n = M M^T, symmetric, on the triangle (k_counts on the observed rows as
-    // an E4M3 plane)
-    {
-        uint8_t *M8 = nullptr;
-        int64_t mrows = 0, S_pad8 = 0;
-        NAPG_ST(prep_onehot8(ctx, c, ws, st, obsv, nv, Workspace::kTmpF, &M8, mrows, S_pad8));
-        Stage s_(ctx->trace, st, "pearson_moments_tc");
-        NAPG_ST(launch_counts(ctx, M8, mrows, S_pad8, nv, nn, own, st));
-    }
-    // P3: all ordered (A tile, B tile) pairs, the mask as A against the four
+    // The E4M3 observed rows for the pair counts, built before the chain below
+    uint8_t *M8 = nullptr;
+    int64_t mrows = 0, S_pad8 = 0;
+    NAPG_ST(prep_onehot8(ctx, c, ws, st, obsv, nv, Workspace::kTmpF, &M8, mrows, S_pad8));
+    // Three independent contractions over the planes, each launched as a
+    // programmatic dependent of the one before, so that its blocks start on the
+    // SMs the previous kernel's last, partial wave leaves idle.
+    Stage s_(ctx->trace, st, "pearson_moments_tc");
+    // P1: all ordered (A tile, B tile) pairs, the mask as A against the four
     // value planes of the B variables stacked: sum_s m_i x~_j = Sx[j][i] and
     // sum_s m_i d_j = D[j][i], written transposed (coalesced stores)
     {
@@ -1264,8 +1280,20 @@ napg_status mixed_pearson(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t 
         P.out_n = nullptr; P.out_s1 = Sx; P.out_s2 = Sxx; P.ld = nv; P.out_transpose = 1;
         P.exp1 = cp.sexp; P.exp2 = cp.texp; P.err = ctx->dev_err;
         P.own = own;
-        Stage s_(ctx->trace, st, "pearson_moments_tc");
         NAPG_ST(launch_stacked(ctx, P, pb, kStackSums, cp.rows_pad, cp.S_pad, kTuneStackMask, st));
+    }
+    // P2: n = M M^T, symmetric, on the triangle (k_counts on the E4M3 rows)
+    NAPG_ST(launch_counts(ctx, M8, mrows, S_pad8, nv, nn, own, st, true));
+    // P3: Sxy on the triangle tiles (k_sxy)
+    {
+        SxyParams P{};
+        if (!make_map(&P.mapH, cp.Xh, cp.rows_pad, cp.S_pad, kTM) || !make_map(&P.mapL, cp.Xl, cp.rows_pad, cp.S_pad, kTM) ||
+            !make_map(&P.mapH32, cp.Xh, cp.rows_pad, cp.S_pad, kTM, 32) ||
+            !make_map(&P.mapL32, cp.Xl, cp.rows_pad, cp.S_pad, kTM, 32))
+            return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
+        P.rows = nv; P.tiles = T; P.nkb = nkb;
+        P.out = Sxy; P.ld = nv; P.sexp = cp.sexp; P.err = ctx->dev_err; P.own = own;
+        NAPG_ST(launch_sxy(ctx, P, T * (T + 1) / 2, st, true));
     }
     return NAPG_OK;
 }
@@ -1317,7 +1345,7 @@ napg_status mixed_groupsum(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStream_t
 // T = H H^T over the 0/1 E4M3 rows of H8 (hrows x S_pad8, rows padded to 128):
 // both triangles of T[R][R], integers exact; own: rows computed (NULL: all)
 static napg_status launch_counts(napg_ctx *ctx, const uint8_t *H8, int64_t hrows, int64_t S_pad8, int32_t R, int32_t *T,
-                                 const uint8_t *own, cudaStream_t st) {
+                                 const uint8_t *own, cudaStream_t st, bool pdl) {
     CountParams P{};
     if (!make_map8(&P.mapA, H8, hrows, S_pad8, kTM) || !make_map8(&P.mapB, H8, hrows, S_pad8, kCountN))
         return fail(ctx, NAPG_E_CUDA, "cuTensorMapEncodeTiled failed");
@@ -1332,8 +1360,7 @@ static napg_status launch_counts(napg_ctx *ctx, const uint8_t *H8, int64_t hrows
     NAPG_CU(ctx, cudaFuncSetAttribute(k_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (tiles == 0) return NAPG_OK;
     count_launch();
-    k_counts<<<tiles, kThreads, smem, st>>>(P);
-    NAPG_CU(ctx, cudaGetLastError());
+    NAPG_CU(ctx, launch_chain(k_counts, (unsigned)tiles, kThreads, smem, st, pdl, P));
     return NAPG_OK;
 }
 
@@ -1343,7 +1370,7 @@ napg_status mixed_contingency(napg_ctx *ctx, Cohort &c, Workspace &ws, cudaStrea
     int64_t hrows = 0, S_pad8 = 0;
     NAPG_ST(prep_onehot8(ctx, c, ws, st, levbits, R, Workspace::kTmpF, &H8, hrows, S_pad8));
     Stage s_(ctx->trace, st, "contingency_tc");
-    return launch_counts(ctx, H8, hrows, S_pad8, R, T, own_lev, st);
+    return launch_counts(ctx, H8, hrows, S_pad8, R, T, own_lev, st, false);
 }
 
 }  // namespace napg

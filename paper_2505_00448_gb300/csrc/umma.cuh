@@ -115,6 +115,16 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Programmatic dependent launch. pdl_trigger lets the stream's next kernel, if
+// it was launched as a programmatic dependent, start its blocks on the SMs this
+// grid leaves free (its tail). pdl_wait holds the calling thread until the
+// stream's previous kernel has completed and its writes are visible; a kernel
+// launched as a dependent calls it before its first global store and before it
+// exits, so that its stores and its completion follow that kernel's. Both are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Instruction descriptor of tcgen05.mma .kind::f8f6f4 with A and B both E4M3
 // (type code 0 in bits 7-9 and 10-12) and D f32: the same fields and values as
 // idesc_f16_f32, the operand format coming from the instruction's kind.
