@@ -755,15 +755,17 @@ __device__ __forceinline__ int scale_exp(double maxabs) {
 // two), and the planes keep 22.
 // Four consecutive values x[s0 .. s0+3] (zero past S): one 16-byte load (two for
 // FP64) when the row is 16-byte aligned and the four are inside it.
-template <typename T>
+// LAST: the values' last use (streaming loads, evicted from L2 first).
+template <bool LAST = false, typename T>
 __device__ __forceinline__ void load4(const T *__restrict__ x, int64_t s0, int64_t S, bool aligned, T (&v)[4]) {
     if (aligned && s0 + 4 <= S) {
         if constexpr (sizeof(T) == 4) {
-            const float4 f = *reinterpret_cast<const float4 *>(x + s0);
+            const float4 *p = reinterpret_cast<const float4 *>(x + s0);
+            const float4 f = LAST ? __ldcs(p) : *p;
             v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
         } else {
-            const double2 a = *reinterpret_cast<const double2 *>(x + s0);
-            const double2 b = *reinterpret_cast<const double2 *>(x + s0 + 2);
+            const double2 *p = reinterpret_cast<const double2 *>(x + s0);
+            const double2 a = LAST ? __ldcs(p) : p[0], b = LAST ? __ldcs(p + 1) : p[1];
             v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
         }
     } else {
@@ -772,157 +774,149 @@ __device__ __forceinline__ void load4(const T *__restrict__ x, int64_t s0, int64
     }
 }
 
-// STAGE: the row and its observed bits are first copied to shared memory (one
-// read from HBM; the three passes then read shared memory), for rows that fit.
-// Every pass takes four samples per thread and step.
-template <typename T, bool STAGE>
-__global__ void __launch_bounds__(1024) k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad,
-                                                      const int32_t *__restrict__ vars, int32_t nv,
-                                                      const uint32_t *__restrict__ obsv, int64_t W, __half *Pm,
-                                                      __half *Pxh, __half *Pxl, __half *Pdh, __half *Pdl,
-                                                      double *shift, double *vsq, int8_t *sexp, int8_t *texp) {
-    extern __shared__ __align__(16) unsigned char pl_smem[];
-    const int i = blockIdx.x;
-    const int64_t base = (int64_t)i * S_pad;
-    // the planes are written four samples (8 bytes) per thread and step (S_pad is
-    // a multiple of 64, so every row starts 128-byte aligned)
-    uint2 *m4 = reinterpret_cast<uint2 *>(Pm + base), *xh4 = reinterpret_cast<uint2 *>(Pxh + base),
-          *xl4 = reinterpret_cast<uint2 *>(Pxl + base), *dh4 = reinterpret_cast<uint2 *>(Pdh + base),
-          *dl4 = reinterpret_cast<uint2 *>(Pdl + base);
-    const int64_t n4 = S_pad / 4;
-    if (i >= nv) {
-        const uint2 z4 = make_uint2(0u, 0u);
-        for (int64_t q = threadIdx.x; q < n4; q += blockDim.x) { m4[q] = z4; xh4[q] = z4; xl4[q] = z4; dh4[q] = z4; dl4[q] = z4; }
-        return;
-    }
-    const T *x = X + (int64_t)vars[i] * S;
-    const uint32_t *ob = obsv + (int64_t)i * W;
-    if (STAGE) {
-        T *xs = reinterpret_cast<T *>(pl_smem);
-        uint32_t *obs = reinterpret_cast<uint32_t *>(pl_smem + (size_t)S_pad * sizeof(T));
-        // 16-byte loads, four in flight per thread, when the row is 16-byte aligned
-        int64_t done = 0;
-        if ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
-            const int64_t nvec = (int64_t)(S * sizeof(T)) / 16;
-            const uint4 *xv = reinterpret_cast<const uint4 *>(x);
-            uint4 *sv = reinterpret_cast<uint4 *>(xs);
-#pragma unroll 4
-            for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) sv[q] = xv[q];
-            done = nvec * (int64_t)(16 / sizeof(T));
-        }
-        for (int64_t s = done + threadIdx.x; s < S; s += blockDim.x) xs[s] = x[s];
-        for (int64_t w = threadIdx.x; w < W; w += blockDim.x) obs[w] = ob[w];
-        __syncthreads();
-        x = xs;
-        ob = obs;
-    }
-    __shared__ float red[4][32];
-    __shared__ int redc[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const bool al = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    const int64_t nq = (S + 3) / 4;
-    // pass 1: the shift c = mean of the observed values (FP32)
-    float s1 = 0.f;
-    int cn = 0;
-    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
-        const int64_t s0 = 4 * q;
-        const uint32_t obits = (ob[s0 >> 5] >> (s0 & 31)) & 0xfu;
-        if (!obits) continue;
-        T xv[4];
-        load4(x, s0, S, al, xv);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if ((obits >> k) & 1u) { s1 += (float)xv[k]; ++cn; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        s1 += __shfl_down_sync(0xffffffffu, s1, o);
-        cn += __shfl_down_sync(0xffffffffu, cn, o);
-    }
-    if (lane == 0) { red[0][warp] = s1; redc[warp] = cn; }
-    __syncthreads();
-    float tot = 0.f;
-    int cnt = 0;
-    for (int k = 0; k < nw; ++k) { tot += red[0][k]; cnt += redc[k]; }   // every thread, same order
-    const float c = cnt > 0 ? tot / (float)cnt : 0.f;
-    __syncthreads();
-    // pass 2: v = mean (x - c)^2, the largest |x - c| and the range of (x - c)^2,
-    // which bounds |(x - c)^2 - v| (the square planes' scale)
-    float s2 = 0.f, mx = 0.f, sqmax = 0.f, sqmin = 3.0e38f;
-    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
-        const int64_t s0 = 4 * q;
-        const uint32_t obits = (ob[s0 >> 5] >> (s0 & 31)) & 0xfu;
-        if (!obits) continue;
-        T xv[4];
-        load4(x, s0, S, al, xv);
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if ((obits >> k) & 1u) {
-                const float d = (float)(xv[k] - (T)c);
-                const float sq = d * d;
-                s2 = fmaf(d, d, s2);
-                mx = fmaxf(mx, fabsf(d));
-                sqmax = fmaxf(sqmax, sq);
-                sqmin = fminf(sqmin, sq);
+// (count, mean, sum of squared deviations) of two parts of a row, merged
+// (Chan, Golub and LeVeque's pairwise update), in FP32
+__device__ __forceinline__ void chan_merge(float &n, float &m, float &q, float n2, float m2, float q2) {
+    const float nt = n + n2;
+    if (nt == 0.f) return;
+    const float d = m2 - m, f = n2 / nt;
+    m = fmaf(d, f, m);
+    q = q + q2 + d * d * n * f;
+    n = nt;
+}
+
+// Persistent: kPlaneRowsPerSM blocks per SM take the (padded) rows in turn.
+// Pass 1 streams the row once for the observed count, mean and squared
+// deviations (each thread about its own first observed value, merged across
+// threads by chan_merge) and the extremes, which give the largest |x - c| and
+// bound |(x - c)^2 - v| by max(max (x - c)^2 - v, v); pass 2 reads the row again
+// from L2 (the rows in flight take a few tens of MB; its loads and the plane
+// stores are marked streaming, evicted first, so that they do not push the
+// rows out) and writes the planes. Four samples per thread and step, several
+// steps in flight.
+constexpr int kPlaneThreads = 512, kPlaneRowsPerSM = 3;
+
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads, kPlaneRowsPerSM) k_planes_cont(const T *__restrict__ X, int64_t S, int64_t S_pad,
+                                                              const int32_t *__restrict__ vars, int32_t nv,
+                                                              int32_t rows_pad, const uint32_t *__restrict__ obsv,
+                                                              int64_t W, __half *Pm, __half *Pxh, __half *Pxl,
+                                                              __half *Pdh, __half *Pdl, double *shift, double *vsq,
+                                                              int8_t *sexp, int8_t *texp) {
+    __shared__ float red[5][kPlaneThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nw = kPlaneThreads / 32;
+    const int64_t n4 = S_pad / 4, nq = (S + 3) / 4;
+    for (int i = blockIdx.x; i < rows_pad; i += gridDim.x) {
+        const int64_t base = (int64_t)i * S_pad;
+        // the planes are written four samples (8 bytes) per thread and step (S_pad
+        // is a multiple of 64, so every row starts 128-byte aligned)
+        uint2 *m4 = reinterpret_cast<uint2 *>(Pm + base), *xh4 = reinterpret_cast<uint2 *>(Pxh + base),
+              *xl4 = reinterpret_cast<uint2 *>(Pxl + base), *dh4 = reinterpret_cast<uint2 *>(Pdh + base),
+              *dl4 = reinterpret_cast<uint2 *>(Pdl + base);
+        if (i >= nv) {
+            const uint2 z4 = make_uint2(0u, 0u);
+            for (int64_t q = threadIdx.x; q < n4; q += kPlaneThreads) {
+                __stcs(m4 + q, z4); __stcs(xh4 + q, z4); __stcs(xl4 + q, z4); __stcs(dh4 + q, z4); __stcs(dl4 + q, z4);
             }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        s2 += __shfl_down_sync(0xffffffffu, s2, o);
-        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        sqmax = fmaxf(sqmax, __shfl_down_sync(0xffffffffu, sqmax, o));
-        sqmin = fminf(sqmin, __shfl_down_sync(0xffffffffu, sqmin, o));
-    }
-    if (lane == 0) { red[0][warp] = s2; red[1][warp] = mx; red[2][warp] = sqmax; red[3][warp] = sqmin; }
-    __syncthreads();
-    float ts2 = 0.f, tmx = 0.f, tmax = 0.f, tmin = 3.0e38f;
-    for (int k = 0; k < nw; ++k) {
-        ts2 += red[0][k];
-        tmx = fmaxf(tmx, red[1][k]);
-        tmax = fmaxf(tmax, red[2][k]);
-        tmin = fminf(tmin, red[3][k]);
-    }
-    const float v = cnt > 0 ? ts2 / (float)cnt : 0.f;
-    const float md = cnt > 0 ? fmaxf(tmax - v, v - tmin) : 0.f;
-    const int es = scale_exp((double)tmx), et = scale_exp((double)md);
-    if (threadIdx.x == 0) { shift[i] = (double)c; vsq[i] = (double)v; sexp[i] = (int8_t)es; texp[i] = (int8_t)et; }
-    const float fs = exp2f((float)es), ft = exp2f((float)et);   // exact powers of two
-    // pass 3: the planes, four samples per thread and step
-    for (int64_t q = threadIdx.x; q < n4; q += blockDim.x) {
-        const int64_t s0 = 4 * q;
-        const uint32_t obits = s0 < S ? (ob[s0 >> 5] >> (s0 & 31)) & 0xfu : 0u;
-        T xv[4] = {T(0), T(0), T(0), T(0)};
-        if (obits) load4(x, s0, S, al, xv);
-        __align__(8) __half hm[4];
-        __align__(8) __half hxh[4];
-        __align__(8) __half hxl[4];
-        __align__(8) __half hdh[4];
-        __align__(8) __half hdl[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t s = s0 + k;
-            const bool o = s < S && ((obits >> k) & 1u);
-            float xt = 0.f;
-            if (o) xt = (float)(xv[k] - (T)c);
-            const float xs = xt * fs;                                  // exact scaling
-            const __half h = __float2half_rn(xs);
-            const __half l = __float2half_rn(xs - __half2float(h));    // the difference is exact in FP32
-            // d = xt^2 - v with the square's rounding error recovered by FMA
-            const float sq = xt * xt;
-            const float sq_err = fmaf(xt, xt, -sq);
-            const float ds = ((sq - v) + sq_err) * ft;
-            const __half dh = __float2half_rn(ds);
-            const __half dl = __float2half_rn(ds - __half2float(dh));
-            const __half z = __float2half(0.f);
-            hm[k] = o ? __float2half(1.f) : z;
-            hxh[k] = o ? h : z;
-            hxl[k] = o ? l : z;
-            hdh[k] = o ? dh : z;
-            hdl[k] = o ? dl : z;
+            continue;
         }
-        m4[q] = *reinterpret_cast<const uint2 *>(hm);
-        xh4[q] = *reinterpret_cast<const uint2 *>(hxh);
-        xl4[q] = *reinterpret_cast<const uint2 *>(hxl);
-        dh4[q] = *reinterpret_cast<const uint2 *>(hdh);
-        dl4[q] = *reinterpret_cast<const uint2 *>(hdl);
+        const T *x = X + (int64_t)vars[i] * S;
+        const uint32_t *ob = obsv + (int64_t)i * W;
+        const bool al = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+        // pass 1
+        float cn = 0.f, sh = 0.f, s1 = 0.f, s2 = 0.f;
+        T hi = T(-3.0e38f), lo = T(3.0e38f);
+        bool have = false;
+#pragma unroll 4
+        for (int64_t q = threadIdx.x; q < nq; q += kPlaneThreads) {
+            const int64_t s0 = 4 * q;
+            const uint32_t obits = (ob[s0 >> 5] >> (s0 & 31)) & 0xfu;
+            T xv[4];
+            load4(x, s0, S, al, xv);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((obits >> k) & 1u) {
+                    if (!have) { sh = (float)xv[k]; have = true; }
+                    const float d = (float)(xv[k] - (T)sh);
+                    cn += 1.f;
+                    s1 += d;
+                    s2 = fmaf(d, d, s2);
+                    hi = xv[k] > hi ? xv[k] : hi;
+                    lo = xv[k] < lo ? xv[k] : lo;
+                }
+        }
+        // this thread's (count, mean, squared deviations) about its own mean
+        float m = 0.f, qd = 0.f;
+        if (cn > 0.f) {
+            const float a = s1 / cn;
+            m = sh + a;
+            qd = fmaxf(fmaf(-a, s1, s2), 0.f);
+        }
+        float fhi = (float)hi, flo = (float)lo;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float n2 = __shfl_down_sync(0xffffffffu, cn, o), m2 = __shfl_down_sync(0xffffffffu, m, o),
+                        q2 = __shfl_down_sync(0xffffffffu, qd, o);
+            chan_merge(cn, m, qd, n2, m2, q2);
+            fhi = fmaxf(fhi, __shfl_down_sync(0xffffffffu, fhi, o));
+            flo = fminf(flo, __shfl_down_sync(0xffffffffu, flo, o));
+        }
+        if (lane == 0) { red[0][warp] = cn; red[1][warp] = m; red[2][warp] = qd; red[3][warp] = fhi; red[4][warp] = flo; }
+        __syncthreads();
+        float tn = 0.f, tm = 0.f, tq = 0.f, thi = -3.0e38f, tlo = 3.0e38f;
+        for (int k = 0; k < nw; ++k) {          // every thread, same order
+            chan_merge(tn, tm, tq, red[0][k], red[1][k], red[2][k]);
+            thi = fmaxf(thi, red[3][k]);
+            tlo = fminf(tlo, red[4][k]);
+        }
+        __syncthreads();                          // red is reused by the next row
+        const float c = tn > 0.f ? tm : 0.f;
+        const float v = tn > 0.f ? tq / tn : 0.f;
+        const float tmx = tn > 0.f ? fmaxf((float)((T)thi - (T)c), (float)((T)c - (T)tlo)) : 0.f;
+        const float md = tn > 0.f ? fmaxf(tmx * tmx - v, v) : 0.f;
+        const int es = scale_exp((double)tmx), et = scale_exp((double)md);
+        if (threadIdx.x == 0) { shift[i] = (double)c; vsq[i] = (double)v; sexp[i] = (int8_t)es; texp[i] = (int8_t)et; }
+        const float fs = exp2f((float)es), ft = exp2f((float)et);   // exact powers of two
+        // pass 2: the planes, four samples per thread and step
+#pragma unroll 2
+        for (int64_t q = threadIdx.x; q < n4; q += kPlaneThreads) {
+            const int64_t s0 = 4 * q;
+            const uint32_t obits = s0 < S ? (ob[s0 >> 5] >> (s0 & 31)) & 0xfu : 0u;
+            T xv[4] = {T(0), T(0), T(0), T(0)};
+            if (obits) load4<true>(x, s0, S, al, xv);
+            __align__(8) __half hm[4];
+            __align__(8) __half hxh[4];
+            __align__(8) __half hxl[4];
+            __align__(8) __half hdh[4];
+            __align__(8) __half hdl[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t s = s0 + k;
+                const bool o = s < S && ((obits >> k) & 1u);
+                float xt = 0.f;
+                if (o) xt = (float)(xv[k] - (T)c);
+                const float xs = xt * fs;                                  // exact scaling
+                const __half h = __float2half_rn(xs);
+                const __half l = __float2half_rn(xs - __half2float(h));    // the difference is exact in FP32
+                // d = xt^2 - v with the square's rounding error recovered by FMA
+                const float sq = xt * xt;
+                const float sq_err = fmaf(xt, xt, -sq);
+                const float ds = ((sq - v) + sq_err) * ft;
+                const __half dh = __float2half_rn(ds);
+                const __half dl = __float2half_rn(ds - __half2float(dh));
+                const __half z = __float2half(0.f);
+                hm[k] = o ? __float2half(1.f) : z;
+                hxh[k] = o ? h : z;
+                hxl[k] = o ? l : z;
+                hdh[k] = o ? dh : z;
+                hdl[k] = o ? dl : z;
+            }
+            __stcs(m4 + q, *reinterpret_cast<const uint2 *>(hm));
+            __stcs(xh4 + q, *reinterpret_cast<const uint2 *>(hxh));
+            __stcs(xl4 + q, *reinterpret_cast<const uint2 *>(hxl));
+            __stcs(dh4 + q, *reinterpret_cast<const uint2 *>(hdh));
+            __stcs(dl4 + q, *reinterpret_cast<const uint2 *>(hdl));
+        }
     }
 }
 
@@ -1147,10 +1141,6 @@ static napg_status launch_stacked(napg_ctx *ctx, StackParams P, const void *cons
     return tuned_launch(ctx, key, 4, run, st);
 }
 
-// Rows up to this many bytes (values plus observed bits) are staged in shared
-// memory by the plane builder (one 1024-thread CTA per SM).
-constexpr size_t kPlaneStageMax = 220 * 1024;
-
 template <typename T, typename... Rest>
 static const T *kern_x_type(void (*)(const T *, Rest...));
 
@@ -1185,21 +1175,18 @@ static napg_status prep_cont_planes(napg_ctx *ctx, Cohort &c, Workspace &ws, cud
     if (!hit) {
         key.valid = false;
         Stage s_(ctx->trace, st, "planes_f16");
-        const size_t esz = c.dtype == NAPG_F32 ? sizeof(float) : sizeof(double);
-        const size_t stage_bytes = (size_t)cp.S_pad * esz + (size_t)(c.W + 1) * sizeof(uint32_t);
-        const bool staged = stage_bytes <= kPlaneStageMax;
+        const unsigned grid = (unsigned)std::min<int64_t>(cp.rows_pad, (int64_t)kPlaneRowsPerSM *
+                                                          (ctx->sm_count > 0 ? ctx->sm_count : 152));
         auto launch = [&](auto kern) -> napg_status {
-            if (staged) NAPG_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                          (int)stage_bytes));
             count_launch();
-            kern<<<(unsigned)cp.rows_pad, staged ? 1024 : 256, staged ? stage_bytes : 0, st>>>(
-                (decltype(kern_x_type(kern)))c.X, c.S, cp.S_pad, vars_dev, nv, obsv, c.W, cp.M, cp.Xh,
-                cp.Xl, cp.Dh, cp.Dl, pshift, pvsq, cp.sexp, cp.texp);
+            kern<<<grid, kPlaneThreads, 0, st>>>((decltype(kern_x_type(kern)))c.X, c.S, cp.S_pad, vars_dev, nv,
+                                                 (int32_t)cp.rows_pad, obsv, c.W, cp.M, cp.Xh, cp.Xl, cp.Dh, cp.Dl,
+                                                 pshift, pvsq, cp.sexp, cp.texp);
             NAPG_CU(ctx, cudaGetLastError());
             return NAPG_OK;
         };
-        if (c.dtype == NAPG_F32) NAPG_ST(staged ? launch(k_planes_cont<float, true>) : launch(k_planes_cont<float, false>));
-        else NAPG_ST(staged ? launch(k_planes_cont<double, true>) : launch(k_planes_cont<double, false>));
+        if (c.dtype == NAPG_F32) NAPG_ST(launch(k_planes_cont<float>));
+        else NAPG_ST(launch(k_planes_cont<double>));
         if (cache_vars && first_slot == Workspace::kTmpA) {
             key.valid = true;
             key.gen = c.gen;
