@@ -439,6 +439,44 @@ __device__ __forceinline__ double xval(const RescueArgs &r, int64_t idx) {
 
 __device__ __forceinline__ bool bit(const uint32_t *w, int64_t s) { return (w[s >> 5] >> (s & 31)) & 1u; }
 
+// The p-value of a rescued pair with statistic s and parameters a, b (n for r;
+// d1, d2 for F; the degrees of freedom for t). With a job queue the pair's job
+// joins the others (the evaluation kernels write p; 0 at once when it certainly
+// underflows), so that one thread of the rescue does not run the special
+// function alone while its block waits; without one it is formed here.
+__device__ __forceinline__ double rescue_p(const RescueArgs &r, int kind, double s, double a, double b, int64_t idx,
+                                           int32_t mirror) {
+    if (kind == kPjCorr && fabs(s) >= 1.0) return 0.0;
+    if (r.q.jobs) return pjob_push_p(r.q, PJob{s, a, b, idx, kind, mirror});
+    if (kind == kPjCorr) return sf::corr_p(s, a);
+    if (kind == kPjF) return sf::f_sf(s, a, b);
+    return sf::t_two_sided(s, a);
+}
+
+// f(k) for this thread's share of the samples k < S set in ctx, oa and ob: one
+// 32-sample word per thread and step, the set samples of each byte of the word
+// in one unrolled group, so that their loads are in flight together (a loop
+// over single samples waits out one memory latency per sample). The order in
+// which a thread visits its samples is fixed, so the sums are reproducible.
+template <typename F>
+__device__ __forceinline__ void for_co_observed(const uint32_t *ctxw, const uint32_t *oa, const uint32_t *ob,
+                                                int64_t S, F &&f) {
+    const int64_t W = (S + 31) >> 5;
+    for (int64_t w = threadIdx.x; w < W; w += blockDim.x) {
+        uint32_t m = ctxw[w] & oa[w] & ob[w];
+        if (w == W - 1 && (S & 31)) m &= (1u << (S & 31)) - 1u;
+        if (!m) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t bq = (m >> (8 * q)) & 0xffu;
+            if (!bq) continue;
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                if ((bq >> b) & 1u) f(w * 32 + 8 * q + b);
+        }
+    }
+}
+
 __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nflag, int32_t max_flags,
                          double *stat, double *pval, int32_t *nout, int32_t symmetric) {
     const int32_t cnt = min(*nflag, max_flags);
@@ -468,7 +506,7 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
                     sxx += dx * dx; syy += dy * dy; sxy += dx * dy;
                 }
                 s = (va == vb) ? 1.0 : fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
-                p = (n <= 2) ? dnan() : sf::corr_p(s, (double)n);
+                p = (n <= 2) ? dnan() : rescue_p(r, kPjCorr, s, (double)n, 0.0, t, symmetric ? ncols : 0);
             }
             put(stat, pval, nout, t, s, p, (int32_t)n);
             if (symmetric) put(stat, pval, nout, (int64_t)ib * ncols + ia, s, p, (int32_t)n);
@@ -521,7 +559,7 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
                 }
                 const double d1 = (double)(k - 1), d2 = (double)(n - k);
                 s = (ssb / d1) / (ssw / d2);
-                p = sf::f_sf(s, d1, d2);
+                p = rescue_p(r, kPjF, s, d1, d2, t, 0);
             }
         } else {  // t-test
             const int64_t n0 = ng[0], n1 = ng[1];
@@ -531,7 +569,7 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
                     const double df = (double)(n - 2);
                     const double sp2 = (ss[0] + ss[1]) / df;
                     s = (m0 - m1) / sqrt(sp2 * (1.0 / (double)n0 + 1.0 / (double)n1));
-                    p = sf::t_two_sided(s, df);
+                    p = rescue_p(r, kPjT, s, df, 0.0, t, 0);
                 }
             } else if (cst[0] && cst[1]) {
                 if (first[0] != first[1]) { s = first[0] > first[1] ? dinf() : -dinf(); p = 0.0; }
@@ -540,7 +578,7 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
                 const double se2 = e0 + e1;
                 s = (m0 - m1) / sqrt(se2);
                 const double nu = se2 * se2 / (e0 * e0 / (double)(n0 - 1) + e1 * e1 / (double)(n1 - 1));
-                p = sf::t_two_sided(s, nu);
+                p = rescue_p(r, kPjT, s, nu, 0.0, t, 0);
             }
         }
         put(stat, pval, nout, t, s, p, (int32_t)n);
@@ -595,12 +633,11 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
         double s = dnan(), p = dnan(), es = dnan(), dof = dnan();
         if (r.test == NAPG_PEARSON) {
             double n = 0, sx = 0, sy = 0, mnx = inf, mxx = -inf, mny = inf, mxy = -inf;
-            for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
-                if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+            for_co_observed(r.ctxw, oa, ob, r.S, [&](int64_t k) {
                 const double x = xval(r, (int64_t)va * r.S + k), y = xval(r, (int64_t)vb * r.S + k);
                 n += 1; sx += x; sy += y;
                 mnx = fmin(mnx, x); mxx = fmax(mxx, x); mny = fmin(mny, y); mxy = fmax(mxy, y);
-            }
+            });
             n = block_reduce(n, 0, sh); sx = block_reduce(sx, 0, sh); sy = block_reduce(sy, 0, sh);
             mnx = block_reduce(mnx, 1, sh); mxx = block_reduce(mxx, 2, sh);
             mny = block_reduce(mny, 1, sh); mxy = block_reduce(mxy, 2, sh);
@@ -608,14 +645,13 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
             if (ni > 1 && mnx != mxx && mny != mxy) {
                 const double mx = sx / n, my = sy / n;
                 double sxx = 0, syy = 0, sxy = 0;
-                for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
-                    if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+                for_co_observed(r.ctxw, oa, ob, r.S, [&](int64_t k) {
                     const double dx = xval(r, (int64_t)va * r.S + k) - mx, dy = xval(r, (int64_t)vb * r.S + k) - my;
                     sxx += dx * dx; syy += dy * dy; sxy += dx * dy;
-                }
+                });
                 sxx = block_reduce(sxx, 0, sh); syy = block_reduce(syy, 0, sh); sxy = block_reduce(sxy, 0, sh);
                 s = (va == vb) ? 1.0 : fmin(1.0, fmax(-1.0, sxy / (sqrt(sxx) * sqrt(syy))));
-                if (threadIdx.x == 0) p = (ni <= 2) ? dnan() : sf::corr_p(s, n);
+                if (threadIdx.x == 0) p = (ni <= 2) ? dnan() : rescue_p(r, kPjCorr, s, n, 0.0, t, symmetric ? ncols : 0);
             }
             if (threadIdx.x == 0) {
                 put(stat, pval, nout, t, s, p, (int32_t)ni);
@@ -629,28 +665,26 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
         double ng[MAXC], sum[MAXC], mn[MAXC], mx[MAXC], ss[MAXC];
 #pragma unroll
         for (int g = 0; g < MAXC; ++g) { ng[g] = 0; sum[g] = 0; mn[g] = inf; mx[g] = -inf; ss[g] = 0; }
-        for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
-            if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+        for_co_observed(r.ctxw, oa, ob, r.S, [&](int64_t k) {
             const int l = la[k];
             const double y = xval(r, (int64_t)vb * r.S + k);
 #pragma unroll
             for (int g = 0; g < MAXC; ++g)
                 if (l == g) { ng[g] += 1; sum[g] += y; mn[g] = fmin(mn[g], y); mx[g] = fmax(mx[g], y); }
-        }
+        });
 #pragma unroll
         for (int g = 0; g < MAXC; ++g) {
             if (g >= c) break;
             ng[g] = block_reduce(ng[g], 0, sh); sum[g] = block_reduce(sum[g], 0, sh);
             mn[g] = block_reduce(mn[g], 1, sh); mx[g] = block_reduce(mx[g], 2, sh);
         }
-        for (int64_t k = threadIdx.x; k < r.S; k += blockDim.x) {
-            if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
+        for_co_observed(r.ctxw, oa, ob, r.S, [&](int64_t k) {
             const int l = la[k];
             const double y = xval(r, (int64_t)vb * r.S + k);
 #pragma unroll
             for (int g = 0; g < MAXC; ++g)
                 if (l == g) { const double d = y - sum[g] / ng[g]; ss[g] += d * d; }
-        }
+        });
 #pragma unroll
         for (int g = 0; g < MAXC; ++g) {
             if (g >= c) break;
@@ -689,7 +723,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                     }
                     const double d1 = (double)(k - 1), d2 = n - (double)k;
                     s = (ssb / d1) / (ssw / d2);
-                    p = sf::f_sf(s, d1, d2);
+                    p = rescue_p(r, kPjF, s, d1, d2, t, 0);
                 }
             } else {
                 const double n0 = ng[0], n1 = ng[1];
@@ -699,7 +733,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                         const double df = n - 2.0;
                         const double sp2 = (ss[0] + ss[1]) / df;
                         s = (m0 - m1) / sqrt(sp2 * (1.0 / n0 + 1.0 / n1));
-                        p = sf::t_two_sided(s, df);
+                        p = rescue_p(r, kPjT, s, df, 0.0, t, 0);
                         es = (m0 - m1) / sqrt(sp2);
                         dof = df;
                     }
@@ -711,7 +745,7 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
                     const double se2 = e0 + e1;
                     s = (m0 - m1) / sqrt(se2);
                     const double nu = se2 * se2 / (e0 * e0 / (n0 - 1.0) + e1 * e1 / (n1 - 1.0));
-                    p = sf::t_two_sided(s, nu);
+                    p = rescue_p(r, kPjT, s, nu, 0.0, t, 0);
                     es = (m0 - m1) / sqrt(0.5 * (ss[0] / (n0 - 1.0) + ss[1] / (n1 - 1.0)));
                     dof = nu;
                 }

@@ -442,8 +442,10 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         NAPG_ST(pjobs_setup(ctx, ws, st, (int64_t)na * (na + 1) / 2, a.pval != nullptr, pj));
         PearsonFin f{Sxy, Sx, Sxx, nn, shift, na, mixed ? kMixedRelTol : kPlainRelTol, vsq, pj.q, d_va, a.own};
         { Stage s_(ctx->trace, st, "finalize_pearson"); launch_finalize_pearson(f, a.stat, a.pval, a.n, flags, counter, st); }
-        pjobs_run(ctx, pj, a.pval, st);
+        // the rescued pairs queue their p-values with the others, before the evaluation
+        rsc.q = pj.q;
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)(nn2 / 2 + na + 1), a.stat, a.pval, a.n, 1, 0, st); }
+        pjobs_run(ctx, pj, a.pval, st);
     } else if (t == NAPG_ANOVA || t == NAPG_TTEST) {
         const int64_t rb = (int64_t)R * nb;
         int32_t *gn = WS(kIntA, int32_t, rb);
@@ -469,8 +471,9 @@ napg_status run_on_stream(napg_ctx *ctx, Workspace &ws, cudaStream_t st, const R
         GroupFin f{gn, g1, g2, R, d_lo, d_nl, levcnt, na, nb, t, a.opt.welch, mixed ? kMixedRelTol : kPlainRelTol,
                    vsq, pj.q, g2tot, t == NAPG_TTEST ? a.es1 : nullptr, t == NAPG_TTEST ? a.es2 : nullptr};
         { Stage s_(ctx->trace, st, "finalize_groups"); launch_finalize_groups(f, a.stat, a.pval, a.n, flags, counter, st); }
-        pjobs_run(ctx, pj, a.pval, st);
+        rsc.q = pj.q;
         { Stage s_(ctx->trace, st, "rescue"); launch_rescue(rsc, flags, counter, (int32_t)((int64_t)na * nb + 1), a.stat, a.pval, a.n, 0, maxlev, st); }
+        pjobs_run(ctx, pj, a.pval, st);
     } else if (t == NAPG_CHI2) {
         int32_t *T = WS(kIntA, int32_t, (int64_t)R * R);
         if (st_) return st_;

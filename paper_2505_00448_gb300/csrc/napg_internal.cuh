@@ -311,6 +311,7 @@ struct RescueArgs {
     int32_t welch; const int32_t *nlev_a; const int32_t *present; const int32_t *levoff;
     double *es;          // t-test: Cohen's d of the rescued pairs (NULL: not asked)
     double *es2;         // t-test: degrees of freedom of the rescued pairs (NULL: not asked)
+    PJobQueue q;         // the call's p-value jobs (q.jobs NULL: the rescue forms p itself)
 };
 void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t *flag_count, int32_t max_flags,
                    double *stat, double *pval, int32_t *nout, int32_t symmetric, int32_t max_levels,

@@ -50,6 +50,33 @@ def test_mixed_pearson(napg, offset, lognormal):
     c.close()
 
 
+@pytest.mark.parametrize("lognormal", [True, False])
+def test_mixed_pearson_exact_copies(napg, lognormal):
+    """Columns with exact copies and power-of-two multiples (r = 1 on every
+    co-observed set; each copy has its own missing samples): the split x3 Sxy
+    (the lo x lo product left out) and the centred-square planes still give r
+    within the bar, on heavy-tailed (lognormal) and offset (1e4 sigma) columns."""
+    rng = np.random.default_rng(31)
+    base = synth.small_cohort(203, n_cont=40, n_cat=0, S=20_000 + 3, miss=0.0, dtype=np.float32,
+                              offset=0.0 if lognormal else 1e4, lognormal=lognormal)
+    src = base["X"]
+    X = np.concatenate([src, src, 4.0 * src]).astype(np.float32)
+    X[rng.random(X.shape) < 0.2] = np.nan
+    F = X.shape[0]
+    coh = {"X": X, "vtype": np.zeros(F, np.uint8), "nlev": np.zeros(F, np.int32), "missing": float("nan"),
+           "cont": np.arange(F, dtype=np.int32), "cat": np.zeros(0, np.int32)}
+    c = napg.Context(0)
+    c.load_cohort(coh["X"], coh["vtype"], coh["nlev"], coh["missing"])
+    va = coh["cont"]
+    g = c.run("pearson", va, out="numpy", precision="mixed")
+    ref = oracle_run("pearson", coh, va)
+    compare("pearson", g, ref, stat_tol=("abs", 1e-6))
+    k = np.arange(40)
+    for off in (40, 80):
+        assert np.abs(g["stat"][k, k + off] - 1.0).max() <= 1e-6
+    c.close()
+
+
 def test_mixed_pearson_context_and_ragged(napg):
     rng = np.random.default_rng(9)
     coh = synth.small_cohort(202, n_cont=131, n_cat=0, S=2000 + 5, miss=0.3, dtype=np.float32)
