@@ -343,7 +343,7 @@ def stage_rooflines(stage_ms, steps, coh, tests, peaks):
                      peak_source=(("measured HBM copy (MEASURED_PEAKS)" if hbm_meas else
                                    "fallback 6,800 GB/s (no measured peak)") +
                                   " as the byte model's reference rate; the kernel is bound by instruction issue "
-                                  "(ncu: 65-80% of issue slots, profiles/rank_kernels_rank_cohort.md)"))
+                                  "(ncu: 65-80% of issue slots)"))
             tr = load_traffic(name)
             e["dram_share_of_model"] = tr / alg if tr else None      # both per step
         elif bound == "hbm":
