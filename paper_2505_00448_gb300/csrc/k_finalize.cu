@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_finalize_pearson(PearsonFin f, double *
                     r = fmin(1.0, fmax(-1.0, r));
                     if (n <= 2) p = dnan();
                     else if (fabs(r) >= 1.0) p = 0.0;
-                    else if (f.q.jobs) p = pjob_push_p(f.q, PJob{r, nd, 0.0, ij, kPjCorr, (int32_t)nv});
+                    else if (f.q.jobs) p = pjob_push_corr(f.q, r, nd, ij, (int32_t)nv);
                 }
             }
             put(stat, pval, nout, ij, r, p, n);       // p of a queued job is written by the evaluation
@@ -164,7 +164,7 @@ __global__ void k_finalize_groups(GroupFin f, double *stat, double *pval, int32_
                 } else {
                     const double d1 = (double)(k - 1), d2 = (double)(n - k);
                     s = (ssb * d2) / (ssw * d1);          // (ssb / d1) / (ssw / d2), one division
-                    if (f.q.jobs) p = pjob_push_p(f.q, PJob{s, d1, d2, t, kPjF, 0});
+                    if (f.q.jobs) p = pjob_push_f(f.q, s, d1, d2, t);
                 }
             }
         } else {  // two-sample t (levels 0 and 1)
@@ -337,7 +337,7 @@ __global__ void k_finalize_spearman(SpearmanFin f, double *stat, double *pval, i
                 r = fmin(1.0, fmax(-1.0, r));
                 if (n <= 2) p = dnan();
                 else if (fabs(r) >= 1.0) p = 0.0;
-                else if (f.pq.jobs) p = pjob_push_p(f.pq, PJob{r, (double)n, 0.0, t, kPjCorr, f.symmetric ? f.nb : 0});
+                else if (f.pq.jobs) p = pjob_push_corr(f.pq, r, (double)n, t, f.symmetric ? f.nb : 0);
             }
         }
         put(stat, pval, nout, t, r, p, (int32_t)n);

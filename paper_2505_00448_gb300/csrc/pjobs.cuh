@@ -108,4 +108,49 @@ __device__ __forceinline__ double pjob_push_p(const PJobQueue &q, const PJob &j)
     return __longlong_as_double(0x7ff8000000000000LL);
 }
 
+// pjob_push_p for a correlation job (statistic r, n observations), b = 1/2:
+// the job's placement (its key and the certain-underflow test) in FP32. Both
+// are decided with margins far above FP32 rounding: a job that lands on the
+// other side of a key boundary is evaluated by a branch that is accurate there
+// too (the large-a expansion also holds just below x = 1/2, and the general
+// path re-derives its own branch), and one that lands on the other side of an
+// underflow threshold has p below 1e-320 either way. The finalize kernels are
+// bound by the FP64 pipe, which this leaves to the statistic.
+__device__ __forceinline__ double pjob_push_corr(const PJobQueue &q, double r, double n, int64_t idx,
+                                                 int32_t mirror) {
+    const float rf = (float)r, nf = (float)n;
+    const float a = 0.5f * nf - 1.0f, y = rf * rf, x = 1.0f - y, ay = a * y;
+    if (a >= 20.0f && ((y <= 0.5f && (a - 0.25f) * y >= 746.5f) || ay >= 2001.0f)) return 0.0;
+    int k;
+    if (x >= 0.5f && a >= 20.0f) {
+        k = kPjKeyLargeA + min(7, log_bucket((double)ay) >> 1);
+    } else {
+        const bool swapped = x > (a + 1.0f) / (a + 2.5f);
+        k = (swapped ? 32 : 0) + log_bucket((double)(swapped ? 0.5f * x : ay));
+    }
+    pjob_push(q, PJob{r, n, 0.0, idx, kPjCorr, mirror}, k);
+    return __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// The same for an F job (statistic F, degrees of freedom d1, d2): x, y and the
+// tests in FP32 where d2 + d1 F is within its range, else the generic path.
+__device__ __forceinline__ double pjob_push_f(const PJobQueue &q, double F, double d1, double d2, int64_t idx) {
+    const PJob j{F, d1, d2, idx, kPjF, 0};
+    const double v = d2 + d1 * F;
+    if (!(v >= 1e-30 && v <= 1e30)) return pjob_push_p(q, j);
+    const float inv = __frcp_rn((float)v), a = 0.5f * (float)d2, b = 0.5f * (float)d1;
+    const float y = (float)(d1 * F) * inv, x = (float)d2 * inv;
+    if (a >= 20.0f && b <= 32.0f && ((b == 0.5f && y <= 0.5f && (a - 0.25f) * y >= 746.5f) || a * y >= 2001.0f))
+        return 0.0;
+    int k;
+    if (x >= 0.5f && a >= 20.0f && b <= 32.0f && b <= a) {
+        k = kPjKeyLargeA + (min(20, (int)(2.0f * b)) - 1) * 8 + min(7, log_bucket((double)(a * y)) >> 1);
+    } else {
+        const bool swapped = x > (a + 1.0f) / (a + b + 2.0f);
+        k = (swapped ? 32 : 0) + log_bucket((double)(swapped ? b * x : a * y));
+    }
+    pjob_push(q, j, k);
+    return __longlong_as_double(0x7ff8000000000000LL);
+}
+
 }  // namespace napg
