@@ -29,6 +29,13 @@ __device__ __forceinline__ double rcp_count(int32_t n) {
     return r;
 }
 
+// 1/n with one Newton step (relative error below 2^-45): for sums of positive
+// terms, where no cancellation magnifies it (the chi-squared cells)
+__device__ __forceinline__ double rcp_count1(int32_t n) {
+    const double r = (double)__frcp_rn(__int2float_rn(n));
+    return r * fma(-(double)n, r, 2.0);
+}
+
 __device__ __forceinline__ void put(double *stat, double *pval, int32_t *nout, int64_t idx, double s, double p,
                                     int32_t n) {
     if (stat) stat[idx] = s;
@@ -226,7 +233,9 @@ __global__ void NAME(Chi2Fin f, double *stat, double *pval, int32_t *nout) { \
          t += (int64_t)gridDim.x * blockDim.x) { \
         int a, b; \
         if (f.symmetric) { \
-            int64_t i = (int64_t)((2.0 * nn + 1.0 - sqrt((2.0 * nn + 1.0) * (2.0 * nn + 1.0) - 8.0 * (double)t)) / 2.0); \
+            /* row from an FP32 estimate, corrected exactly in integers below */ \
+            const float q2 = (float)(2 * nn + 1); \
+            int64_t i = (int64_t)((q2 - sqrtf(fmaxf(q2 * q2 - 8.0f * (float)t, 0.0f))) * 0.5f); \
             if (i < 0) i = 0; \
             if (i > nn - 1) i = nn - 1; \
             while (i > 0 && i * (2 * nn - i + 1) / 2 > t) --i; \
@@ -269,16 +278,16 @@ UNROLL \
         double s = dnan(), p = dnan(); \
         if (!empty) { \
             const bool yates = f.yates && ka == 2 && kb == 2; \
-            const double nd = (double)n, inv_n = rcp_count((int32_t)n); \
+            const double nd = (double)n, inv_n = rcp_count1((int32_t)n); \
             double icol[MAXC]; \
 UNROLL \
-            for (int h = 0; h < MAXC; ++h) icol[h] = (h < cb && col[h] > 0) ? rcp_count(col[h]) : 0.0; \
+            for (int h = 0; h < MAXC; ++h) icol[h] = (h < cb && col[h] > 0) ? rcp_count1(col[h]) : 0.0; \
             double chi = 0.0; \
 UNROLL \
             for (int g = 0; g < MAXC; ++g) { \
                 if (g >= ca) break; \
                 if (!f.present[oa + g]) continue; \
-                const double irow = rcp_count(row[g]); \
+                const double irow = rcp_count1(row[g]); \
                 double acc = 0.0; \
 UNROLL \
                 for (int h = 0; h < MAXC; ++h) { \
