@@ -329,6 +329,23 @@ static __constant__ double kInvQuad[157] = {
 // comparisons on the integer pipe
 __device__ __forceinline__ int expo_field(double v) { return (__double2hiint(v) >> 20) & 0x7FF; }
 
+// ln(1 - y) for 0 <= y < 2^-7 from its Taylor series (DLMF 4.6.1),
+// -(y + y^2 (1/2 + y/3 + ... + y^6/8)): the first omitted term, y^9/9, is below
+// 2^-56 of the sum, and the leading term y is exact, so the result is within
+// about one unit in the last place. Eight FP64 instructions where log1p takes
+// about two dozen; the large-a expansion's jobs mostly have such y (r^2 of
+// weak correlations, the beta argument of small F and t).
+__device__ __forceinline__ double log1m_small(double y) {
+    double p = 0.125;
+    p = fma(p, y, 1.0 / 7.0);
+    p = fma(p, y, 1.0 / 6.0);
+    p = fma(p, y, 0.2);
+    p = fma(p, y, 0.25);
+    p = fma(p, y, 1.0 / 3.0);
+    p = fma(p, y, 0.5);
+    return -fma(y * y, p, y);
+}
+
 // c_k(b) = g_k (b)_{2k}, k = 1..20: the coefficients of the expansion below for
 // one b (row 2b - 1 of a table of kBgratRows rows), by the recurrence for g_k
 constexpr int kBgratTerms = 20, kBgratRows = 64;
@@ -390,7 +407,7 @@ struct LargeATab {
 static __device__ double ibeta_large_a(double a, double b, double x, double y, const double *coef,
                                        LargeATab lat) {
     const double T = a + 0.5 * (b - 1.0);
-    const double u = -T * ((x <= 0.5) ? log(x) : log1p(-y));
+    const double u = -T * ((x <= 0.5) ? log(x) : (y < 0.0078125 ? log1m_small(y) : log1p(-y)));
     // the result is below the smallest subnormal: for b = 1/2 once u >= 746
     // (see ibeta_underflows), else when p <= 2 e^-u u^(b+41) is
     if (b == 0.5 && u >= 746.0) return 0.0;
