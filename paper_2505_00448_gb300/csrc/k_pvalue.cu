@@ -17,27 +17,49 @@ __global__ void k_pj_scan(const int32_t *hist, int32_t *offs, int32_t *cursor) {
     }
 }
 
-// Lanes of a warp with the same key take consecutive slots with one atomic
-// (most jobs share a few keys, so per-job atomics would serialise).
-__global__ void k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t capacity, const int32_t *offs,
-                             int32_t *cursor, PJob *sorted) {
+// A block takes kScatterPer jobs per thread at a time into registers; jobs
+// with the same key take consecutive slots of the block's share of that key
+// (shared-memory counts, one atomic per warp and key), and the block claims
+// its share of each key's range with one global atomic per key it holds. Most
+// jobs share a few keys: per-warp global atomics on those keys' cursors
+// serialised the scatter.
+constexpr int kScatterPer = 4;
+
+__global__ void __launch_bounds__(256) k_pj_scatter(const PJob *jobs, const int32_t *count, int32_t capacity,
+                                                    const int32_t *offs, int32_t *cursor, PJob *sorted) {
+    __shared__ int32_t s_cnt[kPjBins];
+    __shared__ int32_t s_base[kPjBins];
     const int32_t n = min(*count, capacity);
     const int lane = threadIdx.x & 31;
-    const int32_t stride = gridDim.x * blockDim.x;
-    for (int32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n; t0 += stride) {   // warp-uniform
-        const int32_t t = t0 + lane;
-        PJob j;
-        int k = kPjBins;                     // no job
-        if (t < n) {
-            j = jobs[t];
-            k = j.kind >> 8;
+    const int32_t chunk = (int32_t)blockDim.x * kScatterPer;
+    for (int32_t c0 = blockIdx.x * chunk; c0 < n; c0 += gridDim.x * chunk) {   // block-uniform
+        for (int k = threadIdx.x; k < kPjBins; k += blockDim.x) s_cnt[k] = 0;
+        __syncthreads();
+        PJob j[kScatterPer];
+        int key[kScatterPer], rank[kScatterPer];
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u) {
+            const int32_t t = c0 + u * (int32_t)blockDim.x + (int32_t)threadIdx.x;
+            key[u] = kPjBins;                   // no job
+            if (t < n) {
+                j[u] = jobs[t];
+                key[u] = min(j[u].kind >> 8, kPjBins);
+            }
+            const unsigned same = __match_any_sync(0xffffffffu, key[u]);
+            const int leader = __ffs(same) - 1;
+            int r = 0;
+            if (lane == leader && key[u] < kPjBins) r = atomicAdd(&s_cnt[key[u]], __popc(same));
+            r = __shfl_sync(0xffffffffu, r, leader);
+            rank[u] = r + __popc(same & ((1u << lane) - 1u));
         }
-        const unsigned same = __match_any_sync(0xffffffffu, k);
-        const int leader = __ffs(same) - 1;
-        int base = 0;
-        if (lane == leader && k < kPjBins) base = atomicAdd(&cursor[k], __popc(same));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (k < kPjBins) sorted[offs[k] + base + __popc(same & ((1u << lane) - 1u))] = j;
+        __syncthreads();
+        for (int k = threadIdx.x; k < kPjBins; k += blockDim.x)
+            if (s_cnt[k] > 0) s_base[k] = offs[k] + atomicAdd(&cursor[k], s_cnt[k]);
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kScatterPer; ++u)
+            if (key[u] < kPjBins) sorted[s_base[key[u]] + rank[u]] = j[u];
+        __syncthreads();                        // the counts are reused
     }
 }
 
