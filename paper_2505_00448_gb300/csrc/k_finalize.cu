@@ -537,10 +537,12 @@ __global__ void k_rescue(RescueArgs r, const int32_t *flags, const int32_t *nfla
             if (ng[g] == 0) first[g] = y; else cst[g] &= (y == first[g]);
             sum[g] += y; ng[g] += 1; tot += y; ++n;
         }
+        double mean[kMaxLevels];                 // the level means, formed once
+        for (int g = 0; g < c; ++g) mean[g] = ng[g] > 0 ? sum[g] / (double)ng[g] : 0.0;
         for (int64_t k = 0; k < r.S; ++k) {
             if (!(bit(r.ctxw, k) && bit(oa, k) && bit(ob, k))) continue;
             const int g = la[k];
-            const double d = xval(r, (int64_t)vb * r.S + k) - sum[g] / (double)ng[g];
+            const double d = xval(r, (int64_t)vb * r.S + k) - mean[g];
             ss[g] += d * d;
         }
         for (int g = 0; g < c; ++g) if (cst[g]) ss[g] = 0.0;
@@ -626,8 +628,12 @@ __device__ double block_reduce(double v, int op, double *sh) {
     return sh[32];
 }
 
-template <int MAXC>
-__global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_t *flags, const int32_t *nflag,
+// NT threads a pair: the few rescued pairs run on a few SMs while the others
+// idle, so the time is one pair's instruction latency chain, which more threads
+// shorten (512 up to 10 levels; 256 for 16, whose per-level sums need the
+// registers)
+template <int MAXC, int NT>
+__global__ void __launch_bounds__(NT) k_rescue_block(RescueArgs r, const int32_t *flags, const int32_t *nflag,
                                                       int32_t max_flags, double *stat, double *pval, int32_t *nout,
                                                       int32_t symmetric) {
     __shared__ double sh[33];
@@ -687,12 +693,15 @@ __global__ void __launch_bounds__(256) k_rescue_block(RescueArgs r, const int32_
             ng[g] = block_reduce(ng[g], 0, sh); sum[g] = block_reduce(sum[g], 0, sh);
             mn[g] = block_reduce(mn[g], 1, sh); mx[g] = block_reduce(mx[g], 2, sh);
         }
+        double mean[MAXC];                       // the level means, formed once
+#pragma unroll
+        for (int g = 0; g < MAXC; ++g) mean[g] = (g < c && ng[g] > 0) ? sum[g] / ng[g] : 0.0;
         for_co_observed(r.ctxw, oa, ob, r.S, [&](int64_t k) {
             const int l = la[k];
             const double y = xval(r, (int64_t)vb * r.S + k);
 #pragma unroll
             for (int g = 0; g < MAXC; ++g)
-                if (l == g) { const double d = y - sum[g] / ng[g]; ss[g] += d * d; }
+                if (l == g) { const double d = y - mean[g]; ss[g] += d * d; }
         });
 #pragma unroll
         for (int g = 0; g < MAXC; ++g) {
@@ -773,13 +782,13 @@ void launch_rescue(const RescueArgs &r, const int32_t *flag_list, const int32_t 
     const unsigned blocks = 152 * 8;
     if (r.test == NAPG_PEARSON || max_levels <= 4) {
         count_launch();
-        k_rescue_block<4><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+        k_rescue_block<4, 512><<<blocks, 512, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
     } else if (max_levels <= 10) {
         count_launch();
-        k_rescue_block<10><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+        k_rescue_block<10, 512><<<blocks, 512, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
     } else if (max_levels <= 16) {
         count_launch();
-        k_rescue_block<16><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
+        k_rescue_block<16, 256><<<blocks, 256, 0, st>>>(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric);
     } else {
         launch_rescue_serial(r, flag_list, flag_count, max_flags, stat, pval, nout, symmetric, st);
     }
